@@ -1,0 +1,263 @@
+"""Seeded synthetic inputs: meshes, media, sources, receivers, states.
+
+This module holds none of the numerical method's arithmetic.  It only builds
+inputs (vertex coordinates, CCW cell polygons, subdomain tags, per-cell
+material arrays, point positions, random DOF vectors) that both the CPU
+oracle and the GPU library consume.
+
+Workload shapes follow the paper's academic bilayer (Sec. 5.2: fluid over
+solid, flat interface) and its basin case (Sec. 5.3: water over a solid with a
+sedimentary basin); the exact sizes are the synthetic stand-ins documented in
+the design doc, because the paper's meshes, gmsh files and SEM3D traces are not
+available.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+FLUID, SOLID = 0, 1
+
+
+@dataclass
+class MeshData:
+    xy: np.ndarray          # (nv, 2) float64
+    cell_ptr: np.ndarray    # (nc+1,) int64
+    cell_vtx: np.ndarray    # int64, CCW
+    cell_domain: np.ndarray  # (nc,) uint8
+    vertex_rep: np.ndarray | None = None
+
+    @property
+    def n_cells(self):
+        return len(self.cell_ptr) - 1
+
+    def centroids_approx(self):
+        """Vertex averages (only used to tag subdomains and sample media)."""
+        out = np.empty((self.n_cells, 2))
+        for c in range(self.n_cells):
+            vs = self.cell_vtx[self.cell_ptr[c]:self.cell_ptr[c + 1]]
+            out[c] = self.xy[vs].mean(axis=0)
+        return out
+
+
+def _grid_vertices(nx, ny, x0, x1, y0, y1):
+    xs = x0 + (x1 - x0) * np.arange(nx + 1) / nx
+    ys = y0 + (y1 - y0) * np.arange(ny + 1) / ny
+    X, Y = np.meshgrid(xs, ys, indexing="xy")          # (ny+1, nx+1)
+    xy = np.stack([X.ravel(), Y.ravel()], axis=1)
+    vid = lambda i, j: j * (nx + 1) + i
+    return xy, vid
+
+
+def _finish(xy, polys, y_interface, vertex_rep=None):
+    cell_ptr = np.zeros(len(polys) + 1, dtype=np.int64)
+    cell_ptr[1:] = np.cumsum([len(p) for p in polys])
+    cell_vtx = np.array([v for p in polys for v in p], dtype=np.int64)
+    md = MeshData(xy=np.asarray(xy, dtype=np.float64), cell_ptr=cell_ptr, cell_vtx=cell_vtx,
+                  cell_domain=np.zeros(len(polys), dtype=np.uint8), vertex_rep=vertex_rep)
+    cen = md.centroids_approx()
+    md.cell_domain = np.where(cen[:, 1] < y_interface, SOLID, FLUID).astype(np.uint8)
+    return md
+
+
+def tri_grid(nx, ny, x0=0.0, x1=1.0, y0=0.0, y1=1.0, y_interface=0.5, periodic_x=False):
+    """Squares split by the diagonal in the (1, 1) direction: 2 nx ny right triangles."""
+    xy, vid = _grid_vertices(nx, ny, x0, x1, y0, y1)
+    polys = []
+    for j in range(ny):
+        for i in range(nx):
+            a, b, c, d = vid(i, j), vid(i + 1, j), vid(i + 1, j + 1), vid(i, j + 1)
+            polys.append([a, b, c])
+            polys.append([a, c, d])
+    rep = _periodic_rep(nx, ny, vid) if periodic_x else None
+    return _finish(xy, polys, y_interface, rep)
+
+
+def quad_grid(nx, ny, x0=0.0, x1=1.0, y0=0.0, y1=1.0, y_interface=0.5, periodic_x=False):
+    """nx * ny axis-aligned rectangles."""
+    xy, vid = _grid_vertices(nx, ny, x0, x1, y0, y1)
+    polys = []
+    for j in range(ny):
+        for i in range(nx):
+            polys.append([vid(i, j), vid(i + 1, j), vid(i + 1, j + 1), vid(i, j + 1)])
+    rep = _periodic_rep(nx, ny, vid) if periodic_x else None
+    return _finish(xy, polys, y_interface, rep)
+
+
+def hybrid_grid(nx, ny, x0, x1, y0, y1, y_split, y_interface):
+    """Quads below y_split, each square split into two triangles above it."""
+    xy, vid = _grid_vertices(nx, ny, x0, x1, y0, y1)
+    polys = []
+    for j in range(ny):
+        yc = y0 + (y1 - y0) * (j + 0.5) / ny
+        for i in range(nx):
+            a, b, c, d = vid(i, j), vid(i + 1, j), vid(i + 1, j + 1), vid(i, j + 1)
+            if yc < y_split:
+                polys.append([a, b, c, d])
+            else:
+                polys.append([a, b, c])
+                polys.append([a, c, d])
+    return _finish(xy, polys, y_interface)
+
+
+def hanging_node_patch(nx, ny, x0=0.0, x1=1.0, y0=0.0, y1=1.0, y_interface=0.5, refine_rows=(0,)):
+    """Quad grid where the listed rows are refined 2x; the coarse neighbours of
+    refined cells become pentagons/hexagons (hanging nodes as vertices)."""
+    # Build a fine vertex lattice (2nx x 2ny) and pick the vertices each cell uses.
+    fx, fy = 2 * nx, 2 * ny
+    xy, vid = _grid_vertices(fx, fy, x0, x1, y0, y1)
+    refined = set(refine_rows)
+    polys = []
+    used = set()
+    for j in range(ny):
+        for i in range(nx):
+            if j in refined:
+                for jj in range(2):
+                    for ii in range(2):
+                        I, J = 2 * i + ii, 2 * j + jj
+                        p = [vid(I, J), vid(I + 1, J), vid(I + 1, J + 1), vid(I, J + 1)]
+                        polys.append(p)
+                continue
+            I, J = 2 * i, 2 * j
+            p = [vid(I, J)]
+            if (j - 1) in refined:
+                p.append(vid(I + 1, J))            # hanging node on the bottom edge
+            p.append(vid(I + 2, J))
+            p.append(vid(I + 2, J + 2))
+            if (j + 1) in refined:
+                p.append(vid(I + 1, J + 2))        # hanging node on the top edge
+            p.append(vid(I, J + 2))
+            polys.append(p)
+    for p in polys:
+        used.update(p)
+    # compact the vertex numbering
+    order = sorted(used)
+    remap = {v: n for n, v in enumerate(order)}
+    polys = [[remap[v] for v in p] for p in polys]
+    return _finish(xy[order], polys, y_interface)
+
+
+def _periodic_rep(nx, ny, vid):
+    rep = np.arange((nx + 1) * (ny + 1), dtype=np.int64)
+    for j in range(ny + 1):
+        rep[vid(nx, j)] = vid(0, j)
+    return rep
+
+
+# ---- media -------------------------------------------------------------------
+
+def lame_from_speeds(rho, vp, vs):
+    mu = rho * vs * vs
+    lam = rho * vp * vp - 2.0 * mu
+    return lam, mu
+
+
+def layered_media(md: MeshData, fluid=(1.0, 1.5), solid=(2.5, 3.0, 1.7)):
+    """Per-cell (rho, lam, mu, kappa): homogeneous fluid (rho, c) over solid (rho, vp, vs)."""
+    nc = md.n_cells
+    rho = np.empty(nc); lam = np.zeros(nc); mu = np.zeros(nc); kappa = np.zeros(nc)
+    for c in range(nc):
+        if md.cell_domain[c] == FLUID:
+            rho[c] = fluid[0]
+            kappa[c] = fluid[0] * fluid[1] ** 2
+        else:
+            rho[c] = solid[0]
+            lam[c], mu[c] = lame_from_speeds(solid[0], solid[1], solid[2])
+    return rho, lam, mu, kappa
+
+
+def gaussian_random_field(seed, x0, x1, y0, y1, corr=0.05, spacing=1.0 / 256):
+    """Seeded white noise on a grid convolved with a Gaussian (std ``corr``),
+    normalised to max |g| = 1.  Returns a sampler g(x, y) (nearest grid point)."""
+    rng = np.random.default_rng(seed)
+    nx = int(round((x1 - x0) / spacing)) + 1
+    ny = int(round((y1 - y0) / spacing)) + 1
+    noise = rng.standard_normal((ny, nx))
+    kx = np.fft.fftfreq(nx, d=spacing)
+    ky = np.fft.fftfreq(ny, d=spacing)
+    KX, KY = np.meshgrid(kx, ky, indexing="xy")
+    filt = np.exp(-2.0 * (np.pi * corr) ** 2 * (KX ** 2 + KY ** 2))
+    g = np.real(np.fft.ifft2(np.fft.fft2(noise) * filt))
+    g /= np.max(np.abs(g))
+
+    def sample(x, y):
+        i = np.clip(np.rint((np.asarray(x) - x0) / spacing).astype(int), 0, nx - 1)
+        j = np.clip(np.rint((np.asarray(y) - y0) / spacing).astype(int), 0, ny - 1)
+        return g[j, i]
+    return sample
+
+
+def random_field_media(md: MeshData, seeds=(1, 2), base=(2.5, 3.0, 1.7), amp=0.2,
+                       fluid=(1.0, 1.5), box=(0.0, 2.0, 0.0, 1.0)):
+    """Solid: vp, vs share field g1 (keeps vp/vs fixed, lambda > 0), rho uses g2;
+    value = base * (1 + amp * g).  Fluid: homogeneous water (rho, c)."""
+    g1 = gaussian_random_field(seeds[0], *box)
+    g2 = gaussian_random_field(seeds[1], *box)
+    cen = md.centroids_approx()
+    a = g1(cen[:, 0], cen[:, 1])
+    b = g2(cen[:, 0], cen[:, 1])
+    nc = md.n_cells
+    rho = np.empty(nc); lam = np.zeros(nc); mu = np.zeros(nc); kappa = np.zeros(nc)
+    for c in range(nc):
+        if md.cell_domain[c] == FLUID:
+            rho[c] = fluid[0]
+            kappa[c] = fluid[0] * fluid[1] ** 2
+        else:
+            r = base[0] * (1.0 + amp * b[c])
+            vp = base[1] * (1.0 + amp * a[c])
+            vs = base[2] * (1.0 + amp * a[c])
+            rho[c] = r
+            lam[c], mu[c] = lame_from_speeds(r, vp, vs)
+    return rho, lam, mu, kappa
+
+
+# ---- points and states -----------------------------------------------------------
+
+def seeded_point(seed, x0, x1, y0, y1, margin=0.05):
+    rng = np.random.default_rng(seed)
+    return (x0 + margin + (x1 - x0 - 2 * margin) * rng.random(),
+            y0 + margin + (y1 - y0 - 2 * margin) * rng.random())
+
+
+def receivers_on_line(n, x0, x1, y):
+    """n points evenly inside (x0, x1) at height y: x = x0 + (i + 1/2)(x1 - x0)/n."""
+    return [(x0 + (i + 0.5) * (x1 - x0) / n, y) for i in range(n)]
+
+
+def random_state(n_values, seed):
+    """Seeded standard-normal DOF vector (canonical layout)."""
+    return np.random.default_rng(seed).standard_normal(n_values)
+
+
+def ricker(t, f0, t0=None, amp=1.0):
+    """Ricker wavelet w(t) = amp (1 - 2 pi^2 f0^2 (t-t0)^2) exp(-pi^2 f0^2 (t-t0)^2), t0 = 1/f0."""
+    t0 = 1.0 / f0 if t0 is None else t0
+    a = (np.pi * f0 * (t - t0)) ** 2
+    return amp * (1.0 - 2.0 * a) * np.exp(-a)
+
+
+# ---- the named workloads ----------------------------------------------------------
+
+def academic_c1():
+    """512 right triangles on the unit square, solid below y = 0.5 (rho 2.5,
+    vp 3.0, vs 1.7), water above (rho 1, c 1.5); k = 1, ERK4, 200 steps,
+    Ricker f0 = 10 point force (e_y) at a seeded solid point, 8 receivers on
+    the interface y = 0.5."""
+    md = tri_grid(16, 16)
+    media = layered_media(md)
+    src = seeded_point(0, 0.0, 1.0, 0.0, 0.5)
+    rec = receivers_on_line(8, 0.0, 1.0, 0.5)
+    return dict(mesh=md, media=media, k=1, tableau="erk4", nsteps=200, cfl_star=0.265,
+                h=1.0 / 16, c_max=3.0, source=src, f0=10.0, receivers=rec)
+
+
+def bilayer_c2(nx=1024, ny=512, k=2):
+    """[0,2]x[0,1] quads, solid below y = 0.5 with a seeded +-20 % random field
+    (vp, vs share g1 seed 1, rho g2 seed 2), water above; 256 receivers at y = 0.75."""
+    md = quad_grid(nx, ny, 0.0, 2.0, 0.0, 1.0, 0.5)
+    media = random_field_media(md, seeds=(1, 2))
+    src = seeded_point(3, 0.0, 2.0, 0.0, 0.5)
+    rec = receivers_on_line(256, 0.0, 2.0, 0.75)
+    return dict(mesh=md, media=media, k=k, source=src, f0=10.0, receivers=rec,
+                h=1.0 / ny, c_max=float(np.sqrt((media[1] + 2 * media[2]) / media[0]).max()))
