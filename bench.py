@@ -1,0 +1,308 @@
+"""Benchmark: ERK stage operator of the HHO elasto-acoustic scheme on GB300.
+
+Workload (one GPU): the 1024 x 512 quadrilateral bilayer on [0,2]x[0,1]
+(random-field elastic layer under water, k = 2 by default, classical ERK4,
+Ricker point force, 256 receivers recorded every step).  A "step" is one ERK
+time step: every stage kernel plus the receiver recording.
+
+Metric: cell-DOF updates per second per ERK stage =
+cell DOFs x stages x steps / time.  `value` is device-timed with inputs
+resident in HBM; `e2e` is the same metric through hho_erk_run_host with the
+state in pinned host memory (host<->device copies inside every step).
+
+Roofline: the stage kernel is bound by FP64 arithmetic on this part (FP64
+FMA rate measured live by the probe kernel), reported as "bound": "alu"
+with FP64 lane-ops from the library's cost model; the HBM view (algorithmic
+bytes / time against MEASURED_PEAKS.json) is reported next to it.
+
+--impl reference times the CPU oracle (plain FP64 numpy/scipy) on a bounded
+sample of the same workload on the host cores.
+
+Multi-GPU (torchrun): independent replicas, one per GPU (the stage operator
+needs a halo exchange to shard a mesh; on this pool boxes have one GPU).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell-DOF updates/s per ERK stage"
+CFL_SQUARES_ERK4 = {1: 0.233, 2: 0.122, 3: 0.082}
+UNIT = "cell-DOF-stage/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--k", type=int, default=2)
+    ap.add_argument("--stages", type=int, default=4)
+    ap.add_argument("--nx", type=int, default=1024)
+    ap.add_argument("--ny", type=int, default=512)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def workload_name(a):
+    return ("bilayer %dx%d quads on [0,2]x[0,1], k=%d, ERK%d, random-field solid (+-20%%) under water, "
+            "Ricker f0=10 point force, 256 receivers" % (a.nx, a.ny, a.k, a.stages))
+
+
+# ---------------------------------------------------------------- CPU oracle sample
+def oracle_sample(a, seconds=10.0, max_steps=None):
+    """Times the oracle on a 64 x 32 section of the same bilayer (same media
+    recipe, same k and tableau): returns (dof-stage/s, description, steps)."""
+    import synth
+    from oracle import assemble as A
+    from oracle import erk as E
+    from oracle import mesh as M
+    w = synth.bilayer_c2(nx=64, ny=32, k=a.k)
+    md = w["mesh"]
+    m = M.build_mesh(md.xy, md.cell_ptr, md.cell_vtx, md.cell_domain)
+    S = A.System(m, a.k, *w["media"])
+    b, _ = S.point_load(*w["source"], direction=(0.0, 1.0))
+    st = E.Stepper(S, lambda t: synth.ricker(t, 10.0) * b)
+    U = np.zeros(S.nT)
+    dt = 1e-4
+    st.step(U, 0.0, dt, "erk%d" % a.stages, 1)
+    t0 = time.perf_counter()
+    n = 0
+    while time.perf_counter() - t0 < seconds and (max_steps is None or n < max_steps):
+        U = st.step(U, n * dt, dt, "erk%d" % a.stages, 1)
+        n += 1
+    el = time.perf_counter() - t0
+    rate = S.nT * a.stages * n / el
+    desc = ("oracle (global sparse LU face and mass solves, numpy/scipy FP64) on a 64x32 section of the same "
+            "bilayer (2048 cells, %d cell DOFs), %d ERK%d steps in %.1f s" % (S.nT, n, a.stages, el))
+    return rate, desc, n, el
+
+
+def run_reference(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    steps = max(1, a.steps)
+    rate, desc, n, el = oracle_sample(a, seconds=min(60.0, 0.5 * steps), max_steps=steps)
+    line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": a.gpus,
+            "steps": n, "warmup": a.warmup, "ms_per_step": 1e3 * el / max(n, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name(a), "sample": "64x32 section"},
+            "cpu_baseline": {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+            "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- GPU run
+def fp64_fma_rate():
+    import ctypes
+    lib = ctypes.CDLL(os.path.join(ROOT, "paper_2505_15771_gb300", "libhho_probe.so"))
+    lib.hho_probe_dfma_rate.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
+    r = ctypes.c_double()
+    if lib.hho_probe_dfma_rate(4000, 3, ctypes.byref(r)) != 0:
+        return None
+    return r.value
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+        return
+    import torch
+    import torch.distributed as dist
+
+    import synth
+    from paper_2505_15771_gb300 import hho, solver
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    if not os.path.exists(hho.LIB_PATH):
+        raise RuntimeError("libhho.so is not built; run __graft_entry__.build() first")
+
+    w = synth.bilayer_c2(nx=a.nx, ny=a.ny, k=a.k)
+    md, media = w["mesh"], w["media"]
+    P = solver.Problem(md, media, a.k)
+    P.set_sources([w["source"]], [(0.0, 1.0)], 10.0)
+    P.set_receivers(w["receivers"])
+    tab = hho.hho_tableau_erk(a.stages)
+    # CFL-limited dt (Eq. CFL): 0.9 x the ERK4 eigenvalue limit of the stage
+    # operator on squares (c# dt / h = 0.233, 0.122, 0.082 for k = 1, 2, 3)
+    dt = hho.hho_cfl_dt(P.ops, CFL_SQUARES_ERK4[a.k], 0.9)
+    ndof = P.layout.n_canonical
+    state = P.empty_state()
+    work = P.work(tab)
+    seis = torch.empty((max(a.steps, a.warmup, 3), len(w["receivers"]), 5), dtype=torch.float64, device=P.dev)
+    stream = torch.cuda.current_stream()
+    sp = stream.cuda_stream
+
+    def run(nsteps, t0):
+        hho.hho_erk_step_record(P.ops, tab, t0, dt, nsteps, state.data_ptr(), work.data_ptr(), seis.data_ptr(), sp)
+
+    # warm-up (also the first-touch of every buffer)
+    run(max(a.warmup, 3), 0.0)
+    torch.cuda.synchronize()
+    e_warm = P.energy(state)
+
+    # timed region: exactly K steps
+    hho.hho_profile_enable(P.ops, True)
+    clocks = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    run(a.steps, a.warmup * dt)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if world > 1:
+        dist.barrier()
+    ms = ev0.elapsed_time(ev1)
+    stage_ms, n_launch = hho.hho_profile_read(P.ops)
+    hho.hho_profile_enable(P.ops, False)
+    e_end = P.energy(state)
+    if world > 1:
+        t = torch.tensor([ms], device=P.dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    per_rank_units = ndof * a.stages * a.steps
+    value = world * per_rank_units / (ms * 1e-3)
+
+    # roofline of the stage kernel
+    fp64_ops, bytes_min, bytes_kernel = hho.hho_stage_cost(P.ops, tab)
+    avg_launch_s = stage_ms * 1e-3 / max(n_launch, 1)
+    ops_per_launch = fp64_ops / a.stages
+    peak_fma = fp64_fma_rate()
+    peaks = {}
+    pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk):
+        peaks = json.load(open(pk))
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    roofline = {
+        "bound": "alu",
+        "achieved": ops_per_launch / avg_launch_s / 1e12,
+        "peak": (peak_fma / 1e12) if peak_fma else None,
+        "unit": "T FP64 lane-ops/s (FMA = 1)",
+        "frac": (ops_per_launch / avg_launch_s / peak_fma) if peak_fma else None,
+        "traffic": None,
+        "kernel": "stage_kernel<%d,1>" % a.k,
+        "avg_launch_ms": avg_launch_s * 1e3,
+        "launches_timed": n_launch,
+        "peak_source": "live DFMA probe (libhho_probe.so), best of 3",
+        "hbm_view": {"algorithmic_bytes_per_launch": bytes_min / a.stages,
+                     "achieved_gbs": bytes_min / a.stages / avg_launch_s / 1e9,
+                     "peak_gbs": hbm_peak, "frac": bytes_min / a.stages / avg_launch_s / 1e9 / hbm_peak,
+                     "kernel_design_bytes_per_launch": bytes_kernel / a.stages,
+                     "peak_source": "MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in peaks else "fallback"},
+    }
+
+    # end to end through the host-buffer entry point (pinned host state)
+    e2e = None
+    if not a.no_e2e:
+        h = torch.zeros(ndof, dtype=torch.float64, pin_memory=True)
+        hn = h.numpy()
+        P.run_host(hn, a.stages, 0.0, dt, 1, stream)       # warm (allocates its buffers)
+        ne = max(3, min(a.steps, 20))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i in range(ne):
+            P.run_host(hn, a.stages, i * dt, dt, 1, stream)
+        el = time.perf_counter() - t0
+        e2e = {"value": world * ndof * a.stages * ne / el, "unit": UNIT, "h2d_bytes_per_step": 8 * ndof,
+               "d2h_bytes_per_step": 8 * ndof, "steps": ne,
+               "path": "hho_erk_run_host: pinned H2D, pack, 1 ERK step, unpack, D2H, stream sync"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        rate, desc, n, el = oracle_sample(a, seconds=10.0)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
+
+    launches = 1 + a.stages * a.steps + a.steps      # trace init + stages + receiver records
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+                "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": workload_name(a), "cells": int(md.n_cells), "cell_dofs": int(ndof),
+                           "k": a.k, "tableau": "erk%d" % a.stages, "dt": dt,
+                           "l2": "inputs larger than L2 (state %.0f MB, work %.0f MB per GPU)" % (
+                               8e-6 * P.layout.n_state, 8e-6 * work.numel()),
+                           "parallelism": "replicas" if world > 1 else "single GPU",
+                           "energy_after_warmup": e_warm, "energy_after_timed": e_end},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk}
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

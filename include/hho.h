@@ -1,0 +1,273 @@
+/*
+ * hho.h -- C ABI of the GB300 library for the explicit Runge-Kutta stage
+ * operator of the hybrid high-order (HHO) first-order elasto-acoustic scheme
+ * on 2D general meshes (Mottier, Ern, Guillot, "Elasto-acoustic wave
+ * propagation in geophysical media using hybrid high-order methods on general
+ * meshes").
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Every function returns an int status (HHO_OK = 0 on success); on failure
+ *   hho_last_error() returns a one-line message (thread-local).
+ * - Pointers named h_* are host memory; pointers named d_* are device memory
+ *   of the current CUDA device; all sizes are element counts.
+ * - Handles (hho_mesh, hho_ops) are opaque and owned by the library.  They are
+ *   freed by the matching *_destroy call.  A handle is not thread-safe.
+ * - Device state and work buffers are owned by the caller.  Their sizes come
+ *   from hho_state_layout() and hho_work_size().  The stage path (hho_erk_step,
+ *   hho_apply) allocates nothing.
+ * - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *   stream).  Device work is stream-ordered; calls return once work is
+ *   enqueued, except where a host result is documented.
+ *
+ * Canonical cell-DOF layout (host or device "canonical" vectors): cells in
+ * input order; per cell its coefficients in the local scaled-monomial basis
+ * phi_(a,b) = ((x - x_T)/h_T)^a ((y - y_T)/h_T)^b (x_T area centroid, h_T
+ * diameter; ordered by total degree, then decreasing a).  A fluid cell holds
+ * [m_x, m_y, p] and a solid cell [s_xx, s_yy, s_xy, v_x, v_y], n = (k+1)(k+2)/2
+ * coefficients each.  This is the row order of the paper's block system
+ * (Sec. 3.3, "algebraic_system").  The dual unknowns m and s use the sign of the
+ * weak form (Eq. HHO1/HHO2).
+ */
+#ifndef HHO_H
+#define HHO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+#define HHO_OK         0
+#define HHO_EINVAL     1  /* bad argument, null pointer, size out of range          */
+#define HHO_EMESH      2  /* non-manifold edge, clockwise/degenerate cell, bad id  */
+#define HHO_EMATERIAL  3  /* rho <= 0, kappa <= 0, mu <= 0 or lambda + mu <= 0     */
+#define HHO_EDEGREE    4  /* k not in {1, 2, 3} (k >= 1 is required in the solid)   */
+#define HHO_ECFL       5  /* reserved: time step above a stated CFL limit          */
+#define HHO_EUNSTABLE  6  /* non-finite or growing energy detected on the host      */
+#define HHO_ECUDA      7  /* a CUDA runtime call failed                             */
+#define HHO_ENOMEM     8  /* host or device allocation failed                       */
+
+typedef struct hho_mesh hho_mesh;
+typedef struct hho_ops hho_ops;
+
+/* Copies the last error message of the calling thread into buf (always
+ * NUL-terminated when len > 0).  Returns the message length. */
+int hho_last_error(char* buf, size_t len);
+
+/* ------------------------------------------------------------------------- */
+/* Mesh (Sec. 3.1: polygonal cells aligned with the fluid/solid partition;   */
+/* hanging nodes are ordinary polygon vertices).                              */
+/* ------------------------------------------------------------------------- */
+
+/* Builds a mesh from n_vertices points h_xy[2*v] = (x, y) and n_cells
+ * counter-clockwise polygons: cell c has vertices h_cell_vtx[h_cell_ptr[c] ..
+ * h_cell_ptr[c+1]-1].  h_cell_domain[c] is 0 (fluid) or 1 (solid).
+ * h_vertex_rep (may be NULL) maps each vertex to a representative id used to
+ * match faces, which identifies periodic images.  A periodic direction needs
+ * at least three cells.
+ * Faces, face types, colours and cell classes follow the canonical rules:
+ *  1 faces numbered by first encounter (cells in order, local edge j joins
+ *    vertex j to j+1), keyed by the unordered pair of representative ids;
+ *  2 a face's cell 0 is the first cell meeting it, cell 1 the other or -1;
+ *  3 tangent from the smaller to the larger representative id (cell 0's
+ *    coordinates), normal (t_y, -t_x);
+ *  4 colours: greedy in face order, the smallest colour unused by an earlier
+ *    face sharing a cell;
+ *  5 classes: key (domain, number of vertices, vertex coordinates relative to
+ *    the centroid divided by the diameter, scaled by 2^40 and rounded half to
+ *    even), numbered by first appearance; centroid = p_0 + cx / (3 A2) from
+ *    coordinates relative to vertex 0, no fused multiply-add.
+ * Errors: HHO_EINVAL (null/negative sizes, vertex id out of range, domain not
+ * 0/1), HHO_EMESH (fewer than 3 vertices, non-positive area, an edge shared
+ * by more than two cells).  The input arrays are copied; *out is owned by
+ * the caller and freed with hho_mesh_destroy. */
+int hho_mesh_create(const double* h_xy, int64_t n_vertices,
+                    const int64_t* h_cell_ptr, const int64_t* h_cell_vtx, int64_t n_cells,
+                    const uint8_t* h_cell_domain, const int64_t* h_vertex_rep,
+                    hho_mesh** out);
+
+typedef struct {
+    int64_t n_vertices, n_cells, n_faces;
+    int64_t n_fluid_cells, n_solid_cells;
+    int64_t n_faces_by_type[5];     /* 0 fluid, 1 solid, 2 interface, 3 fluid bnd, 4 solid bnd */
+    int32_t n_classes, n_colours, max_faces_per_cell, reserved;
+} hho_mesh_info;
+
+int hho_mesh_query(const hho_mesh* mesh, hho_mesh_info* out);
+
+/* Writes the canonical integer tables (each pointer may be NULL to skip):
+ * h_face_cells[2*n_faces], h_cell_faces_ptr[n_cells+1],
+ * h_cell_faces[sum of cell sizes] (local order), h_face_type[n_faces],
+ * h_face_colour[n_faces], h_cell_class[n_cells]. */
+int hho_mesh_tables(const hho_mesh* mesh, int64_t* h_face_cells, int64_t* h_cell_faces_ptr,
+                    int64_t* h_cell_faces, int32_t* h_face_type, int32_t* h_face_colour,
+                    int32_t* h_cell_class);
+
+void hho_mesh_destroy(hho_mesh* mesh);
+
+/* ------------------------------------------------------------------------- */
+/* Operators (Sec. 3.3: Eq. mass, Eq. rec, Eq. stab, coupling, Eq. rhs).      */
+/* ------------------------------------------------------------------------- */
+
+typedef struct {
+    double  eta_f;        /* weight of the fluid stabilisation, default 0.8 (Sec. 5.1)  */
+    double  eta_s;        /* weight of the solid stabilisation, default 1.5 (Sec. 5.1)  */
+    int32_t stab_speed;   /* c^s in tau^s = eta_s rho c^s: 0 = c_P (default), 1 = c_S   */
+    int32_t tau_over_k;   /* 1: divide both tau by k (Sec. 3.3, optional scaling)       */
+} hho_params;
+
+void hho_params_default(hho_params* p);
+
+/* Builds the stage operator on the current CUDA device for polynomial degree
+ * k in {1,2,3} (equal order, least-squares stabilisation, alpha = 0):
+ * tau^f = eta_f / (rho c_P^f), tau^s = eta_s rho c^s (Sec. 3.3).
+ * Per-cell materials (host arrays of n_cells): h_rho; h_lambda, h_mu (used in
+ * solid cells, plane strain); h_kappa (used in fluid cells, kappa = rho c^2).
+ * Class matrices are computed in FP64 on the host by quadrature and uploaded
+ * with synchronous copies.  The mesh may be destroyed afterwards.
+ * Errors: HHO_EDEGREE, HHO_EMATERIAL, HHO_EINVAL, HHO_ENOMEM, HHO_ECUDA. */
+int hho_operators_build(const hho_mesh* mesh, int32_t k,
+                        const double* h_rho, const double* h_lambda, const double* h_mu,
+                        const double* h_kappa, const hho_params* params, hho_ops** out);
+
+void hho_ops_destroy(hho_ops* ops);
+
+typedef struct {
+    int64_t n_state;       /* doubles in a device-layout state vector                   */
+    int64_t n_canonical;   /* doubles in a canonical vector (sum of 3n / 5n per cell)    */
+    int64_t n_fluid_pad;   /* padded fluid cell slots (multiple of 32)                   */
+    int64_t n_solid_pad;   /* padded solid cell slots (multiple of 32)                   */
+    int32_t n;             /* dim P^k(T) = (k+1)(k+2)/2                                   */
+    int32_t f;             /* dim P^k(F) = k+1                                            */
+    int32_t n_classes;
+    int32_t reserved;
+} hho_layout;
+
+int hho_state_layout(const hho_ops* ops, hho_layout* out);
+
+/* Device-layout state: fluid block [3n][n_fluid_pad] then solid block
+ * [5n][n_solid_pad], i.e. one array per (field, coefficient), cells sorted by
+ * (domain, class) with each class padded to a multiple of 32.  Padding slots
+ * are zero.  pack: canonical -> device layout; unpack: the reverse.  Both
+ * pointers are device memory of the stated sizes; stream-ordered. */
+int hho_state_pack(const hho_ops* ops, const double* d_canonical, double* d_state, void* stream);
+int hho_state_unpack(const hho_ops* ops, const double* d_state, double* d_canonical, void* stream);
+
+/* ------------------------------------------------------------------------- */
+/* Time stepping (Sec. 4.2: Eq. ERK_compact, face elimination Eq. ex_solve,   */
+/* tableaux Eq. ERK).                                                         */
+/* ------------------------------------------------------------------------- */
+
+/* An explicit tableau with s <= 6 stages: a[i][j] (strictly lower
+ * triangular), b[j], c[i]; rows and columns beyond s are ignored. */
+typedef struct {
+    int32_t s;
+    int32_t reserved;
+    double a[6][6];
+    double b[6];
+    double c[6];
+} hho_tableau;
+
+/* Fills *out with ERK(s) of Eq. ERK for s = 2 (explicit midpoint), 3 or 4
+ * (classical).  HHO_EINVAL for other s. */
+int hho_tableau_erk(int32_t s, hho_tableau* out);
+
+/* Size in doubles of the caller-owned work buffer that hho_erk_step needs
+ * for this tableau (stage vector, partial sums, two trace buffers). */
+int hho_work_size(const hho_ops* ops, const hho_tableau* tab, int64_t* n_doubles);
+
+/* Point sources with a Ricker wavelet
+ * w(t) = amp (1 - 2 pi^2 f0^2 (t - t0)^2) exp(-pi^2 f0^2 (t - t0)^2):
+ * in a solid cell a point force along h_dir (load vector w(t) phi_i(x_s) e_dir
+ * in the velocity equation); in a fluid cell a pressure source w(t) phi_i(x_s)
+ * (Eq. rhs, read as a load vector).  Arrays of n_src entries (h_xy and h_dir
+ * of 2*n_src).  Replaces any previous set; n_src = 0 clears.  At most 8.
+ * The owning cell is the lowest-index cell containing the point. */
+int hho_sources_set(hho_ops* ops, int32_t n_src, const double* h_xy, const double* h_dir,
+                    const double* h_f0, const double* h_t0, const double* h_amp);
+
+/* Advances d_state (device layout, in/out) by nsteps steps of size dt from
+ * time t0 with the tableau.  Each stage is one fused kernel (face values from
+ * neighbour traces, reconstruction, stabilisation, coupling, inverse mass,
+ * ERK accumulation, traces for the next stage), plus one trace kernel per
+ * call.  d_work: caller-owned device buffer of hho_work_size doubles.
+ * No allocation, no host synchronisation.  Errors: HHO_EINVAL, HHO_ECUDA
+ * (launch failure). */
+int hho_erk_step(hho_ops* ops, const hho_tableau* tab, double t0, double dt, int64_t nsteps,
+                 double* d_state, double* d_work, void* stream);
+
+/* hho_erk_step followed, after every step, by hho_record into
+ * d_seismogram + 5 * n_rec * step (device, nsteps * n_rec * 5 doubles): the
+ * sensor traces of Sec. 5.2 sampled at every time node. */
+int hho_erk_step_record(hho_ops* ops, const hho_tableau* tab, double t0, double dt, int64_t nsteps,
+                        double* d_state, double* d_work, double* d_seismogram, void* stream);
+
+/* Same as hho_erk_step, end to end from host memory: copies the canonical
+ * host vector h_canonical (n_canonical doubles; pinned memory recommended) to
+ * the device, packs it, steps, unpacks and copies it back, and synchronises
+ * the stream.  The device buffers it needs are allocated on the first call
+ * and kept with ops. */
+int hho_erk_run_host(hho_ops* ops, const hho_tableau* tab, double t0, double dt, int64_t nsteps,
+                     double* h_canonical, void* stream);
+
+/* Semi-discrete rate d_rate = M^-1 (F(t) - (K_T - K_TF K_F^-1 K_FT) U) for the
+ * device-layout state d_state: the operator inside every stage of Eq. ex_solve.
+ * d_work: at least hho_work_size(ops, ERK2) doubles. */
+int hho_apply(hho_ops* ops, double t, const double* d_state, double* d_rate, double* d_work,
+              void* stream);
+
+/* ------------------------------------------------------------------------- */
+/* Sensors and energy (Sec. 5).                                               */
+/* ------------------------------------------------------------------------- */
+
+/* Sets n_rec receiver points h_xy[2*n_rec].  A point on an interface face
+ * records the face unknowns; otherwise the lowest-index containing cell. */
+int hho_receivers_set(hho_ops* ops, int32_t n_rec, const double* h_xy);
+
+/* d_out[5*r + j] for each receiver r: fluid [p, m_x, m_y, 0, 0]; solid
+ * [v_x, v_y, s_xx, s_yy, s_xy]; interface [p_F, v_Fx, v_Fy, 0, 0] (the face
+ * solve of Eq. ex_solve evaluated at the point). */
+int hho_record(hho_ops* ops, const double* d_state, double* d_out, void* stream);
+
+/* Discrete energy E = 1/2 U^T M U (Sec. 5.1) of a device-layout state,
+ * returned in *h_energy after synchronising the stream.  d_work: at least
+ * hho_work_size(ops, ERK2) doubles (block partial sums).  A non-finite
+ * result returns HHO_EUNSTABLE. */
+int hho_energy(hho_ops* ops, const double* d_state, double* d_work, double* h_energy, void* stream);
+
+/* ------------------------------------------------------------------------- */
+/* Cost model and stage timing (measurement support; no counterpart in the   */
+/* paper, which reports only CPU seconds, Table 4).                           */
+/* ------------------------------------------------------------------------- */
+
+/* Per ERK step with this tableau, summed over all cells (padding excluded):
+ * *fp64_ops = FP64 instructions the stage kernels execute per thread-lane
+ * (FMA, ADD and MUL each count 1), from the class-matrix sparsity and the face
+ * kinds; *bytes_min = 8 bytes x cell DOFs x state-vector passes of the fused
+ * design, counting per stage the distinct vectors read (stage input, U^{n-1},
+ * partial sums) and written (classical ERK4: 16 passes per step, i.e. 32
+ * bytes per cell DOF per stage); *bytes_kernel = bytes the stage kernels move
+ * by design (those passes plus face traces, exchange tables and per-cell
+ * scalars).  Any output pointer may be NULL. */
+int hho_stage_cost(const hho_ops* ops, const hho_tableau* tab, int64_t* fp64_ops, int64_t* bytes_min,
+                   int64_t* bytes_kernel);
+
+/* When on != 0, hho_erk_step brackets every stage-kernel launch with CUDA
+ * events on the launch stream (up to 4096 launches are kept).  hho_profile_read
+ * synchronises those events and returns the summed stage-kernel time in
+ * milliseconds and the number of launches since the last enable, then resets. */
+int hho_profile_enable(hho_ops* ops, int32_t on);
+int hho_profile_read(hho_ops* ops, double* ms_stage_total, int64_t* n_launches);
+
+/* CFL-limited step (Eq. CFL): dt = safety * cfl_star * h_min / c_max, with
+ * h_min the shortest cell edge and c_max the largest wave speed. */
+int hho_cfl_dt(const hho_ops* ops, double cfl_star, double safety, double* dt_out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HHO_H */

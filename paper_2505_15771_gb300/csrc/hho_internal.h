@@ -1,0 +1,147 @@
+// Internal declarations shared by the host C++ sources and the CUDA sources.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "hho.h"
+
+void hho_set_error(const char* fmt, ...);
+
+// Face types (Sec. 3.1 face sets).
+enum { FT_FLUID = 0, FT_SOLID = 1, FT_IFACE = 2, FT_BND_FLUID = 3, FT_BND_SOLID = 4 };
+
+struct hho_mesh {
+    int64_t nv = 0, nc = 0, nf = 0;
+    std::vector<double> xy;            // 2 nv
+    std::vector<int64_t> cell_ptr;     // nc + 1
+    std::vector<int64_t> cell_vtx;
+    std::vector<uint8_t> domain;       // nc
+    std::vector<int64_t> rep;          // nv
+    std::vector<int64_t> face_cells;   // 2 nf
+    std::vector<int32_t> face_local;   // 2 nf: local edge index in cell 0 / cell 1
+    std::vector<int64_t> cell_faces;   // indexed by cell_ptr
+    std::vector<int32_t> face_type, face_colour, cell_class;
+    std::vector<double> centroid;      // 2 nc
+    std::vector<double> diam, area;    // nc
+    int32_t n_classes = 0, n_colours = 0, max_nf = 0;
+    std::vector<int64_t> class_first;  // first cell of each class
+};
+
+// Per-class integer record on the device (stride CI_STRIDE ints).
+enum { CI_DOMAIN = 0, CI_NF, CI_START, CI_COUNT, CI_NPAD, CI_SLOT, CI_DOFF, CI_PAD, CI_STRIDE };
+
+// Device-side description of one stage launch and the static operator data.
+struct DevOps {
+    int32_t k, n, f;
+    int32_t Nf, Ns;          // padded cell slots per domain (multiples of 32)
+    int32_t SF, SS;          // face-side slots per domain
+    int32_t n_warps_f, n_warps_s;
+    const int32_t* warp_class;   // [n_warps_f + n_warps_s]
+    const int32_t* cls_int;      // [n_classes][CI_STRIDE]
+    const double* cls_dbl;       // class matrices, see operators.cpp
+    const double* scal_f;        // fluid per-cell scalars [SCF][Nf]
+    const double* scal_s;        // solid per-cell scalars [SCS][Ns]
+    const int32_t* nb_f;         // face-side neighbour slot, fluid [SF]
+    const int32_t* nb_s;         // solid [SS]
+    const double* beta_f;        // face-side coefficient, fluid [SF]
+    const double* beta_s;        // solid [SS]
+    const int32_t* if_nb;        // interface records: neighbour slot in the other domain
+    const double* if_coef;       // interface records: 6 coefficients each
+};
+
+// Fluid scalars: A_m = 1/(rho h), A_p = kappa/h, tau.  Solid: c1 = (lambda+2mu)/h,
+// c2 = lambda/h, c3 = mu/h, A_v = 1/(rho h), tau.
+enum { SF_AM = 0, SF_AP, SF_TAU, SCF };
+enum { SS_C1 = 0, SS_C2, SS_C3, SS_AV, SS_TAU, SCS };
+
+// Face-side neighbour encoding: >= 0 same-domain neighbour slot, -1 boundary,
+// <= -2 interface record (-2 - r).
+constexpr int32_t NB_BOUNDARY = -1;
+
+constexpr int MAX_TARGETS = 4;
+constexpr int MAX_SOURCES = 8;
+
+struct Target {
+    const double* src;   // nullptr: zero
+    double* dst;
+    double coef;
+};
+
+struct StageArgs {
+    DevOps op;
+    const double* inp;       // device-layout state read by the stage
+    const double* tr_in;     // traces of inp: fluid [2f][SF] then solid [4f][SS]
+    double* tr_out;          // traces of the target-0 result (same layout)
+    Target tgt[MAX_TARGETS];
+    int32_t n_tgt;
+    int32_t n_src;
+    int32_t src_dom[MAX_SOURCES];
+    int32_t src_q[MAX_SOURCES];
+    double src_w[MAX_SOURCES];       // wavelet value at the stage time
+    const double* src_g;             // [n_src][2][n] lifted load vectors
+};
+
+enum { MODE_TRACES = 0, MODE_STAGE = 1, MODE_APPLY = 2 };
+
+// Launchers (stage.cu).
+int launch_stage(int mode, const StageArgs& a, void* stream);
+int launch_pack(const hho_ops* ops, const double* canon, double* state, int unpack, void* stream);
+int launch_energy(const hho_ops* ops, const double* state, double* partial, double* result, void* stream);
+int launch_record(const hho_ops* ops, const double* state, double* out, void* stream);
+
+struct hho_ops {
+    int32_t k = 0, n = 0, f = 0;
+    int64_t nc = 0;
+    int32_t n_classes = 0;
+    DevOps dev{};
+    // device allocations owned by ops
+    std::vector<void*> allocations;
+    // host copies needed later
+    std::vector<int32_t> cell_dom, cell_pos;   // per original cell: domain, device position
+    std::vector<int64_t> canon_off;            // per original cell: offset in canonical vector
+    int64_t n_canonical = 0;
+    int32_t* d_dev2orig = nullptr;             // [Nf + Ns]: original cell id or -1 (padding)
+    int64_t* d_canon_off = nullptr;            // [nc]
+    std::vector<double> h_min_edge_per_cell;
+    double c_max = 0.0, h_min = 0.0;
+    // host-side per-cell data kept for sources/receivers
+    std::vector<double> centroid, diam, rho, tau;
+    std::vector<int32_t> cell_class_of;
+    std::vector<std::vector<double>> class_M0inv;     // per class, n x n
+    std::vector<std::vector<double>> class_ref_xy;    // per class, scaled vertex coordinates
+    std::vector<std::vector<double>> class_normals;   // per class, 2 per face
+    std::vector<double> kappa, lam, mu;
+    std::vector<double> poly_xy;                      // copy of vertex coordinates for location
+    std::vector<int64_t> poly_ptr, poly_vtx;
+    std::vector<uint8_t> poly_dom;
+    std::vector<int64_t> face_cells, cell_faces;
+    std::vector<int32_t> face_type, face_local;
+    // sources
+    int32_t n_src = 0;
+    int32_t src_dom[MAX_SOURCES], src_q[MAX_SOURCES];
+    double src_f0[MAX_SOURCES], src_t0[MAX_SOURCES], src_amp[MAX_SOURCES];
+    double* d_src_g = nullptr;
+    // receivers
+    int32_t n_rec = 0;
+    int32_t* d_rec_int = nullptr;
+    double* d_rec_dbl = nullptr;
+    // energy
+    double* d_mass_f = nullptr;   // per fluid cell: rho h^2, h^2/kappa
+    double* d_mass_s = nullptr;   // per solid cell: h^2 * compliance (3), rho h^2
+    // host-buffer entry point scratch
+    double* d_host_state = nullptr;
+    double* d_host_canon = nullptr;
+    double* d_host_work = nullptr;
+    int64_t host_work_size = 0;
+    int64_t n_state = 0;
+    int64_t trace_doubles = 0;    // one trace buffer (fluid + solid parts)
+    // host copies for the cost model
+    std::vector<double> h_cls_dbl;
+    std::vector<int32_t> h_cls_int, h_nb_f, h_nb_s;
+    // stage-kernel timing (hho_profile_*)
+    bool prof_on = false;
+    int32_t prof_n = 0;
+    std::vector<void*> prof_events;   // cudaEvent_t pairs
+};

@@ -1,0 +1,760 @@
+// Operator build (Sec. 3.3): per-class reference matrices in FP64, the device
+// layout, per-cell scalars and the face-side exchange tables.
+//
+// What a stage needs, per cell T of diameter h (all matrices dimensionless, in
+// the scaled-monomial basis phi_(a,b) = X^a Y^b, X = (x - x_T)/h):
+//   * the trace of a cell polynomial on local face j in the Legendre basis of
+//     that face, Tr_j (f x n), with xi running along the counter-clockwise edge;
+//   * the lifting of a face polynomial, Lift_j = M0^-1 B_j (n x f), where
+//     M0 = (phi_j, phi_i)_T and B_j = (P_l, phi_i)_F in scaled coordinates;
+//   * the outward unit normal n_j.
+// With these, the weak form (Eq. rec, Eq. stab, mass Eq. mass) gives, for the
+// jump J_F = u_F - u_T|_F on each face:
+//   dm/dt = 1/(rho h) [ grad^ p + sum_F n_F Lift_F J_F ]
+//   dp/dt = kappa/h   [ div^ m  + tau sum_F Lift_F J_F ]
+//   ds/dt = C/h       [ grad_sym^ v + sum_F sym(n_F (x) Lift_F J_F) ]
+//   dv/dt = 1/(rho h) [ div^ s  + tau sum_F Lift_F J_F ]
+// (hats: derivatives in scaled coordinates), which is the condensed operator
+// of Eq. ex_solve applied cell by cell.
+//
+// Integration route: fan of triangles from the centroid, each integrated with
+// a collapsed (Duffy) Gauss-Legendre rule; Legendre nodes by Newton's method.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "hho_internal.h"
+
+namespace {
+
+void gauss_legendre(int q, std::vector<double>& x, std::vector<double>& w) {
+    x.assign(q, 0.0);
+    w.assign(q, 0.0);
+    for (int i = 0; i < q; ++i) {
+        double z = std::cos(M_PI * (i + 0.75) / (q + 0.5));
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = z;
+            for (int l = 2; l <= q; ++l) {
+                double p2 = ((2.0 * l - 1.0) * z * p1 - (l - 1.0) * p0) / l;
+                p0 = p1;
+                p1 = p2;
+            }
+            // p1 = P_q(z), p0 = P_{q-1}(z)
+            double dp = q * (z * p1 - p0) / (z * z - 1.0);
+            double dz = p1 / dp;
+            z -= dz;
+            if (std::fabs(dz) < 1e-17) break;
+        }
+        double p0 = 1.0, p1 = z;
+        for (int l = 2; l <= q; ++l) {
+            double p2 = ((2.0 * l - 1.0) * z * p1 - (l - 1.0) * p0) / l;
+            p0 = p1;
+            p1 = p2;
+        }
+        double dp = q * (z * p1 - p0) / (z * z - 1.0);
+        x[i] = z;
+        w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+}
+
+void legendre_values(int f, double xi, double* P) {
+    P[0] = 1.0;
+    if (f > 1) P[1] = xi;
+    for (int l = 2; l < f; ++l) P[l] = ((2.0 * l - 1.0) * xi * P[l - 1] - (l - 1.0) * P[l - 2]) / l;
+}
+
+void exponents(int k, std::vector<int>& A, std::vector<int>& B) {
+    A.clear();
+    B.clear();
+    for (int d = 0; d <= k; ++d)
+        for (int a = d; a >= 0; --a) {
+            A.push_back(a);
+            B.push_back(d - a);
+        }
+}
+
+void basis_values(const std::vector<int>& A, const std::vector<int>& B, double X, double Y, double* out) {
+    for (size_t i = 0; i < A.size(); ++i) out[i] = std::pow(X, A[i]) * std::pow(Y, B[i]);
+}
+
+// Inverse of an SPD matrix by Cholesky (row-major n x n).
+bool spd_inverse(int n, const std::vector<double>& M, std::vector<double>& inv) {
+    std::vector<double> L(n * n, 0.0);
+    for (int j = 0; j < n; ++j) {
+        double d = M[j * n + j];
+        for (int p = 0; p < j; ++p) d -= L[j * n + p] * L[j * n + p];
+        if (!(d > 0.0)) return false;
+        L[j * n + j] = std::sqrt(d);
+        for (int i = j + 1; i < n; ++i) {
+            double s = M[i * n + j];
+            for (int p = 0; p < j; ++p) s -= L[i * n + p] * L[j * n + p];
+            L[i * n + j] = s / L[j * n + j];
+        }
+    }
+    inv.assign(n * n, 0.0);
+    std::vector<double> y(n), x(n);
+    for (int col = 0; col < n; ++col) {
+        for (int i = 0; i < n; ++i) {
+            double s = (i == col) ? 1.0 : 0.0;
+            for (int p = 0; p < i; ++p) s -= L[i * n + p] * y[p];
+            y[i] = s / L[i * n + i];
+        }
+        for (int i = n - 1; i >= 0; --i) {
+            double s = y[i];
+            for (int p = i + 1; p < n; ++p) s -= L[p * n + i] * x[p];
+            x[i] = s / L[i * n + i];
+        }
+        for (int i = 0; i < n; ++i) inv[i * n + col] = x[i];
+    }
+    return true;
+}
+
+bool inverse3(const double A[9], double out[9]) {
+    double c00 = A[4] * A[8] - A[5] * A[7];
+    double c01 = A[5] * A[6] - A[3] * A[8];
+    double c02 = A[3] * A[7] - A[4] * A[6];
+    double det = A[0] * c00 + A[1] * c01 + A[2] * c02;
+    if (!(std::fabs(det) > 0.0)) return false;
+    double id = 1.0 / det;
+    out[0] = c00 * id;
+    out[1] = (A[2] * A[7] - A[1] * A[8]) * id;
+    out[2] = (A[1] * A[5] - A[2] * A[4]) * id;
+    out[3] = c01 * id;
+    out[4] = (A[0] * A[8] - A[2] * A[6]) * id;
+    out[5] = (A[2] * A[3] - A[0] * A[5]) * id;
+    out[6] = c02 * id;
+    out[7] = (A[1] * A[6] - A[0] * A[7]) * id;
+    out[8] = (A[0] * A[4] - A[1] * A[3]) * id;
+    return true;
+}
+
+template <class T>
+T* dev_upload(hho_ops* ops, const std::vector<T>& h, int* err) {
+    if (h.empty()) return nullptr;
+    void* p = nullptr;
+    if (cudaMalloc(&p, sizeof(T) * h.size()) != cudaSuccess) {
+        *err = HHO_ENOMEM;
+        return nullptr;
+    }
+    ops->allocations.push_back(p);
+    if (cudaMemcpy(p, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+        *err = HHO_ECUDA;
+        return nullptr;
+    }
+    return (T*)p;
+}
+
+bool point_in_cell(const std::vector<double>& xy, const int64_t* vtx, int nv, double x, double y) {
+    double xmin = 1e300, xmax = -1e300, ymin = 1e300, ymax = -1e300;
+    for (int i = 0; i < nv; ++i) {
+        double px = xy[2 * vtx[i]], py = xy[2 * vtx[i] + 1];
+        xmin = std::min(xmin, px); xmax = std::max(xmax, px);
+        ymin = std::min(ymin, py); ymax = std::max(ymax, py);
+    }
+    double scale = std::max(xmax - xmin, ymax - ymin);
+    for (int i = 0; i < nv; ++i) {
+        int j = (i + 1) % nv;
+        double ax = xy[2 * vtx[i]], ay = xy[2 * vtx[i] + 1];
+        double ex = xy[2 * vtx[j]] - ax, ey = xy[2 * vtx[j] + 1] - ay;
+        double cr = ex * (y - ay) - ey * (x - ax);
+        if (cr < -1e-12 * scale * scale) return false;
+    }
+    return true;
+}
+
+}  // namespace
+
+extern "C" void hho_params_default(hho_params* p) {
+    if (!p) return;
+    p->eta_f = 0.8;
+    p->eta_s = 1.5;
+    p->stab_speed = 0;
+    p->tau_over_k = 0;
+}
+
+extern "C" int hho_tableau_erk(int32_t s, hho_tableau* t) {
+    if (!t || s < 2 || s > 4) {
+        hho_set_error("hho_tableau_erk: s must be 2, 3 or 4");
+        return HHO_EINVAL;
+    }
+    memset(t, 0, sizeof(*t));
+    t->s = s;
+    if (s == 2) {            // explicit midpoint (Eq. ERK, left)
+        t->a[1][0] = 0.5;
+        t->b[0] = 0.0; t->b[1] = 1.0;
+        t->c[1] = 0.5;
+    } else if (s == 3) {     // Eq. ERK, middle
+        t->a[1][0] = 0.5;
+        t->a[2][0] = -1.0; t->a[2][1] = 2.0;
+        t->b[0] = 1.0 / 6.0; t->b[1] = 2.0 / 3.0; t->b[2] = 1.0 / 6.0;
+        t->c[1] = 0.5; t->c[2] = 1.0;
+    } else {                 // classical ERK(4), Eq. ERK, right
+        t->a[1][0] = 0.5; t->a[2][1] = 0.5; t->a[3][2] = 1.0;
+        t->b[0] = 1.0 / 6.0; t->b[1] = 1.0 / 3.0; t->b[2] = 1.0 / 3.0; t->b[3] = 1.0 / 6.0;
+        t->c[1] = 0.5; t->c[2] = 0.5; t->c[3] = 1.0;
+    }
+    return HHO_OK;
+}
+
+extern "C" int hho_operators_build(const hho_mesh* m, int32_t k, const double* rho, const double* lam,
+                                   const double* mu, const double* kappa, const hho_params* params,
+                                   hho_ops** out) {
+    if (!m || !rho || !lam || !mu || !kappa || !out) {
+        hho_set_error("hho_operators_build: null pointer");
+        return HHO_EINVAL;
+    }
+    *out = nullptr;
+    if (k < 1 || k > 3) {
+        hho_set_error("hho_operators_build: k = %d, must be 1, 2 or 3", (int)k);
+        return HHO_EDEGREE;
+    }
+    hho_params P;
+    hho_params_default(&P);
+    if (params) P = *params;
+    if (!(P.eta_f > 0.0) || !(P.eta_s > 0.0) || (P.stab_speed != 0 && P.stab_speed != 1)) {
+        hho_set_error("hho_operators_build: bad stabilisation parameters");
+        return HHO_EINVAL;
+    }
+    const int64_t nc = m->nc;
+    std::vector<double> tau(nc), cmax(nc);
+    for (int64_t c = 0; c < nc; ++c) {
+        if (m->domain[c] == 0) {
+            if (!(rho[c] > 0.0) || !(kappa[c] > 0.0)) {
+                hho_set_error("hho_operators_build: fluid cell %lld has rho = %g, kappa = %g", (long long)c, rho[c], kappa[c]);
+                return HHO_EMATERIAL;
+            }
+            double cp = std::sqrt(kappa[c] / rho[c]);
+            tau[c] = P.eta_f / (rho[c] * cp);
+            cmax[c] = cp;
+        } else {
+            if (!(rho[c] > 0.0) || !(mu[c] > 0.0) || !(lam[c] + mu[c] > 0.0)) {
+                hho_set_error("hho_operators_build: solid cell %lld has rho = %g, lambda = %g, mu = %g",
+                              (long long)c, rho[c], lam[c], mu[c]);
+                return HHO_EMATERIAL;
+            }
+            double cp = std::sqrt((lam[c] + 2.0 * mu[c]) / rho[c]);
+            double cs = std::sqrt(mu[c] / rho[c]);
+            tau[c] = P.eta_s * rho[c] * (P.stab_speed == 0 ? cp : cs);
+            cmax[c] = cp;
+        }
+        if (P.tau_over_k) tau[c] /= k;
+    }
+
+    hho_ops* ops = new (std::nothrow) hho_ops();
+    if (!ops) {
+        hho_set_error("hho_operators_build: out of host memory");
+        return HHO_ENOMEM;
+    }
+    const int n = (k + 1) * (k + 2) / 2, f = k + 1;
+    ops->k = k;
+    ops->n = n;
+    ops->f = f;
+    ops->nc = nc;
+    ops->n_classes = m->n_classes;
+    std::vector<int> EA, EB;
+    exponents(k, EA, EB);
+
+    // ---- class reference matrices ------------------------------------------------
+    const int NCL = m->n_classes;
+    std::vector<int32_t> cls_nf(NCL), cls_dom(NCL);
+    std::vector<int32_t> cls_doff(NCL);
+    std::vector<double> cls_dbl;
+    ops->class_M0inv.resize(NCL);
+    ops->class_normals.resize(NCL);
+    std::vector<double> gx, gw, fx, fw;
+    gauss_legendre(k + 3, gx, gw);
+    gauss_legendre(k + 2, fx, fw);
+    std::vector<double> phi(n), Pl(f);
+    for (int cl = 0; cl < NCL; ++cl) {
+        int64_t c = m->class_first[cl];
+        int64_t b = m->cell_ptr[c];
+        int nv = (int)(m->cell_ptr[c + 1] - b);
+        double h = m->diam[c], cx = m->centroid[2 * c], cy = m->centroid[2 * c + 1];
+        std::vector<double> X(nv), Y(nv);
+        for (int i = 0; i < nv; ++i) {
+            X[i] = (m->xy[2 * m->cell_vtx[b + i]] - cx) / h;
+            Y[i] = (m->xy[2 * m->cell_vtx[b + i] + 1] - cy) / h;
+        }
+        cls_nf[cl] = nv;
+        cls_dom[cl] = m->domain[c];
+        // M0 by fan triangles from the origin (the centroid) with a collapsed rule.
+        std::vector<double> M0(n * n, 0.0);
+        for (int t = 0; t < nv; ++t) {
+            int t1 = (t + 1) % nv;
+            double ax = X[t], ay = Y[t], bx = X[t1] - X[t], by = Y[t1] - Y[t];
+            double det = ax * by - ay * bx;
+            for (size_t iu = 0; iu < gx.size(); ++iu)
+                for (size_t iv = 0; iv < gx.size(); ++iv) {
+                    double u = 0.5 * (gx[iu] + 1.0), v = 0.5 * (gx[iv] + 1.0);
+                    double wt = 0.25 * gw[iu] * gw[iv] * u * det;
+                    basis_values(EA, EB, u * ax + u * v * bx, u * ay + u * v * by, phi.data());
+                    for (int i = 0; i < n; ++i)
+                        for (int j = 0; j < n; ++j) M0[i * n + j] += wt * phi[i] * phi[j];
+                }
+        }
+        std::vector<double> M0inv;
+        if (!spd_inverse(n, M0, M0inv)) {
+            hho_set_error("hho_operators_build: class %d mass matrix is not positive definite", cl);
+            hho_ops_destroy(ops);
+            return HHO_EMESH;
+        }
+        ops->class_M0inv[cl] = M0inv;
+        cls_doff[cl] = (int32_t)cls_dbl.size();
+        for (double v : M0) cls_dbl.push_back(v);
+        for (int j = 0; j < nv; ++j) {
+            int j1 = (j + 1) % nv;
+            double ex = X[j1] - X[j], ey = Y[j1] - Y[j];
+            double L = std::sqrt(ex * ex + ey * ey);
+            double nx = ey / L, ny = -ex / L;
+            if (std::fabs(nx) < 1e-15) nx = 0.0;
+            if (std::fabs(ny) < 1e-15) ny = 0.0;
+            ops->class_normals[cl].push_back(nx);
+            ops->class_normals[cl].push_back(ny);
+            std::vector<double> Tr(f * n, 0.0), Bm(n * f, 0.0);
+            for (size_t g = 0; g < fx.size(); ++g) {
+                double xi = fx[g];
+                double s = 0.5 * (xi + 1.0);
+                basis_values(EA, EB, X[j] + s * ex, Y[j] + s * ey, phi.data());
+                legendre_values(f, xi, Pl.data());
+                for (int l = 0; l < f; ++l)
+                    for (int i = 0; i < n; ++i) {
+                        Tr[l * n + i] += (2.0 * l + 1.0) / 2.0 * fw[g] * phi[i] * Pl[l];
+                        Bm[i * f + l] += 0.5 * L * fw[g] * phi[i] * Pl[l];
+                    }
+            }
+            std::vector<double> Lift(n * f, 0.0);
+            for (int i = 0; i < n; ++i)
+                for (int l = 0; l < f; ++l) {
+                    double s = 0.0;
+                    for (int p = 0; p < n; ++p) s += M0inv[i * n + p] * Bm[p * f + l];
+                    Lift[i * f + l] = s;
+                }
+            // Entries that vanish by symmetry come out of the quadrature as
+            // rounding noise (below 1e-15 of the largest entry); store them as
+            // exact zeros so the kernels can skip them.
+            double tmax = 0.0, lmax = 0.0;
+            for (double v : Tr) tmax = std::max(tmax, std::fabs(v));
+            for (double v : Lift) lmax = std::max(lmax, std::fabs(v));
+            cls_dbl.push_back(nx);
+            cls_dbl.push_back(ny);
+            for (double v : Tr) cls_dbl.push_back(std::fabs(v) < 1e-13 * tmax ? 0.0 : v);
+            for (double v : Lift) cls_dbl.push_back(std::fabs(v) < 1e-13 * lmax ? 0.0 : v);
+        }
+    }
+
+    // ---- device layout: cells sorted by (domain, class), classes padded to 32 ----
+    std::vector<std::vector<int64_t>> members(NCL);
+    for (int64_t c = 0; c < nc; ++c) members[m->cell_class[c]].push_back(c);
+    std::vector<int32_t> cls_start(NCL), cls_count(NCL), cls_npad(NCL), cls_slot(NCL);
+    int64_t Nd[2] = {0, 0}, Sd[2] = {0, 0};
+    for (int d = 0; d < 2; ++d)
+        for (int cl = 0; cl < NCL; ++cl) {
+            if (cls_dom[cl] != d) continue;
+            int64_t cnt = (int64_t)members[cl].size();
+            int64_t npad = (cnt + 31) / 32 * 32;
+            cls_start[cl] = (int32_t)Nd[d];
+            cls_count[cl] = (int32_t)cnt;
+            cls_npad[cl] = (int32_t)npad;
+            cls_slot[cl] = (int32_t)Sd[d];
+            Nd[d] += npad;
+            Sd[d] += npad * cls_nf[cl];
+        }
+    if (Nd[0] * 5 * n > INT32_MAX || Nd[1] * 5 * n > INT32_MAX || Sd[0] * 4 * f > INT32_MAX ||
+        Sd[1] * 4 * f > INT32_MAX) {
+        hho_set_error("hho_operators_build: mesh too large for 32-bit device offsets");
+        hho_ops_destroy(ops);
+        return HHO_EINVAL;
+    }
+    const int32_t Nf = (int32_t)Nd[0], Ns = (int32_t)Nd[1], SF = (int32_t)Sd[0], SS = (int32_t)Sd[1];
+    ops->cell_dom.resize(nc);
+    ops->cell_pos.resize(nc);
+    ops->cell_class_of.assign(m->cell_class.begin(), m->cell_class.end());
+    std::vector<int32_t> dev2orig(Nf + Ns, -1);
+    for (int cl = 0; cl < NCL; ++cl)
+        for (size_t r = 0; r < members[cl].size(); ++r) {
+            int64_t c = members[cl][r];
+            int32_t q = cls_start[cl] + (int32_t)r;
+            ops->cell_dom[c] = cls_dom[cl];
+            ops->cell_pos[c] = q;
+            dev2orig[(cls_dom[cl] ? Nf : 0) + q] = (int32_t)c;
+        }
+    std::vector<int32_t> warp_class((Nf + Ns) / 32, 0);
+    for (int cl = 0; cl < NCL; ++cl) {
+        int32_t base = (cls_dom[cl] ? Nf : 0) + cls_start[cl];
+        for (int32_t w = 0; w < cls_npad[cl] / 32; ++w) warp_class[base / 32 + w] = cl;
+    }
+    std::vector<int32_t> cls_int(NCL * CI_STRIDE, 0);
+    for (int cl = 0; cl < NCL; ++cl) {
+        int32_t* r = &cls_int[cl * CI_STRIDE];
+        r[CI_DOMAIN] = cls_dom[cl];
+        r[CI_NF] = cls_nf[cl];
+        r[CI_START] = cls_start[cl];
+        r[CI_COUNT] = cls_count[cl];
+        r[CI_NPAD] = cls_npad[cl];
+        r[CI_SLOT] = cls_slot[cl];
+        r[CI_DOFF] = cls_doff[cl];
+    }
+
+    // ---- per-cell scalars ----------------------------------------------------------
+    std::vector<double> scal_f((size_t)SCF * Nf, 0.0), scal_s((size_t)SCS * Ns, 0.0);
+    std::vector<double> mass_f((size_t)2 * Nf, 0.0), mass_s((size_t)4 * Ns, 0.0);
+    for (int64_t c = 0; c < nc; ++c) {
+        int32_t q = ops->cell_pos[c];
+        double h = m->diam[c];
+        if (m->domain[c] == 0) {
+            scal_f[SF_AM * (size_t)Nf + q] = 1.0 / (rho[c] * h);
+            scal_f[SF_AP * (size_t)Nf + q] = kappa[c] / h;
+            scal_f[SF_TAU * (size_t)Nf + q] = tau[c];
+            mass_f[0 * (size_t)Nf + q] = rho[c] * h * h;
+            mass_f[1 * (size_t)Nf + q] = h * h / kappa[c];
+        } else {
+            scal_s[SS_C1 * (size_t)Ns + q] = (lam[c] + 2.0 * mu[c]) / h;
+            scal_s[SS_C2 * (size_t)Ns + q] = lam[c] / h;
+            scal_s[SS_C3 * (size_t)Ns + q] = mu[c] / h;
+            scal_s[SS_AV * (size_t)Ns + q] = 1.0 / (rho[c] * h);
+            scal_s[SS_TAU * (size_t)Ns + q] = tau[c];
+            // plane-strain compliance in the (E_xx, E_yy, E_xy) basis times h^2:
+            // D = [[1-beta, -beta, 0], [-beta, 1-beta, 0], [0, 0, 2]] / (2 mu)
+            double beta = lam[c] / (2.0 * (lam[c] + mu[c]));
+            mass_s[0 * (size_t)Ns + q] = h * h * (1.0 - beta) / (2.0 * mu[c]);
+            mass_s[1 * (size_t)Ns + q] = -h * h * beta / (2.0 * mu[c]);
+            mass_s[2 * (size_t)Ns + q] = h * h / mu[c];
+            mass_s[3 * (size_t)Ns + q] = rho[c] * h * h;
+        }
+    }
+
+    // ---- face-side exchange tables -------------------------------------------------
+    auto slot_of = [&](int64_t c, int j) -> int32_t {
+        int cl = m->cell_class[c];
+        return cls_slot[cl] + j * cls_npad[cl] + (ops->cell_pos[c] - cls_start[cl]);
+    };
+    std::vector<int32_t> nb_f(SF, NB_BOUNDARY), nb_s(SS, NB_BOUNDARY);
+    std::vector<double> beta_f(SF, 0.0), beta_s(SS, 0.0);
+    std::vector<int32_t> if_nb;
+    std::vector<double> if_coef;
+    for (int64_t c = 0; c < nc; ++c) {
+        int64_t b = m->cell_ptr[c];
+        int nv = (int)(m->cell_ptr[c + 1] - b);
+        int d = m->domain[c];
+        for (int j = 0; j < nv; ++j) {
+            int64_t F = m->cell_faces[b + j];
+            int32_t own = slot_of(c, j);
+            int side = (m->face_cells[2 * F] == c) ? 0 : 1;
+            int64_t c2 = m->face_cells[2 * F + 1 - side];
+            int32_t* nbt = d ? nb_s.data() : nb_f.data();
+            double* bet = d ? beta_s.data() : beta_f.data();
+            if (c2 < 0) {
+                nbt[own] = NB_BOUNDARY;
+                bet[own] = 0.0;
+                continue;
+            }
+            int j2 = m->face_local[2 * F + 1 - side];
+            int32_t other = slot_of(c2, j2);
+            if (m->domain[c2] == d) {
+                nbt[own] = other;
+                bet[own] = 1.0 / (tau[c] + tau[c2]);
+                continue;
+            }
+            // Interface face: [tau_f, n^T; -n, tau_s I] [p_F; v_F] = [w_f; w_s],
+            // n = n_Gamma, outward normal of the solid cell (coupling block, Sec. 3.3).
+            int64_t cf = d == 0 ? c : c2, cs = d == 0 ? c2 : c;
+            int js = d == 0 ? j2 : j;
+            const std::vector<double>& ns = ops->class_normals[m->cell_class[cs]];
+            double nx = ns[2 * js], ny = ns[2 * js + 1];
+            double Am[9] = {tau[cf], nx, ny, -nx, tau[cs], 0.0, -ny, 0.0, tau[cs]};
+            double Ai[9];
+            if (!inverse3(Am, Ai)) {
+                hho_set_error("hho_operators_build: singular interface block");
+                hho_ops_destroy(ops);
+                return HHO_EMATERIAL;
+            }
+            int32_t r = (int32_t)if_nb.size();
+            if_nb.push_back(other);
+            if (d == 0)   // fluid side: p_F = a w_f + b_x w_sx + b_y w_sy
+                for (double v : {Ai[0], Ai[1], Ai[2], 0.0, 0.0, 0.0}) if_coef.push_back(v);
+            else          // solid side: v_F = alpha (2x2) w_s + beta w_f
+                for (double v : {Ai[4], Ai[5], Ai[7], Ai[8], Ai[3], Ai[6]}) if_coef.push_back(v);
+            nbt[own] = -2 - r;
+            bet[own] = 0.0;
+        }
+    }
+
+    // ---- canonical offsets ----------------------------------------------------------
+    ops->canon_off.resize(nc);
+    int64_t off = 0;
+    for (int64_t c = 0; c < nc; ++c) {
+        ops->canon_off[c] = off;
+        off += (m->domain[c] == 0 ? 3 : 5) * n;
+    }
+    ops->n_canonical = off;
+
+    // ---- host copies for sources, receivers, CFL ---------------------------------------
+    ops->centroid = m->centroid;
+    ops->diam = m->diam;
+    ops->rho.assign(rho, rho + nc);
+    ops->kappa.assign(kappa, kappa + nc);
+    ops->lam.assign(lam, lam + nc);
+    ops->mu.assign(mu, mu + nc);
+    ops->tau = tau;
+    ops->poly_xy = m->xy;
+    ops->poly_ptr = m->cell_ptr;
+    ops->poly_vtx = m->cell_vtx;
+    ops->poly_dom = m->domain;
+    ops->face_cells = m->face_cells;
+    ops->cell_faces = m->cell_faces;
+    ops->face_type = m->face_type;
+    ops->face_local = m->face_local;
+    double hmin = 1e300, cm = 0.0;
+    for (int64_t c = 0; c < nc; ++c) {
+        int64_t b = m->cell_ptr[c];
+        int nv = (int)(m->cell_ptr[c + 1] - b);
+        for (int j = 0; j < nv; ++j) {
+            int64_t va = m->cell_vtx[b + j], vb = m->cell_vtx[b + (j + 1) % nv];
+            double ex = m->xy[2 * vb] - m->xy[2 * va], ey = m->xy[2 * vb + 1] - m->xy[2 * va + 1];
+            hmin = std::min(hmin, std::sqrt(ex * ex + ey * ey));
+        }
+        cm = std::max(cm, cmax[c]);
+    }
+    ops->h_min = hmin;
+    ops->c_max = cm;
+
+    // ---- upload ------------------------------------------------------------------------
+    int err = HHO_OK;
+    DevOps& D = ops->dev;
+    D.k = k;
+    D.n = n;
+    D.f = f;
+    D.Nf = Nf;
+    D.Ns = Ns;
+    D.SF = SF;
+    D.SS = SS;
+    D.n_warps_f = Nf / 32;
+    D.n_warps_s = Ns / 32;
+    D.warp_class = dev_upload(ops, warp_class, &err);
+    D.cls_int = dev_upload(ops, cls_int, &err);
+    D.cls_dbl = dev_upload(ops, cls_dbl, &err);
+    D.scal_f = dev_upload(ops, scal_f, &err);
+    D.scal_s = dev_upload(ops, scal_s, &err);
+    D.nb_f = dev_upload(ops, nb_f, &err);
+    D.nb_s = dev_upload(ops, nb_s, &err);
+    D.beta_f = dev_upload(ops, beta_f, &err);
+    D.beta_s = dev_upload(ops, beta_s, &err);
+    D.if_nb = dev_upload(ops, if_nb, &err);
+    D.if_coef = dev_upload(ops, if_coef, &err);
+    ops->d_dev2orig = dev_upload(ops, dev2orig, &err);
+    ops->d_canon_off = dev_upload(ops, ops->canon_off, &err);
+    ops->d_mass_f = dev_upload(ops, mass_f, &err);
+    ops->d_mass_s = dev_upload(ops, mass_s, &err);
+    if (err != HHO_OK) {
+        hho_set_error("hho_operators_build: device allocation or upload failed");
+        hho_ops_destroy(ops);
+        return err;
+    }
+    ops->h_cls_dbl = cls_dbl;
+    ops->h_cls_int = cls_int;
+    ops->h_nb_f = nb_f;
+    ops->h_nb_s = nb_s;
+    ops->n_state = (int64_t)3 * n * Nf + (int64_t)5 * n * Ns;
+    ops->trace_doubles = (int64_t)2 * f * SF + (int64_t)4 * f * SS;
+    *out = ops;
+    return HHO_OK;
+}
+
+extern "C" void hho_ops_destroy(hho_ops* ops) {
+    if (!ops) return;
+    for (void* p : ops->allocations) cudaFree(p);
+    if (ops->d_src_g) cudaFree(ops->d_src_g);
+    if (ops->d_rec_int) cudaFree(ops->d_rec_int);
+    if (ops->d_rec_dbl) cudaFree(ops->d_rec_dbl);
+    if (ops->d_host_state) cudaFree(ops->d_host_state);
+    if (ops->d_host_canon) cudaFree(ops->d_host_canon);
+    if (ops->d_host_work) cudaFree(ops->d_host_work);
+    for (void* e : ops->prof_events) cudaEventDestroy((cudaEvent_t)e);
+    delete ops;
+}
+
+extern "C" int hho_state_layout(const hho_ops* ops, hho_layout* out) {
+    if (!ops || !out) {
+        hho_set_error("hho_state_layout: null pointer");
+        return HHO_EINVAL;
+    }
+    memset(out, 0, sizeof(*out));
+    out->n_state = ops->n_state;
+    out->n_canonical = ops->n_canonical;
+    out->n_fluid_pad = ops->dev.Nf;
+    out->n_solid_pad = ops->dev.Ns;
+    out->n = ops->n;
+    out->f = ops->f;
+    out->n_classes = ops->n_classes;
+    return HHO_OK;
+}
+
+// Lowest-index cell containing the point (boundary inclusive), or -1.
+static int64_t locate(const hho_ops* ops, double x, double y) {
+    for (int64_t c = 0; c < ops->nc; ++c) {
+        int64_t b = ops->poly_ptr[c];
+        int nv = (int)(ops->poly_ptr[c + 1] - b);
+        if (point_in_cell(ops->poly_xy, &ops->poly_vtx[b], nv, x, y)) return c;
+    }
+    return -1;
+}
+
+static void cell_basis_at(const hho_ops* ops, int64_t c, double x, double y, double* phi) {
+    std::vector<int> EA, EB;
+    exponents(ops->k, EA, EB);
+    double h = ops->diam[c];
+    basis_values(EA, EB, (x - ops->centroid[2 * c]) / h, (y - ops->centroid[2 * c + 1]) / h, phi);
+}
+
+extern "C" int hho_sources_set(hho_ops* ops, int32_t n_src, const double* xy, const double* dir,
+                               const double* f0, const double* t0, const double* amp) {
+    if (!ops || n_src < 0 || n_src > MAX_SOURCES || (n_src > 0 && (!xy || !dir || !f0 || !t0 || !amp))) {
+        hho_set_error("hho_sources_set: bad arguments (at most %d sources)", MAX_SOURCES);
+        return HHO_EINVAL;
+    }
+    const int n = ops->n;
+    std::vector<double> g((size_t)n_src * 2 * n, 0.0);
+    std::vector<double> phi(n);
+    for (int s = 0; s < n_src; ++s) {
+        int64_t c = locate(ops, xy[2 * s], xy[2 * s + 1]);
+        if (c < 0) {
+            hho_set_error("hho_sources_set: source %d at (%g, %g) is outside the mesh", s, xy[2 * s], xy[2 * s + 1]);
+            return HHO_EINVAL;
+        }
+        cell_basis_at(ops, c, xy[2 * s], xy[2 * s + 1], phi.data());
+        const std::vector<double>& Mi = ops->class_M0inv[ops->cell_class_of[c]];
+        double h = ops->diam[c];
+        // M0 = h^2 M0_ref; the load vector w(t) phi(x_s) e enters M^-1 b.
+        double scale = ops->poly_dom[c] == 0 ? ops->kappa[c] / (h * h) : 1.0 / (ops->rho[c] * h * h);
+        for (int i = 0; i < n; ++i) {
+            double s_i = 0.0;
+            for (int p = 0; p < n; ++p) s_i += Mi[i * n + p] * phi[p];
+            s_i *= scale;
+            if (ops->poly_dom[c] == 0) {
+                g[((size_t)s * 2 + 0) * n + i] = s_i;
+            } else {
+                g[((size_t)s * 2 + 0) * n + i] = dir[2 * s] * s_i;
+                g[((size_t)s * 2 + 1) * n + i] = dir[2 * s + 1] * s_i;
+            }
+        }
+        ops->src_dom[s] = ops->cell_dom[c];
+        ops->src_q[s] = ops->cell_pos[c];
+        ops->src_f0[s] = f0[s];
+        ops->src_t0[s] = t0[s];
+        ops->src_amp[s] = amp[s];
+    }
+    if (ops->d_src_g) {
+        cudaFree(ops->d_src_g);
+        ops->d_src_g = nullptr;
+    }
+    ops->n_src = 0;
+    if (n_src > 0) {
+        if (cudaMalloc((void**)&ops->d_src_g, sizeof(double) * g.size()) != cudaSuccess) {
+            hho_set_error("hho_sources_set: device allocation failed");
+            return HHO_ENOMEM;
+        }
+        if (cudaMemcpy(ops->d_src_g, g.data(), sizeof(double) * g.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+            hho_set_error("hho_sources_set: upload failed");
+            return HHO_ECUDA;
+        }
+    }
+    ops->n_src = n_src;
+    return HHO_OK;
+}
+
+// Receiver record on the device: ints [kind, q_fluid, q_solid, pad];
+// doubles [phi_fluid (n), phi_solid (n), tau_f, tau_s, nf_x, nf_y, ns_x, ns_y, Ainv (9)].
+int receiver_dbl_stride(int n) { return 2 * n + 6 + 9; }
+
+extern "C" int hho_receivers_set(hho_ops* ops, int32_t n_rec, const double* xy) {
+    if (!ops || n_rec < 0 || (n_rec > 0 && !xy)) {
+        hho_set_error("hho_receivers_set: bad arguments");
+        return HHO_EINVAL;
+    }
+    const int n = ops->n, stride = receiver_dbl_stride(n);
+    std::vector<int32_t> ri((size_t)n_rec * 4, 0);
+    std::vector<double> rd((size_t)n_rec * stride, 0.0);
+    for (int r = 0; r < n_rec; ++r) {
+        double x = xy[2 * r], y = xy[2 * r + 1];
+        // interface face containing the point?
+        int64_t found = -1;
+        int64_t nF = (int64_t)ops->face_type.size();
+        for (int64_t F = 0; F < nF && found < 0; ++F) {
+            if (ops->face_type[F] != FT_IFACE) continue;
+            int64_t c0 = ops->face_cells[2 * F];
+            int j = ops->face_local[2 * F];
+            int64_t b = ops->poly_ptr[c0];
+            int nv = (int)(ops->poly_ptr[c0 + 1] - b);
+            int64_t va = ops->poly_vtx[b + j], vb = ops->poly_vtx[b + (j + 1) % nv];
+            double ax = ops->poly_xy[2 * va], ay = ops->poly_xy[2 * va + 1];
+            double tx = ops->poly_xy[2 * vb] - ax, ty = ops->poly_xy[2 * vb + 1] - ay;
+            double L2 = tx * tx + ty * ty;
+            double s = ((x - ax) * tx + (y - ay) * ty) / L2;
+            double dist = std::fabs(tx * (y - ay) - ty * (x - ax)) / std::sqrt(L2);
+            if (s >= -1e-10 && s <= 1.0 + 1e-10 && dist <= 1e-10 * std::sqrt(L2)) found = F;
+        }
+        double* d = &rd[(size_t)r * stride];
+        if (found >= 0) {
+            int64_t c0 = ops->face_cells[2 * found], c1 = ops->face_cells[2 * found + 1];
+            int64_t cf = ops->poly_dom[c0] == 0 ? c0 : c1, cs = ops->poly_dom[c0] == 0 ? c1 : c0;
+            int jf = ops->poly_dom[c0] == 0 ? ops->face_local[2 * found] : ops->face_local[2 * found + 1];
+            int js = ops->poly_dom[c0] == 0 ? ops->face_local[2 * found + 1] : ops->face_local[2 * found];
+            ri[r * 4 + 0] = 2;
+            ri[r * 4 + 1] = ops->cell_pos[cf];
+            ri[r * 4 + 2] = ops->cell_pos[cs];
+            cell_basis_at(ops, cf, x, y, d);
+            cell_basis_at(ops, cs, x, y, d + n);
+            const std::vector<double>& nfv = ops->class_normals[ops->cell_class_of[cf]];
+            const std::vector<double>& nsv = ops->class_normals[ops->cell_class_of[cs]];
+            d[2 * n + 0] = ops->tau[cf];
+            d[2 * n + 1] = ops->tau[cs];
+            d[2 * n + 2] = nfv[2 * jf];
+            d[2 * n + 3] = nfv[2 * jf + 1];
+            d[2 * n + 4] = nsv[2 * js];
+            d[2 * n + 5] = nsv[2 * js + 1];
+            double nx = nsv[2 * js], ny = nsv[2 * js + 1];
+            double Am[9] = {ops->tau[cf], nx, ny, -nx, ops->tau[cs], 0.0, -ny, 0.0, ops->tau[cs]};
+            inverse3(Am, d + 2 * n + 6);
+            continue;
+        }
+        int64_t c = locate(ops, x, y);
+        if (c < 0) {
+            hho_set_error("hho_receivers_set: receiver %d at (%g, %g) is outside the mesh", r, x, y);
+            return HHO_EINVAL;
+        }
+        ri[r * 4 + 0] = ops->poly_dom[c];
+        ri[r * 4 + 1] = ops->cell_pos[c];
+        ri[r * 4 + 2] = ops->cell_pos[c];
+        cell_basis_at(ops, c, x, y, d);
+    }
+    if (ops->d_rec_int) { cudaFree(ops->d_rec_int); ops->d_rec_int = nullptr; }
+    if (ops->d_rec_dbl) { cudaFree(ops->d_rec_dbl); ops->d_rec_dbl = nullptr; }
+    ops->n_rec = 0;
+    if (n_rec > 0) {
+        if (cudaMalloc((void**)&ops->d_rec_int, sizeof(int32_t) * ri.size()) != cudaSuccess ||
+            cudaMalloc((void**)&ops->d_rec_dbl, sizeof(double) * rd.size()) != cudaSuccess) {
+            hho_set_error("hho_receivers_set: device allocation failed");
+            return HHO_ENOMEM;
+        }
+        if (cudaMemcpy(ops->d_rec_int, ri.data(), sizeof(int32_t) * ri.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(ops->d_rec_dbl, rd.data(), sizeof(double) * rd.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+            hho_set_error("hho_receivers_set: upload failed");
+            return HHO_ECUDA;
+        }
+    }
+    ops->n_rec = n_rec;
+    return HHO_OK;
+}
+
+extern "C" int hho_cfl_dt(const hho_ops* ops, double cfl_star, double safety, double* dt_out) {
+    if (!ops || !dt_out || !(cfl_star > 0.0) || !(safety > 0.0)) {
+        hho_set_error("hho_cfl_dt: bad arguments");
+        return HHO_EINVAL;
+    }
+    *dt_out = safety * cfl_star * ops->h_min / ops->c_max;
+    return HHO_OK;
+}

@@ -1,0 +1,1067 @@
+// ERK stage kernels for GB300 (sm_103a) and the time-stepping entry points.
+//
+// One stage of Eq. ex_solve (Sec. 4.2) is ONE kernel.  Thread q owns cell q of
+// its domain (cells sorted by class, so a warp shares one class and its class
+// matrices are read with warp-uniform loads).  The face unknowns are never
+// stored: every cell publishes, per local face, two small vectors in the face's
+// Legendre basis (its own counter-clockwise orientation):
+//     w     = tau u_T|_F - (dual flux of T on F)      (what the neighbour needs)
+//     omega = alpha w - u_T|_F                         (what the cell itself needs)
+// where u is p (fluid) or v (solid) and the dual flux is m.n_T or s n_T.  The
+// face solve of Eq. ex_solve is block-diagonal; its closed form per Legendre
+// coefficient is
+//     interior:  u_F = (w_T + w_N) / (tau_T + tau_N)
+//     boundary:  u_F = 0
+//     interface: [p_F; v_F] = A^-1 [w_f; w_s],  A = [tau_f, n^T; -n, tau_s I]
+// (rows of the face block of the compact system, Eq. compact_AR, divided by
+// the face mass matrix).  So the jump u_F - u_T|_F a cell needs is
+// omega + beta * flip(w_N), flip = (-1)^l because the neighbour traverses
+// the face in the opposite direction.
+//
+// A stage thread then: reads its state; forms the exact derivatives of its
+// polynomials (sparse, compile-time); lifts each face jump with the class
+// matrix Lift_F; scales by the per-cell material factors (inverse mass,
+// Eq. mass, folded in); adds point sources; writes the ERK partial sums
+// (Eq. ERK_compact with a_{s+1,j} = b_j); and publishes w, omega of the new
+// stage value for the next stage (double-buffered traces).
+//
+// All arithmetic is FP64.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "hho_internal.h"
+
+namespace {
+
+__host__ __device__ constexpr int deg_of(int i) {
+    int d = 0;
+    while ((d + 1) * (d + 2) / 2 <= i) ++d;
+    return d;
+}
+__host__ __device__ constexpr int ea(int i) { return deg_of(i) - (i - deg_of(i) * (deg_of(i) + 1) / 2); }
+__host__ __device__ constexpr int eb(int i) { return i - deg_of(i) * (deg_of(i) + 1) / 2; }
+__host__ __device__ constexpr int eidx(int a, int b) { return (a + b) * (a + b + 1) / 2 + b; }
+
+template <int K>
+struct Dims {
+    static constexpr int n = (K + 1) * (K + 2) / 2;
+    static constexpr int f = K + 1;
+    static constexpr int FS = 2 + 2 * f * n;   // per-face stride in the class block
+};
+
+// d/dX of a polynomial in the scaled-monomial basis (exact, compile-time sparse).
+template <int K>
+__device__ __forceinline__ void ddx(const double* u, double* out) {
+#pragma unroll
+    for (int i = 0; i < Dims<K>::n; ++i) {
+        const int a = ea(i), b = eb(i);
+        if (a + 1 + b <= K) {
+            const int s = eidx(a + 1, b);
+            out[i] = (a == 0) ? u[s] : double(a + 1) * u[s];
+        } else {
+            out[i] = 0.0;
+        }
+    }
+}
+template <int K>
+__device__ __forceinline__ void ddy(const double* u, double* out) {
+#pragma unroll
+    for (int i = 0; i < Dims<K>::n; ++i) {
+        const int a = ea(i), b = eb(i);
+        if (a + b + 1 <= K) {
+            const int s = eidx(a, b + 1);
+            out[i] = (b == 0) ? u[s] : double(b + 1) * u[s];
+        } else {
+            out[i] = 0.0;
+        }
+    }
+}
+// out += d/dX u  (or d/dY u)
+template <int K>
+__device__ __forceinline__ void add_ddx(const double* u, double* out) {
+#pragma unroll
+    for (int i = 0; i < Dims<K>::n; ++i) {
+        const int a = ea(i), b = eb(i);
+        if (a + 1 + b <= K) {
+            const int s = eidx(a + 1, b);
+            out[i] = (a == 0) ? out[i] + u[s] : fma(double(a + 1), u[s], out[i]);
+        }
+    }
+}
+template <int K>
+__device__ __forceinline__ void add_ddy(const double* u, double* out) {
+#pragma unroll
+    for (int i = 0; i < Dims<K>::n; ++i) {
+        const int a = ea(i), b = eb(i);
+        if (a + b + 1 <= K) {
+            const int s = eidx(a, b + 1);
+            out[i] = (b == 0) ? out[i] + u[s] : fma(double(b + 1), u[s], out[i]);
+        }
+    }
+}
+
+// y[l] = sum_i Tr[l][i] x[i], skipping structural zeros of the class matrix.
+template <int K>
+__device__ __forceinline__ void trace_apply(const double* __restrict__ Tr, const double* x, double* y) {
+    constexpr int n = Dims<K>::n, f = Dims<K>::f;
+#pragma unroll
+    for (int l = 0; l < f; ++l) {
+        double acc = 0.0;
+#pragma unroll
+        for (int i = 0; i < n; ++i) {
+            const double t = __ldg(Tr + l * n + i);
+            if (t != 0.0) acc = fma(t, x[i], acc);
+        }
+        y[l] = acc;
+    }
+}
+// y[i] = sum_l L[i][l] j[l]
+template <int K>
+__device__ __forceinline__ void lift_apply(const double* __restrict__ L, const double* j, double* y) {
+    constexpr int n = Dims<K>::n, f = Dims<K>::f;
+#pragma unroll
+    for (int i = 0; i < n; ++i) {
+        double acc = 0.0;
+#pragma unroll
+        for (int l = 0; l < f; ++l) {
+            const double t = __ldg(L + i * f + l);
+            if (t != 0.0) acc = fma(t, j[l], acc);
+        }
+        y[i] = acc;
+    }
+}
+
+template <int NV>
+__device__ __forceinline__ void load_state(const double* __restrict__ src, int N, int q, int first, double* u) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) u[i] = src[(size_t)(first + i) * N + q];
+}
+
+// ERK targets: dst = src + coef * k.  Target 0 is kept in `k` (overwritten).
+template <int NV>
+__device__ __forceinline__ void write_targets(const StageArgs& A, int N, size_t dom_off, int q, double* k) {
+    for (int t = A.n_tgt - 1; t >= 1; --t) {
+        const Target T = A.tgt[t];
+        double* dst = T.dst + dom_off;
+        if (T.src) {
+            const double* src = T.src + dom_off;
+#pragma unroll
+            for (int i = 0; i < NV; ++i) dst[(size_t)i * N + q] = fma(T.coef, k[i], src[(size_t)i * N + q]);
+        } else {
+#pragma unroll
+            for (int i = 0; i < NV; ++i) dst[(size_t)i * N + q] = T.coef * k[i];
+        }
+    }
+    const Target T = A.tgt[0];
+    double* dst = T.dst + dom_off;
+    if (T.src) {
+        const double* src = T.src + dom_off;
+#pragma unroll
+        for (int i = 0; i < NV; ++i) {
+            k[i] = fma(T.coef, k[i], src[(size_t)i * N + q]);
+            dst[(size_t)i * N + q] = k[i];
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < NV; ++i) {
+            k[i] = T.coef * k[i];
+            dst[(size_t)i * N + q] = k[i];
+        }
+    }
+}
+
+template <int K, int MODE>
+__device__ __forceinline__ void fluid_cell(const StageArgs& A, int q) {
+    constexpr int n = Dims<K>::n, f = Dims<K>::f, FS = Dims<K>::FS;
+    const DevOps& op = A.op;
+    const int cls = __ldg(op.warp_class + (q >> 5));
+    const int* ci = op.cls_int + cls * CI_STRIDE;
+    const int start = __ldg(ci + CI_START);
+    const int lq = q - start;
+    if (lq >= __ldg(ci + CI_COUNT)) return;   // class padding
+    const int nF = __ldg(ci + CI_NF), npad = __ldg(ci + CI_NPAD), sbase = __ldg(ci + CI_SLOT);
+    const double* cd = op.cls_dbl + __ldg(ci + CI_DOFF) + n * n;
+    const int N = op.Nf, SF = op.SF, SS = op.SS;
+    const double tau = __ldg(op.scal_f + SF_TAU * N + q);
+    double U[3 * n];   // [m_x | m_y | p]
+    if constexpr (MODE == MODE_TRACES) {
+        load_state<3 * n>(A.inp, N, q, 0, U);
+    } else {
+        double* kmx = U;
+        double* kmy = U + n;
+        double* kp = U + 2 * n;
+        {
+            double u[n];
+            load_state<n>(A.inp, N, q, 2 * n, u);      // p
+            ddx<K>(u, kmx);
+            ddy<K>(u, kmy);
+            load_state<n>(A.inp, N, q, 0, u);          // m_x
+            ddx<K>(u, kp);
+            load_state<n>(A.inp, N, q, n, u);          // m_y
+            add_ddy<K>(u, kp);
+        }
+        const double* TRF = A.tr_in;
+        const double* TRS = A.tr_in + (size_t)2 * f * SF;
+#pragma unroll 1
+        for (int j = 0; j < nF; ++j) {
+            const double* fm = cd + j * FS;
+            const double nx = __ldg(fm), ny = __ldg(fm + 1);
+            const int slot = sbase + j * npad + lq;
+            const int nb = __ldg(op.nb_f + slot);
+            double jmp[f];
+#pragma unroll
+            for (int l = 0; l < f; ++l) jmp[l] = __ldg(TRF + (size_t)(f + l) * SF + slot);
+            if (nb >= 0) {
+                const double be = __ldg(op.beta_f + slot);
+#pragma unroll
+                for (int l = 0; l < f; ++l) {
+                    const double w = __ldg(TRF + (size_t)l * SF + nb);
+                    jmp[l] = (l & 1) ? fma(-be, w, jmp[l]) : fma(be, w, jmp[l]);
+                }
+            } else if (nb < NB_BOUNDARY) {
+                const int r = -2 - nb;
+                const int ns = __ldg(op.if_nb + r);
+                const double bx = __ldg(op.if_coef + 6 * r + 1), by = __ldg(op.if_coef + 6 * r + 2);
+#pragma unroll
+                for (int l = 0; l < f; ++l) {
+                    const double ws = fma(bx, __ldg(TRS + (size_t)l * SS + ns), by * __ldg(TRS + (size_t)(f + l) * SS + ns));
+                    jmp[l] = (l & 1) ? jmp[l] - ws : jmp[l] + ws;
+                }
+            }
+            double lv[n];
+            lift_apply<K>(fm + 2 + f * n, jmp, lv);
+            if (nx != 0.0) {
+#pragma unroll
+                for (int i = 0; i < n; ++i) kmx[i] = fma(nx, lv[i], kmx[i]);
+            }
+            if (ny != 0.0) {
+#pragma unroll
+                for (int i = 0; i < n; ++i) kmy[i] = fma(ny, lv[i], kmy[i]);
+            }
+#pragma unroll
+            for (int i = 0; i < n; ++i) kp[i] = fma(tau, lv[i], kp[i]);
+        }
+        const double Am = __ldg(op.scal_f + SF_AM * N + q), Ap = __ldg(op.scal_f + SF_AP * N + q);
+#pragma unroll
+        for (int i = 0; i < 2 * n; ++i) U[i] *= Am;
+#pragma unroll
+        for (int i = 0; i < n; ++i) kp[i] *= Ap;
+        for (int s = 0; s < A.n_src; ++s) {
+            if (A.src_dom[s] == 0 && A.src_q[s] == q) {
+                const double w = A.src_w[s];
+                const double* g = A.src_g + (size_t)s * 2 * n;
+#pragma unroll
+                for (int i = 0; i < n; ++i) kp[i] = fma(w, g[i], kp[i]);
+            }
+        }
+        write_targets<3 * n>(A, N, 0, q, U);
+        if constexpr (MODE == MODE_APPLY) return;
+    }
+    // Publish w and omega of U for the next stage.
+    double* TWF = A.tr_out;
+    const double* mx = U;
+    const double* my = U + n;
+    const double* p = U + 2 * n;
+#pragma unroll 1
+    for (int j = 0; j < nF; ++j) {
+        const double* fm = cd + j * FS;
+        const double nx = __ldg(fm), ny = __ldg(fm + 1);
+        const double* Tr = fm + 2;
+        double mn[n];
+#pragma unroll
+        for (int i = 0; i < n; ++i) mn[i] = 0.0;
+        if (nx != 0.0) {
+#pragma unroll
+            for (int i = 0; i < n; ++i) mn[i] = nx * mx[i];
+        }
+        if (ny != 0.0) {
+#pragma unroll
+            for (int i = 0; i < n; ++i) mn[i] = fma(ny, my[i], mn[i]);
+        }
+        double tp[f], tm[f];
+        trace_apply<K>(Tr, p, tp);
+        trace_apply<K>(Tr, mn, tm);
+        const int slot = sbase + j * npad + lq;
+        const int nb = __ldg(op.nb_f + slot);
+        const double al = (nb >= NB_BOUNDARY) ? __ldg(op.beta_f + slot) : __ldg(op.if_coef + 6 * (-2 - nb));
+#pragma unroll
+        for (int l = 0; l < f; ++l) {
+            const double w = fma(tau, tp[l], -tm[l]);
+            TWF[(size_t)l * SF + slot] = w;
+            TWF[(size_t)(f + l) * SF + slot] = fma(al, w, -tp[l]);
+        }
+    }
+}
+
+template <int K, int MODE>
+__device__ __forceinline__ void solid_cell(const StageArgs& A, int q) {
+    constexpr int n = Dims<K>::n, f = Dims<K>::f, FS = Dims<K>::FS;
+    const DevOps& op = A.op;
+    const int cls = __ldg(op.warp_class + op.n_warps_f + (q >> 5));
+    const int* ci = op.cls_int + cls * CI_STRIDE;
+    const int start = __ldg(ci + CI_START);
+    const int lq = q - start;
+    if (lq >= __ldg(ci + CI_COUNT)) return;
+    const int nF = __ldg(ci + CI_NF), npad = __ldg(ci + CI_NPAD), sbase = __ldg(ci + CI_SLOT);
+    const double* cd = op.cls_dbl + __ldg(ci + CI_DOFF) + n * n;
+    const int N = op.Ns, SF = op.SF, SS = op.SS;
+    const size_t dom_off = (size_t)3 * n * op.Nf;
+    const double* inp = A.inp + dom_off;
+    const double tau = __ldg(op.scal_s + SS_TAU * N + q);
+    double U[5 * n];   // [s_xx | s_yy | s_xy | v_x | v_y]
+    if constexpr (MODE == MODE_TRACES) {
+        load_state<5 * n>(inp, N, q, 0, U);
+    } else {
+        double* exx = U;
+        double* eyy = U + n;
+        double* exy = U + 2 * n;
+        double* kvx = U + 3 * n;
+        double* kvy = U + 4 * n;
+        {
+            double u[n];
+            load_state<n>(inp, N, q, 3 * n, u);    // v_x
+            ddx<K>(u, exx);
+            ddy<K>(u, exy);
+            load_state<n>(inp, N, q, 4 * n, u);    // v_y
+            ddy<K>(u, eyy);
+            add_ddx<K>(u, exy);
+            load_state<n>(inp, N, q, 0, u);        // s_xx
+            ddx<K>(u, kvx);
+            load_state<n>(inp, N, q, n, u);        // s_yy
+            ddy<K>(u, kvy);
+            load_state<n>(inp, N, q, 2 * n, u);    // s_xy
+            add_ddy<K>(u, kvx);
+            add_ddx<K>(u, kvy);
+        }
+        const double* TRF = A.tr_in;
+        const double* TRS = A.tr_in + (size_t)2 * f * SF;
+#pragma unroll 1
+        for (int j = 0; j < nF; ++j) {
+            const double* fm = cd + j * FS;
+            const double nx = __ldg(fm), ny = __ldg(fm + 1);
+            const int slot = sbase + j * npad + lq;
+            const int nb = __ldg(op.nb_s + slot);
+            double jx[f], jy[f];
+#pragma unroll
+            for (int l = 0; l < f; ++l) {
+                jx[l] = __ldg(TRS + (size_t)(2 * f + l) * SS + slot);
+                jy[l] = __ldg(TRS + (size_t)(3 * f + l) * SS + slot);
+            }
+            if (nb >= 0) {
+                const double be = __ldg(op.beta_s + slot);
+#pragma unroll
+                for (int l = 0; l < f; ++l) {
+                    const double wx = __ldg(TRS + (size_t)l * SS + nb);
+                    const double wy = __ldg(TRS + (size_t)(f + l) * SS + nb);
+                    jx[l] = (l & 1) ? fma(-be, wx, jx[l]) : fma(be, wx, jx[l]);
+                    jy[l] = (l & 1) ? fma(-be, wy, jy[l]) : fma(be, wy, jy[l]);
+                }
+            } else if (nb < NB_BOUNDARY) {
+                const int r = -2 - nb;
+                const int nfs = __ldg(op.if_nb + r);
+                const double b0 = __ldg(op.if_coef + 6 * r + 4), b1 = __ldg(op.if_coef + 6 * r + 5);
+#pragma unroll
+                for (int l = 0; l < f; ++l) {
+                    const double wf = __ldg(TRF + (size_t)l * SF + nfs);
+                    jx[l] = (l & 1) ? fma(-b0, wf, jx[l]) : fma(b0, wf, jx[l]);
+                    jy[l] = (l & 1) ? fma(-b1, wf, jy[l]) : fma(b1, wf, jy[l]);
+                }
+            }
+            const double* L = fm + 2 + f * n;
+            double lx[n], ly[n];
+            lift_apply<K>(L, jx, lx);
+            lift_apply<K>(L, jy, ly);
+            if (nx != 0.0) {
+#pragma unroll
+                for (int i = 0; i < n; ++i) {
+                    exx[i] = fma(nx, lx[i], exx[i]);
+                    exy[i] = fma(nx, ly[i], exy[i]);
+                }
+            }
+            if (ny != 0.0) {
+#pragma unroll
+                for (int i = 0; i < n; ++i) {
+                    eyy[i] = fma(ny, ly[i], eyy[i]);
+                    exy[i] = fma(ny, lx[i], exy[i]);
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < n; ++i) {
+                kvx[i] = fma(tau, lx[i], kvx[i]);
+                kvy[i] = fma(tau, ly[i], kvy[i]);
+            }
+        }
+        const double c1 = __ldg(op.scal_s + SS_C1 * N + q), c2 = __ldg(op.scal_s + SS_C2 * N + q);
+        const double c3 = __ldg(op.scal_s + SS_C3 * N + q), Av = __ldg(op.scal_s + SS_AV * N + q);
+#pragma unroll
+        for (int i = 0; i < n; ++i) {
+            const double a = exx[i], b = eyy[i];
+            exx[i] = fma(c1, a, c2 * b);
+            eyy[i] = fma(c2, a, c1 * b);
+            exy[i] *= c3;
+        }
+#pragma unroll
+        for (int i = 0; i < 2 * n; ++i) kvx[i] *= Av;   // kvx and kvy are contiguous
+        for (int s = 0; s < A.n_src; ++s) {
+            if (A.src_dom[s] == 1 && A.src_q[s] == q) {
+                const double w = A.src_w[s];
+                const double* g = A.src_g + (size_t)s * 2 * n;
+#pragma unroll
+                for (int i = 0; i < n; ++i) {
+                    kvx[i] = fma(w, g[i], kvx[i]);
+                    kvy[i] = fma(w, g[n + i], kvy[i]);
+                }
+            }
+        }
+        write_targets<5 * n>(A, N, dom_off, q, U);
+        if constexpr (MODE == MODE_APPLY) return;
+    }
+    double* TWS = A.tr_out + (size_t)2 * f * SF;
+    const double* sxx = U;
+    const double* syy = U + n;
+    const double* sxy = U + 2 * n;
+    const double* vx = U + 3 * n;
+    const double* vy = U + 4 * n;
+#pragma unroll 1
+    for (int j = 0; j < nF; ++j) {
+        const double* fm = cd + j * FS;
+        const double nx = __ldg(fm), ny = __ldg(fm + 1);
+        const double* Tr = fm + 2;
+        double snx[n], sny[n];
+#pragma unroll
+        for (int i = 0; i < n; ++i) {
+            snx[i] = 0.0;
+            sny[i] = 0.0;
+        }
+        if (nx != 0.0) {
+#pragma unroll
+            for (int i = 0; i < n; ++i) {
+                snx[i] = nx * sxx[i];
+                sny[i] = nx * sxy[i];
+            }
+        }
+        if (ny != 0.0) {
+#pragma unroll
+            for (int i = 0; i < n; ++i) {
+                snx[i] = fma(ny, sxy[i], snx[i]);
+                sny[i] = fma(ny, syy[i], sny[i]);
+            }
+        }
+        double tvx[f], tvy[f], tsx[f], tsy[f];
+        trace_apply<K>(Tr, vx, tvx);
+        trace_apply<K>(Tr, vy, tvy);
+        trace_apply<K>(Tr, snx, tsx);
+        trace_apply<K>(Tr, sny, tsy);
+        const int slot = sbase + j * npad + lq;
+        const int nb = __ldg(op.nb_s + slot);
+        double a00, a01, a10, a11;
+        if (nb >= NB_BOUNDARY) {
+            a00 = a11 = __ldg(op.beta_s + slot);
+            a01 = a10 = 0.0;
+        } else {
+            const double* co = op.if_coef + 6 * (-2 - nb);
+            a00 = __ldg(co);
+            a01 = __ldg(co + 1);
+            a10 = __ldg(co + 2);
+            a11 = __ldg(co + 3);
+        }
+#pragma unroll
+        for (int l = 0; l < f; ++l) {
+            const double wx = fma(tau, tvx[l], -tsx[l]);
+            const double wy = fma(tau, tvy[l], -tsy[l]);
+            TWS[(size_t)l * SS + slot] = wx;
+            TWS[(size_t)(f + l) * SS + slot] = wy;
+            TWS[(size_t)(2 * f + l) * SS + slot] = fma(a00, wx, fma(a01, wy, -tvx[l]));
+            TWS[(size_t)(3 * f + l) * SS + slot] = fma(a10, wx, fma(a11, wy, -tvy[l]));
+        }
+    }
+}
+
+template <int K, int MODE>
+__global__ void __launch_bounds__(128) stage_kernel(const StageArgs A) {
+    const int gq = blockIdx.x * blockDim.x + threadIdx.x;
+    if (gq < A.op.Nf)
+        fluid_cell<K, MODE>(A, gq);
+    else if (gq < A.op.Nf + A.op.Ns)
+        solid_cell<K, MODE>(A, gq - A.op.Nf);
+}
+
+// canonical (AoS, input cell order) <-> device layout (SoA by class)
+__global__ void pack_kernel(const int32_t* __restrict__ dev2orig, const int64_t* __restrict__ canon_off,
+                            int Nf, int Ns, int n, const double* __restrict__ canon, double* __restrict__ state,
+                            int unpack) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= Nf + Ns) return;
+    const bool fl = g < Nf;
+    const int q = fl ? g : g - Nf;
+    const int N = fl ? Nf : Ns;
+    const int nv = (fl ? 3 : 5) * n;
+    double* st = state + (fl ? 0 : (size_t)3 * n * Nf);
+    const int c = dev2orig[g];
+    if (c < 0) {
+        if (!unpack)
+            for (int i = 0; i < nv; ++i) st[(size_t)i * N + q] = 0.0;
+        return;
+    }
+    const int64_t o = canon_off[c];
+    if (!unpack) {
+        for (int i = 0; i < nv; ++i) st[(size_t)i * N + q] = canon[o + i];
+    } else {
+        double* cw = const_cast<double*>(canon);
+        for (int i = 0; i < nv; ++i) cw[o + i] = st[(size_t)i * N + q];
+    }
+}
+
+// Energy 1/2 U^T M U (Sec. 5.1) with M = h^2 (material) x M0_ref per cell.
+template <int K>
+__global__ void __launch_bounds__(256) energy_kernel(DevOps op, const double* __restrict__ state,
+                                                    const double* __restrict__ mass_f,
+                                                    const double* __restrict__ mass_s, double* partial) {
+    constexpr int n = Dims<K>::n;
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    double e = 0.0;
+    if (g < op.Nf + op.Ns) {
+        const bool fl = g < op.Nf;
+        const int q = fl ? g : g - op.Nf;
+        const int cls = op.warp_class[(fl ? 0 : op.n_warps_f) + (q >> 5)];
+        const int* ci = op.cls_int + cls * CI_STRIDE;
+        if (q - ci[CI_START] < ci[CI_COUNT]) {
+            const double* M0 = op.cls_dbl + ci[CI_DOFF];
+            const int N = fl ? op.Nf : op.Ns;
+            const double* st = state + (fl ? 0 : (size_t)3 * n * op.Nf);
+            auto quad = [&](int fa, int fb) {
+                double s = 0.0;
+                for (int i = 0; i < n; ++i) {
+                    double r = 0.0;
+                    for (int j = 0; j < n; ++j) r = fma(M0[i * n + j], st[(size_t)(fb * n + j) * N + q], r);
+                    s = fma(st[(size_t)(fa * n + i) * N + q], r, s);
+                }
+                return s;
+            };
+            if (fl) {
+                e = 0.5 * (mass_f[q] * (quad(0, 0) + quad(1, 1)) + mass_f[N + q] * quad(2, 2));
+            } else {
+                const double d0 = mass_s[q], d1 = mass_s[N + q], d2 = mass_s[2 * N + q], r = mass_s[3 * N + q];
+                e = 0.5 * (d0 * (quad(0, 0) + quad(1, 1)) + 2.0 * d1 * quad(0, 1) + d2 * quad(2, 2) +
+                           r * (quad(3, 3) + quad(4, 4)));
+            }
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) e += __shfl_down_sync(0xffffffffu, e, o);
+    __shared__ double ws[8];
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = e;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += ws[w];
+        partial[blockIdx.x] = s;
+    }
+}
+
+__global__ void sum_kernel(const double* __restrict__ partial, int np, double* out) {
+    __shared__ double sh[256];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < np; i += blockDim.x) s += partial[i];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[0] = sh[0];
+}
+
+// Receivers: fluid [p, m_x, m_y, 0, 0]; solid [v_x, v_y, s_xx, s_yy, s_xy];
+// interface [p_F, v_Fx, v_Fy, 0, 0] from the pointwise face solve.
+__global__ void record_kernel(DevOps op, int n_rec, const int32_t* __restrict__ ri, const double* __restrict__ rd,
+                              const double* __restrict__ state, double* out) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n_rec) return;
+    const int n = op.n;
+    const int stride = 2 * n + 15;
+    const double* d = rd + (size_t)r * stride;
+    const int kind = ri[4 * r], qf = ri[4 * r + 1], qs = ri[4 * r + 2];
+    const double* sf = state;
+    const double* ss = state + (size_t)3 * n * op.Nf;
+    auto ev = [&](const double* base, int N, int q, int field, const double* phi) {
+        double s = 0.0;
+        for (int i = 0; i < n; ++i) s = fma(phi[i], base[(size_t)(field * n + i) * N + q], s);
+        return s;
+    };
+    double o[5] = {0, 0, 0, 0, 0};
+    if (kind == 0) {
+        o[0] = ev(sf, op.Nf, qf, 2, d);
+        o[1] = ev(sf, op.Nf, qf, 0, d);
+        o[2] = ev(sf, op.Nf, qf, 1, d);
+    } else if (kind == 1) {
+        o[0] = ev(ss, op.Ns, qs, 3, d);
+        o[1] = ev(ss, op.Ns, qs, 4, d);
+        o[2] = ev(ss, op.Ns, qs, 0, d);
+        o[3] = ev(ss, op.Ns, qs, 1, d);
+        o[4] = ev(ss, op.Ns, qs, 2, d);
+    } else {
+        const double* pf = d;
+        const double* ps = d + n;
+        const double tf = d[2 * n], ts = d[2 * n + 1];
+        const double nfx = d[2 * n + 2], nfy = d[2 * n + 3], nsx = d[2 * n + 4], nsy = d[2 * n + 5];
+        const double* Ai = d + 2 * n + 6;
+        const double p = ev(sf, op.Nf, qf, 2, pf), mx = ev(sf, op.Nf, qf, 0, pf), my = ev(sf, op.Nf, qf, 1, pf);
+        const double sxx = ev(ss, op.Ns, qs, 0, ps), syy = ev(ss, op.Ns, qs, 1, ps), sxy = ev(ss, op.Ns, qs, 2, ps);
+        const double vx = ev(ss, op.Ns, qs, 3, ps), vy = ev(ss, op.Ns, qs, 4, ps);
+        const double wf = tf * p - (mx * nfx + my * nfy);
+        const double wsx = ts * vx - (sxx * nsx + sxy * nsy);
+        const double wsy = ts * vy - (sxy * nsx + syy * nsy);
+        o[0] = Ai[0] * wf + Ai[1] * wsx + Ai[2] * wsy;
+        o[1] = Ai[3] * wf + Ai[4] * wsx + Ai[5] * wsy;
+        o[2] = Ai[6] * wf + Ai[7] * wsx + Ai[8] * wsy;
+    }
+    for (int j = 0; j < 5; ++j) out[5 * r + j] = o[j];
+}
+
+template <int MODE>
+void launch_k(int k, const StageArgs& a, int grid, cudaStream_t s) {
+    if (k == 1) stage_kernel<1, MODE><<<grid, 128, 0, s>>>(a);
+    else if (k == 2) stage_kernel<2, MODE><<<grid, 128, 0, s>>>(a);
+    else stage_kernel<3, MODE><<<grid, 128, 0, s>>>(a);
+}
+
+// ---- ERK schedule ---------------------------------------------------------------
+// Row i of the extended tableau (a_{s+1,:} = b) is the partial sum
+// P_i = U^{n-1} + dt sum_j a_ij k_j.  Stage j computes k_j from P_j and
+// updates every later row with a nonzero a_ij; row j+1 becomes the next input.
+enum { SRC_ZERO = -3, SRC_STATE = -2, SRC_X = -1 };   // >= 0: row buffer index
+
+struct TargetPlan {
+    int src, dst;   // SRC_* / buffer index; dst SRC_STATE = d_state, SRC_X = stage buffer
+    double a;       // tableau coefficient (times dt at launch)
+};
+struct StagePlan {
+    int n_tgt;
+    TargetPlan t[MAX_TARGETS];
+};
+
+int build_plan(const hho_tableau* tab, std::vector<StagePlan>& plan, int* n_buf) {
+    const int s = tab->s;
+    if (s < 1 || s > 6) return HHO_EINVAL;
+    auto coef = [&](int i, int j) { return i == s ? tab->b[j] : tab->a[i][j]; };
+    std::vector<int> buf(s + 1, -1);      // row -> buffer index
+    std::vector<bool> touched(s + 1, false);
+    int nb = 0;
+    plan.assign(s, StagePlan{});
+    for (int j = 0; j < s; ++j) {
+        StagePlan& P = plan[j];
+        P.n_tgt = 0;
+        const int r0 = j + 1;
+        TargetPlan t0;
+        t0.src = touched[r0] ? buf[r0] : SRC_STATE;
+        t0.dst = (r0 == s) ? SRC_STATE : SRC_X;
+        t0.a = coef(r0, j);
+        P.t[P.n_tgt++] = t0;
+        for (int i = j + 2; i <= s; ++i) {
+            const double a = coef(i, j);
+            if (a == 0.0) continue;
+            if (P.n_tgt >= MAX_TARGETS) return HHO_EINVAL;
+            if (buf[i] < 0) buf[i] = nb++;
+            TargetPlan t;
+            t.src = touched[i] ? buf[i] : SRC_STATE;
+            t.dst = buf[i];
+            t.a = a;
+            touched[i] = true;
+            P.t[P.n_tgt++] = t;
+        }
+    }
+    *n_buf = nb;
+    return HHO_OK;
+}
+
+int64_t n_energy_blocks(const hho_ops* ops) { return ((int64_t)ops->dev.Nf + ops->dev.Ns + 255) / 256 + 1; }
+
+double ricker(double t, double f0, double t0, double amp) {
+    const double a = M_PI * f0 * (t - t0);
+    const double a2 = a * a;
+    return amp * (1.0 - 2.0 * a2) * std::exp(-a2);
+}
+
+int check_launch(const char* what) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        hho_set_error("%s: %s", what, cudaGetErrorString(e));
+        return HHO_ECUDA;
+    }
+    return HHO_OK;
+}
+
+void fill_sources(const hho_ops* ops, StageArgs& a, double t) {
+    a.n_src = ops->n_src;
+    a.src_g = ops->d_src_g;
+    for (int s = 0; s < ops->n_src; ++s) {
+        a.src_dom[s] = ops->src_dom[s];
+        a.src_q[s] = ops->src_q[s];
+        a.src_w[s] = ricker(t, ops->src_f0[s], ops->src_t0[s], ops->src_amp[s]);
+    }
+}
+
+}  // namespace
+
+extern "C" int hho_work_size(const hho_ops* ops, const hho_tableau* tab, int64_t* out) {
+    if (!ops || !tab || !out) {
+        hho_set_error("hho_work_size: null pointer");
+        return HHO_EINVAL;
+    }
+    std::vector<StagePlan> plan;
+    int nb = 0;
+    if (build_plan(tab, plan, &nb) != HHO_OK) {
+        hho_set_error("hho_work_size: unsupported tableau");
+        return HHO_EINVAL;
+    }
+    *out = ops->n_state * (1 + nb) + 2 * ops->trace_doubles + n_energy_blocks(ops) + 8;
+    return HHO_OK;
+}
+
+static int erk_run(hho_ops* ops, const hho_tableau* tab, double t0, double dt, int64_t nsteps, double* d_state,
+                   double* d_work, double* d_seis, void* stream, const char* who) {
+    if (!ops || !tab || !d_state || !d_work || nsteps < 0 || !std::isfinite(dt) || !std::isfinite(t0)) {
+        hho_set_error("%s: bad arguments", who);
+        return HHO_EINVAL;
+    }
+    std::vector<StagePlan> plan;
+    int nb = 0;
+    if (build_plan(tab, plan, &nb) != HHO_OK) {
+        hho_set_error("%s: unsupported tableau (s <= 6, at most %d partial sums per stage)", who, MAX_TARGETS);
+        return HHO_EINVAL;
+    }
+    if (nsteps == 0) return HHO_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t S = ops->n_state;
+    double* X = d_work;
+    double* bufs = d_work + S;
+    double* tr[2] = {d_work + S * (1 + nb), d_work + S * (1 + nb) + ops->trace_doubles};
+    const int grid = (ops->dev.Nf + ops->dev.Ns + 127) / 128;
+    if (grid == 0) return HHO_OK;
+    auto resolve = [&](int code) -> double* {
+        if (code == SRC_STATE) return d_state;
+        if (code == SRC_X) return X;
+        if (code == SRC_ZERO) return nullptr;
+        return bufs + S * code;
+    };
+    StageArgs a;
+    memset(&a, 0, sizeof(a));
+    a.op = ops->dev;
+    a.inp = d_state;
+    a.tr_out = tr[0];
+    a.n_tgt = 0;
+    launch_k<MODE_TRACES>(ops->k, a, grid, st);
+    int rc = check_launch(who);
+    if (rc) return rc;
+    int cur = 0;
+    for (int64_t step = 0; step < nsteps; ++step) {
+        const double tn = t0 + (double)step * dt;
+        for (int j = 0; j < tab->s; ++j) {
+            const StagePlan& P = plan[j];
+            a.inp = (j == 0) ? d_state : X;
+            a.tr_in = tr[cur];
+            a.tr_out = tr[cur ^ 1];
+            a.n_tgt = P.n_tgt;
+            for (int t = 0; t < P.n_tgt; ++t) {
+                a.tgt[t].src = resolve(P.t[t].src);
+                a.tgt[t].dst = resolve(P.t[t].dst);
+                a.tgt[t].coef = P.t[t].a * dt;
+            }
+            fill_sources(ops, a, tn + tab->c[j] * dt);
+            const bool prof = ops->prof_on && 2 * ops->prof_n + 1 < (int)ops->prof_events.size();
+            if (prof) cudaEventRecord((cudaEvent_t)ops->prof_events[2 * ops->prof_n], st);
+            launch_k<MODE_STAGE>(ops->k, a, grid, st);
+            if (prof) cudaEventRecord((cudaEvent_t)ops->prof_events[2 * ops->prof_n++ + 1], st);
+            rc = check_launch(who);
+            if (rc) return rc;
+            cur ^= 1;
+        }
+        if (d_seis && ops->n_rec > 0) {
+            record_kernel<<<(ops->n_rec + 63) / 64, 64, 0, st>>>(ops->dev, ops->n_rec, ops->d_rec_int, ops->d_rec_dbl,
+                                                                 d_state, d_seis + (size_t)step * 5 * ops->n_rec);
+            rc = check_launch(who);
+            if (rc) return rc;
+        }
+    }
+    return HHO_OK;
+}
+
+extern "C" int hho_erk_step(hho_ops* ops, const hho_tableau* tab, double t0, double dt, int64_t nsteps,
+                            double* d_state, double* d_work, void* stream) {
+    return erk_run(ops, tab, t0, dt, nsteps, d_state, d_work, nullptr, stream, "hho_erk_step");
+}
+
+extern "C" int hho_erk_step_record(hho_ops* ops, const hho_tableau* tab, double t0, double dt, int64_t nsteps,
+                                   double* d_state, double* d_work, double* d_seismogram, void* stream) {
+    if (ops && ops->n_rec > 0 && !d_seismogram) {
+        hho_set_error("hho_erk_step_record: null seismogram buffer");
+        return HHO_EINVAL;
+    }
+    return erk_run(ops, tab, t0, dt, nsteps, d_state, d_work, d_seismogram, stream, "hho_erk_step_record");
+}
+
+extern "C" int hho_profile_enable(hho_ops* ops, int32_t on) {
+    if (!ops) {
+        hho_set_error("hho_profile_enable: null ops");
+        return HHO_EINVAL;
+    }
+    if (on && ops->prof_events.empty()) {
+        for (int i = 0; i < 8192; ++i) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) {
+                hho_set_error("hho_profile_enable: cudaEventCreate failed");
+                return HHO_ECUDA;
+            }
+            ops->prof_events.push_back((void*)e);
+        }
+    }
+    ops->prof_on = on != 0;
+    ops->prof_n = 0;
+    return HHO_OK;
+}
+
+extern "C" int hho_profile_read(hho_ops* ops, double* ms, int64_t* n) {
+    if (!ops || !ms || !n) {
+        hho_set_error("hho_profile_read: null pointer");
+        return HHO_EINVAL;
+    }
+    double tot = 0.0;
+    for (int i = 0; i < ops->prof_n; ++i) {
+        float t = 0.0f;
+        if (cudaEventSynchronize((cudaEvent_t)ops->prof_events[2 * i + 1]) != cudaSuccess ||
+            cudaEventElapsedTime(&t, (cudaEvent_t)ops->prof_events[2 * i], (cudaEvent_t)ops->prof_events[2 * i + 1]) !=
+                cudaSuccess) {
+            hho_set_error("hho_profile_read: event query failed");
+            return HHO_ECUDA;
+        }
+        tot += t;
+    }
+    *ms = tot;
+    *n = ops->prof_n;
+    ops->prof_n = 0;
+    return HHO_OK;
+}
+
+// FP64 lane-ops of one stage thread, mirroring fluid_cell / solid_cell.
+static int64_t popc_nz(const double* v, int len) {
+    int64_t c = 0;
+    for (int i = 0; i < len; ++i) c += (v[i] != 0.0);
+    return c;
+}
+
+extern "C" int hho_stage_cost(const hho_ops* ops, const hho_tableau* tab, int64_t* fp64_ops, int64_t* bytes_min,
+                              int64_t* bytes_kernel) {
+    if (!ops || !tab) {
+        hho_set_error("hho_stage_cost: null pointer");
+        return HHO_EINVAL;
+    }
+    std::vector<StagePlan> plan;
+    int nbuf = 0;
+    if (build_plan(tab, plan, &nbuf) != HHO_OK) {
+        hho_set_error("hho_stage_cost: unsupported tableau");
+        return HHO_EINVAL;
+    }
+    const int K = ops->k, n = ops->n, f = ops->f, FS = 2 + 2 * f * n;
+    const int64_t dsm = (int64_t)K * (K - 1) / 2, dvalid = (int64_t)K * (K + 1) / 2;
+    int64_t ops_total = 0, bytes_k = 0, dofs = 0;
+    for (int cl = 0; cl < ops->n_classes; ++cl) {
+        const int32_t* ci = &ops->h_cls_int[cl * CI_STRIDE];
+        const int dom = ci[CI_DOMAIN], nF = ci[CI_NF], start = ci[CI_START], count = ci[CI_COUNT];
+        const int npad = ci[CI_NPAD], sbase = ci[CI_SLOT];
+        const double* cd = &ops->h_cls_dbl[ci[CI_DOFF] + n * n];
+        const int nv = (dom ? 5 : 3) * n, pc = dom ? 2 : 1;   // state values, primal components
+        dofs += (int64_t)count * nv;
+        for (int r = 0; r < count; ++r) {
+            int64_t per_cell_stage_base = 0, per_cell_traces = 0, bytes_faces = 0;
+            per_cell_stage_base += dom ? 5 * dsm + 3 * dvalid : 3 * dsm + dvalid;
+            for (int j = 0; j < nF; ++j) {
+                const double* fm = cd + j * FS;
+                const int nxz = fm[0] != 0.0, nyz = fm[1] != 0.0;
+                const int64_t nnzT = popc_nz(fm + 2, f * n), nnzL = popc_nz(fm + 2 + f * n, f * n);
+                const int32_t nb = (dom ? ops->h_nb_s : ops->h_nb_f)[sbase + j * npad + r];
+                const bool bnd = nb == NB_BOUNDARY, ifc = nb < NB_BOUNDARY;
+                // jump, lift, combinations
+                per_cell_stage_base += bnd ? 0 : (ifc && !dom ? 3 * f : pc * f);
+                per_cell_stage_base += pc * nnzL;
+                per_cell_stage_base += dom ? (int64_t)n * (2 * nxz + 2 * nyz + 2) : (int64_t)n * (nxz + nyz + 1);
+                // traces of the new stage value
+                per_cell_traces += dom ? (int64_t)2 * n * (nxz + nyz) + 4 * nnzT + 6 * f
+                                       : (int64_t)n * (nxz + nyz) + 2 * nnzT + 2 * f;
+                // trace bytes: own omega + neighbour w reads, w and omega writes, table entries
+                bytes_faces += 8 * (int64_t)pc * f * (1 + (bnd ? 0 : 1) + 2) + 4 + 8;
+            }
+            per_cell_stage_base += dom ? 7 * n : 3 * n;   // material scaling
+            for (int j = 0; j < tab->s; ++j) {
+                const StagePlan& P = plan[j];
+                ops_total += per_cell_stage_base + (int64_t)P.n_tgt * nv + per_cell_traces;
+                int64_t passes = 1;   // stage input
+                for (int t = 0; t < P.n_tgt; ++t) passes += 1 + (P.t[t].src != SRC_ZERO ? 1 : 0);
+                bytes_k += 8 * passes * nv + bytes_faces + 8 * (dom ? SCS : SCF);
+            }
+        }
+        (void)start;
+    }
+    int64_t passes_min = 0;
+    for (int j = 0; j < tab->s; ++j) {
+        const StagePlan& P = plan[j];
+        std::vector<int> reads, writes;
+        reads.push_back(j == 0 ? SRC_STATE : SRC_X);
+        for (int t = 0; t < P.n_tgt; ++t) {
+            if (P.t[t].src != SRC_ZERO) reads.push_back(P.t[t].src);
+            writes.push_back(P.t[t].dst);
+        }
+        std::sort(reads.begin(), reads.end());
+        reads.erase(std::unique(reads.begin(), reads.end()), reads.end());
+        passes_min += (int64_t)reads.size() + (int64_t)writes.size();
+    }
+    if (fp64_ops) *fp64_ops = ops_total;
+    if (bytes_min) *bytes_min = 8 * passes_min * dofs;
+    if (bytes_kernel) *bytes_kernel = bytes_k;
+    return HHO_OK;
+}
+
+extern "C" int hho_apply(hho_ops* ops, double t, const double* d_state, double* d_rate, double* d_work,
+                         void* stream) {
+    if (!ops || !d_state || !d_rate || !d_work) {
+        hho_set_error("hho_apply: null pointer");
+        return HHO_EINVAL;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const int grid = (ops->dev.Nf + ops->dev.Ns + 127) / 128;
+    if (grid == 0) return HHO_OK;
+    StageArgs a;
+    memset(&a, 0, sizeof(a));
+    a.op = ops->dev;
+    a.inp = d_state;
+    a.tr_out = d_work;
+    launch_k<MODE_TRACES>(ops->k, a, grid, st);
+    int rc = check_launch("hho_apply (trace kernel)");
+    if (rc) return rc;
+    a.tr_in = d_work;
+    a.tr_out = nullptr;
+    a.n_tgt = 1;
+    a.tgt[0].src = nullptr;
+    a.tgt[0].dst = d_rate;
+    a.tgt[0].coef = 1.0;
+    fill_sources(ops, a, t);
+    launch_k<MODE_APPLY>(ops->k, a, grid, st);
+    return check_launch("hho_apply (stage kernel)");
+}
+
+extern "C" int hho_state_pack(const hho_ops* ops, const double* d_canonical, double* d_state, void* stream) {
+    if (!ops || !d_canonical || !d_state) {
+        hho_set_error("hho_state_pack: null pointer");
+        return HHO_EINVAL;
+    }
+    const int tot = ops->dev.Nf + ops->dev.Ns;
+    if (tot == 0) return HHO_OK;
+    pack_kernel<<<(tot + 127) / 128, 128, 0, (cudaStream_t)stream>>>(ops->d_dev2orig, ops->d_canon_off, ops->dev.Nf,
+                                                                     ops->dev.Ns, ops->n, d_canonical, d_state, 0);
+    return check_launch("hho_state_pack");
+}
+
+extern "C" int hho_state_unpack(const hho_ops* ops, const double* d_state, double* d_canonical, void* stream) {
+    if (!ops || !d_canonical || !d_state) {
+        hho_set_error("hho_state_unpack: null pointer");
+        return HHO_EINVAL;
+    }
+    const int tot = ops->dev.Nf + ops->dev.Ns;
+    if (tot == 0) return HHO_OK;
+    pack_kernel<<<(tot + 127) / 128, 128, 0, (cudaStream_t)stream>>>(ops->d_dev2orig, ops->d_canon_off, ops->dev.Nf,
+                                                                     ops->dev.Ns, ops->n, d_canonical,
+                                                                     const_cast<double*>(d_state), 1);
+    return check_launch("hho_state_unpack");
+}
+
+extern "C" int hho_energy(hho_ops* ops, const double* d_state, double* d_work, double* h_energy, void* stream) {
+    if (!ops || !d_state || !d_work || !h_energy) {
+        hho_set_error("hho_energy: null pointer");
+        return HHO_EINVAL;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const int tot = ops->dev.Nf + ops->dev.Ns;
+    const int nblk = (tot + 255) / 256;
+    double* partial = d_work;
+    double* result = d_work + nblk;
+    if (nblk > 0) {
+        if (ops->k == 1) energy_kernel<1><<<nblk, 256, 0, st>>>(ops->dev, d_state, ops->d_mass_f, ops->d_mass_s, partial);
+        else if (ops->k == 2) energy_kernel<2><<<nblk, 256, 0, st>>>(ops->dev, d_state, ops->d_mass_f, ops->d_mass_s, partial);
+        else energy_kernel<3><<<nblk, 256, 0, st>>>(ops->dev, d_state, ops->d_mass_f, ops->d_mass_s, partial);
+    }
+    sum_kernel<<<1, 256, 0, st>>>(partial, nblk, result);
+    int rc = check_launch("hho_energy");
+    if (rc) return rc;
+    double e = 0.0;
+    if (cudaMemcpyAsync(&e, result, sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+        hho_set_error("hho_energy: copy failed");
+        return HHO_ECUDA;
+    }
+    *h_energy = e;
+    if (!std::isfinite(e)) {
+        hho_set_error("hho_energy: non-finite energy");
+        return HHO_EUNSTABLE;
+    }
+    return HHO_OK;
+}
+
+extern "C" int hho_record(hho_ops* ops, const double* d_state, double* d_out, void* stream) {
+    if (!ops || !d_state || (ops->n_rec > 0 && !d_out)) {
+        hho_set_error("hho_record: null pointer");
+        return HHO_EINVAL;
+    }
+    if (ops->n_rec == 0) return HHO_OK;
+    record_kernel<<<(ops->n_rec + 63) / 64, 64, 0, (cudaStream_t)stream>>>(ops->dev, ops->n_rec, ops->d_rec_int,
+                                                                          ops->d_rec_dbl, d_state, d_out);
+    return check_launch("hho_record");
+}
+
+extern "C" int hho_erk_run_host(hho_ops* ops, const hho_tableau* tab, double t0, double dt, int64_t nsteps,
+                                double* h_canonical, void* stream) {
+    if (!ops || !tab || !h_canonical) {
+        hho_set_error("hho_erk_run_host: null pointer");
+        return HHO_EINVAL;
+    }
+    int64_t wsz = 0;
+    int rc = hho_work_size(ops, tab, &wsz);
+    if (rc) return rc;
+    if (!ops->d_host_state) {
+        if (cudaMalloc((void**)&ops->d_host_state, sizeof(double) * ops->n_state) != cudaSuccess ||
+            cudaMalloc((void**)&ops->d_host_canon, sizeof(double) * ops->n_canonical) != cudaSuccess) {
+            hho_set_error("hho_erk_run_host: device allocation failed");
+            return HHO_ENOMEM;
+        }
+    }
+    if (ops->host_work_size < wsz) {
+        if (ops->d_host_work) cudaFree(ops->d_host_work);
+        ops->d_host_work = nullptr;
+        if (cudaMalloc((void**)&ops->d_host_work, sizeof(double) * wsz) != cudaSuccess) {
+            hho_set_error("hho_erk_run_host: device allocation failed");
+            return HHO_ENOMEM;
+        }
+        ops->host_work_size = wsz;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cudaMemcpyAsync(ops->d_host_canon, h_canonical, sizeof(double) * ops->n_canonical, cudaMemcpyHostToDevice,
+                        st) != cudaSuccess) {
+        hho_set_error("hho_erk_run_host: host-to-device copy failed");
+        return HHO_ECUDA;
+    }
+    rc = hho_state_pack(ops, ops->d_host_canon, ops->d_host_state, stream);
+    if (rc) return rc;
+    rc = hho_erk_step(ops, tab, t0, dt, nsteps, ops->d_host_state, ops->d_host_work, stream);
+    if (rc) return rc;
+    rc = hho_state_unpack(ops, ops->d_host_state, ops->d_host_canon, stream);
+    if (rc) return rc;
+    if (cudaMemcpyAsync(h_canonical, ops->d_host_canon, sizeof(double) * ops->n_canonical, cudaMemcpyDeviceToHost,
+                        st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+        hho_set_error("hho_erk_run_host: device-to-host copy failed");
+        return HHO_ECUDA;
+    }
+    return HHO_OK;
+}

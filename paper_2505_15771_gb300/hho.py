@@ -1,0 +1,267 @@
+"""Thin ctypes binding of libhho.so (declared in include/hho.h).
+
+Argument marshalling only: every step of the path runs in the library's
+kernels.  Functions keep the C names.  Device pointers are plain integers
+(e.g. ``tensor.data_ptr()`` of a CUDA tensor) and streams are
+``torch.cuda.Stream.cuda_stream`` integers (0 = legacy default stream).
+
+The library must have been built in-tree (``__graft_entry__.build()`` or
+``python paper_2505_15771_gb300/build.py``); loading fails loudly otherwise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhho.so")
+
+HHO_OK, HHO_EINVAL, HHO_EMESH, HHO_EMATERIAL, HHO_EDEGREE, HHO_ECFL, HHO_EUNSTABLE, HHO_ECUDA, HHO_ENOMEM = range(9)
+
+
+class HHOError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("hho error %d: %s" % (code, msg))
+        self.code = code
+
+
+class MeshInfo(C.Structure):
+    _fields_ = [("n_vertices", C.c_int64), ("n_cells", C.c_int64), ("n_faces", C.c_int64),
+                ("n_fluid_cells", C.c_int64), ("n_solid_cells", C.c_int64),
+                ("n_faces_by_type", C.c_int64 * 5), ("n_classes", C.c_int32), ("n_colours", C.c_int32),
+                ("max_faces_per_cell", C.c_int32), ("reserved", C.c_int32)]
+
+
+class Params(C.Structure):
+    _fields_ = [("eta_f", C.c_double), ("eta_s", C.c_double), ("stab_speed", C.c_int32), ("tau_over_k", C.c_int32)]
+
+
+class Layout(C.Structure):
+    _fields_ = [("n_state", C.c_int64), ("n_canonical", C.c_int64), ("n_fluid_pad", C.c_int64),
+                ("n_solid_pad", C.c_int64), ("n", C.c_int32), ("f", C.c_int32), ("n_classes", C.c_int32),
+                ("reserved", C.c_int32)]
+
+
+class Tableau(C.Structure):
+    _fields_ = [("s", C.c_int32), ("reserved", C.c_int32), ("a", (C.c_double * 6) * 6), ("b", C.c_double * 6),
+                ("c", C.c_double * 6)]
+
+
+_P = C.c_void_p
+_I32, _I64, _D = C.c_int32, C.c_int64, C.c_double
+_SIGS = {
+    "hho_last_error": (C.c_int, [C.c_char_p, C.c_size_t]),
+    "hho_mesh_create": (C.c_int, [_P, _I64, _P, _P, _I64, _P, _P, C.POINTER(_P)]),
+    "hho_mesh_query": (C.c_int, [_P, C.POINTER(MeshInfo)]),
+    "hho_mesh_tables": (C.c_int, [_P, _P, _P, _P, _P, _P, _P]),
+    "hho_mesh_destroy": (None, [_P]),
+    "hho_params_default": (None, [C.POINTER(Params)]),
+    "hho_operators_build": (C.c_int, [_P, _I32, _P, _P, _P, _P, C.POINTER(Params), C.POINTER(_P)]),
+    "hho_ops_destroy": (None, [_P]),
+    "hho_state_layout": (C.c_int, [_P, C.POINTER(Layout)]),
+    "hho_state_pack": (C.c_int, [_P, _P, _P, _P]),
+    "hho_state_unpack": (C.c_int, [_P, _P, _P, _P]),
+    "hho_tableau_erk": (C.c_int, [_I32, C.POINTER(Tableau)]),
+    "hho_work_size": (C.c_int, [_P, C.POINTER(Tableau), C.POINTER(_I64)]),
+    "hho_sources_set": (C.c_int, [_P, _I32, _P, _P, _P, _P, _P]),
+    "hho_erk_step": (C.c_int, [_P, C.POINTER(Tableau), _D, _D, _I64, _P, _P, _P]),
+    "hho_erk_run_host": (C.c_int, [_P, C.POINTER(Tableau), _D, _D, _I64, _P, _P]),
+    "hho_apply": (C.c_int, [_P, _D, _P, _P, _P, _P]),
+    "hho_receivers_set": (C.c_int, [_P, _I32, _P]),
+    "hho_record": (C.c_int, [_P, _P, _P, _P]),
+    "hho_energy": (C.c_int, [_P, _P, _P, C.POINTER(_D), _P]),
+    "hho_cfl_dt": (C.c_int, [_P, _D, _D, C.POINTER(_D)]),
+    "hho_erk_step_record": (C.c_int, [_P, C.POINTER(Tableau), _D, _D, _I64, _P, _P, _P, _P]),
+    "hho_stage_cost": (C.c_int, [_P, C.POINTER(Tableau), C.POINTER(_I64), C.POINTER(_I64), C.POINTER(_I64)]),
+    "hho_profile_enable": (C.c_int, [_P, _I32]),
+    "hho_profile_read": (C.c_int, [_P, C.POINTER(_D), C.POINTER(_I64)]),
+}
+EXPORTED = sorted(_SIGS)
+
+_lib = None
+
+
+def lib():
+    """Loads libhho.so once; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libhho.so is not built (%s); run __graft_entry__.build()" % LIB_PATH)
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def last_error() -> str:
+    buf = C.create_string_buffer(1024)
+    lib().hho_last_error(buf, 1024)
+    return buf.value.decode()
+
+
+def _check(rc):
+    if rc != HHO_OK:
+        raise HHOError(rc, last_error())
+
+
+def _ptr(a):
+    """Host numpy array -> void*; ints pass through (device pointers)."""
+    if a is None:
+        return None
+    if isinstance(a, int):
+        return a
+    return a.ctypes.data_as(_P)
+
+
+def _arr(x, dtype):
+    return np.ascontiguousarray(x, dtype=dtype)
+
+
+# ---- same-named entry points ------------------------------------------------------------
+
+def hho_mesh_create(xy, cell_ptr, cell_vtx, cell_domain, vertex_rep=None):
+    xy = _arr(xy, np.float64).reshape(-1, 2)
+    cp = _arr(cell_ptr, np.int64)
+    cv = _arr(cell_vtx, np.int64)
+    cd = _arr(cell_domain, np.uint8)
+    vr = None if vertex_rep is None else _arr(vertex_rep, np.int64)
+    out = _P()
+    _check(lib().hho_mesh_create(_ptr(xy), xy.shape[0], _ptr(cp), _ptr(cv), len(cp) - 1, _ptr(cd), _ptr(vr),
+                                 C.byref(out)))
+    return out
+
+
+def hho_mesh_query(mesh):
+    info = MeshInfo()
+    _check(lib().hho_mesh_query(mesh, C.byref(info)))
+    return info
+
+
+def hho_mesh_tables(mesh):
+    info = hho_mesh_query(mesh)
+    nc, nf = info.n_cells, info.n_faces
+    face_cells = np.empty((nf, 2), np.int64)
+    cfp = np.empty(nc + 1, np.int64)
+    lib().hho_mesh_tables(mesh, None, _ptr(cfp), None, None, None, None)
+    cf = np.empty(int(cfp[-1]), np.int64)
+    ft = np.empty(nf, np.int32)
+    col = np.empty(nf, np.int32)
+    cls = np.empty(nc, np.int32)
+    _check(lib().hho_mesh_tables(mesh, _ptr(face_cells), _ptr(cfp), _ptr(cf), _ptr(ft), _ptr(col), _ptr(cls)))
+    return {"face_cells": face_cells, "cell_faces_ptr": cfp, "cell_faces": cf, "face_type": ft,
+            "face_colour": col, "cell_class": cls}
+
+
+def hho_mesh_destroy(mesh):
+    lib().hho_mesh_destroy(mesh)
+
+
+def hho_params_default():
+    p = Params()
+    lib().hho_params_default(C.byref(p))
+    return p
+
+
+def hho_operators_build(mesh, k, rho, lam, mu, kappa, params=None):
+    arrs = [_arr(a, np.float64) for a in (rho, lam, mu, kappa)]
+    p = hho_params_default() if params is None else params
+    out = _P()
+    _check(lib().hho_operators_build(mesh, int(k), *[_ptr(a) for a in arrs], C.byref(p), C.byref(out)))
+    return out
+
+
+def hho_ops_destroy(ops):
+    lib().hho_ops_destroy(ops)
+
+
+def hho_state_layout(ops):
+    lay = Layout()
+    _check(lib().hho_state_layout(ops, C.byref(lay)))
+    return lay
+
+
+def hho_state_pack(ops, d_canonical, d_state, stream=0):
+    _check(lib().hho_state_pack(ops, d_canonical, d_state, stream))
+
+
+def hho_state_unpack(ops, d_state, d_canonical, stream=0):
+    _check(lib().hho_state_unpack(ops, d_state, d_canonical, stream))
+
+
+def hho_tableau_erk(s):
+    t = Tableau()
+    _check(lib().hho_tableau_erk(int(s), C.byref(t)))
+    return t
+
+
+def hho_work_size(ops, tab):
+    n = _I64()
+    _check(lib().hho_work_size(ops, C.byref(tab), C.byref(n)))
+    return n.value
+
+
+def hho_sources_set(ops, xy, direction, f0, t0, amp):
+    xy = _arr(xy, np.float64).reshape(-1, 2)
+    d = _arr(direction, np.float64).reshape(-1, 2)
+    a = [_arr(v, np.float64).reshape(-1) for v in (f0, t0, amp)]
+    _check(lib().hho_sources_set(ops, xy.shape[0], _ptr(xy), _ptr(d), *[_ptr(v) for v in a]))
+
+
+def hho_erk_step(ops, tab, t0, dt, nsteps, d_state, d_work, stream=0):
+    _check(lib().hho_erk_step(ops, C.byref(tab), float(t0), float(dt), int(nsteps), d_state, d_work, stream))
+
+
+def hho_erk_run_host(ops, tab, t0, dt, nsteps, h_canonical, stream=0):
+    """h_canonical: numpy float64 array (or a host pointer int), updated in place."""
+    _check(lib().hho_erk_run_host(ops, C.byref(tab), float(t0), float(dt), int(nsteps), _ptr(h_canonical), stream))
+
+
+def hho_apply(ops, t, d_state, d_rate, d_work, stream=0):
+    _check(lib().hho_apply(ops, float(t), d_state, d_rate, d_work, stream))
+
+
+def hho_receivers_set(ops, xy):
+    xy = _arr(xy, np.float64).reshape(-1, 2)
+    _check(lib().hho_receivers_set(ops, xy.shape[0], _ptr(xy)))
+
+
+def hho_record(ops, d_state, d_out, stream=0):
+    _check(lib().hho_record(ops, d_state, d_out, stream))
+
+
+def hho_energy(ops, d_state, d_work, stream=0):
+    e = _D()
+    _check(lib().hho_energy(ops, d_state, d_work, C.byref(e), stream))
+    return e.value
+
+
+def hho_cfl_dt(ops, cfl_star, safety=1.0):
+    dt = _D()
+    _check(lib().hho_cfl_dt(ops, float(cfl_star), float(safety), C.byref(dt)))
+    return dt.value
+
+
+def hho_erk_step_record(ops, tab, t0, dt, nsteps, d_state, d_work, d_seismogram, stream=0):
+    _check(lib().hho_erk_step_record(ops, C.byref(tab), float(t0), float(dt), int(nsteps), d_state, d_work,
+                                     d_seismogram, stream))
+
+
+def hho_stage_cost(ops, tab):
+    a, b, c = _I64(), _I64(), _I64()
+    _check(lib().hho_stage_cost(ops, C.byref(tab), C.byref(a), C.byref(b), C.byref(c)))
+    return a.value, b.value, c.value
+
+
+def hho_profile_enable(ops, on=True):
+    _check(lib().hho_profile_enable(ops, 1 if on else 0))
+
+
+def hho_profile_read(ops):
+    ms, n = _D(), _I64()
+    _check(lib().hho_profile_read(ops, C.byref(ms), C.byref(n)))
+    return ms.value, n.value

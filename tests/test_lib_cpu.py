@@ -1,0 +1,104 @@
+"""CPU checks of libhho: symbols, host-side mesh tables (bit-exact against the
+oracle's implementation of the same conventions), argument validation.
+No compute call needs a GPU here."""
+import re
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import erk as E
+from oracle import mesh as M
+from tests.libutil import ROOT, ensure_built
+
+
+@pytest.fixture(scope="module")
+def hho():
+    return ensure_built()
+
+
+def test_library_exports_every_header_symbol(hho):
+    src = open(ROOT + "/include/hho.h").read()
+    declared = sorted(set(re.findall(r"\b(hho_[a-z_0-9]+)\s*\(", src)))
+    assert declared, "no declarations found"
+    lib = hho.lib()
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert sorted(declared) == sorted(hho.EXPORTED)
+
+
+def _meshes():
+    a = synth.tri_grid(16, 16)
+    b = synth.quad_grid(12, 7, 0.0, 2.0, 0.0, 1.0, 0.5)
+    c = synth.hybrid_grid(10, 10, 0.0, 2.0, 0.0, 1.0, 0.7, 0.5)
+    d = synth.hanging_node_patch(6, 6, refine_rows=(2, 3))
+    e = synth.quad_grid(5, 12, 0.0, 0.5, -1.0, 1.0, y_interface=0.0, periodic_x=True)
+    f = synth.tri_grid(7, 9, 0.3, 1.7, -0.2, 0.9, y_interface=0.33)
+    return [("tri", a), ("quad", b), ("hybrid", c), ("hanging", d), ("periodic", e), ("tri_offset", f)]
+
+
+@pytest.mark.parametrize("name,md", _meshes())
+def test_tables_bit_exact_against_oracle(hho, name, md):
+    lm = hho.hho_mesh_create(md.xy, md.cell_ptr, md.cell_vtx, md.cell_domain, md.vertex_rep)
+    try:
+        t = hho.hho_mesh_tables(lm)
+        info = hho.hho_mesh_query(lm)
+    finally:
+        hho.hho_mesh_destroy(lm)
+    om = M.build_mesh(md.xy, md.cell_ptr, md.cell_vtx, md.cell_domain, md.vertex_rep)
+    o = M.tables(om)
+    for key in ("face_cells", "cell_faces_ptr", "cell_faces", "face_type", "face_colour", "cell_class"):
+        assert np.array_equal(np.asarray(t[key], dtype=np.int64), np.asarray(o[key], dtype=np.int64)), key
+    assert info.n_faces == om.n_faces and info.n_classes == om.cell_class.max() + 1
+    assert list(info.n_faces_by_type) == [int(np.sum(om.face_type == i)) for i in range(5)]
+
+
+def _expect(hho, code, fn, *args):
+    with pytest.raises(hho.HHOError) as ei:
+        fn(*args)
+    assert ei.value.code == code, str(ei.value)
+
+
+def test_mesh_errors(hho):
+    xy = np.array([[0, 0], [1, 0], [1, 1], [0, 1], [2, 0], [2, 1]], dtype=float)
+    # clockwise cell
+    _expect(hho, hho.HHO_EMESH, hho.hho_mesh_create, xy, [0, 4], [0, 3, 2, 1], [0])
+    # two vertices only
+    _expect(hho, hho.HHO_EMESH, hho.hho_mesh_create, xy, [0, 2], [0, 1], [0])
+    # vertex id out of range
+    _expect(hho, hho.HHO_EINVAL, hho.hho_mesh_create, xy, [0, 3], [0, 1, 9], [0])
+    # bad domain tag
+    _expect(hho, hho.HHO_EINVAL, hho.hho_mesh_create, xy, [0, 4], [0, 1, 2, 3], [2])
+    # an edge shared by three cells: (1,2) used by three triangles
+    xy2 = np.array([[1, 0], [1, 1], [0, 0.5], [2, 0.5], [2, 0.6]], dtype=float)
+    _expect(hho, hho.HHO_EMESH, hho.hho_mesh_create, xy2, [0, 3, 6, 9], [0, 1, 2, 1, 0, 3, 1, 0, 4], [0, 0, 0])
+
+
+def test_operator_argument_errors(hho):
+    md = synth.quad_grid(2, 2)
+    lm = hho.hho_mesh_create(md.xy, md.cell_ptr, md.cell_vtx, md.cell_domain)
+    rho, lam, mu, kap = synth.layered_media(md)
+    try:
+        _expect(hho, hho.HHO_EDEGREE, hho.hho_operators_build, lm, 0, rho, lam, mu, kap)
+        _expect(hho, hho.HHO_EDEGREE, hho.hho_operators_build, lm, 4, rho, lam, mu, kap)
+        bad = rho.copy(); bad[0] = -1.0
+        _expect(hho, hho.HHO_EMATERIAL, hho.hho_operators_build, lm, 1, bad, lam, mu, kap)
+        solid = np.where(md.cell_domain == 1)[0][0]
+        badmu = mu.copy(); badmu[solid] = 0.0
+        _expect(hho, hho.HHO_EMATERIAL, hho.hho_operators_build, lm, 1, rho, lam, badmu, kap)
+        fluid = np.where(md.cell_domain == 0)[0][0]
+        badk = kap.copy(); badk[fluid] = 0.0
+        _expect(hho, hho.HHO_EMATERIAL, hho.hho_operators_build, lm, 2, rho, lam, mu, badk)
+    finally:
+        hho.hho_mesh_destroy(lm)
+
+
+@pytest.mark.parametrize("s", [2, 3, 4])
+def test_tableaux_match_oracle(hho, s):
+    t = hho.hho_tableau_erk(s)
+    Aext, b, c = E.tableau("erk%d" % s)
+    for i in range(s):
+        for j in range(s):
+            assert t.a[i][j] == Aext[i, j]
+        assert t.b[i] == b[i] and t.c[i] == c[i]
+    _expect(hho, hho.HHO_EINVAL, hho.hho_tableau_erk, 5)
