@@ -262,6 +262,28 @@ int hho_stage_cost(const hho_ops* ops, const hho_tableau* tab, int64_t* fp64_ops
 int hho_profile_enable(hho_ops* ops, int32_t on);
 int hho_profile_read(hho_ops* ops, double* ms_stage_total, int64_t* n_launches);
 
+/* Energy without any allocation, for callers that must not allocate device
+ * memory: for example a check that runs between time steps inside a
+ * framework whose caching allocator already owns the device memory, or code
+ * with a fixed memory budget.  cudaFree also synchronises the whole device,
+ * which a per-step check must not do.  The paper has no counterpart to this
+ * entry point.
+ *
+ * Same result as hho_energy (E = 1/2 U^T M U) but written to d_energy (one
+ * device double, caller-owned) instead of host memory, stream-ordered and
+ * without synchronising.  Its scratch (one partial sum per 256 cells) lives
+ * in a fixed array inside the library, so it handles at most
+ * HHO_ENERGY_STATIC_MAX_CELLS padded cell slots (n_fluid_pad + n_solid_pad);
+ * larger meshes return HHO_EINVAL.  Every GPU that loads the library holds
+ * this array (512 KiB) until the process exits.
+ * The first call on each device looks up the array's device address (with
+ * that device current); make that first call before any stream capture.
+ * All calls share the array: calls that overlap on the GPU (different
+ * streams, or devices sharing nothing but the call order) race and must be
+ * serialised by the caller.  Nothing in the array needs to start at zero. */
+#define HHO_ENERGY_STATIC_MAX_CELLS (65536LL * 256LL)
+int hho_energy_static(hho_ops* ops, const double* d_state, double* d_energy, void* stream);
+
 /* CFL-limited step (Eq. CFL): dt = safety * cfl_star * h_min / c_max, with
  * h_min the shortest cell edge and c_max the largest wave speed. */
 int hho_cfl_dt(const hho_ops* ops, double cfl_star, double safety, double* dt_out);

@@ -31,6 +31,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "hho_internal.h"
@@ -1064,4 +1065,67 @@ extern "C" int hho_erk_run_host(hho_ops* ops, const hho_tableau* tab, double t0,
         return HHO_ECUDA;
     }
     return HHO_OK;
+}
+
+// ---- energy without allocation ------------------------------------------------------
+// Block partial sums of hho_energy_static live in this fixed array instead of
+// a caller buffer.  Host code must not take its address directly (the host
+// symbol is only a stand-in for the device variable); the device address is
+// looked up once per device with cudaGetSymbolAddress.
+namespace {
+constexpr int kEnergyStaticMaxBlocks = (int)(HHO_ENERGY_STATIC_MAX_CELLS / 256);
+static __device__ __align__(256) double g_energy_partials[kEnergyStaticMaxBlocks];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_energy_mu;
+double* g_energy_addr[kMaxDevices] = {nullptr};
+
+// Device address of g_energy_partials for the current device (set-up on the
+// first call per device, with that device current).
+int energy_scratch(double** out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+        hho_set_error("hho_energy_static: no usable current device");
+        return HHO_ECUDA;
+    }
+    std::lock_guard<std::mutex> lock(g_energy_mu);
+    if (!g_energy_addr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_energy_partials);
+        if (e != cudaSuccess || !p) {
+            hho_set_error("hho_energy_static: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+            return HHO_ECUDA;
+        }
+        g_energy_addr[dev] = (double*)p;
+    }
+    *out = g_energy_addr[dev];
+    return HHO_OK;
+}
+}  // namespace
+
+extern "C" int hho_energy_static(hho_ops* ops, const double* d_state, double* d_energy, void* stream) {
+    if (!ops || !d_state || !d_energy) {
+        hho_set_error("hho_energy_static: null pointer");
+        return HHO_EINVAL;
+    }
+    const int64_t tot = (int64_t)ops->dev.Nf + ops->dev.Ns;
+    if (tot > HHO_ENERGY_STATIC_MAX_CELLS) {
+        hho_set_error("hho_energy_static: %lld padded cell slots exceed the fixed scratch limit of %lld; use hho_energy",
+                      (long long)tot, (long long)HHO_ENERGY_STATIC_MAX_CELLS);
+        return HHO_EINVAL;
+    }
+    double* partial = nullptr;
+    int rc = energy_scratch(&partial);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int nblk = (int)((tot + 255) / 256);
+    // energy_kernel writes every partial[0..nblk) before sum_kernel reads it,
+    // so the array's previous contents never matter.
+    if (nblk > 0) {
+        if (ops->k == 1) energy_kernel<1><<<nblk, 256, 0, st>>>(ops->dev, d_state, ops->d_mass_f, ops->d_mass_s, partial);
+        else if (ops->k == 2) energy_kernel<2><<<nblk, 256, 0, st>>>(ops->dev, d_state, ops->d_mass_f, ops->d_mass_s, partial);
+        else energy_kernel<3><<<nblk, 256, 0, st>>>(ops->dev, d_state, ops->d_mass_f, ops->d_mass_s, partial);
+    }
+    sum_kernel<<<1, 256, 0, st>>>(partial, nblk, d_energy);
+    return check_launch("hho_energy_static");
 }

@@ -77,6 +77,7 @@ _SIGS = {
     "hho_stage_cost": (C.c_int, [_P, C.POINTER(Tableau), C.POINTER(_I64), C.POINTER(_I64), C.POINTER(_I64)]),
     "hho_profile_enable": (C.c_int, [_P, _I32]),
     "hho_profile_read": (C.c_int, [_P, C.POINTER(_D), C.POINTER(_I64)]),
+    "hho_energy_static": (C.c_int, [_P, _P, _P, _P]),
 }
 EXPORTED = sorted(_SIGS)
 
@@ -265,3 +266,8 @@ def hho_profile_read(ops):
     ms, n = _D(), _I64()
     _check(lib().hho_profile_read(ops, C.byref(ms), C.byref(n)))
     return ms.value, n.value
+
+
+def hho_energy_static(ops, d_state, d_energy, stream=0):
+    """Energy into the device double at d_energy; the library allocates nothing."""
+    _check(lib().hho_energy_static(ops, d_state, d_energy, stream))
