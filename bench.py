@@ -156,6 +156,24 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- GPU run
+def measured_traffic(k, cell_dofs):
+    """DRAM bytes per stage launch from the committed ncu summary, if it was
+    taken on the current stage kernel source (same sha256) and the same k;
+    scaled from the captured case by cell DOFs.  None otherwise."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "stage_kernel_traffic.json")
+    if not os.path.exists(path):
+        return None
+    rec = json.load(open(path))
+    src = open(os.path.join(ROOT, "paper_2505_15771_gb300", "csrc", "stage.cu"), "rb").read()
+    if rec.get("stage_cu_sha256") != hashlib.sha256(src).hexdigest():
+        return None
+    entry = rec.get("k%d" % k)
+    if not entry:
+        return None
+    return entry["dram_bytes_per_launch_per_cell_dof"] * cell_dofs
+
+
 def fp64_fma_rate():
     import ctypes
     lib = ctypes.CDLL(os.path.join(ROOT, "paper_2505_15771_gb300", "libhho_probe.so"))
@@ -254,7 +272,7 @@ def main():
         "peak": (peak_fma / 1e12) if peak_fma else None,
         "unit": "T FP64 lane-ops/s (FMA = 1)",
         "frac": (ops_per_launch / avg_launch_s / peak_fma) if peak_fma else None,
-        "traffic": None,
+        "traffic": measured_traffic(a.k, ndof),
         "kernel": "stage_kernel<%d,1>" % a.k,
         "avg_launch_ms": avg_launch_s * 1e3,
         "launches_timed": n_launch,

@@ -30,7 +30,12 @@ struct hho_mesh {
 };
 
 // Per-class integer record on the device (stride CI_STRIDE ints).
-enum { CI_DOMAIN = 0, CI_NF, CI_START, CI_COUNT, CI_NPAD, CI_SLOT, CI_DOFF, CI_PAD, CI_STRIDE };
+enum { CI_DOMAIN = 0, CI_NF, CI_START, CI_COUNT, CI_NPAD, CI_SLOT, CI_DOFF, CI_KIND, CI_STRIDE };
+
+// Class kinds: generic polygon (dense class matrices) or axis-aligned
+// rectangle with faces ordered bottom, right, top, left, whose trace and
+// lifting matrices have a sparsity pattern fixed by monomial parity.
+enum { KIND_GENERIC = 0, KIND_RECT = 1 };
 
 // Device-side description of one stage launch and the static operator data.
 struct DevOps {
@@ -52,9 +57,9 @@ struct DevOps {
 };
 
 // Fluid scalars: A_m = 1/(rho h), A_p = kappa/h, tau.  Solid: c1 = (lambda+2mu)/h,
-// c2 = lambda/h, c3 = mu/h, A_v = 1/(rho h), tau.
+// r = lambda/(lambda+2mu), c3 = mu/h, A_v = 1/(rho h), tau.
 enum { SF_AM = 0, SF_AP, SF_TAU, SCF };
-enum { SS_C1 = 0, SS_C2, SS_C3, SS_AV, SS_TAU, SCS };
+enum { SS_C1 = 0, SS_R, SS_C3, SS_AV, SS_TAU, SCS };
 
 // Face-side neighbour encoding: >= 0 same-domain neighbour slot, -1 boundary,
 // <= -2 interface record (-2 - r).
@@ -85,12 +90,6 @@ struct StageArgs {
 
 enum { MODE_TRACES = 0, MODE_STAGE = 1, MODE_APPLY = 2 };
 
-// Launchers (stage.cu).
-int launch_stage(int mode, const StageArgs& a, void* stream);
-int launch_pack(const hho_ops* ops, const double* canon, double* state, int unpack, void* stream);
-int launch_energy(const hho_ops* ops, const double* state, double* partial, double* result, void* stream);
-int launch_record(const hho_ops* ops, const double* state, double* out, void* stream);
-
 struct hho_ops {
     int32_t k = 0, n = 0, f = 0;
     int64_t nc = 0;
@@ -104,13 +103,11 @@ struct hho_ops {
     int64_t n_canonical = 0;
     int32_t* d_dev2orig = nullptr;             // [Nf + Ns]: original cell id or -1 (padding)
     int64_t* d_canon_off = nullptr;            // [nc]
-    std::vector<double> h_min_edge_per_cell;
     double c_max = 0.0, h_min = 0.0;
     // host-side per-cell data kept for sources/receivers
     std::vector<double> centroid, diam, rho, tau;
     std::vector<int32_t> cell_class_of;
     std::vector<std::vector<double>> class_M0inv;     // per class, n x n
-    std::vector<std::vector<double>> class_ref_xy;    // per class, scaled vertex coordinates
     std::vector<std::vector<double>> class_normals;   // per class, 2 per face
     std::vector<double> kappa, lam, mu;
     std::vector<double> poly_xy;                      // copy of vertex coordinates for location

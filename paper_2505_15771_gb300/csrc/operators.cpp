@@ -346,6 +346,35 @@ extern "C" int hho_operators_build(const hho_mesh* m, int32_t k, const double* r
         }
     }
 
+    // ---- class kinds: axis-aligned rectangles (faces bottom, right, top, left) ----
+    // The rectangle kernels skip, at compile time, the entries that vanish by
+    // parity: on a horizontal face a cell monomial X^a Y^b traces to a
+    // multiple of xi^a, so Tr[l][i] = 0 unless l <= a and l = a (mod 2);
+    // Lift[i][l] = 0 unless a_i = l (mod 2) (M0 couples only equal parities);
+    // vertical faces use b.  The pattern is checked against the computed
+    // matrices before a class is marked.
+    std::vector<int32_t> cls_kind(NCL, KIND_GENERIC);
+    for (int cl = 0; cl < NCL; ++cl) {
+        if (cls_nf[cl] != 4) continue;
+        const double want[4][2] = {{0.0, -1.0}, {1.0, 0.0}, {0.0, 1.0}, {-1.0, 0.0}};
+        const double* cd = &cls_dbl[cls_doff[cl] + n * n];
+        const int FS = 2 + 2 * f * n;
+        bool ok = true;
+        for (int j = 0; j < 4 && ok; ++j) {
+            const double* fm = cd + j * FS;
+            if (fm[0] != want[j][0] || fm[1] != want[j][1]) ok = false;
+            for (int l = 0; l < f && ok; ++l)
+                for (int i = 0; i < n && ok; ++i) {
+                    int e = (j % 2 == 0) ? EA[i] : EB[i];
+                    bool tr_nz = e >= l && ((e - l) % 2) == 0;
+                    bool li_nz = ((e + l) % 2) == 0;
+                    if (!tr_nz && fm[2 + l * n + i] != 0.0) ok = false;
+                    if (!li_nz && fm[2 + f * n + i * f + l] != 0.0) ok = false;
+                }
+        }
+        if (ok) cls_kind[cl] = KIND_RECT;
+    }
+
     // ---- device layout: cells sorted by (domain, class), classes padded to 32 ----
     std::vector<std::vector<int64_t>> members(NCL);
     for (int64_t c = 0; c < nc; ++c) members[m->cell_class[c]].push_back(c);
@@ -397,6 +426,7 @@ extern "C" int hho_operators_build(const hho_mesh* m, int32_t k, const double* r
         r[CI_NPAD] = cls_npad[cl];
         r[CI_SLOT] = cls_slot[cl];
         r[CI_DOFF] = cls_doff[cl];
+        r[CI_KIND] = cls_kind[cl];
     }
 
     // ---- per-cell scalars ----------------------------------------------------------
@@ -413,7 +443,7 @@ extern "C" int hho_operators_build(const hho_mesh* m, int32_t k, const double* r
             mass_f[1 * (size_t)Nf + q] = h * h / kappa[c];
         } else {
             scal_s[SS_C1 * (size_t)Ns + q] = (lam[c] + 2.0 * mu[c]) / h;
-            scal_s[SS_C2 * (size_t)Ns + q] = lam[c] / h;
+            scal_s[SS_R * (size_t)Ns + q] = lam[c] / (lam[c] + 2.0 * mu[c]);
             scal_s[SS_C3 * (size_t)Ns + q] = mu[c] / h;
             scal_s[SS_AV * (size_t)Ns + q] = 1.0 / (rho[c] * h);
             scal_s[SS_TAU * (size_t)Ns + q] = tau[c];

@@ -105,34 +105,63 @@ __device__ __forceinline__ void add_ddy(const double* u, double* out) {
     }
 }
 
-// y[l] = sum_i Tr[l][i] x[i], skipping structural zeros of the class matrix.
-template <int K>
+// ---- face policies ---------------------------------------------------------------
+// GenericFace: any polygon face; normals and class matrices read at run time,
+// every matrix entry used (no run-time tests on FP64 values).
+// RectFace<J>: face J of an axis-aligned rectangle (J = 0 bottom, 1 right,
+// 2 top, 3 left); normals and the parity sparsity of Tr and Lift are
+// compile-time constants, entries outside the pattern are never loaded.
+struct GenericFace {
+    static constexpr bool rect = false;
+    static constexpr int NX = 0, NY = 0;
+    __host__ __device__ static constexpr bool tr_nz(int, int) { return true; }
+    __host__ __device__ static constexpr bool lift_nz(int, int) { return true; }
+};
+template <int J>
+struct RectFace {
+    static constexpr bool rect = true;
+    static constexpr int NX = (J == 1) ? 1 : (J == 3 ? -1 : 0);
+    static constexpr int NY = (J == 0) ? -1 : (J == 2 ? 1 : 0);
+    __host__ __device__ static constexpr int e(int i) { return (J % 2 == 0) ? ea(i) : eb(i); }
+    __host__ __device__ static constexpr bool tr_nz(int l, int i) { return e(i) >= l && ((e(i) - l) % 2) == 0; }
+    __host__ __device__ static constexpr bool lift_nz(int i, int l) { return ((e(i) + l) % 2) == 0; }
+};
+
+// y[l] = sum_i Tr[l][i] x[i] over the policy's pattern.
+template <int K, class P>
 __device__ __forceinline__ void trace_apply(const double* __restrict__ Tr, const double* x, double* y) {
     constexpr int n = Dims<K>::n, f = Dims<K>::f;
 #pragma unroll
     for (int l = 0; l < f; ++l) {
         double acc = 0.0;
 #pragma unroll
-        for (int i = 0; i < n; ++i) {
-            const double t = __ldg(Tr + l * n + i);
-            if (t != 0.0) acc = fma(t, x[i], acc);
-        }
+        for (int i = 0; i < n; ++i)
+            if (P::tr_nz(l, i)) acc = fma(__ldg(Tr + l * n + i), x[i], acc);
         y[l] = acc;
     }
 }
-// y[i] = sum_l L[i][l] j[l]
-template <int K>
+// y[i] = sum_l L[i][l] j[l] over the policy's pattern.
+template <int K, class P>
 __device__ __forceinline__ void lift_apply(const double* __restrict__ L, const double* j, double* y) {
     constexpr int n = Dims<K>::n, f = Dims<K>::f;
 #pragma unroll
     for (int i = 0; i < n; ++i) {
         double acc = 0.0;
 #pragma unroll
-        for (int l = 0; l < f; ++l) {
-            const double t = __ldg(L + i * f + l);
-            if (t != 0.0) acc = fma(t, j[l], acc);
-        }
+        for (int l = 0; l < f; ++l)
+            if (P::lift_nz(i, l)) acc = fma(__ldg(L + i * f + l), j[l], acc);
         y[i] = acc;
+    }
+}
+// y += s * x for a compile-time sign s in {-1, 0, 1}
+template <int S, int NN>
+__device__ __forceinline__ void axpy_sign(const double* x, double* y) {
+    if constexpr (S == 1) {
+#pragma unroll
+        for (int i = 0; i < NN; ++i) y[i] += x[i];
+    } else if constexpr (S == -1) {
+#pragma unroll
+        for (int i = 0; i < NN; ++i) y[i] -= x[i];
     }
 }
 
@@ -142,180 +171,373 @@ __device__ __forceinline__ void load_state(const double* __restrict__ src, int N
     for (int i = 0; i < NV; ++i) u[i] = src[(size_t)(first + i) * N + q];
 }
 
-// ERK targets: dst = src + coef * k.  Target 0 is kept in `k` (overwritten).
-template <int NV>
-__device__ __forceinline__ void write_targets(const StageArgs& A, int N, size_t dom_off, int q, double* k) {
+// ERK targets: dst = src + coef * scale_g * k, where g = GRP(i) picks the
+// per-cell material factor of value i (the inverse mass, folded into the
+// target coefficient).  Target 0 is kept in `k` (overwritten).
+template <int NV, class GRP>
+__device__ __forceinline__ void write_targets(const StageArgs& A, int N, size_t dom_off, int q, double* k,
+                                              const double* sc) {
     for (int t = A.n_tgt - 1; t >= 1; --t) {
         const Target T = A.tgt[t];
+        const double c[3] = {T.coef * sc[0], T.coef * sc[1], T.coef * sc[2]};
         double* dst = T.dst + dom_off;
         if (T.src) {
             const double* src = T.src + dom_off;
 #pragma unroll
-            for (int i = 0; i < NV; ++i) dst[(size_t)i * N + q] = fma(T.coef, k[i], src[(size_t)i * N + q]);
+            for (int i = 0; i < NV; ++i) dst[(size_t)i * N + q] = fma(c[GRP::g(i)], k[i], src[(size_t)i * N + q]);
         } else {
 #pragma unroll
-            for (int i = 0; i < NV; ++i) dst[(size_t)i * N + q] = T.coef * k[i];
+            for (int i = 0; i < NV; ++i) dst[(size_t)i * N + q] = c[GRP::g(i)] * k[i];
         }
     }
     const Target T = A.tgt[0];
+    const double c[3] = {T.coef * sc[0], T.coef * sc[1], T.coef * sc[2]};
     double* dst = T.dst + dom_off;
     if (T.src) {
         const double* src = T.src + dom_off;
 #pragma unroll
         for (int i = 0; i < NV; ++i) {
-            k[i] = fma(T.coef, k[i], src[(size_t)i * N + q]);
+            k[i] = fma(c[GRP::g(i)], k[i], src[(size_t)i * N + q]);
             dst[(size_t)i * N + q] = k[i];
         }
     } else {
 #pragma unroll
         for (int i = 0; i < NV; ++i) {
-            k[i] = T.coef * k[i];
+            k[i] = c[GRP::g(i)] * k[i];
             dst[(size_t)i * N + q] = k[i];
         }
+    }
+}
+template <int n>
+struct FluidGroups {   // [m_x, m_y | p]
+    __host__ __device__ static constexpr int g(int i) { return i < 2 * n ? 0 : 1; }
+};
+template <int n>
+struct SolidGroups {   // [s_xx, s_yy | s_xy | v_x, v_y]
+    __host__ __device__ static constexpr int g(int i) { return i < 2 * n ? 0 : (i < 3 * n ? 1 : 2); }
+};
+
+// ---- fluid cells -------------------------------------------------------------------
+struct FluidCtx {
+    int q, lq, nF, npad, sbase, N, SF, SS;
+    const double* cd;
+    double tau;
+};
+
+// Lift the face jump of one face into the raw rate accumulators
+// (kmx, kmy: grad p part; kp: div m part, tau folded).
+template <int K, class P>
+__device__ __forceinline__ void fluid_face_rate(const StageArgs& A, const FluidCtx& c, int j, double* kmx, double* kmy,
+                                                double* kp) {
+    constexpr int n = Dims<K>::n, f = Dims<K>::f, FS = Dims<K>::FS;
+    const DevOps& op = A.op;
+    const double* fm = c.cd + j * FS;
+    const double* TRF = A.tr_in;
+    const double* TRS = A.tr_in + (size_t)2 * f * c.SF;
+    const int slot = c.sbase + j * c.npad + c.lq;
+    const int nb = __ldg(op.nb_f + slot);
+    double jmp[f];
+#pragma unroll
+    for (int l = 0; l < f; ++l) jmp[l] = __ldg(TRF + (size_t)(f + l) * c.SF + slot);
+    if (nb >= 0) {
+        const double be = __ldg(op.beta_f + slot);
+#pragma unroll
+        for (int l = 0; l < f; ++l) {
+            const double w = __ldg(TRF + (size_t)l * c.SF + nb);
+            jmp[l] = (l & 1) ? fma(-be, w, jmp[l]) : fma(be, w, jmp[l]);
+        }
+    } else if (nb < NB_BOUNDARY) {
+        const int r = -2 - nb;
+        const int ns = __ldg(op.if_nb + r);
+        const double bx = __ldg(op.if_coef + 6 * r + 1), by = __ldg(op.if_coef + 6 * r + 2);
+#pragma unroll
+        for (int l = 0; l < f; ++l) {
+            const double ws = fma(bx, __ldg(TRS + (size_t)l * c.SS + ns), by * __ldg(TRS + (size_t)(f + l) * c.SS + ns));
+            jmp[l] = (l & 1) ? jmp[l] - ws : jmp[l] + ws;
+        }
+    }
+    double lv[n];
+    lift_apply<K, P>(fm + 2 + f * n, jmp, lv);
+    if constexpr (P::rect) {
+        axpy_sign<P::NX, n>(lv, kmx);
+        axpy_sign<P::NY, n>(lv, kmy);
+    } else {
+        const double nx = __ldg(fm), ny = __ldg(fm + 1);
+#pragma unroll
+        for (int i = 0; i < n; ++i) {
+            kmx[i] = fma(nx, lv[i], kmx[i]);
+            kmy[i] = fma(ny, lv[i], kmy[i]);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < n; ++i) kp[i] = fma(c.tau, lv[i], kp[i]);
+}
+
+// Publish w = tau p|_F - (m.n)|_F and omega = alpha w - p|_F for one face.
+template <int K, class P>
+__device__ __forceinline__ void fluid_face_trace(const StageArgs& A, const FluidCtx& c, int j, const double* U) {
+    constexpr int n = Dims<K>::n, f = Dims<K>::f, FS = Dims<K>::FS;
+    const DevOps& op = A.op;
+    const double* fm = c.cd + j * FS;
+    const double* Tr = fm + 2;
+    const double* mx = U;
+    const double* my = U + n;
+    const double* p = U + 2 * n;
+    double tp[f], tm[f];
+    trace_apply<K, P>(Tr, p, tp);
+    if constexpr (P::rect) {
+        if constexpr (P::NX != 0) trace_apply<K, P>(Tr, mx, tm);
+        else trace_apply<K, P>(Tr, my, tm);
+    } else {
+        const double nx = __ldg(fm), ny = __ldg(fm + 1);
+        double mn[n];
+#pragma unroll
+        for (int i = 0; i < n; ++i) mn[i] = fma(nx, mx[i], ny * my[i]);
+        trace_apply<K, P>(Tr, mn, tm);
+    }
+    constexpr double sgn = P::rect ? double(P::NX + P::NY) : 1.0;   // rect: tm holds the unsigned trace
+    const int slot = c.sbase + j * c.npad + c.lq;
+    const int nb = __ldg(op.nb_f + slot);
+    const double al = (nb >= NB_BOUNDARY) ? __ldg(op.beta_f + slot) : __ldg(op.if_coef + 6 * (-2 - nb));
+    double* TWF = A.tr_out;
+#pragma unroll
+    for (int l = 0; l < f; ++l) {
+        const double w = (sgn > 0.0) ? fma(c.tau, tp[l], -tm[l]) : fma(c.tau, tp[l], tm[l]);
+        TWF[(size_t)l * c.SF + slot] = w;
+        TWF[(size_t)(f + l) * c.SF + slot] = fma(al, w, -tp[l]);
     }
 }
 
 template <int K, int MODE>
 __device__ __forceinline__ void fluid_cell(const StageArgs& A, int q) {
-    constexpr int n = Dims<K>::n, f = Dims<K>::f, FS = Dims<K>::FS;
+    constexpr int n = Dims<K>::n;
     const DevOps& op = A.op;
     const int cls = __ldg(op.warp_class + (q >> 5));
     const int* ci = op.cls_int + cls * CI_STRIDE;
-    const int start = __ldg(ci + CI_START);
-    const int lq = q - start;
-    if (lq >= __ldg(ci + CI_COUNT)) return;   // class padding
-    const int nF = __ldg(ci + CI_NF), npad = __ldg(ci + CI_NPAD), sbase = __ldg(ci + CI_SLOT);
-    const double* cd = op.cls_dbl + __ldg(ci + CI_DOFF) + n * n;
-    const int N = op.Nf, SF = op.SF, SS = op.SS;
-    const double tau = __ldg(op.scal_f + SF_TAU * N + q);
+    FluidCtx c;
+    c.q = q;
+    c.lq = q - __ldg(ci + CI_START);
+    if (c.lq >= __ldg(ci + CI_COUNT)) return;   // class padding
+    c.nF = __ldg(ci + CI_NF);
+    c.npad = __ldg(ci + CI_NPAD);
+    c.sbase = __ldg(ci + CI_SLOT);
+    c.cd = op.cls_dbl + __ldg(ci + CI_DOFF) + n * n;
+    c.N = op.Nf;
+    c.SF = op.SF;
+    c.SS = op.SS;
+    c.tau = __ldg(op.scal_f + SF_TAU * c.N + q);
+    const bool rect = __ldg(ci + CI_KIND) == KIND_RECT;
     double U[3 * n];   // [m_x | m_y | p]
     if constexpr (MODE == MODE_TRACES) {
-        load_state<3 * n>(A.inp, N, q, 0, U);
+        load_state<3 * n>(A.inp, c.N, q, 0, U);
     } else {
         double* kmx = U;
         double* kmy = U + n;
         double* kp = U + 2 * n;
         {
             double u[n];
-            load_state<n>(A.inp, N, q, 2 * n, u);      // p
+            load_state<n>(A.inp, c.N, q, 2 * n, u);      // p
             ddx<K>(u, kmx);
             ddy<K>(u, kmy);
-            load_state<n>(A.inp, N, q, 0, u);          // m_x
+            load_state<n>(A.inp, c.N, q, 0, u);          // m_x
             ddx<K>(u, kp);
-            load_state<n>(A.inp, N, q, n, u);          // m_y
+            load_state<n>(A.inp, c.N, q, n, u);          // m_y
             add_ddy<K>(u, kp);
         }
-        const double* TRF = A.tr_in;
-        const double* TRS = A.tr_in + (size_t)2 * f * SF;
+        if (rect) {
+            fluid_face_rate<K, RectFace<0>>(A, c, 0, kmx, kmy, kp);
+            fluid_face_rate<K, RectFace<1>>(A, c, 1, kmx, kmy, kp);
+            fluid_face_rate<K, RectFace<2>>(A, c, 2, kmx, kmy, kp);
+            fluid_face_rate<K, RectFace<3>>(A, c, 3, kmx, kmy, kp);
+        } else {
 #pragma unroll 1
-        for (int j = 0; j < nF; ++j) {
-            const double* fm = cd + j * FS;
-            const double nx = __ldg(fm), ny = __ldg(fm + 1);
-            const int slot = sbase + j * npad + lq;
-            const int nb = __ldg(op.nb_f + slot);
-            double jmp[f];
-#pragma unroll
-            for (int l = 0; l < f; ++l) jmp[l] = __ldg(TRF + (size_t)(f + l) * SF + slot);
-            if (nb >= 0) {
-                const double be = __ldg(op.beta_f + slot);
-#pragma unroll
-                for (int l = 0; l < f; ++l) {
-                    const double w = __ldg(TRF + (size_t)l * SF + nb);
-                    jmp[l] = (l & 1) ? fma(-be, w, jmp[l]) : fma(be, w, jmp[l]);
-                }
-            } else if (nb < NB_BOUNDARY) {
-                const int r = -2 - nb;
-                const int ns = __ldg(op.if_nb + r);
-                const double bx = __ldg(op.if_coef + 6 * r + 1), by = __ldg(op.if_coef + 6 * r + 2);
-#pragma unroll
-                for (int l = 0; l < f; ++l) {
-                    const double ws = fma(bx, __ldg(TRS + (size_t)l * SS + ns), by * __ldg(TRS + (size_t)(f + l) * SS + ns));
-                    jmp[l] = (l & 1) ? jmp[l] - ws : jmp[l] + ws;
-                }
-            }
-            double lv[n];
-            lift_apply<K>(fm + 2 + f * n, jmp, lv);
-            if (nx != 0.0) {
-#pragma unroll
-                for (int i = 0; i < n; ++i) kmx[i] = fma(nx, lv[i], kmx[i]);
-            }
-            if (ny != 0.0) {
-#pragma unroll
-                for (int i = 0; i < n; ++i) kmy[i] = fma(ny, lv[i], kmy[i]);
-            }
-#pragma unroll
-            for (int i = 0; i < n; ++i) kp[i] = fma(tau, lv[i], kp[i]);
+            for (int j = 0; j < c.nF; ++j) fluid_face_rate<K, GenericFace>(A, c, j, kmx, kmy, kp);
         }
-        const double Am = __ldg(op.scal_f + SF_AM * N + q), Ap = __ldg(op.scal_f + SF_AP * N + q);
-#pragma unroll
-        for (int i = 0; i < 2 * n; ++i) U[i] *= Am;
-#pragma unroll
-        for (int i = 0; i < n; ++i) kp[i] *= Ap;
         for (int s = 0; s < A.n_src; ++s) {
             if (A.src_dom[s] == 0 && A.src_q[s] == q) {
-                const double w = A.src_w[s];
+                // the source vector is stored already multiplied by kappa/h^2 M0^-1;
+                // divide by the A_p folded into the targets
+                const double w = A.src_w[s] / __ldg(op.scal_f + SF_AP * c.N + q);
                 const double* g = A.src_g + (size_t)s * 2 * n;
 #pragma unroll
                 for (int i = 0; i < n; ++i) kp[i] = fma(w, g[i], kp[i]);
             }
         }
-        write_targets<3 * n>(A, N, 0, q, U);
+        const double sc[3] = {__ldg(op.scal_f + SF_AM * c.N + q), __ldg(op.scal_f + SF_AP * c.N + q), 0.0};
+        write_targets<3 * n, FluidGroups<n>>(A, c.N, 0, q, U, sc);
         if constexpr (MODE == MODE_APPLY) return;
     }
-    // Publish w and omega of U for the next stage.
-    double* TWF = A.tr_out;
-    const double* mx = U;
-    const double* my = U + n;
-    const double* p = U + 2 * n;
+    if (rect) {
+        fluid_face_trace<K, RectFace<0>>(A, c, 0, U);
+        fluid_face_trace<K, RectFace<1>>(A, c, 1, U);
+        fluid_face_trace<K, RectFace<2>>(A, c, 2, U);
+        fluid_face_trace<K, RectFace<3>>(A, c, 3, U);
+    } else {
 #pragma unroll 1
-    for (int j = 0; j < nF; ++j) {
-        const double* fm = cd + j * FS;
-        const double nx = __ldg(fm), ny = __ldg(fm + 1);
-        const double* Tr = fm + 2;
-        double mn[n];
+        for (int j = 0; j < c.nF; ++j) fluid_face_trace<K, GenericFace>(A, c, j, U);
+    }
+}
+
+// ---- solid cells -------------------------------------------------------------------
+struct SolidCtx {
+    int q, lq, nF, npad, sbase, N, SF, SS;
+    const double* cd;
+    double tau;
+};
+
+// Lift one face's velocity jump into the raw accumulators: e (strain rate,
+// symmetric-gradient part) and kv (div s part, tau folded).
+template <int K, class P>
+__device__ __forceinline__ void solid_face_rate(const StageArgs& A, const SolidCtx& c, int j, double* exx, double* eyy,
+                                                double* exy, double* kvx, double* kvy) {
+    constexpr int n = Dims<K>::n, f = Dims<K>::f, FS = Dims<K>::FS;
+    const DevOps& op = A.op;
+    const double* fm = c.cd + j * FS;
+    const double* TRF = A.tr_in;
+    const double* TRS = A.tr_in + (size_t)2 * f * c.SF;
+    const int slot = c.sbase + j * c.npad + c.lq;
+    const int nb = __ldg(op.nb_s + slot);
+    double jx[f], jy[f];
 #pragma unroll
-        for (int i = 0; i < n; ++i) mn[i] = 0.0;
-        if (nx != 0.0) {
-#pragma unroll
-            for (int i = 0; i < n; ++i) mn[i] = nx * mx[i];
-        }
-        if (ny != 0.0) {
-#pragma unroll
-            for (int i = 0; i < n; ++i) mn[i] = fma(ny, my[i], mn[i]);
-        }
-        double tp[f], tm[f];
-        trace_apply<K>(Tr, p, tp);
-        trace_apply<K>(Tr, mn, tm);
-        const int slot = sbase + j * npad + lq;
-        const int nb = __ldg(op.nb_f + slot);
-        const double al = (nb >= NB_BOUNDARY) ? __ldg(op.beta_f + slot) : __ldg(op.if_coef + 6 * (-2 - nb));
+    for (int l = 0; l < f; ++l) {
+        jx[l] = __ldg(TRS + (size_t)(2 * f + l) * c.SS + slot);
+        jy[l] = __ldg(TRS + (size_t)(3 * f + l) * c.SS + slot);
+    }
+    if (nb >= 0) {
+        const double be = __ldg(op.beta_s + slot);
 #pragma unroll
         for (int l = 0; l < f; ++l) {
-            const double w = fma(tau, tp[l], -tm[l]);
-            TWF[(size_t)l * SF + slot] = w;
-            TWF[(size_t)(f + l) * SF + slot] = fma(al, w, -tp[l]);
+            const double wx = __ldg(TRS + (size_t)l * c.SS + nb);
+            const double wy = __ldg(TRS + (size_t)(f + l) * c.SS + nb);
+            jx[l] = (l & 1) ? fma(-be, wx, jx[l]) : fma(be, wx, jx[l]);
+            jy[l] = (l & 1) ? fma(-be, wy, jy[l]) : fma(be, wy, jy[l]);
+        }
+    } else if (nb < NB_BOUNDARY) {
+        const int r = -2 - nb;
+        const int nfs = __ldg(op.if_nb + r);
+        const double b0 = __ldg(op.if_coef + 6 * r + 4), b1 = __ldg(op.if_coef + 6 * r + 5);
+#pragma unroll
+        for (int l = 0; l < f; ++l) {
+            const double wf = __ldg(TRF + (size_t)l * c.SF + nfs);
+            jx[l] = (l & 1) ? fma(-b0, wf, jx[l]) : fma(b0, wf, jx[l]);
+            jy[l] = (l & 1) ? fma(-b1, wf, jy[l]) : fma(b1, wf, jy[l]);
+        }
+    }
+    const double* L = fm + 2 + f * n;
+    double lx[n], ly[n];
+    lift_apply<K, P>(L, jx, lx);
+    lift_apply<K, P>(L, jy, ly);
+    if constexpr (P::rect) {
+        axpy_sign<P::NX, n>(lx, exx);
+        axpy_sign<P::NX, n>(ly, exy);
+        axpy_sign<P::NY, n>(ly, eyy);
+        axpy_sign<P::NY, n>(lx, exy);
+    } else {
+        const double nx = __ldg(fm), ny = __ldg(fm + 1);
+#pragma unroll
+        for (int i = 0; i < n; ++i) {
+            exx[i] = fma(nx, lx[i], exx[i]);
+            eyy[i] = fma(ny, ly[i], eyy[i]);
+            exy[i] = fma(nx, ly[i], fma(ny, lx[i], exy[i]));
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < n; ++i) {
+        kvx[i] = fma(c.tau, lx[i], kvx[i]);
+        kvy[i] = fma(c.tau, ly[i], kvy[i]);
+    }
+}
+
+// Publish w = tau v|_F - (s n)|_F and omega = alpha w - v|_F for one face.
+template <int K, class P>
+__device__ __forceinline__ void solid_face_trace(const StageArgs& A, const SolidCtx& c, int j, const double* U) {
+    constexpr int n = Dims<K>::n, f = Dims<K>::f, FS = Dims<K>::FS;
+    const DevOps& op = A.op;
+    const double* fm = c.cd + j * FS;
+    const double* Tr = fm + 2;
+    const double* sxx = U;
+    const double* syy = U + n;
+    const double* sxy = U + 2 * n;
+    const double* vx = U + 3 * n;
+    const double* vy = U + 4 * n;
+    double tvx[f], tvy[f], tsx[f], tsy[f];
+    trace_apply<K, P>(Tr, vx, tvx);
+    trace_apply<K, P>(Tr, vy, tvy);
+    double sgn = 1.0;
+    if constexpr (P::rect) {
+        // s n = (nx s_xx + ny s_xy, nx s_xy + ny s_yy) with one of nx, ny = +-1
+        if constexpr (P::NX != 0) {
+            trace_apply<K, P>(Tr, sxx, tsx);
+            trace_apply<K, P>(Tr, sxy, tsy);
+        } else {
+            trace_apply<K, P>(Tr, sxy, tsx);
+            trace_apply<K, P>(Tr, syy, tsy);
+        }
+        sgn = double(P::NX + P::NY);
+    } else {
+        const double nx = __ldg(fm), ny = __ldg(fm + 1);
+        double snx[n], sny[n];
+#pragma unroll
+        for (int i = 0; i < n; ++i) {
+            snx[i] = fma(nx, sxx[i], ny * sxy[i]);
+            sny[i] = fma(nx, sxy[i], ny * syy[i]);
+        }
+        trace_apply<K, P>(Tr, snx, tsx);
+        trace_apply<K, P>(Tr, sny, tsy);
+    }
+    const int slot = c.sbase + j * c.npad + c.lq;
+    const int nb = __ldg(op.nb_s + slot);
+    double* TWS = A.tr_out + (size_t)2 * f * c.SF;
+    if (nb >= NB_BOUNDARY) {
+        const double be = __ldg(op.beta_s + slot);
+#pragma unroll
+        for (int l = 0; l < f; ++l) {
+            const double wx = (sgn > 0.0) ? fma(c.tau, tvx[l], -tsx[l]) : fma(c.tau, tvx[l], tsx[l]);
+            const double wy = (sgn > 0.0) ? fma(c.tau, tvy[l], -tsy[l]) : fma(c.tau, tvy[l], tsy[l]);
+            TWS[(size_t)l * c.SS + slot] = wx;
+            TWS[(size_t)(f + l) * c.SS + slot] = wy;
+            TWS[(size_t)(2 * f + l) * c.SS + slot] = fma(be, wx, -tvx[l]);
+            TWS[(size_t)(3 * f + l) * c.SS + slot] = fma(be, wy, -tvy[l]);
+        }
+    } else {
+        const double* co = op.if_coef + 6 * (-2 - nb);
+        const double a00 = __ldg(co), a01 = __ldg(co + 1), a10 = __ldg(co + 2), a11 = __ldg(co + 3);
+#pragma unroll
+        for (int l = 0; l < f; ++l) {
+            const double wx = (sgn > 0.0) ? fma(c.tau, tvx[l], -tsx[l]) : fma(c.tau, tvx[l], tsx[l]);
+            const double wy = (sgn > 0.0) ? fma(c.tau, tvy[l], -tsy[l]) : fma(c.tau, tvy[l], tsy[l]);
+            TWS[(size_t)l * c.SS + slot] = wx;
+            TWS[(size_t)(f + l) * c.SS + slot] = wy;
+            TWS[(size_t)(2 * f + l) * c.SS + slot] = fma(a00, wx, fma(a01, wy, -tvx[l]));
+            TWS[(size_t)(3 * f + l) * c.SS + slot] = fma(a10, wx, fma(a11, wy, -tvy[l]));
         }
     }
 }
 
 template <int K, int MODE>
 __device__ __forceinline__ void solid_cell(const StageArgs& A, int q) {
-    constexpr int n = Dims<K>::n, f = Dims<K>::f, FS = Dims<K>::FS;
+    constexpr int n = Dims<K>::n;
     const DevOps& op = A.op;
     const int cls = __ldg(op.warp_class + op.n_warps_f + (q >> 5));
     const int* ci = op.cls_int + cls * CI_STRIDE;
-    const int start = __ldg(ci + CI_START);
-    const int lq = q - start;
-    if (lq >= __ldg(ci + CI_COUNT)) return;
-    const int nF = __ldg(ci + CI_NF), npad = __ldg(ci + CI_NPAD), sbase = __ldg(ci + CI_SLOT);
-    const double* cd = op.cls_dbl + __ldg(ci + CI_DOFF) + n * n;
-    const int N = op.Ns, SF = op.SF, SS = op.SS;
+    SolidCtx c;
+    c.q = q;
+    c.lq = q - __ldg(ci + CI_START);
+    if (c.lq >= __ldg(ci + CI_COUNT)) return;
+    c.nF = __ldg(ci + CI_NF);
+    c.npad = __ldg(ci + CI_NPAD);
+    c.sbase = __ldg(ci + CI_SLOT);
+    c.cd = op.cls_dbl + __ldg(ci + CI_DOFF) + n * n;
+    c.N = op.Ns;
+    c.SF = op.SF;
+    c.SS = op.SS;
+    c.tau = __ldg(op.scal_s + SS_TAU * c.N + q);
+    const bool rect = __ldg(ci + CI_KIND) == KIND_RECT;
     const size_t dom_off = (size_t)3 * n * op.Nf;
     const double* inp = A.inp + dom_off;
-    const double tau = __ldg(op.scal_s + SS_TAU * N + q);
     double U[5 * n];   // [s_xx | s_yy | s_xy | v_x | v_y]
     if constexpr (MODE == MODE_TRACES) {
-        load_state<5 * n>(inp, N, q, 0, U);
+        load_state<5 * n>(inp, c.N, q, 0, U);
     } else {
         double* exx = U;
         double* eyy = U + n;
@@ -324,92 +546,41 @@ __device__ __forceinline__ void solid_cell(const StageArgs& A, int q) {
         double* kvy = U + 4 * n;
         {
             double u[n];
-            load_state<n>(inp, N, q, 3 * n, u);    // v_x
+            load_state<n>(inp, c.N, q, 3 * n, u);    // v_x
             ddx<K>(u, exx);
             ddy<K>(u, exy);
-            load_state<n>(inp, N, q, 4 * n, u);    // v_y
+            load_state<n>(inp, c.N, q, 4 * n, u);    // v_y
             ddy<K>(u, eyy);
             add_ddx<K>(u, exy);
-            load_state<n>(inp, N, q, 0, u);        // s_xx
+            load_state<n>(inp, c.N, q, 0, u);        // s_xx
             ddx<K>(u, kvx);
-            load_state<n>(inp, N, q, n, u);        // s_yy
+            load_state<n>(inp, c.N, q, n, u);        // s_yy
             ddy<K>(u, kvy);
-            load_state<n>(inp, N, q, 2 * n, u);    // s_xy
+            load_state<n>(inp, c.N, q, 2 * n, u);    // s_xy
             add_ddy<K>(u, kvx);
             add_ddx<K>(u, kvy);
         }
-        const double* TRF = A.tr_in;
-        const double* TRS = A.tr_in + (size_t)2 * f * SF;
+        if (rect) {
+            solid_face_rate<K, RectFace<0>>(A, c, 0, exx, eyy, exy, kvx, kvy);
+            solid_face_rate<K, RectFace<1>>(A, c, 1, exx, eyy, exy, kvx, kvy);
+            solid_face_rate<K, RectFace<2>>(A, c, 2, exx, eyy, exy, kvx, kvy);
+            solid_face_rate<K, RectFace<3>>(A, c, 3, exx, eyy, exy, kvx, kvy);
+        } else {
 #pragma unroll 1
-        for (int j = 0; j < nF; ++j) {
-            const double* fm = cd + j * FS;
-            const double nx = __ldg(fm), ny = __ldg(fm + 1);
-            const int slot = sbase + j * npad + lq;
-            const int nb = __ldg(op.nb_s + slot);
-            double jx[f], jy[f];
-#pragma unroll
-            for (int l = 0; l < f; ++l) {
-                jx[l] = __ldg(TRS + (size_t)(2 * f + l) * SS + slot);
-                jy[l] = __ldg(TRS + (size_t)(3 * f + l) * SS + slot);
-            }
-            if (nb >= 0) {
-                const double be = __ldg(op.beta_s + slot);
-#pragma unroll
-                for (int l = 0; l < f; ++l) {
-                    const double wx = __ldg(TRS + (size_t)l * SS + nb);
-                    const double wy = __ldg(TRS + (size_t)(f + l) * SS + nb);
-                    jx[l] = (l & 1) ? fma(-be, wx, jx[l]) : fma(be, wx, jx[l]);
-                    jy[l] = (l & 1) ? fma(-be, wy, jy[l]) : fma(be, wy, jy[l]);
-                }
-            } else if (nb < NB_BOUNDARY) {
-                const int r = -2 - nb;
-                const int nfs = __ldg(op.if_nb + r);
-                const double b0 = __ldg(op.if_coef + 6 * r + 4), b1 = __ldg(op.if_coef + 6 * r + 5);
-#pragma unroll
-                for (int l = 0; l < f; ++l) {
-                    const double wf = __ldg(TRF + (size_t)l * SF + nfs);
-                    jx[l] = (l & 1) ? fma(-b0, wf, jx[l]) : fma(b0, wf, jx[l]);
-                    jy[l] = (l & 1) ? fma(-b1, wf, jy[l]) : fma(b1, wf, jy[l]);
-                }
-            }
-            const double* L = fm + 2 + f * n;
-            double lx[n], ly[n];
-            lift_apply<K>(L, jx, lx);
-            lift_apply<K>(L, jy, ly);
-            if (nx != 0.0) {
-#pragma unroll
-                for (int i = 0; i < n; ++i) {
-                    exx[i] = fma(nx, lx[i], exx[i]);
-                    exy[i] = fma(nx, ly[i], exy[i]);
-                }
-            }
-            if (ny != 0.0) {
-#pragma unroll
-                for (int i = 0; i < n; ++i) {
-                    eyy[i] = fma(ny, ly[i], eyy[i]);
-                    exy[i] = fma(ny, lx[i], exy[i]);
-                }
-            }
-#pragma unroll
-            for (int i = 0; i < n; ++i) {
-                kvx[i] = fma(tau, lx[i], kvx[i]);
-                kvy[i] = fma(tau, ly[i], kvy[i]);
-            }
+            for (int j = 0; j < c.nF; ++j) solid_face_rate<K, GenericFace>(A, c, j, exx, eyy, exy, kvx, kvy);
         }
-        const double c1 = __ldg(op.scal_s + SS_C1 * N + q), c2 = __ldg(op.scal_s + SS_C2 * N + q);
-        const double c3 = __ldg(op.scal_s + SS_C3 * N + q), Av = __ldg(op.scal_s + SS_AV * N + q);
+        // stress rate = C e = c1 [(e_xx + r e_yy), (e_yy + r e_xx)], c3 e_xy; c1, c3 folded into targets
+        const double r = __ldg(op.scal_s + SS_R * c.N + q);
 #pragma unroll
         for (int i = 0; i < n; ++i) {
             const double a = exx[i], b = eyy[i];
-            exx[i] = fma(c1, a, c2 * b);
-            eyy[i] = fma(c2, a, c1 * b);
-            exy[i] *= c3;
+            exx[i] = fma(r, b, a);
+            eyy[i] = fma(r, a, b);
         }
-#pragma unroll
-        for (int i = 0; i < 2 * n; ++i) kvx[i] *= Av;   // kvx and kvy are contiguous
+        const double Av = __ldg(op.scal_s + SS_AV * c.N + q);
         for (int s = 0; s < A.n_src; ++s) {
             if (A.src_dom[s] == 1 && A.src_q[s] == q) {
-                const double w = A.src_w[s];
+                const double w = A.src_w[s] / Av;
                 const double* g = A.src_g + (size_t)s * 2 * n;
 #pragma unroll
                 for (int i = 0; i < n; ++i) {
@@ -418,67 +589,18 @@ __device__ __forceinline__ void solid_cell(const StageArgs& A, int q) {
                 }
             }
         }
-        write_targets<5 * n>(A, N, dom_off, q, U);
+        const double sc[3] = {__ldg(op.scal_s + SS_C1 * c.N + q), __ldg(op.scal_s + SS_C3 * c.N + q), Av};
+        write_targets<5 * n, SolidGroups<n>>(A, c.N, dom_off, q, U, sc);
         if constexpr (MODE == MODE_APPLY) return;
     }
-    double* TWS = A.tr_out + (size_t)2 * f * SF;
-    const double* sxx = U;
-    const double* syy = U + n;
-    const double* sxy = U + 2 * n;
-    const double* vx = U + 3 * n;
-    const double* vy = U + 4 * n;
+    if (rect) {
+        solid_face_trace<K, RectFace<0>>(A, c, 0, U);
+        solid_face_trace<K, RectFace<1>>(A, c, 1, U);
+        solid_face_trace<K, RectFace<2>>(A, c, 2, U);
+        solid_face_trace<K, RectFace<3>>(A, c, 3, U);
+    } else {
 #pragma unroll 1
-    for (int j = 0; j < nF; ++j) {
-        const double* fm = cd + j * FS;
-        const double nx = __ldg(fm), ny = __ldg(fm + 1);
-        const double* Tr = fm + 2;
-        double snx[n], sny[n];
-#pragma unroll
-        for (int i = 0; i < n; ++i) {
-            snx[i] = 0.0;
-            sny[i] = 0.0;
-        }
-        if (nx != 0.0) {
-#pragma unroll
-            for (int i = 0; i < n; ++i) {
-                snx[i] = nx * sxx[i];
-                sny[i] = nx * sxy[i];
-            }
-        }
-        if (ny != 0.0) {
-#pragma unroll
-            for (int i = 0; i < n; ++i) {
-                snx[i] = fma(ny, sxy[i], snx[i]);
-                sny[i] = fma(ny, syy[i], sny[i]);
-            }
-        }
-        double tvx[f], tvy[f], tsx[f], tsy[f];
-        trace_apply<K>(Tr, vx, tvx);
-        trace_apply<K>(Tr, vy, tvy);
-        trace_apply<K>(Tr, snx, tsx);
-        trace_apply<K>(Tr, sny, tsy);
-        const int slot = sbase + j * npad + lq;
-        const int nb = __ldg(op.nb_s + slot);
-        double a00, a01, a10, a11;
-        if (nb >= NB_BOUNDARY) {
-            a00 = a11 = __ldg(op.beta_s + slot);
-            a01 = a10 = 0.0;
-        } else {
-            const double* co = op.if_coef + 6 * (-2 - nb);
-            a00 = __ldg(co);
-            a01 = __ldg(co + 1);
-            a10 = __ldg(co + 2);
-            a11 = __ldg(co + 3);
-        }
-#pragma unroll
-        for (int l = 0; l < f; ++l) {
-            const double wx = fma(tau, tvx[l], -tsx[l]);
-            const double wy = fma(tau, tvy[l], -tsy[l]);
-            TWS[(size_t)l * SS + slot] = wx;
-            TWS[(size_t)(f + l) * SS + slot] = wy;
-            TWS[(size_t)(2 * f + l) * SS + slot] = fma(a00, wx, fma(a01, wy, -tvx[l]));
-            TWS[(size_t)(3 * f + l) * SS + slot] = fma(a10, wx, fma(a11, wy, -tvy[l]));
-        }
+        for (int j = 0; j < c.nF; ++j) solid_face_trace<K, GenericFace>(A, c, j, U);
     }
 }
 
@@ -848,12 +970,6 @@ extern "C" int hho_profile_read(hho_ops* ops, double* ms, int64_t* n) {
 }
 
 // FP64 lane-ops of one stage thread, mirroring fluid_cell / solid_cell.
-static int64_t popc_nz(const double* v, int len) {
-    int64_t c = 0;
-    for (int i = 0; i < len; ++i) c += (v[i] != 0.0);
-    return c;
-}
-
 extern "C" int hho_stage_cost(const hho_ops* ops, const hho_tableau* tab, int64_t* fp64_ops, int64_t* bytes_min,
                               int64_t* bytes_kernel) {
     if (!ops || !tab) {
@@ -866,45 +982,47 @@ extern "C" int hho_stage_cost(const hho_ops* ops, const hho_tableau* tab, int64_
         hho_set_error("hho_stage_cost: unsupported tableau");
         return HHO_EINVAL;
     }
-    const int K = ops->k, n = ops->n, f = ops->f, FS = 2 + 2 * f * n;
+    const int K = ops->k, n = ops->n, f = ops->f;
     const int64_t dsm = (int64_t)K * (K - 1) / 2, dvalid = (int64_t)K * (K + 1) / 2;
+    // entries of the rectangle parity patterns (the same count on every face)
+    int64_t rect_tr = 0, rect_lift = 0;
+    for (int i = 0; i < n; ++i) {
+        const int e = ea(i);
+        for (int l = 0; l < f; ++l) {
+            rect_tr += (e >= l && ((e - l) % 2) == 0);
+            rect_lift += (((e + l) % 2) == 0);
+        }
+    }
     int64_t ops_total = 0, bytes_k = 0, dofs = 0;
     for (int cl = 0; cl < ops->n_classes; ++cl) {
         const int32_t* ci = &ops->h_cls_int[cl * CI_STRIDE];
-        const int dom = ci[CI_DOMAIN], nF = ci[CI_NF], start = ci[CI_START], count = ci[CI_COUNT];
+        const int dom = ci[CI_DOMAIN], nF = ci[CI_NF], count = ci[CI_COUNT];
         const int npad = ci[CI_NPAD], sbase = ci[CI_SLOT];
-        const double* cd = &ops->h_cls_dbl[ci[CI_DOFF] + n * n];
+        const bool rect = ci[CI_KIND] == KIND_RECT;
         const int nv = (dom ? 5 : 3) * n, pc = dom ? 2 : 1;   // state values, primal components
+        const int64_t nnzT = rect ? rect_tr : (int64_t)f * n, nnzL = rect ? rect_lift : (int64_t)f * n;
         dofs += (int64_t)count * nv;
         for (int r = 0; r < count; ++r) {
-            int64_t per_cell_stage_base = 0, per_cell_traces = 0, bytes_faces = 0;
-            per_cell_stage_base += dom ? 5 * dsm + 3 * dvalid : 3 * dsm + dvalid;
+            int64_t rate = dom ? 5 * dsm + 3 * dvalid + 2 * n : 3 * dsm + dvalid;   // derivatives (+ stress mix)
+            int64_t traces = 0, bytes_faces = 0;
             for (int j = 0; j < nF; ++j) {
-                const double* fm = cd + j * FS;
-                const int nxz = fm[0] != 0.0, nyz = fm[1] != 0.0;
-                const int64_t nnzT = popc_nz(fm + 2, f * n), nnzL = popc_nz(fm + 2 + f * n, f * n);
                 const int32_t nb = (dom ? ops->h_nb_s : ops->h_nb_f)[sbase + j * npad + r];
                 const bool bnd = nb == NB_BOUNDARY, ifc = nb < NB_BOUNDARY;
-                // jump, lift, combinations
-                per_cell_stage_base += bnd ? 0 : (ifc && !dom ? 3 * f : pc * f);
-                per_cell_stage_base += pc * nnzL;
-                per_cell_stage_base += dom ? (int64_t)n * (2 * nxz + 2 * nyz + 2) : (int64_t)n * (nxz + nyz + 1);
-                // traces of the new stage value
-                per_cell_traces += dom ? (int64_t)2 * n * (nxz + nyz) + 4 * nnzT + 6 * f
-                                       : (int64_t)n * (nxz + nyz) + 2 * nnzT + 2 * f;
-                // trace bytes: own omega + neighbour w reads, w and omega writes, table entries
+                rate += bnd ? 0 : (ifc && !dom ? 3 * f : pc * f);                  // jump
+                rate += pc * nnzL;                                                  // lift
+                rate += dom ? (rect ? 4 * n : 6 * n) : (rect ? 2 * n : 3 * n);    // normal / tau combinations
+                traces += dom ? (rect ? 4 * nnzT : 4 * n + 4 * nnzT) + 2 * f + (ifc ? 4 * f : 2 * f)
+                              : (rect ? 2 * nnzT : 2 * n + 2 * nnzT) + 2 * f;
                 bytes_faces += 8 * (int64_t)pc * f * (1 + (bnd ? 0 : 1) + 2) + 4 + 8;
             }
-            per_cell_stage_base += dom ? 7 * n : 3 * n;   // material scaling
             for (int j = 0; j < tab->s; ++j) {
                 const StagePlan& P = plan[j];
-                ops_total += per_cell_stage_base + (int64_t)P.n_tgt * nv + per_cell_traces;
+                ops_total += rate + (int64_t)P.n_tgt * (nv + 3) + traces;
                 int64_t passes = 1;   // stage input
                 for (int t = 0; t < P.n_tgt; ++t) passes += 1 + (P.t[t].src != SRC_ZERO ? 1 : 0);
                 bytes_k += 8 * passes * nv + bytes_faces + 8 * (dom ? SCS : SCF);
             }
         }
-        (void)start;
     }
     int64_t passes_min = 0;
     for (int j = 0; j < tab->s; ++j) {
