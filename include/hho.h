@@ -220,6 +220,44 @@ int hho_apply(hho_ops* ops, double t, const double* d_state, double* d_rate, dou
               void* stream);
 
 /* ------------------------------------------------------------------------- */
+/* Batched shots: S independent states (right-hand sides, e.g. one point     */
+/* source each) on the same mesh, advanced by the same stage kernels with    */
+/* the shot index as the second grid dimension, in FP64 or FP32.  Each shot  */
+/* follows Eq. ERK_compact / Eq. ex_solve exactly as the single-shot path.   */
+/* ------------------------------------------------------------------------- */
+
+#define HHO_F64 0   /* state, traces and arithmetic in FP64 */
+#define HHO_F32 1   /* state, traces and arithmetic in FP32; operators built in FP64 and rounded */
+
+/* Element counts (of the precision's type) of a batched state
+ * (n_shots x n_state, shot-major) and of the work buffer hho_batch_erk_step
+ * needs for this tableau. */
+int hho_batch_sizes(const hho_ops* ops, const hho_tableau* tab, int32_t n_shots, int32_t precision,
+                    int64_t* state_elems, int64_t* work_elems);
+
+/* Canonical FP64 vectors [n_shots][n_canonical] (device) <-> batched device
+ * state of the given precision (rounded to FP32 for HHO_F32). */
+int hho_batch_pack(const hho_ops* ops, int32_t n_shots, int32_t precision, const double* d_canonical,
+                   void* d_state, void* stream);
+int hho_batch_unpack(const hho_ops* ops, int32_t n_shots, int32_t precision, const void* d_state,
+                     double* d_canonical, void* stream);
+
+/* One point source per shot: shot s has its source at h_xy[2s..2s+1] with
+ * direction h_dir[2s..2s+1] (solid cells; pressure source in fluid cells),
+ * all shots sharing the Ricker wavelet (f0, t0, amp) of hho_sources_set.
+ * Sources set with hho_sources_set still act on every shot.  n_shots = 0
+ * clears. */
+int hho_batch_sources_set(hho_ops* ops, int32_t n_shots, const double* h_xy, const double* h_dir, double f0,
+                          double t0, double amp);
+
+/* Advances n_shots batched states by nsteps ERK steps (one launch per stage
+ * for all shots).  d_seismogram (may be NULL): receiver traces
+ * [nsteps][n_shots][n_rec][5] in the state's precision, recorded after
+ * every step.  No allocation, no host synchronisation. */
+int hho_batch_erk_step(hho_ops* ops, const hho_tableau* tab, int32_t n_shots, int32_t precision, double t0,
+                       double dt, int64_t nsteps, void* d_state, void* d_work, void* d_seismogram, void* stream);
+
+/* ------------------------------------------------------------------------- */
 /* Sensors and energy (Sec. 5).                                               */
 /* ------------------------------------------------------------------------- */
 

@@ -54,6 +54,13 @@ struct DevOps {
     const double* beta_s;        // solid [SS]
     const int32_t* if_nb;        // interface records: neighbour slot in the other domain
     const double* if_coef;       // interface records: 6 coefficients each
+    // FP32 copies of the same data, for the FP32 batched path
+    const float* cls_f32;
+    const float* scal_f_f32;
+    const float* scal_s_f32;
+    const float* beta_f_f32;
+    const float* beta_s_f32;
+    const float* if_coef_f32;
 };
 
 // Fluid scalars: A_m = 1/(rho h), A_p = kappa/h, tau.  Solid: c1 = (lambda+2mu)/h,
@@ -68,24 +75,37 @@ constexpr int32_t NB_BOUNDARY = -1;
 constexpr int MAX_TARGETS = 4;
 constexpr int MAX_SOURCES = 8;
 
-struct Target {
-    const double* src;   // nullptr: zero
-    double* dst;
-    double coef;
+template <class T>
+struct TargetT {
+    const T* src;   // nullptr: zero
+    T* dst;
+    T coef;
 };
 
-struct StageArgs {
+// One stage launch.  Shots are blockIdx.y; every state, trace and target
+// pointer is the base of shot 0 and advances by state_stride / trace_stride
+// elements per shot.
+template <class T>
+struct StageArgsT {
     DevOps op;
-    const double* inp;       // device-layout state read by the stage
-    const double* tr_in;     // traces of inp: fluid [2f][SF] then solid [4f][SS]
-    double* tr_out;          // traces of the target-0 result (same layout)
-    Target tgt[MAX_TARGETS];
+    const T* inp;            // device-layout state read by the stage
+    const T* tr_in;          // traces of inp: fluid [2f][SF] then solid [4f][SS]
+    T* tr_out;               // traces of the target-0 result (same layout)
+    TargetT<T> tgt[MAX_TARGETS];
     int32_t n_tgt;
+    int32_t pad0;
+    int64_t state_stride, trace_stride;
+    // point sources applied to every shot
     int32_t n_src;
     int32_t src_dom[MAX_SOURCES];
     int32_t src_q[MAX_SOURCES];
-    double src_w[MAX_SOURCES];       // wavelet value at the stage time
-    const double* src_g;             // [n_src][2][n] lifted load vectors
+    T src_w[MAX_SOURCES];            // wavelet value at the stage time
+    const T* src_g;                  // [n_src][2][n] lifted load vectors
+    // one point source per shot (batched shots); shot_src_q == nullptr: none
+    const int32_t* shot_src_dom;
+    const int32_t* shot_src_q;
+    const T* shot_src_g;             // [shots][2][n]
+    T shot_src_w;
 };
 
 enum { MODE_TRACES = 0, MODE_STAGE = 1, MODE_APPLY = 2 };
@@ -115,6 +135,14 @@ struct hho_ops {
     std::vector<uint8_t> poly_dom;
     std::vector<int64_t> face_cells, cell_faces;
     std::vector<int32_t> face_type, face_local;
+    // per-shot sources of the batched path
+    int32_t n_shot_src = 0;
+    int32_t* d_shot_src_dom = nullptr;
+    int32_t* d_shot_src_q = nullptr;
+    double* d_shot_src_g = nullptr;
+    float* d_shot_src_g32 = nullptr;
+    double shot_f0 = 0.0, shot_t0 = 0.0, shot_amp = 0.0;
+    float* d_src_g32 = nullptr;
     // sources
     int32_t n_src = 0;
     int32_t src_dom[MAX_SOURCES], src_q[MAX_SOURCES];

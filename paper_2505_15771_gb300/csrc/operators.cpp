@@ -575,6 +575,13 @@ extern "C" int hho_operators_build(const hho_mesh* m, int32_t k, const double* r
     D.beta_s = dev_upload(ops, beta_s, &err);
     D.if_nb = dev_upload(ops, if_nb, &err);
     D.if_coef = dev_upload(ops, if_coef, &err);
+    auto to_f32 = [](const std::vector<double>& v) { return std::vector<float>(v.begin(), v.end()); };
+    D.cls_f32 = dev_upload(ops, to_f32(cls_dbl), &err);
+    D.scal_f_f32 = dev_upload(ops, to_f32(scal_f), &err);
+    D.scal_s_f32 = dev_upload(ops, to_f32(scal_s), &err);
+    D.beta_f_f32 = dev_upload(ops, to_f32(beta_f), &err);
+    D.beta_s_f32 = dev_upload(ops, to_f32(beta_s), &err);
+    D.if_coef_f32 = dev_upload(ops, to_f32(if_coef), &err);
     ops->d_dev2orig = dev_upload(ops, dev2orig, &err);
     ops->d_canon_off = dev_upload(ops, ops->canon_off, &err);
     ops->d_mass_f = dev_upload(ops, mass_f, &err);
@@ -598,6 +605,11 @@ extern "C" void hho_ops_destroy(hho_ops* ops) {
     if (!ops) return;
     for (void* p : ops->allocations) cudaFree(p);
     if (ops->d_src_g) cudaFree(ops->d_src_g);
+    if (ops->d_src_g32) cudaFree(ops->d_src_g32);
+    if (ops->d_shot_src_dom) cudaFree(ops->d_shot_src_dom);
+    if (ops->d_shot_src_q) cudaFree(ops->d_shot_src_q);
+    if (ops->d_shot_src_g) cudaFree(ops->d_shot_src_g);
+    if (ops->d_shot_src_g32) cudaFree(ops->d_shot_src_g32);
     if (ops->d_rec_int) cudaFree(ops->d_rec_int);
     if (ops->d_rec_dbl) cudaFree(ops->d_rec_dbl);
     if (ops->d_host_state) cudaFree(ops->d_host_state);
@@ -681,13 +693,20 @@ extern "C" int hho_sources_set(hho_ops* ops, int32_t n_src, const double* xy, co
         cudaFree(ops->d_src_g);
         ops->d_src_g = nullptr;
     }
+    if (ops->d_src_g32) {
+        cudaFree(ops->d_src_g32);
+        ops->d_src_g32 = nullptr;
+    }
     ops->n_src = 0;
     if (n_src > 0) {
-        if (cudaMalloc((void**)&ops->d_src_g, sizeof(double) * g.size()) != cudaSuccess) {
+        std::vector<float> g32(g.begin(), g.end());
+        if (cudaMalloc((void**)&ops->d_src_g, sizeof(double) * g.size()) != cudaSuccess ||
+            cudaMalloc((void**)&ops->d_src_g32, sizeof(float) * g.size()) != cudaSuccess) {
             hho_set_error("hho_sources_set: device allocation failed");
             return HHO_ENOMEM;
         }
-        if (cudaMemcpy(ops->d_src_g, g.data(), sizeof(double) * g.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+        if (cudaMemcpy(ops->d_src_g, g.data(), sizeof(double) * g.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(ops->d_src_g32, g32.data(), sizeof(float) * g.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
             hho_set_error("hho_sources_set: upload failed");
             return HHO_ECUDA;
         }
@@ -786,5 +805,69 @@ extern "C" int hho_cfl_dt(const hho_ops* ops, double cfl_star, double safety, do
         return HHO_EINVAL;
     }
     *dt_out = safety * cfl_star * ops->h_min / ops->c_max;
+    return HHO_OK;
+}
+
+extern "C" int hho_batch_sources_set(hho_ops* ops, int32_t n_shots, const double* xy, const double* dir, double f0,
+                                     double t0, double amp) {
+    if (!ops || n_shots < 0 || (n_shots > 0 && (!xy || !dir))) {
+        hho_set_error("hho_batch_sources_set: bad arguments");
+        return HHO_EINVAL;
+    }
+    const int n = ops->n;
+    std::vector<int32_t> dom(n_shots), q(n_shots);
+    std::vector<double> g((size_t)n_shots * 2 * n, 0.0);
+    std::vector<double> phi(n);
+    for (int s = 0; s < n_shots; ++s) {
+        int64_t c = locate(ops, xy[2 * s], xy[2 * s + 1]);
+        if (c < 0) {
+            hho_set_error("hho_batch_sources_set: shot %d source at (%g, %g) is outside the mesh", s, xy[2 * s],
+                          xy[2 * s + 1]);
+            return HHO_EINVAL;
+        }
+        cell_basis_at(ops, c, xy[2 * s], xy[2 * s + 1], phi.data());
+        const std::vector<double>& Mi = ops->class_M0inv[ops->cell_class_of[c]];
+        double h = ops->diam[c];
+        double scale = ops->poly_dom[c] == 0 ? ops->kappa[c] / (h * h) : 1.0 / (ops->rho[c] * h * h);
+        for (int i = 0; i < n; ++i) {
+            double v = 0.0;
+            for (int p = 0; p < n; ++p) v += Mi[i * n + p] * phi[p];
+            v *= scale;
+            if (ops->poly_dom[c] == 0) {
+                g[((size_t)s * 2 + 0) * n + i] = v;
+            } else {
+                g[((size_t)s * 2 + 0) * n + i] = dir[2 * s] * v;
+                g[((size_t)s * 2 + 1) * n + i] = dir[2 * s + 1] * v;
+            }
+        }
+        dom[s] = ops->cell_dom[c];
+        q[s] = ops->cell_pos[c];
+    }
+    for (void** p : {(void**)&ops->d_shot_src_dom, (void**)&ops->d_shot_src_q, (void**)&ops->d_shot_src_g,
+                     (void**)&ops->d_shot_src_g32}) {
+        if (*p) cudaFree(*p);
+        *p = nullptr;
+    }
+    ops->n_shot_src = 0;
+    if (n_shots == 0) return HHO_OK;
+    std::vector<float> g32(g.begin(), g.end());
+    if (cudaMalloc((void**)&ops->d_shot_src_dom, sizeof(int32_t) * n_shots) != cudaSuccess ||
+        cudaMalloc((void**)&ops->d_shot_src_q, sizeof(int32_t) * n_shots) != cudaSuccess ||
+        cudaMalloc((void**)&ops->d_shot_src_g, sizeof(double) * g.size()) != cudaSuccess ||
+        cudaMalloc((void**)&ops->d_shot_src_g32, sizeof(float) * g.size()) != cudaSuccess) {
+        hho_set_error("hho_batch_sources_set: device allocation failed");
+        return HHO_ENOMEM;
+    }
+    if (cudaMemcpy(ops->d_shot_src_dom, dom.data(), sizeof(int32_t) * n_shots, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(ops->d_shot_src_q, q.data(), sizeof(int32_t) * n_shots, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(ops->d_shot_src_g, g.data(), sizeof(double) * g.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(ops->d_shot_src_g32, g32.data(), sizeof(float) * g.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+        hho_set_error("hho_batch_sources_set: upload failed");
+        return HHO_ECUDA;
+    }
+    ops->n_shot_src = n_shots;
+    ops->shot_f0 = f0;
+    ops->shot_t0 = t0;
+    ops->shot_amp = amp;
     return HHO_OK;
 }

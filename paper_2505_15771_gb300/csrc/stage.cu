@@ -25,7 +25,8 @@
 // (Eq. ERK_compact with a_{s+1,j} = b_j); and publishes w, omega of the new
 // stage value for the next stage (double-buffered traces).
 //
-// All arithmetic is FP64.
+// Arithmetic is FP64 for the single-shot path; the batched path runs the same
+// kernels in FP64 or FP32 (shots on blockIdx.y).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -54,60 +55,82 @@ struct Dims {
     static constexpr int FS = 2 + 2 * f * n;   // per-face stride in the class block
 };
 
+// Operator data in the arithmetic type T (FP64, or its FP32 copy).
+template <class T>
+struct OpData;
+template <>
+struct OpData<double> {
+    __device__ static const double* cls(const DevOps& o) { return o.cls_dbl; }
+    __device__ static const double* scal_f(const DevOps& o) { return o.scal_f; }
+    __device__ static const double* scal_s(const DevOps& o) { return o.scal_s; }
+    __device__ static const double* beta_f(const DevOps& o) { return o.beta_f; }
+    __device__ static const double* beta_s(const DevOps& o) { return o.beta_s; }
+    __device__ static const double* if_coef(const DevOps& o) { return o.if_coef; }
+};
+template <>
+struct OpData<float> {
+    __device__ static const float* cls(const DevOps& o) { return o.cls_f32; }
+    __device__ static const float* scal_f(const DevOps& o) { return o.scal_f_f32; }
+    __device__ static const float* scal_s(const DevOps& o) { return o.scal_s_f32; }
+    __device__ static const float* beta_f(const DevOps& o) { return o.beta_f_f32; }
+    __device__ static const float* beta_s(const DevOps& o) { return o.beta_s_f32; }
+    __device__ static const float* if_coef(const DevOps& o) { return o.if_coef_f32; }
+};
+
 // d/dX of a polynomial in the scaled-monomial basis (exact, compile-time sparse).
-template <int K>
-__device__ __forceinline__ void ddx(const double* u, double* out) {
+template <class T, int K>
+__device__ __forceinline__ void ddx(const T* u, T* out) {
 #pragma unroll
     for (int i = 0; i < Dims<K>::n; ++i) {
         const int a = ea(i), b = eb(i);
         if (a + 1 + b <= K) {
             const int s = eidx(a + 1, b);
-            out[i] = (a == 0) ? u[s] : double(a + 1) * u[s];
+            out[i] = (a == 0) ? u[s] : T(a + 1) * u[s];
         } else {
-            out[i] = 0.0;
+            out[i] = T(0);
         }
     }
 }
-template <int K>
-__device__ __forceinline__ void ddy(const double* u, double* out) {
+template <class T, int K>
+__device__ __forceinline__ void ddy(const T* u, T* out) {
 #pragma unroll
     for (int i = 0; i < Dims<K>::n; ++i) {
         const int a = ea(i), b = eb(i);
         if (a + b + 1 <= K) {
             const int s = eidx(a, b + 1);
-            out[i] = (b == 0) ? u[s] : double(b + 1) * u[s];
+            out[i] = (b == 0) ? u[s] : T(b + 1) * u[s];
         } else {
-            out[i] = 0.0;
+            out[i] = T(0);
         }
     }
 }
 // out += d/dX u  (or d/dY u)
-template <int K>
-__device__ __forceinline__ void add_ddx(const double* u, double* out) {
+template <class T, int K>
+__device__ __forceinline__ void add_ddx(const T* u, T* out) {
 #pragma unroll
     for (int i = 0; i < Dims<K>::n; ++i) {
         const int a = ea(i), b = eb(i);
         if (a + 1 + b <= K) {
             const int s = eidx(a + 1, b);
-            out[i] = (a == 0) ? out[i] + u[s] : fma(double(a + 1), u[s], out[i]);
+            out[i] = (a == 0) ? out[i] + u[s] : fma(T(a + 1), u[s], out[i]);
         }
     }
 }
-template <int K>
-__device__ __forceinline__ void add_ddy(const double* u, double* out) {
+template <class T, int K>
+__device__ __forceinline__ void add_ddy(const T* u, T* out) {
 #pragma unroll
     for (int i = 0; i < Dims<K>::n; ++i) {
         const int a = ea(i), b = eb(i);
         if (a + b + 1 <= K) {
             const int s = eidx(a, b + 1);
-            out[i] = (b == 0) ? out[i] + u[s] : fma(double(b + 1), u[s], out[i]);
+            out[i] = (b == 0) ? out[i] + u[s] : fma(T(b + 1), u[s], out[i]);
         }
     }
 }
 
 // ---- face policies ---------------------------------------------------------------
 // GenericFace: any polygon face; normals and class matrices read at run time,
-// every matrix entry used (no run-time tests on FP64 values).
+// every matrix entry used (no run-time tests on floating-point values).
 // RectFace<J>: face J of an axis-aligned rectangle (J = 0 bottom, 1 right,
 // 2 top, 3 left); normals and the parity sparsity of Tr and Lift are
 // compile-time constants, entries outside the pattern are never loaded.
@@ -128,12 +151,12 @@ struct RectFace {
 };
 
 // y[l] = sum_i Tr[l][i] x[i] over the policy's pattern.
-template <int K, class P>
-__device__ __forceinline__ void trace_apply(const double* __restrict__ Tr, const double* x, double* y) {
+template <class T, int K, class P>
+__device__ __forceinline__ void trace_apply(const T* __restrict__ Tr, const T* x, T* y) {
     constexpr int n = Dims<K>::n, f = Dims<K>::f;
 #pragma unroll
     for (int l = 0; l < f; ++l) {
-        double acc = 0.0;
+        T acc = T(0);
 #pragma unroll
         for (int i = 0; i < n; ++i)
             if (P::tr_nz(l, i)) acc = fma(__ldg(Tr + l * n + i), x[i], acc);
@@ -141,12 +164,12 @@ __device__ __forceinline__ void trace_apply(const double* __restrict__ Tr, const
     }
 }
 // y[i] = sum_l L[i][l] j[l] over the policy's pattern.
-template <int K, class P>
-__device__ __forceinline__ void lift_apply(const double* __restrict__ L, const double* j, double* y) {
+template <class T, int K, class P>
+__device__ __forceinline__ void lift_apply(const T* __restrict__ L, const T* j, T* y) {
     constexpr int n = Dims<K>::n, f = Dims<K>::f;
 #pragma unroll
     for (int i = 0; i < n; ++i) {
-        double acc = 0.0;
+        T acc = T(0);
 #pragma unroll
         for (int l = 0; l < f; ++l)
             if (P::lift_nz(i, l)) acc = fma(__ldg(L + i * f + l), j[l], acc);
@@ -154,8 +177,8 @@ __device__ __forceinline__ void lift_apply(const double* __restrict__ L, const d
     }
 }
 // y += s * x for a compile-time sign s in {-1, 0, 1}
-template <int S, int NN>
-__device__ __forceinline__ void axpy_sign(const double* x, double* y) {
+template <int S, int NN, class T>
+__device__ __forceinline__ void axpy_sign(const T* x, T* y) {
     if constexpr (S == 1) {
 #pragma unroll
         for (int i = 0; i < NN; ++i) y[i] += x[i];
@@ -165,24 +188,24 @@ __device__ __forceinline__ void axpy_sign(const double* x, double* y) {
     }
 }
 
-template <int NV>
-__device__ __forceinline__ void load_state(const double* __restrict__ src, int N, int q, int first, double* u) {
+template <int NV, class T>
+__device__ __forceinline__ void load_state(const T* __restrict__ src, int N, int q, int first, T* u) {
 #pragma unroll
     for (int i = 0; i < NV; ++i) u[i] = src[(size_t)(first + i) * N + q];
 }
 
 // ERK targets: dst = src + coef * scale_g * k, where g = GRP(i) picks the
 // per-cell material factor of value i (the inverse mass, folded into the
-// target coefficient).  Target 0 is kept in `k` (overwritten).
-template <int NV, class GRP>
-__device__ __forceinline__ void write_targets(const StageArgs& A, int N, size_t dom_off, int q, double* k,
-                                              const double* sc) {
+// target coefficient).  Target 0 is kept in `k` (overwritten).  `off` is the
+// offset of this shot's domain block.
+template <int NV, class GRP, class T>
+__device__ __forceinline__ void write_targets(const StageArgsT<T>& A, int N, size_t off, int q, T* k, const T* sc) {
     for (int t = A.n_tgt - 1; t >= 1; --t) {
-        const Target T = A.tgt[t];
-        const double c[3] = {T.coef * sc[0], T.coef * sc[1], T.coef * sc[2]};
-        double* dst = T.dst + dom_off;
-        if (T.src) {
-            const double* src = T.src + dom_off;
+        const TargetT<T> G = A.tgt[t];
+        const T c[3] = {G.coef * sc[0], G.coef * sc[1], G.coef * sc[2]};
+        T* dst = G.dst + off;
+        if (G.src) {
+            const T* src = G.src + off;
 #pragma unroll
             for (int i = 0; i < NV; ++i) dst[(size_t)i * N + q] = fma(c[GRP::g(i)], k[i], src[(size_t)i * N + q]);
         } else {
@@ -190,11 +213,11 @@ __device__ __forceinline__ void write_targets(const StageArgs& A, int N, size_t 
             for (int i = 0; i < NV; ++i) dst[(size_t)i * N + q] = c[GRP::g(i)] * k[i];
         }
     }
-    const Target T = A.tgt[0];
-    const double c[3] = {T.coef * sc[0], T.coef * sc[1], T.coef * sc[2]};
-    double* dst = T.dst + dom_off;
-    if (T.src) {
-        const double* src = T.src + dom_off;
+    const TargetT<T> G = A.tgt[0];
+    const T c[3] = {G.coef * sc[0], G.coef * sc[1], G.coef * sc[2]};
+    T* dst = G.dst + off;
+    if (G.src) {
+        const T* src = G.src + off;
 #pragma unroll
         for (int i = 0; i < NV; ++i) {
             k[i] = fma(c[GRP::g(i)], k[i], src[(size_t)i * N + q]);
@@ -217,52 +240,57 @@ struct SolidGroups {   // [s_xx, s_yy | s_xy | v_x, v_y]
     __host__ __device__ static constexpr int g(int i) { return i < 2 * n ? 0 : (i < 3 * n ? 1 : 2); }
 };
 
-// ---- fluid cells -------------------------------------------------------------------
-struct FluidCtx {
+// Per-thread view of one (cell, shot): class layout and this shot's buffers.
+template <class T>
+struct CellCtx {
     int q, lq, nF, npad, sbase, N, SF, SS;
-    const double* cd;
-    double tau;
+    const T* cd;       // class face blocks
+    T tau;
+    const T* trf_in;   // this shot's trace buffers (fluid part, solid part)
+    const T* trs_in;
+    T* trf_out;
+    T* trs_out;
 };
 
+// ---- fluid cells -------------------------------------------------------------------
 // Lift the face jump of one face into the raw rate accumulators
 // (kmx, kmy: grad p part; kp: div m part, tau folded).
-template <int K, class P>
-__device__ __forceinline__ void fluid_face_rate(const StageArgs& A, const FluidCtx& c, int j, double* kmx, double* kmy,
-                                                double* kp) {
+template <class T, int K, class P>
+__device__ __forceinline__ void fluid_face_rate(const StageArgsT<T>& A, const CellCtx<T>& c, int j, T* kmx, T* kmy,
+                                                T* kp) {
     constexpr int n = Dims<K>::n, f = Dims<K>::f, FS = Dims<K>::FS;
     const DevOps& op = A.op;
-    const double* fm = c.cd + j * FS;
-    const double* TRF = A.tr_in;
-    const double* TRS = A.tr_in + (size_t)2 * f * c.SF;
+    const T* fm = c.cd + j * FS;
     const int slot = c.sbase + j * c.npad + c.lq;
     const int nb = __ldg(op.nb_f + slot);
-    double jmp[f];
+    T jmp[f];
 #pragma unroll
-    for (int l = 0; l < f; ++l) jmp[l] = __ldg(TRF + (size_t)(f + l) * c.SF + slot);
+    for (int l = 0; l < f; ++l) jmp[l] = __ldg(c.trf_in + (size_t)(f + l) * c.SF + slot);
     if (nb >= 0) {
-        const double be = __ldg(op.beta_f + slot);
+        const T be = __ldg(OpData<T>::beta_f(op) + slot);
 #pragma unroll
         for (int l = 0; l < f; ++l) {
-            const double w = __ldg(TRF + (size_t)l * c.SF + nb);
+            const T w = __ldg(c.trf_in + (size_t)l * c.SF + nb);
             jmp[l] = (l & 1) ? fma(-be, w, jmp[l]) : fma(be, w, jmp[l]);
         }
     } else if (nb < NB_BOUNDARY) {
         const int r = -2 - nb;
         const int ns = __ldg(op.if_nb + r);
-        const double bx = __ldg(op.if_coef + 6 * r + 1), by = __ldg(op.if_coef + 6 * r + 2);
+        const T* co = OpData<T>::if_coef(op) + 6 * r;
+        const T bx = __ldg(co + 1), by = __ldg(co + 2);
 #pragma unroll
         for (int l = 0; l < f; ++l) {
-            const double ws = fma(bx, __ldg(TRS + (size_t)l * c.SS + ns), by * __ldg(TRS + (size_t)(f + l) * c.SS + ns));
+            const T ws = fma(bx, __ldg(c.trs_in + (size_t)l * c.SS + ns), by * __ldg(c.trs_in + (size_t)(f + l) * c.SS + ns));
             jmp[l] = (l & 1) ? jmp[l] - ws : jmp[l] + ws;
         }
     }
-    double lv[n];
-    lift_apply<K, P>(fm + 2 + f * n, jmp, lv);
+    T lv[n];
+    lift_apply<T, K, P>(fm + 2 + f * n, jmp, lv);
     if constexpr (P::rect) {
         axpy_sign<P::NX, n>(lv, kmx);
         axpy_sign<P::NY, n>(lv, kmy);
     } else {
-        const double nx = __ldg(fm), ny = __ldg(fm + 1);
+        const T nx = __ldg(fm), ny = __ldg(fm + 1);
 #pragma unroll
         for (int i = 0; i < n; ++i) {
             kmx[i] = fma(nx, lv[i], kmx[i]);
@@ -274,166 +302,171 @@ __device__ __forceinline__ void fluid_face_rate(const StageArgs& A, const FluidC
 }
 
 // Publish w = tau p|_F - (m.n)|_F and omega = alpha w - p|_F for one face.
-template <int K, class P>
-__device__ __forceinline__ void fluid_face_trace(const StageArgs& A, const FluidCtx& c, int j, const double* U) {
+template <class T, int K, class P>
+__device__ __forceinline__ void fluid_face_trace(const StageArgsT<T>& A, const CellCtx<T>& c, int j, const T* U) {
     constexpr int n = Dims<K>::n, f = Dims<K>::f, FS = Dims<K>::FS;
     const DevOps& op = A.op;
-    const double* fm = c.cd + j * FS;
-    const double* Tr = fm + 2;
-    const double* mx = U;
-    const double* my = U + n;
-    const double* p = U + 2 * n;
-    double tp[f], tm[f];
-    trace_apply<K, P>(Tr, p, tp);
+    const T* fm = c.cd + j * FS;
+    const T* Tr = fm + 2;
+    const T* mx = U;
+    const T* my = U + n;
+    const T* p = U + 2 * n;
+    T tp[f], tm[f];
+    trace_apply<T, K, P>(Tr, p, tp);
     if constexpr (P::rect) {
-        if constexpr (P::NX != 0) trace_apply<K, P>(Tr, mx, tm);
-        else trace_apply<K, P>(Tr, my, tm);
+        if constexpr (P::NX != 0) trace_apply<T, K, P>(Tr, mx, tm);
+        else trace_apply<T, K, P>(Tr, my, tm);
     } else {
-        const double nx = __ldg(fm), ny = __ldg(fm + 1);
-        double mn[n];
+        const T nx = __ldg(fm), ny = __ldg(fm + 1);
+        T mn[n];
 #pragma unroll
         for (int i = 0; i < n; ++i) mn[i] = fma(nx, mx[i], ny * my[i]);
-        trace_apply<K, P>(Tr, mn, tm);
+        trace_apply<T, K, P>(Tr, mn, tm);
     }
-    constexpr double sgn = P::rect ? double(P::NX + P::NY) : 1.0;   // rect: tm holds the unsigned trace
+    constexpr int sgn = P::rect ? (P::NX + P::NY) : 1;   // rect: tm holds the unsigned trace
     const int slot = c.sbase + j * c.npad + c.lq;
     const int nb = __ldg(op.nb_f + slot);
-    const double al = (nb >= NB_BOUNDARY) ? __ldg(op.beta_f + slot) : __ldg(op.if_coef + 6 * (-2 - nb));
-    double* TWF = A.tr_out;
+    const T al = (nb >= NB_BOUNDARY) ? __ldg(OpData<T>::beta_f(op) + slot) : __ldg(OpData<T>::if_coef(op) + 6 * (-2 - nb));
 #pragma unroll
     for (int l = 0; l < f; ++l) {
-        const double w = (sgn > 0.0) ? fma(c.tau, tp[l], -tm[l]) : fma(c.tau, tp[l], tm[l]);
-        TWF[(size_t)l * c.SF + slot] = w;
-        TWF[(size_t)(f + l) * c.SF + slot] = fma(al, w, -tp[l]);
+        const T w = (sgn > 0) ? fma(c.tau, tp[l], -tm[l]) : fma(c.tau, tp[l], tm[l]);
+        c.trf_out[(size_t)l * c.SF + slot] = w;
+        c.trf_out[(size_t)(f + l) * c.SF + slot] = fma(al, w, -tp[l]);
     }
 }
 
-template <int K, int MODE>
-__device__ __forceinline__ void fluid_cell(const StageArgs& A, int q) {
-    constexpr int n = Dims<K>::n;
+template <class T, int K, int MODE>
+__device__ __forceinline__ void fluid_cell(const StageArgsT<T>& A, int q, int shot) {
+    constexpr int n = Dims<K>::n, f = Dims<K>::f;
     const DevOps& op = A.op;
     const int cls = __ldg(op.warp_class + (q >> 5));
     const int* ci = op.cls_int + cls * CI_STRIDE;
-    FluidCtx c;
+    CellCtx<T> c;
     c.q = q;
     c.lq = q - __ldg(ci + CI_START);
     if (c.lq >= __ldg(ci + CI_COUNT)) return;   // class padding
     c.nF = __ldg(ci + CI_NF);
     c.npad = __ldg(ci + CI_NPAD);
     c.sbase = __ldg(ci + CI_SLOT);
-    c.cd = op.cls_dbl + __ldg(ci + CI_DOFF) + n * n;
+    c.cd = OpData<T>::cls(op) + __ldg(ci + CI_DOFF) + n * n;
     c.N = op.Nf;
     c.SF = op.SF;
     c.SS = op.SS;
-    c.tau = __ldg(op.scal_f + SF_TAU * c.N + q);
+    c.tau = __ldg(OpData<T>::scal_f(op) + SF_TAU * c.N + q);
+    const size_t toff = (size_t)shot * A.trace_stride;
+    c.trf_in = A.tr_in + toff;
+    c.trs_in = A.tr_in + toff + (size_t)2 * f * c.SF;
+    c.trf_out = A.tr_out + toff;
+    c.trs_out = A.tr_out + toff + (size_t)2 * f * c.SF;
+    const size_t soff = (size_t)shot * A.state_stride;
     const bool rect = __ldg(ci + CI_KIND) == KIND_RECT;
-    double U[3 * n];   // [m_x | m_y | p]
+    T U[3 * n];   // [m_x | m_y | p]
     if constexpr (MODE == MODE_TRACES) {
-        load_state<3 * n>(A.inp, c.N, q, 0, U);
+        load_state<3 * n>(A.inp + soff, c.N, q, 0, U);
     } else {
-        double* kmx = U;
-        double* kmy = U + n;
-        double* kp = U + 2 * n;
+        T* kmx = U;
+        T* kmy = U + n;
+        T* kp = U + 2 * n;
         {
-            double u[n];
-            load_state<n>(A.inp, c.N, q, 2 * n, u);      // p
-            ddx<K>(u, kmx);
-            ddy<K>(u, kmy);
-            load_state<n>(A.inp, c.N, q, 0, u);          // m_x
-            ddx<K>(u, kp);
-            load_state<n>(A.inp, c.N, q, n, u);          // m_y
-            add_ddy<K>(u, kp);
+            T u[n];
+            load_state<n>(A.inp + soff, c.N, q, 2 * n, u);      // p
+            ddx<T, K>(u, kmx);
+            ddy<T, K>(u, kmy);
+            load_state<n>(A.inp + soff, c.N, q, 0, u);          // m_x
+            ddx<T, K>(u, kp);
+            load_state<n>(A.inp + soff, c.N, q, n, u);          // m_y
+            add_ddy<T, K>(u, kp);
         }
         if (rect) {
-            fluid_face_rate<K, RectFace<0>>(A, c, 0, kmx, kmy, kp);
-            fluid_face_rate<K, RectFace<1>>(A, c, 1, kmx, kmy, kp);
-            fluid_face_rate<K, RectFace<2>>(A, c, 2, kmx, kmy, kp);
-            fluid_face_rate<K, RectFace<3>>(A, c, 3, kmx, kmy, kp);
+            fluid_face_rate<T, K, RectFace<0>>(A, c, 0, kmx, kmy, kp);
+            fluid_face_rate<T, K, RectFace<1>>(A, c, 1, kmx, kmy, kp);
+            fluid_face_rate<T, K, RectFace<2>>(A, c, 2, kmx, kmy, kp);
+            fluid_face_rate<T, K, RectFace<3>>(A, c, 3, kmx, kmy, kp);
         } else {
 #pragma unroll 1
-            for (int j = 0; j < c.nF; ++j) fluid_face_rate<K, GenericFace>(A, c, j, kmx, kmy, kp);
+            for (int j = 0; j < c.nF; ++j) fluid_face_rate<T, K, GenericFace>(A, c, j, kmx, kmy, kp);
         }
+        const T Am = __ldg(OpData<T>::scal_f(op) + SF_AM * c.N + q), Ap = __ldg(OpData<T>::scal_f(op) + SF_AP * c.N + q);
+        // Point sources: the stored vector is kappa/h^2 M0^-1 phi(x_s); the
+        // raw rate is multiplied by A_p = kappa/h in the targets.
         for (int s = 0; s < A.n_src; ++s) {
             if (A.src_dom[s] == 0 && A.src_q[s] == q) {
-                // the source vector is stored already multiplied by kappa/h^2 M0^-1;
-                // divide by the A_p folded into the targets
-                const double w = A.src_w[s] / __ldg(op.scal_f + SF_AP * c.N + q);
-                const double* g = A.src_g + (size_t)s * 2 * n;
+                const T w = A.src_w[s] / Ap;
+                const T* g = A.src_g + (size_t)s * 2 * n;
 #pragma unroll
                 for (int i = 0; i < n; ++i) kp[i] = fma(w, g[i], kp[i]);
             }
         }
-        const double sc[3] = {__ldg(op.scal_f + SF_AM * c.N + q), __ldg(op.scal_f + SF_AP * c.N + q), 0.0};
-        write_targets<3 * n, FluidGroups<n>>(A, c.N, 0, q, U, sc);
+        if (A.shot_src_q && A.shot_src_dom[shot] == 0 && A.shot_src_q[shot] == q) {
+            const T w = A.shot_src_w / Ap;
+            const T* g = A.shot_src_g + (size_t)shot * 2 * n;
+#pragma unroll
+            for (int i = 0; i < n; ++i) kp[i] = fma(w, g[i], kp[i]);
+        }
+        const T sc[3] = {Am, Ap, T(0)};
+        write_targets<3 * n, FluidGroups<n>>(A, c.N, soff, q, U, sc);
         if constexpr (MODE == MODE_APPLY) return;
     }
     if (rect) {
-        fluid_face_trace<K, RectFace<0>>(A, c, 0, U);
-        fluid_face_trace<K, RectFace<1>>(A, c, 1, U);
-        fluid_face_trace<K, RectFace<2>>(A, c, 2, U);
-        fluid_face_trace<K, RectFace<3>>(A, c, 3, U);
+        fluid_face_trace<T, K, RectFace<0>>(A, c, 0, U);
+        fluid_face_trace<T, K, RectFace<1>>(A, c, 1, U);
+        fluid_face_trace<T, K, RectFace<2>>(A, c, 2, U);
+        fluid_face_trace<T, K, RectFace<3>>(A, c, 3, U);
     } else {
 #pragma unroll 1
-        for (int j = 0; j < c.nF; ++j) fluid_face_trace<K, GenericFace>(A, c, j, U);
+        for (int j = 0; j < c.nF; ++j) fluid_face_trace<T, K, GenericFace>(A, c, j, U);
     }
 }
 
 // ---- solid cells -------------------------------------------------------------------
-struct SolidCtx {
-    int q, lq, nF, npad, sbase, N, SF, SS;
-    const double* cd;
-    double tau;
-};
-
 // Lift one face's velocity jump into the raw accumulators: e (strain rate,
 // symmetric-gradient part) and kv (div s part, tau folded).
-template <int K, class P>
-__device__ __forceinline__ void solid_face_rate(const StageArgs& A, const SolidCtx& c, int j, double* exx, double* eyy,
-                                                double* exy, double* kvx, double* kvy) {
+template <class T, int K, class P>
+__device__ __forceinline__ void solid_face_rate(const StageArgsT<T>& A, const CellCtx<T>& c, int j, T* exx, T* eyy,
+                                                T* exy, T* kvx, T* kvy) {
     constexpr int n = Dims<K>::n, f = Dims<K>::f, FS = Dims<K>::FS;
     const DevOps& op = A.op;
-    const double* fm = c.cd + j * FS;
-    const double* TRF = A.tr_in;
-    const double* TRS = A.tr_in + (size_t)2 * f * c.SF;
+    const T* fm = c.cd + j * FS;
     const int slot = c.sbase + j * c.npad + c.lq;
     const int nb = __ldg(op.nb_s + slot);
-    double jx[f], jy[f];
+    T jx[f], jy[f];
 #pragma unroll
     for (int l = 0; l < f; ++l) {
-        jx[l] = __ldg(TRS + (size_t)(2 * f + l) * c.SS + slot);
-        jy[l] = __ldg(TRS + (size_t)(3 * f + l) * c.SS + slot);
+        jx[l] = __ldg(c.trs_in + (size_t)(2 * f + l) * c.SS + slot);
+        jy[l] = __ldg(c.trs_in + (size_t)(3 * f + l) * c.SS + slot);
     }
     if (nb >= 0) {
-        const double be = __ldg(op.beta_s + slot);
+        const T be = __ldg(OpData<T>::beta_s(op) + slot);
 #pragma unroll
         for (int l = 0; l < f; ++l) {
-            const double wx = __ldg(TRS + (size_t)l * c.SS + nb);
-            const double wy = __ldg(TRS + (size_t)(f + l) * c.SS + nb);
+            const T wx = __ldg(c.trs_in + (size_t)l * c.SS + nb);
+            const T wy = __ldg(c.trs_in + (size_t)(f + l) * c.SS + nb);
             jx[l] = (l & 1) ? fma(-be, wx, jx[l]) : fma(be, wx, jx[l]);
             jy[l] = (l & 1) ? fma(-be, wy, jy[l]) : fma(be, wy, jy[l]);
         }
     } else if (nb < NB_BOUNDARY) {
         const int r = -2 - nb;
         const int nfs = __ldg(op.if_nb + r);
-        const double b0 = __ldg(op.if_coef + 6 * r + 4), b1 = __ldg(op.if_coef + 6 * r + 5);
+        const T* co = OpData<T>::if_coef(op) + 6 * r;
+        const T b0 = __ldg(co + 4), b1 = __ldg(co + 5);
 #pragma unroll
         for (int l = 0; l < f; ++l) {
-            const double wf = __ldg(TRF + (size_t)l * c.SF + nfs);
+            const T wf = __ldg(c.trf_in + (size_t)l * c.SF + nfs);
             jx[l] = (l & 1) ? fma(-b0, wf, jx[l]) : fma(b0, wf, jx[l]);
             jy[l] = (l & 1) ? fma(-b1, wf, jy[l]) : fma(b1, wf, jy[l]);
         }
     }
-    const double* L = fm + 2 + f * n;
-    double lx[n], ly[n];
-    lift_apply<K, P>(L, jx, lx);
-    lift_apply<K, P>(L, jy, ly);
+    const T* L = fm + 2 + f * n;
+    T lx[n], ly[n];
+    lift_apply<T, K, P>(L, jx, lx);
+    lift_apply<T, K, P>(L, jy, ly);
     if constexpr (P::rect) {
         axpy_sign<P::NX, n>(lx, exx);
         axpy_sign<P::NX, n>(ly, exy);
         axpy_sign<P::NY, n>(ly, eyy);
         axpy_sign<P::NY, n>(lx, exy);
     } else {
-        const double nx = __ldg(fm), ny = __ldg(fm + 1);
+        const T nx = __ldg(fm), ny = __ldg(fm + 1);
 #pragma unroll
         for (int i = 0; i < n; ++i) {
             exx[i] = fma(nx, lx[i], exx[i]);
@@ -449,63 +482,62 @@ __device__ __forceinline__ void solid_face_rate(const StageArgs& A, const SolidC
 }
 
 // Publish w = tau v|_F - (s n)|_F and omega = alpha w - v|_F for one face.
-template <int K, class P>
-__device__ __forceinline__ void solid_face_trace(const StageArgs& A, const SolidCtx& c, int j, const double* U) {
+template <class T, int K, class P>
+__device__ __forceinline__ void solid_face_trace(const StageArgsT<T>& A, const CellCtx<T>& c, int j, const T* U) {
     constexpr int n = Dims<K>::n, f = Dims<K>::f, FS = Dims<K>::FS;
     const DevOps& op = A.op;
-    const double* fm = c.cd + j * FS;
-    const double* Tr = fm + 2;
-    const double* sxx = U;
-    const double* syy = U + n;
-    const double* sxy = U + 2 * n;
-    const double* vx = U + 3 * n;
-    const double* vy = U + 4 * n;
-    double tvx[f], tvy[f], tsx[f], tsy[f];
-    trace_apply<K, P>(Tr, vx, tvx);
-    trace_apply<K, P>(Tr, vy, tvy);
-    double sgn = 1.0;
+    const T* fm = c.cd + j * FS;
+    const T* Tr = fm + 2;
+    const T* sxx = U;
+    const T* syy = U + n;
+    const T* sxy = U + 2 * n;
+    const T* vx = U + 3 * n;
+    const T* vy = U + 4 * n;
+    T tvx[f], tvy[f], tsx[f], tsy[f];
+    trace_apply<T, K, P>(Tr, vx, tvx);
+    trace_apply<T, K, P>(Tr, vy, tvy);
     if constexpr (P::rect) {
         // s n = (nx s_xx + ny s_xy, nx s_xy + ny s_yy) with one of nx, ny = +-1
         if constexpr (P::NX != 0) {
-            trace_apply<K, P>(Tr, sxx, tsx);
-            trace_apply<K, P>(Tr, sxy, tsy);
+            trace_apply<T, K, P>(Tr, sxx, tsx);
+            trace_apply<T, K, P>(Tr, sxy, tsy);
         } else {
-            trace_apply<K, P>(Tr, sxy, tsx);
-            trace_apply<K, P>(Tr, syy, tsy);
+            trace_apply<T, K, P>(Tr, sxy, tsx);
+            trace_apply<T, K, P>(Tr, syy, tsy);
         }
-        sgn = double(P::NX + P::NY);
     } else {
-        const double nx = __ldg(fm), ny = __ldg(fm + 1);
-        double snx[n], sny[n];
+        const T nx = __ldg(fm), ny = __ldg(fm + 1);
+        T snx[n], sny[n];
 #pragma unroll
         for (int i = 0; i < n; ++i) {
             snx[i] = fma(nx, sxx[i], ny * sxy[i]);
             sny[i] = fma(nx, sxy[i], ny * syy[i]);
         }
-        trace_apply<K, P>(Tr, snx, tsx);
-        trace_apply<K, P>(Tr, sny, tsy);
+        trace_apply<T, K, P>(Tr, snx, tsx);
+        trace_apply<T, K, P>(Tr, sny, tsy);
     }
+    constexpr int sgn = P::rect ? (P::NX + P::NY) : 1;
     const int slot = c.sbase + j * c.npad + c.lq;
     const int nb = __ldg(op.nb_s + slot);
-    double* TWS = A.tr_out + (size_t)2 * f * c.SF;
+    T* TWS = c.trs_out;
     if (nb >= NB_BOUNDARY) {
-        const double be = __ldg(op.beta_s + slot);
+        const T be = __ldg(OpData<T>::beta_s(op) + slot);
 #pragma unroll
         for (int l = 0; l < f; ++l) {
-            const double wx = (sgn > 0.0) ? fma(c.tau, tvx[l], -tsx[l]) : fma(c.tau, tvx[l], tsx[l]);
-            const double wy = (sgn > 0.0) ? fma(c.tau, tvy[l], -tsy[l]) : fma(c.tau, tvy[l], tsy[l]);
+            const T wx = (sgn > 0) ? fma(c.tau, tvx[l], -tsx[l]) : fma(c.tau, tvx[l], tsx[l]);
+            const T wy = (sgn > 0) ? fma(c.tau, tvy[l], -tsy[l]) : fma(c.tau, tvy[l], tsy[l]);
             TWS[(size_t)l * c.SS + slot] = wx;
             TWS[(size_t)(f + l) * c.SS + slot] = wy;
             TWS[(size_t)(2 * f + l) * c.SS + slot] = fma(be, wx, -tvx[l]);
             TWS[(size_t)(3 * f + l) * c.SS + slot] = fma(be, wy, -tvy[l]);
         }
     } else {
-        const double* co = op.if_coef + 6 * (-2 - nb);
-        const double a00 = __ldg(co), a01 = __ldg(co + 1), a10 = __ldg(co + 2), a11 = __ldg(co + 3);
+        const T* co = OpData<T>::if_coef(op) + 6 * (-2 - nb);
+        const T a00 = __ldg(co), a01 = __ldg(co + 1), a10 = __ldg(co + 2), a11 = __ldg(co + 3);
 #pragma unroll
         for (int l = 0; l < f; ++l) {
-            const double wx = (sgn > 0.0) ? fma(c.tau, tvx[l], -tsx[l]) : fma(c.tau, tvx[l], tsx[l]);
-            const double wy = (sgn > 0.0) ? fma(c.tau, tvy[l], -tsy[l]) : fma(c.tau, tvy[l], tsy[l]);
+            const T wx = (sgn > 0) ? fma(c.tau, tvx[l], -tsx[l]) : fma(c.tau, tvx[l], tsx[l]);
+            const T wy = (sgn > 0) ? fma(c.tau, tvy[l], -tsy[l]) : fma(c.tau, tvy[l], tsy[l]);
             TWS[(size_t)l * c.SS + slot] = wx;
             TWS[(size_t)(f + l) * c.SS + slot] = wy;
             TWS[(size_t)(2 * f + l) * c.SS + slot] = fma(a00, wx, fma(a01, wy, -tvx[l]));
@@ -514,74 +546,79 @@ __device__ __forceinline__ void solid_face_trace(const StageArgs& A, const Solid
     }
 }
 
-template <int K, int MODE>
-__device__ __forceinline__ void solid_cell(const StageArgs& A, int q) {
-    constexpr int n = Dims<K>::n;
+template <class T, int K, int MODE>
+__device__ __forceinline__ void solid_cell(const StageArgsT<T>& A, int q, int shot) {
+    constexpr int n = Dims<K>::n, f = Dims<K>::f;
     const DevOps& op = A.op;
     const int cls = __ldg(op.warp_class + op.n_warps_f + (q >> 5));
     const int* ci = op.cls_int + cls * CI_STRIDE;
-    SolidCtx c;
+    CellCtx<T> c;
     c.q = q;
     c.lq = q - __ldg(ci + CI_START);
     if (c.lq >= __ldg(ci + CI_COUNT)) return;
     c.nF = __ldg(ci + CI_NF);
     c.npad = __ldg(ci + CI_NPAD);
     c.sbase = __ldg(ci + CI_SLOT);
-    c.cd = op.cls_dbl + __ldg(ci + CI_DOFF) + n * n;
+    c.cd = OpData<T>::cls(op) + __ldg(ci + CI_DOFF) + n * n;
     c.N = op.Ns;
     c.SF = op.SF;
     c.SS = op.SS;
-    c.tau = __ldg(op.scal_s + SS_TAU * c.N + q);
+    c.tau = __ldg(OpData<T>::scal_s(op) + SS_TAU * c.N + q);
+    const size_t toff = (size_t)shot * A.trace_stride;
+    c.trf_in = A.tr_in + toff;
+    c.trs_in = A.tr_in + toff + (size_t)2 * f * c.SF;
+    c.trf_out = A.tr_out + toff;
+    c.trs_out = A.tr_out + toff + (size_t)2 * f * c.SF;
     const bool rect = __ldg(ci + CI_KIND) == KIND_RECT;
-    const size_t dom_off = (size_t)3 * n * op.Nf;
-    const double* inp = A.inp + dom_off;
-    double U[5 * n];   // [s_xx | s_yy | s_xy | v_x | v_y]
+    const size_t soff = (size_t)shot * A.state_stride + (size_t)3 * n * op.Nf;
+    const T* inp = A.inp + soff;
+    T U[5 * n];   // [s_xx | s_yy | s_xy | v_x | v_y]
     if constexpr (MODE == MODE_TRACES) {
         load_state<5 * n>(inp, c.N, q, 0, U);
     } else {
-        double* exx = U;
-        double* eyy = U + n;
-        double* exy = U + 2 * n;
-        double* kvx = U + 3 * n;
-        double* kvy = U + 4 * n;
+        T* exx = U;
+        T* eyy = U + n;
+        T* exy = U + 2 * n;
+        T* kvx = U + 3 * n;
+        T* kvy = U + 4 * n;
         {
-            double u[n];
+            T u[n];
             load_state<n>(inp, c.N, q, 3 * n, u);    // v_x
-            ddx<K>(u, exx);
-            ddy<K>(u, exy);
+            ddx<T, K>(u, exx);
+            ddy<T, K>(u, exy);
             load_state<n>(inp, c.N, q, 4 * n, u);    // v_y
-            ddy<K>(u, eyy);
-            add_ddx<K>(u, exy);
+            ddy<T, K>(u, eyy);
+            add_ddx<T, K>(u, exy);
             load_state<n>(inp, c.N, q, 0, u);        // s_xx
-            ddx<K>(u, kvx);
+            ddx<T, K>(u, kvx);
             load_state<n>(inp, c.N, q, n, u);        // s_yy
-            ddy<K>(u, kvy);
+            ddy<T, K>(u, kvy);
             load_state<n>(inp, c.N, q, 2 * n, u);    // s_xy
-            add_ddy<K>(u, kvx);
-            add_ddx<K>(u, kvy);
+            add_ddy<T, K>(u, kvx);
+            add_ddx<T, K>(u, kvy);
         }
         if (rect) {
-            solid_face_rate<K, RectFace<0>>(A, c, 0, exx, eyy, exy, kvx, kvy);
-            solid_face_rate<K, RectFace<1>>(A, c, 1, exx, eyy, exy, kvx, kvy);
-            solid_face_rate<K, RectFace<2>>(A, c, 2, exx, eyy, exy, kvx, kvy);
-            solid_face_rate<K, RectFace<3>>(A, c, 3, exx, eyy, exy, kvx, kvy);
+            solid_face_rate<T, K, RectFace<0>>(A, c, 0, exx, eyy, exy, kvx, kvy);
+            solid_face_rate<T, K, RectFace<1>>(A, c, 1, exx, eyy, exy, kvx, kvy);
+            solid_face_rate<T, K, RectFace<2>>(A, c, 2, exx, eyy, exy, kvx, kvy);
+            solid_face_rate<T, K, RectFace<3>>(A, c, 3, exx, eyy, exy, kvx, kvy);
         } else {
 #pragma unroll 1
-            for (int j = 0; j < c.nF; ++j) solid_face_rate<K, GenericFace>(A, c, j, exx, eyy, exy, kvx, kvy);
+            for (int j = 0; j < c.nF; ++j) solid_face_rate<T, K, GenericFace>(A, c, j, exx, eyy, exy, kvx, kvy);
         }
         // stress rate = C e = c1 [(e_xx + r e_yy), (e_yy + r e_xx)], c3 e_xy; c1, c3 folded into targets
-        const double r = __ldg(op.scal_s + SS_R * c.N + q);
+        const T r = __ldg(OpData<T>::scal_s(op) + SS_R * c.N + q);
 #pragma unroll
         for (int i = 0; i < n; ++i) {
-            const double a = exx[i], b = eyy[i];
+            const T a = exx[i], b = eyy[i];
             exx[i] = fma(r, b, a);
             eyy[i] = fma(r, a, b);
         }
-        const double Av = __ldg(op.scal_s + SS_AV * c.N + q);
+        const T Av = __ldg(OpData<T>::scal_s(op) + SS_AV * c.N + q);
         for (int s = 0; s < A.n_src; ++s) {
             if (A.src_dom[s] == 1 && A.src_q[s] == q) {
-                const double w = A.src_w[s] / Av;
-                const double* g = A.src_g + (size_t)s * 2 * n;
+                const T w = A.src_w[s] / Av;
+                const T* g = A.src_g + (size_t)s * 2 * n;
 #pragma unroll
                 for (int i = 0; i < n; ++i) {
                     kvx[i] = fma(w, g[i], kvx[i]);
@@ -589,54 +626,77 @@ __device__ __forceinline__ void solid_cell(const StageArgs& A, int q) {
                 }
             }
         }
-        const double sc[3] = {__ldg(op.scal_s + SS_C1 * c.N + q), __ldg(op.scal_s + SS_C3 * c.N + q), Av};
-        write_targets<5 * n, SolidGroups<n>>(A, c.N, dom_off, q, U, sc);
+        if (A.shot_src_q && A.shot_src_dom[shot] == 1 && A.shot_src_q[shot] == q) {
+            const T w = A.shot_src_w / Av;
+            const T* g = A.shot_src_g + (size_t)shot * 2 * n;
+#pragma unroll
+            for (int i = 0; i < n; ++i) {
+                kvx[i] = fma(w, g[i], kvx[i]);
+                kvy[i] = fma(w, g[n + i], kvy[i]);
+            }
+        }
+        const T sc[3] = {__ldg(OpData<T>::scal_s(op) + SS_C1 * c.N + q), __ldg(OpData<T>::scal_s(op) + SS_C3 * c.N + q), Av};
+        write_targets<5 * n, SolidGroups<n>>(A, c.N, soff, q, U, sc);
         if constexpr (MODE == MODE_APPLY) return;
     }
     if (rect) {
-        solid_face_trace<K, RectFace<0>>(A, c, 0, U);
-        solid_face_trace<K, RectFace<1>>(A, c, 1, U);
-        solid_face_trace<K, RectFace<2>>(A, c, 2, U);
-        solid_face_trace<K, RectFace<3>>(A, c, 3, U);
+        solid_face_trace<T, K, RectFace<0>>(A, c, 0, U);
+        solid_face_trace<T, K, RectFace<1>>(A, c, 1, U);
+        solid_face_trace<T, K, RectFace<2>>(A, c, 2, U);
+        solid_face_trace<T, K, RectFace<3>>(A, c, 3, U);
     } else {
 #pragma unroll 1
-        for (int j = 0; j < c.nF; ++j) solid_face_trace<K, GenericFace>(A, c, j, U);
+        for (int j = 0; j < c.nF; ++j) solid_face_trace<T, K, GenericFace>(A, c, j, U);
     }
 }
 
-template <int K, int MODE>
-__global__ void __launch_bounds__(128) stage_kernel(const StageArgs A) {
+// Grid: x over the padded cells of both domains, y over shots.
+template <class T, int K, int MODE>
+__global__ void __launch_bounds__(128) stage_kernel(const StageArgsT<T> A) {
     const int gq = blockIdx.x * blockDim.x + threadIdx.x;
+    const int shot = blockIdx.y;
     if (gq < A.op.Nf)
-        fluid_cell<K, MODE>(A, gq);
+        fluid_cell<T, K, MODE>(A, gq, shot);
     else if (gq < A.op.Nf + A.op.Ns)
-        solid_cell<K, MODE>(A, gq - A.op.Nf);
+        solid_cell<T, K, MODE>(A, gq - A.op.Nf, shot);
 }
 
-// canonical (AoS, input cell order) <-> device layout (SoA by class)
-__global__ void pack_kernel(const int32_t* __restrict__ dev2orig, const int64_t* __restrict__ canon_off,
-                            int Nf, int Ns, int n, const double* __restrict__ canon, double* __restrict__ state,
-                            int unpack) {
+// canonical (AoS, input cell order, FP64) <-> device layout (SoA by class, T);
+// y = shot: canonical shot stride n_canon, state shot stride n_state.
+template <class T>
+__global__ void pack_kernel(const int32_t* __restrict__ dev2orig, const int64_t* __restrict__ canon_off, int Nf,
+                            int Ns, int n, int64_t n_canon, int64_t n_state, const double* __restrict__ canon,
+                            T* __restrict__ state) {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= Nf + Ns) return;
     const bool fl = g < Nf;
     const int q = fl ? g : g - Nf;
     const int N = fl ? Nf : Ns;
     const int nv = (fl ? 3 : 5) * n;
-    double* st = state + (fl ? 0 : (size_t)3 * n * Nf);
+    T* st = state + (size_t)blockIdx.y * n_state + (fl ? 0 : (size_t)3 * n * Nf);
     const int c = dev2orig[g];
     if (c < 0) {
-        if (!unpack)
-            for (int i = 0; i < nv; ++i) st[(size_t)i * N + q] = 0.0;
+        for (int i = 0; i < nv; ++i) st[(size_t)i * N + q] = T(0);
         return;
     }
-    const int64_t o = canon_off[c];
-    if (!unpack) {
-        for (int i = 0; i < nv; ++i) st[(size_t)i * N + q] = canon[o + i];
-    } else {
-        double* cw = const_cast<double*>(canon);
-        for (int i = 0; i < nv; ++i) cw[o + i] = st[(size_t)i * N + q];
-    }
+    const double* cv = canon + (size_t)blockIdx.y * n_canon + canon_off[c];
+    for (int i = 0; i < nv; ++i) st[(size_t)i * N + q] = T(cv[i]);
+}
+template <class T>
+__global__ void unpack_kernel(const int32_t* __restrict__ dev2orig, const int64_t* __restrict__ canon_off, int Nf,
+                              int Ns, int n, int64_t n_canon, int64_t n_state, const T* __restrict__ state,
+                              double* __restrict__ canon) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= Nf + Ns) return;
+    const bool fl = g < Nf;
+    const int q = fl ? g : g - Nf;
+    const int N = fl ? Nf : Ns;
+    const int nv = (fl ? 3 : 5) * n;
+    const T* st = state + (size_t)blockIdx.y * n_state + (fl ? 0 : (size_t)3 * n * Nf);
+    const int c = dev2orig[g];
+    if (c < 0) return;
+    double* cv = canon + (size_t)blockIdx.y * n_canon + canon_off[c];
+    for (int i = 0; i < nv; ++i) cv[i] = double(st[(size_t)i * N + q]);
 }
 
 // Energy 1/2 U^T M U (Sec. 5.1) with M = h^2 (material) x M0_ref per cell.
@@ -700,19 +760,21 @@ __global__ void sum_kernel(const double* __restrict__ partial, int np, double* o
 
 // Receivers: fluid [p, m_x, m_y, 0, 0]; solid [v_x, v_y, s_xx, s_yy, s_xy];
 // interface [p_F, v_Fx, v_Fy, 0, 0] from the pointwise face solve.
+// y = shot: state shot stride n_state, output shot stride 5 n_rec.
+template <class T>
 __global__ void record_kernel(DevOps op, int n_rec, const int32_t* __restrict__ ri, const double* __restrict__ rd,
-                              const double* __restrict__ state, double* out) {
+                              const T* __restrict__ state, int64_t n_state, T* out) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n_rec) return;
     const int n = op.n;
     const int stride = 2 * n + 15;
     const double* d = rd + (size_t)r * stride;
     const int kind = ri[4 * r], qf = ri[4 * r + 1], qs = ri[4 * r + 2];
-    const double* sf = state;
-    const double* ss = state + (size_t)3 * n * op.Nf;
-    auto ev = [&](const double* base, int N, int q, int field, const double* phi) {
+    const T* sf = state + (size_t)blockIdx.y * n_state;
+    const T* ss = sf + (size_t)3 * n * op.Nf;
+    auto ev = [&](const T* base, int N, int q, int field, const double* phi) {
         double s = 0.0;
-        for (int i = 0; i < n; ++i) s = fma(phi[i], base[(size_t)(field * n + i) * N + q], s);
+        for (int i = 0; i < n; ++i) s = fma(phi[i], double(base[(size_t)(field * n + i) * N + q]), s);
         return s;
     };
     double o[5] = {0, 0, 0, 0, 0};
@@ -742,14 +804,15 @@ __global__ void record_kernel(DevOps op, int n_rec, const int32_t* __restrict__ 
         o[1] = Ai[3] * wf + Ai[4] * wsx + Ai[5] * wsy;
         o[2] = Ai[6] * wf + Ai[7] * wsx + Ai[8] * wsy;
     }
-    for (int j = 0; j < 5; ++j) out[5 * r + j] = o[j];
+    T* ob = out + (size_t)blockIdx.y * 5 * n_rec + 5 * r;
+    for (int j = 0; j < 5; ++j) ob[j] = T(o[j]);
 }
 
-template <int MODE>
-void launch_k(int k, const StageArgs& a, int grid, cudaStream_t s) {
-    if (k == 1) stage_kernel<1, MODE><<<grid, 128, 0, s>>>(a);
-    else if (k == 2) stage_kernel<2, MODE><<<grid, 128, 0, s>>>(a);
-    else stage_kernel<3, MODE><<<grid, 128, 0, s>>>(a);
+template <class T, int MODE>
+void launch_k(int k, const StageArgsT<T>& a, dim3 grid, cudaStream_t s) {
+    if (k == 1) stage_kernel<T, 1, MODE><<<grid, 128, 0, s>>>(a);
+    else if (k == 2) stage_kernel<T, 2, MODE><<<grid, 128, 0, s>>>(a);
+    else stage_kernel<T, 3, MODE><<<grid, 128, 0, s>>>(a);
 }
 
 // ---- ERK schedule ---------------------------------------------------------------
@@ -818,13 +881,38 @@ int check_launch(const char* what) {
     return HHO_OK;
 }
 
-void fill_sources(const hho_ops* ops, StageArgs& a, double t) {
+template <class T>
+const T* src_g_of(const hho_ops* ops);
+template <>
+const double* src_g_of<double>(const hho_ops* ops) { return ops->d_src_g; }
+template <>
+const float* src_g_of<float>(const hho_ops* ops) { return ops->d_src_g32; }
+template <class T>
+const T* shot_g_of(const hho_ops* ops);
+template <>
+const double* shot_g_of<double>(const hho_ops* ops) { return ops->d_shot_src_g; }
+template <>
+const float* shot_g_of<float>(const hho_ops* ops) { return ops->d_shot_src_g32; }
+
+template <class T>
+void fill_sources(const hho_ops* ops, StageArgsT<T>& a, double t, int n_shots) {
     a.n_src = ops->n_src;
-    a.src_g = ops->d_src_g;
+    a.src_g = src_g_of<T>(ops);
     for (int s = 0; s < ops->n_src; ++s) {
         a.src_dom[s] = ops->src_dom[s];
         a.src_q[s] = ops->src_q[s];
-        a.src_w[s] = ricker(t, ops->src_f0[s], ops->src_t0[s], ops->src_amp[s]);
+        a.src_w[s] = T(ricker(t, ops->src_f0[s], ops->src_t0[s], ops->src_amp[s]));
+    }
+    if (ops->n_shot_src > 0 && n_shots <= ops->n_shot_src) {
+        a.shot_src_dom = ops->d_shot_src_dom;
+        a.shot_src_q = ops->d_shot_src_q;
+        a.shot_src_g = shot_g_of<T>(ops);
+        a.shot_src_w = T(ricker(t, ops->shot_f0, ops->shot_t0, ops->shot_amp));
+    } else {
+        a.shot_src_dom = nullptr;
+        a.shot_src_q = nullptr;
+        a.shot_src_g = nullptr;
+        a.shot_src_w = T(0);
     }
 }
 
@@ -845,9 +933,13 @@ extern "C" int hho_work_size(const hho_ops* ops, const hho_tableau* tab, int64_t
     return HHO_OK;
 }
 
-static int erk_run(hho_ops* ops, const hho_tableau* tab, double t0, double dt, int64_t nsteps, double* d_state,
-                   double* d_work, double* d_seis, void* stream, const char* who) {
-    if (!ops || !tab || !d_state || !d_work || nsteps < 0 || !std::isfinite(dt) || !std::isfinite(t0)) {
+// Time stepping for n_shots states of element type T.  Work layout (elements
+// of T): [X: S n_state][partial sums: nb S n_state][traces: 2 x S trace].
+template <class T>
+static int erk_run(hho_ops* ops, const hho_tableau* tab, double t0, double dt, int64_t nsteps, int n_shots,
+                   T* d_state, T* d_work, T* d_seis, void* stream, const char* who) {
+    if (!ops || !tab || !d_state || !d_work || nsteps < 0 || n_shots < 1 || n_shots > 65535 || !std::isfinite(dt) ||
+        !std::isfinite(t0)) {
         hho_set_error("%s: bad arguments", who);
         return HHO_EINVAL;
     }
@@ -859,25 +951,28 @@ static int erk_run(hho_ops* ops, const hho_tableau* tab, double t0, double dt, i
     }
     if (nsteps == 0) return HHO_OK;
     cudaStream_t st = (cudaStream_t)stream;
-    const int64_t S = ops->n_state;
-    double* X = d_work;
-    double* bufs = d_work + S;
-    double* tr[2] = {d_work + S * (1 + nb), d_work + S * (1 + nb) + ops->trace_doubles};
-    const int grid = (ops->dev.Nf + ops->dev.Ns + 127) / 128;
-    if (grid == 0) return HHO_OK;
-    auto resolve = [&](int code) -> double* {
+    const int64_t S = ops->n_state * n_shots;
+    const int64_t TRS = ops->trace_doubles * n_shots;
+    T* X = d_work;
+    T* bufs = d_work + S;
+    T* tr[2] = {d_work + S * (1 + nb), d_work + S * (1 + nb) + TRS};
+    const dim3 grid((ops->dev.Nf + ops->dev.Ns + 127) / 128, n_shots);
+    if (grid.x == 0) return HHO_OK;
+    auto resolve = [&](int code) -> T* {
         if (code == SRC_STATE) return d_state;
         if (code == SRC_X) return X;
         if (code == SRC_ZERO) return nullptr;
         return bufs + S * code;
     };
-    StageArgs a;
+    StageArgsT<T> a;
     memset(&a, 0, sizeof(a));
     a.op = ops->dev;
+    a.state_stride = ops->n_state;
+    a.trace_stride = ops->trace_doubles;
     a.inp = d_state;
     a.tr_out = tr[0];
     a.n_tgt = 0;
-    launch_k<MODE_TRACES>(ops->k, a, grid, st);
+    launch_k<T, MODE_TRACES>(ops->k, a, grid, st);
     int rc = check_launch(who);
     if (rc) return rc;
     int cur = 0;
@@ -892,20 +987,21 @@ static int erk_run(hho_ops* ops, const hho_tableau* tab, double t0, double dt, i
             for (int t = 0; t < P.n_tgt; ++t) {
                 a.tgt[t].src = resolve(P.t[t].src);
                 a.tgt[t].dst = resolve(P.t[t].dst);
-                a.tgt[t].coef = P.t[t].a * dt;
+                a.tgt[t].coef = T(P.t[t].a * dt);
             }
-            fill_sources(ops, a, tn + tab->c[j] * dt);
+            fill_sources<T>(ops, a, tn + tab->c[j] * dt, n_shots);
             const bool prof = ops->prof_on && 2 * ops->prof_n + 1 < (int)ops->prof_events.size();
             if (prof) cudaEventRecord((cudaEvent_t)ops->prof_events[2 * ops->prof_n], st);
-            launch_k<MODE_STAGE>(ops->k, a, grid, st);
+            launch_k<T, MODE_STAGE>(ops->k, a, grid, st);
             if (prof) cudaEventRecord((cudaEvent_t)ops->prof_events[2 * ops->prof_n++ + 1], st);
             rc = check_launch(who);
             if (rc) return rc;
             cur ^= 1;
         }
         if (d_seis && ops->n_rec > 0) {
-            record_kernel<<<(ops->n_rec + 63) / 64, 64, 0, st>>>(ops->dev, ops->n_rec, ops->d_rec_int, ops->d_rec_dbl,
-                                                                 d_state, d_seis + (size_t)step * 5 * ops->n_rec);
+            record_kernel<T><<<dim3((ops->n_rec + 63) / 64, n_shots), 64, 0, st>>>(
+                ops->dev, ops->n_rec, ops->d_rec_int, ops->d_rec_dbl, d_state, ops->n_state,
+                d_seis + (size_t)step * 5 * ops->n_rec * n_shots);
             rc = check_launch(who);
             if (rc) return rc;
         }
@@ -915,7 +1011,7 @@ static int erk_run(hho_ops* ops, const hho_tableau* tab, double t0, double dt, i
 
 extern "C" int hho_erk_step(hho_ops* ops, const hho_tableau* tab, double t0, double dt, int64_t nsteps,
                             double* d_state, double* d_work, void* stream) {
-    return erk_run(ops, tab, t0, dt, nsteps, d_state, d_work, nullptr, stream, "hho_erk_step");
+    return erk_run<double>(ops, tab, t0, dt, nsteps, 1, d_state, d_work, nullptr, stream, "hho_erk_step");
 }
 
 extern "C" int hho_erk_step_record(hho_ops* ops, const hho_tableau* tab, double t0, double dt, int64_t nsteps,
@@ -924,7 +1020,87 @@ extern "C" int hho_erk_step_record(hho_ops* ops, const hho_tableau* tab, double 
         hho_set_error("hho_erk_step_record: null seismogram buffer");
         return HHO_EINVAL;
     }
-    return erk_run(ops, tab, t0, dt, nsteps, d_state, d_work, d_seismogram, stream, "hho_erk_step_record");
+    return erk_run<double>(ops, tab, t0, dt, nsteps, 1, d_state, d_work, d_seismogram, stream, "hho_erk_step_record");
+}
+
+// ---- batched shots -----------------------------------------------------------------
+
+static bool batch_args_ok(const hho_ops* ops, int32_t n_shots, int32_t precision, const char* who) {
+    if (!ops || n_shots < 1 || n_shots > 65535 || (precision != HHO_F64 && precision != HHO_F32)) {
+        hho_set_error("%s: bad arguments (1 <= n_shots <= 65535, precision HHO_F64 or HHO_F32)", who);
+        return false;
+    }
+    return true;
+}
+
+extern "C" int hho_batch_sizes(const hho_ops* ops, const hho_tableau* tab, int32_t n_shots, int32_t precision,
+                               int64_t* state_elems, int64_t* work_elems) {
+    if (!batch_args_ok(ops, n_shots, precision, "hho_batch_sizes") || !tab) {
+        if (!tab) hho_set_error("hho_batch_sizes: null tableau");
+        return HHO_EINVAL;
+    }
+    std::vector<StagePlan> plan;
+    int nb = 0;
+    if (build_plan(tab, plan, &nb) != HHO_OK) {
+        hho_set_error("hho_batch_sizes: unsupported tableau");
+        return HHO_EINVAL;
+    }
+    if (state_elems) *state_elems = ops->n_state * n_shots;
+    if (work_elems) *work_elems = (ops->n_state * (1 + nb) + 2 * ops->trace_doubles) * n_shots;
+    return HHO_OK;
+}
+
+extern "C" int hho_batch_pack(const hho_ops* ops, int32_t n_shots, int32_t precision, const double* d_canonical,
+                              void* d_state, void* stream) {
+    if (!batch_args_ok(ops, n_shots, precision, "hho_batch_pack") || !d_canonical || !d_state) {
+        if (ops) hho_set_error("hho_batch_pack: bad arguments");
+        return HHO_EINVAL;
+    }
+    const int tot = ops->dev.Nf + ops->dev.Ns;
+    if (tot == 0) return HHO_OK;
+    const dim3 grid((tot + 127) / 128, n_shots);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (precision == HHO_F64)
+        pack_kernel<double><<<grid, 128, 0, st>>>(ops->d_dev2orig, ops->d_canon_off, ops->dev.Nf, ops->dev.Ns, ops->n,
+                                                  ops->n_canonical, ops->n_state, d_canonical, (double*)d_state);
+    else
+        pack_kernel<float><<<grid, 128, 0, st>>>(ops->d_dev2orig, ops->d_canon_off, ops->dev.Nf, ops->dev.Ns, ops->n,
+                                                 ops->n_canonical, ops->n_state, d_canonical, (float*)d_state);
+    return check_launch("hho_batch_pack");
+}
+
+extern "C" int hho_batch_unpack(const hho_ops* ops, int32_t n_shots, int32_t precision, const void* d_state,
+                                double* d_canonical, void* stream) {
+    if (!batch_args_ok(ops, n_shots, precision, "hho_batch_unpack") || !d_canonical || !d_state) {
+        if (ops) hho_set_error("hho_batch_unpack: bad arguments");
+        return HHO_EINVAL;
+    }
+    const int tot = ops->dev.Nf + ops->dev.Ns;
+    if (tot == 0) return HHO_OK;
+    const dim3 grid((tot + 127) / 128, n_shots);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (precision == HHO_F64)
+        unpack_kernel<double><<<grid, 128, 0, st>>>(ops->d_dev2orig, ops->d_canon_off, ops->dev.Nf, ops->dev.Ns, ops->n,
+                                                    ops->n_canonical, ops->n_state, (const double*)d_state, d_canonical);
+    else
+        unpack_kernel<float><<<grid, 128, 0, st>>>(ops->d_dev2orig, ops->d_canon_off, ops->dev.Nf, ops->dev.Ns, ops->n,
+                                                   ops->n_canonical, ops->n_state, (const float*)d_state, d_canonical);
+    return check_launch("hho_batch_unpack");
+}
+
+extern "C" int hho_batch_erk_step(hho_ops* ops, const hho_tableau* tab, int32_t n_shots, int32_t precision, double t0,
+                                  double dt, int64_t nsteps, void* d_state, void* d_work, void* d_seismogram,
+                                  void* stream) {
+    if (!batch_args_ok(ops, n_shots, precision, "hho_batch_erk_step")) return HHO_EINVAL;
+    if (ops->n_shot_src > 0 && ops->n_shot_src < n_shots) {
+        hho_set_error("hho_batch_erk_step: %d shot sources set for %d shots", ops->n_shot_src, n_shots);
+        return HHO_EINVAL;
+    }
+    if (precision == HHO_F64)
+        return erk_run<double>(ops, tab, t0, dt, nsteps, n_shots, (double*)d_state, (double*)d_work,
+                               (double*)d_seismogram, stream, "hho_batch_erk_step");
+    return erk_run<float>(ops, tab, t0, dt, nsteps, n_shots, (float*)d_state, (float*)d_work, (float*)d_seismogram,
+                          stream, "hho_batch_erk_step");
 }
 
 extern "C" int hho_profile_enable(hho_ops* ops, int32_t on) {
@@ -1050,14 +1226,16 @@ extern "C" int hho_apply(hho_ops* ops, double t, const double* d_state, double* 
         return HHO_EINVAL;
     }
     cudaStream_t st = (cudaStream_t)stream;
-    const int grid = (ops->dev.Nf + ops->dev.Ns + 127) / 128;
-    if (grid == 0) return HHO_OK;
-    StageArgs a;
+    const dim3 grid((ops->dev.Nf + ops->dev.Ns + 127) / 128, 1);
+    if (grid.x == 0) return HHO_OK;
+    StageArgsT<double> a;
     memset(&a, 0, sizeof(a));
     a.op = ops->dev;
+    a.state_stride = ops->n_state;
+    a.trace_stride = ops->trace_doubles;
     a.inp = d_state;
     a.tr_out = d_work;
-    launch_k<MODE_TRACES>(ops->k, a, grid, st);
+    launch_k<double, MODE_TRACES>(ops->k, a, grid, st);
     int rc = check_launch("hho_apply (trace kernel)");
     if (rc) return rc;
     a.tr_in = d_work;
@@ -1066,8 +1244,8 @@ extern "C" int hho_apply(hho_ops* ops, double t, const double* d_state, double* 
     a.tgt[0].src = nullptr;
     a.tgt[0].dst = d_rate;
     a.tgt[0].coef = 1.0;
-    fill_sources(ops, a, t);
-    launch_k<MODE_APPLY>(ops->k, a, grid, st);
+    fill_sources<double>(ops, a, t, 1);
+    launch_k<double, MODE_APPLY>(ops->k, a, grid, st);
     return check_launch("hho_apply (stage kernel)");
 }
 
@@ -1076,11 +1254,7 @@ extern "C" int hho_state_pack(const hho_ops* ops, const double* d_canonical, dou
         hho_set_error("hho_state_pack: null pointer");
         return HHO_EINVAL;
     }
-    const int tot = ops->dev.Nf + ops->dev.Ns;
-    if (tot == 0) return HHO_OK;
-    pack_kernel<<<(tot + 127) / 128, 128, 0, (cudaStream_t)stream>>>(ops->d_dev2orig, ops->d_canon_off, ops->dev.Nf,
-                                                                     ops->dev.Ns, ops->n, d_canonical, d_state, 0);
-    return check_launch("hho_state_pack");
+    return hho_batch_pack(ops, 1, HHO_F64, d_canonical, d_state, stream);
 }
 
 extern "C" int hho_state_unpack(const hho_ops* ops, const double* d_state, double* d_canonical, void* stream) {
@@ -1088,12 +1262,7 @@ extern "C" int hho_state_unpack(const hho_ops* ops, const double* d_state, doubl
         hho_set_error("hho_state_unpack: null pointer");
         return HHO_EINVAL;
     }
-    const int tot = ops->dev.Nf + ops->dev.Ns;
-    if (tot == 0) return HHO_OK;
-    pack_kernel<<<(tot + 127) / 128, 128, 0, (cudaStream_t)stream>>>(ops->d_dev2orig, ops->d_canon_off, ops->dev.Nf,
-                                                                     ops->dev.Ns, ops->n, d_canonical,
-                                                                     const_cast<double*>(d_state), 1);
-    return check_launch("hho_state_unpack");
+    return hho_batch_unpack(ops, 1, HHO_F64, d_state, d_canonical, stream);
 }
 
 extern "C" int hho_energy(hho_ops* ops, const double* d_state, double* d_work, double* h_energy, void* stream) {
@@ -1134,8 +1303,8 @@ extern "C" int hho_record(hho_ops* ops, const double* d_state, double* d_out, vo
         return HHO_EINVAL;
     }
     if (ops->n_rec == 0) return HHO_OK;
-    record_kernel<<<(ops->n_rec + 63) / 64, 64, 0, (cudaStream_t)stream>>>(ops->dev, ops->n_rec, ops->d_rec_int,
-                                                                          ops->d_rec_dbl, d_state, d_out);
+    record_kernel<double><<<dim3((ops->n_rec + 63) / 64, 1), 64, 0, (cudaStream_t)stream>>>(
+        ops->dev, ops->n_rec, ops->d_rec_int, ops->d_rec_dbl, d_state, ops->n_state, d_out);
     return check_launch("hho_record");
 }
 

@@ -18,6 +18,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libhho.so")
 
+HHO_F64, HHO_F32 = 0, 1
 HHO_OK, HHO_EINVAL, HHO_EMESH, HHO_EMATERIAL, HHO_EDEGREE, HHO_ECFL, HHO_EUNSTABLE, HHO_ECUDA, HHO_ENOMEM = range(9)
 
 
@@ -78,6 +79,11 @@ _SIGS = {
     "hho_profile_enable": (C.c_int, [_P, _I32]),
     "hho_profile_read": (C.c_int, [_P, C.POINTER(_D), C.POINTER(_I64)]),
     "hho_energy_static": (C.c_int, [_P, _P, _P, _P]),
+    "hho_batch_sizes": (C.c_int, [_P, C.POINTER(Tableau), _I32, _I32, C.POINTER(_I64), C.POINTER(_I64)]),
+    "hho_batch_pack": (C.c_int, [_P, _I32, _I32, _P, _P, _P]),
+    "hho_batch_unpack": (C.c_int, [_P, _I32, _I32, _P, _P, _P]),
+    "hho_batch_sources_set": (C.c_int, [_P, _I32, _P, _P, _D, _D, _D]),
+    "hho_batch_erk_step": (C.c_int, [_P, C.POINTER(Tableau), _I32, _I32, _D, _D, _I64, _P, _P, _P, _P]),
 }
 EXPORTED = sorted(_SIGS)
 
@@ -271,3 +277,28 @@ def hho_profile_read(ops):
 def hho_energy_static(ops, d_state, d_energy, stream=0):
     """Energy into the device double at d_energy; the library allocates nothing."""
     _check(lib().hho_energy_static(ops, d_state, d_energy, stream))
+
+
+def hho_batch_sizes(ops, tab, n_shots, precision):
+    a, b = _I64(), _I64()
+    _check(lib().hho_batch_sizes(ops, C.byref(tab), int(n_shots), int(precision), C.byref(a), C.byref(b)))
+    return a.value, b.value
+
+
+def hho_batch_pack(ops, n_shots, precision, d_canonical, d_state, stream=0):
+    _check(lib().hho_batch_pack(ops, int(n_shots), int(precision), d_canonical, d_state, stream))
+
+
+def hho_batch_unpack(ops, n_shots, precision, d_state, d_canonical, stream=0):
+    _check(lib().hho_batch_unpack(ops, int(n_shots), int(precision), d_state, d_canonical, stream))
+
+
+def hho_batch_sources_set(ops, xy, direction, f0, t0, amp=1.0):
+    xy = _arr(xy, np.float64).reshape(-1, 2)
+    d = _arr(direction, np.float64).reshape(-1, 2)
+    _check(lib().hho_batch_sources_set(ops, xy.shape[0], _ptr(xy), _ptr(d), float(f0), float(t0), float(amp)))
+
+
+def hho_batch_erk_step(ops, tab, n_shots, precision, t0, dt, nsteps, d_state, d_work, d_seismogram=None, stream=0):
+    _check(lib().hho_batch_erk_step(ops, C.byref(tab), int(n_shots), int(precision), float(t0), float(dt),
+                                    int(nsteps), d_state, d_work, d_seismogram, stream))

@@ -106,6 +106,36 @@ class Problem:
     def energy(self, state, stream=None):
         return hho.hho_energy(self.ops, state.data_ptr(), self.work(2).data_ptr(), _stream(stream))
 
+    # ---- batched shots ---------------------------------------------------------------
+    def batch_buffers(self, s, n_shots, precision=hho.HHO_F64):
+        tab = hho.hho_tableau_erk(s)
+        ns, nw = hho.hho_batch_sizes(self.ops, tab, n_shots, precision)
+        dt = torch.float64 if precision == hho.HHO_F64 else torch.float32
+        return (torch.zeros(ns, dtype=dt, device=self.dev), torch.empty(nw, dtype=dt, device=self.dev))
+
+    def batch_to_device(self, canonicals, precision=hho.HHO_F64, stream=None):
+        """canonicals: [n_shots, n_canonical] host array -> batched device state."""
+        c = torch.as_tensor(np.ascontiguousarray(canonicals, dtype=np.float64)).to(self.dev)
+        S = c.shape[0]
+        dt = torch.float64 if precision == hho.HHO_F64 else torch.float32
+        st = torch.zeros(S * self.layout.n_state, dtype=dt, device=self.dev)
+        hho.hho_batch_pack(self.ops, S, precision, c.data_ptr(), st.data_ptr(), _stream(stream))
+        return st
+
+    def batch_to_canonical(self, state, n_shots, precision=hho.HHO_F64, stream=None):
+        c = torch.empty((n_shots, self.layout.n_canonical), dtype=torch.float64, device=self.dev)
+        hho.hho_batch_unpack(self.ops, n_shots, precision, state.data_ptr(), c.data_ptr(), _stream(stream))
+        return c.cpu().numpy()
+
+    def set_shot_sources(self, xy, direction, f0, t0=None, amp=1.0):
+        hho.hho_batch_sources_set(self.ops, xy, direction, f0, 1.0 / f0 if t0 is None else t0, amp)
+
+    def batch_step(self, state, work, n_shots, s, t0, dt, nsteps, precision=hho.HHO_F64, seismogram=None,
+                   stream=None):
+        tab = hho.hho_tableau_erk(s)
+        hho.hho_batch_erk_step(self.ops, tab, n_shots, precision, t0, dt, nsteps, state.data_ptr(), work.data_ptr(),
+                               None if seismogram is None else seismogram.data_ptr(), _stream(stream))
+
     def run_host(self, canonical, s, t0, dt, nsteps, stream=None):
         """End to end from a host array (updated in place)."""
         tab = hho.hho_tableau_erk(s)

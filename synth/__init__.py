@@ -34,11 +34,10 @@ class MeshData:
 
     def centroids_approx(self):
         """Vertex averages (only used to tag subdomains and sample media)."""
-        out = np.empty((self.n_cells, 2))
-        for c in range(self.n_cells):
-            vs = self.cell_vtx[self.cell_ptr[c]:self.cell_ptr[c + 1]]
-            out[c] = self.xy[vs].mean(axis=0)
-        return out
+        cnt = np.diff(self.cell_ptr)
+        sx = np.add.reduceat(self.xy[self.cell_vtx, 0], self.cell_ptr[:-1])
+        sy = np.add.reduceat(self.xy[self.cell_vtx, 1], self.cell_ptr[:-1])
+        return np.stack([sx / cnt, sy / cnt], axis=1)
 
 
 def _grid_vertices(nx, ny, x0, x1, y0, y1):
@@ -75,30 +74,39 @@ def tri_grid(nx, ny, x0=0.0, x1=1.0, y0=0.0, y1=1.0, y_interface=0.5, periodic_x
 
 
 def quad_grid(nx, ny, x0=0.0, x1=1.0, y0=0.0, y1=1.0, y_interface=0.5, periodic_x=False):
-    """nx * ny axis-aligned rectangles."""
+    """nx * ny axis-aligned rectangles (vertices bottom-left first, counter-clockwise)."""
     xy, vid = _grid_vertices(nx, ny, x0, x1, y0, y1)
-    polys = []
-    for j in range(ny):
-        for i in range(nx):
-            polys.append([vid(i, j), vid(i + 1, j), vid(i + 1, j + 1), vid(i, j + 1)])
+    J, I = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+    a = (J * (nx + 1) + I).ravel()
+    quads = np.stack([a, a + 1, a + nx + 2, a + nx + 1], axis=1)
     rep = _periodic_rep(nx, ny, vid) if periodic_x else None
-    return _finish(xy, polys, y_interface, rep)
+    return _finish_array(xy, quads, y_interface, rep)
 
 
 def hybrid_grid(nx, ny, x0, x1, y0, y1, y_split, y_interface):
-    """Quads below y_split, each square split into two triangles above it."""
+    """Quads below y_split, each square split into two triangles above it
+    (row by row, so cells stay in row order)."""
     xy, vid = _grid_vertices(nx, ny, x0, x1, y0, y1)
-    polys = []
+    ptr = [0]
+    vtx = []
     for j in range(ny):
         yc = y0 + (y1 - y0) * (j + 0.5) / ny
-        for i in range(nx):
-            a, b, c, d = vid(i, j), vid(i + 1, j), vid(i + 1, j + 1), vid(i, j + 1)
-            if yc < y_split:
-                polys.append([a, b, c, d])
-            else:
-                polys.append([a, b, c])
-                polys.append([a, c, d])
-    return _finish(xy, polys, y_interface)
+        a = j * (nx + 1) + np.arange(nx)
+        b, c, d = a + 1, a + nx + 2, a + nx + 1
+        if yc < y_split:
+            cells = np.stack([a, b, c, d], axis=1).ravel()
+            vtx.append(cells)
+            ptr.extend(ptr[-1] + 4 * np.arange(1, nx + 1))
+        else:
+            cells = np.stack([a, b, c, a, c, d], axis=1).ravel()
+            vtx.append(cells)
+            ptr.extend(ptr[-1] + 3 * np.arange(1, 2 * nx + 1))
+    md = MeshData(xy=np.asarray(xy, dtype=np.float64), cell_ptr=np.array(ptr, dtype=np.int64),
+                  cell_vtx=np.concatenate(vtx).astype(np.int64), cell_domain=None)
+    md.cell_domain = np.zeros(md.n_cells, dtype=np.uint8)
+    cen = md.centroids_approx()
+    md.cell_domain = np.where(cen[:, 1] < y_interface, SOLID, FLUID).astype(np.uint8)
+    return md
 
 
 def hanging_node_patch(nx, ny, x0=0.0, x1=1.0, y0=0.0, y1=1.0, y_interface=0.5, refine_rows=(0,)):
@@ -138,6 +146,16 @@ def hanging_node_patch(nx, ny, x0=0.0, x1=1.0, y0=0.0, y1=1.0, y_interface=0.5, 
     return _finish(xy[order], polys, y_interface)
 
 
+def _finish_array(xy, cells, y_interface, vertex_rep=None):
+    nc, nvc = cells.shape
+    md = MeshData(xy=np.asarray(xy, dtype=np.float64), cell_ptr=np.arange(nc + 1, dtype=np.int64) * nvc,
+                  cell_vtx=cells.ravel().astype(np.int64), cell_domain=np.zeros(nc, dtype=np.uint8),
+                  vertex_rep=vertex_rep)
+    cen = md.centroids_approx()
+    md.cell_domain = np.where(cen[:, 1] < y_interface, SOLID, FLUID).astype(np.uint8)
+    return md
+
+
 def _periodic_rep(nx, ny, vid):
     rep = np.arange((nx + 1) * (ny + 1), dtype=np.int64)
     for j in range(ny + 1):
@@ -155,15 +173,12 @@ def lame_from_speeds(rho, vp, vs):
 
 def layered_media(md: MeshData, fluid=(1.0, 1.5), solid=(2.5, 3.0, 1.7)):
     """Per-cell (rho, lam, mu, kappa): homogeneous fluid (rho, c) over solid (rho, vp, vs)."""
-    nc = md.n_cells
-    rho = np.empty(nc); lam = np.zeros(nc); mu = np.zeros(nc); kappa = np.zeros(nc)
-    for c in range(nc):
-        if md.cell_domain[c] == FLUID:
-            rho[c] = fluid[0]
-            kappa[c] = fluid[0] * fluid[1] ** 2
-        else:
-            rho[c] = solid[0]
-            lam[c], mu[c] = lame_from_speeds(solid[0], solid[1], solid[2])
+    fl = md.cell_domain == FLUID
+    ls, ms = lame_from_speeds(solid[0], solid[1], solid[2])
+    rho = np.where(fl, fluid[0], solid[0]).astype(np.float64)
+    kappa = np.where(fl, fluid[0] * fluid[1] ** 2, 0.0)
+    lam = np.where(fl, 0.0, ls)
+    mu = np.where(fl, 0.0, ms)
     return rho, lam, mu, kappa
 
 
@@ -197,18 +212,15 @@ def random_field_media(md: MeshData, seeds=(1, 2), base=(2.5, 3.0, 1.7), amp=0.2
     cen = md.centroids_approx()
     a = g1(cen[:, 0], cen[:, 1])
     b = g2(cen[:, 0], cen[:, 1])
-    nc = md.n_cells
-    rho = np.empty(nc); lam = np.zeros(nc); mu = np.zeros(nc); kappa = np.zeros(nc)
-    for c in range(nc):
-        if md.cell_domain[c] == FLUID:
-            rho[c] = fluid[0]
-            kappa[c] = fluid[0] * fluid[1] ** 2
-        else:
-            r = base[0] * (1.0 + amp * b[c])
-            vp = base[1] * (1.0 + amp * a[c])
-            vs = base[2] * (1.0 + amp * a[c])
-            rho[c] = r
-            lam[c], mu[c] = lame_from_speeds(r, vp, vs)
+    fl = md.cell_domain == FLUID
+    r = base[0] * (1.0 + amp * b)
+    vp = base[1] * (1.0 + amp * a)
+    vs = base[2] * (1.0 + amp * a)
+    ls, ms = lame_from_speeds(r, vp, vs)
+    rho = np.where(fl, fluid[0], r)
+    kappa = np.where(fl, fluid[0] * fluid[1] ** 2, 0.0)
+    lam = np.where(fl, 0.0, ls)
+    mu = np.where(fl, 0.0, ms)
     return rho, lam, mu, kappa
 
 
@@ -250,6 +262,18 @@ def academic_c1():
     rec = receivers_on_line(8, 0.0, 1.0, 0.5)
     return dict(mesh=md, media=media, k=1, tableau="erk4", nsteps=200, cfl_star=0.265,
                 h=1.0 / 16, c_max=3.0, source=src, f0=10.0, receivers=rec)
+
+
+def hybrid_c3(n_shots, nx=1360, ny=680, k=3):
+    """[0,2]x[0,1]: squares below y = 0.7, each split into two triangles above
+    (647,360 quads + 554,880 triangles at 1360x680); solid below y = 0.5 with
+    the seeded random field (seeds 1, 2), water above; n_shots Ricker point
+    forces at seeded solid points (seed 100 + shot); 256 receivers at y = 0.75."""
+    md = hybrid_grid(nx, ny, 0.0, 2.0, 0.0, 1.0, 0.7, 0.5)
+    media = random_field_media(md, seeds=(1, 2))
+    srcs = [seeded_point(100 + s, 0.0, 2.0, 0.0, 0.5) for s in range(n_shots)]
+    rec = receivers_on_line(256, 0.0, 2.0, 0.75)
+    return dict(mesh=md, media=media, k=k, sources=srcs, f0=10.0, receivers=rec, h=1.0 / ny)
 
 
 def bilayer_c2(nx=1024, ny=512, k=2):
