@@ -133,6 +133,18 @@ int hho_operators_build(const hho_mesh* mesh, int32_t k,
                         const double* h_rho, const double* h_lambda, const double* h_mu,
                         const double* h_kappa, const hho_params* params, hho_ops** out);
 
+/* As hho_operators_build, with the stabilisation weights given per cell in
+ * h_tau (n_cells values, > 0) instead of derived from the materials.  With
+ * h_tau = NULL it is hho_operators_build.  Used to evaluate gradients and
+ * finite differences with the stabilisation frozen (see hho_adjoint_vjp). */
+int hho_operators_build_tau(const hho_mesh* mesh, int32_t k, const double* h_rho, const double* h_lambda,
+                            const double* h_mu, const double* h_kappa, const hho_params* params,
+                            const double* h_tau, hho_ops** out);
+
+/* Writes the per-cell stabilisation weights tau used by ops (n_cells values,
+ * input cell order) into h_tau. */
+int hho_ops_tau(const hho_ops* ops, double* h_tau);
+
 void hho_ops_destroy(hho_ops* ops);
 
 typedef struct {
@@ -321,6 +333,20 @@ int hho_profile_read(hho_ops* ops, double* ms_stage_total, int64_t* n_launches);
  * serialised by the caller.  Nothing in the array needs to start at zero. */
 #define HHO_ENERGY_STATIC_MAX_CELLS (65536LL * 256LL)
 int hho_energy_static(hho_ops* ops, const double* d_state, double* d_energy, void* stream);
+
+/* Empirical CFL bracketing, Algorithm 1 of Sec. 5.1, on the GPU stage.
+ * Starting from N = N0 steps over [0, T_f] (dt = T_f / N), each trial copies
+ * d_state0 into the scratch d_state and steps without sources, reading the
+ * energy after every step.  A trial is unstable at the first step whose
+ * energy exceeds (1 + eps) E^0 or (1 + eps) E^{n-1} (read as the signed
+ * relative increase), or is not finite.  After a stable trial, N decreases by
+ * max(1, floor(delta N)).  *n_stable receives the last stable N (-1 if N0 is
+ * unstable) and *n_unstable the first unstable N (-1 if none within
+ * max_trials).  d_state: n_state doubles; d_work: hho_work_size(tab) doubles.
+ * Synchronises the stream after every step. */
+int hho_cfl_bracket(hho_ops* ops, const hho_tableau* tab, const double* d_state0, double T_f, int64_t N0,
+                    double eps, double delta, int64_t max_trials, double* d_state, double* d_work,
+                    int64_t* n_stable, int64_t* n_unstable, void* stream);
 
 /* CFL-limited step (Eq. CFL): dt = safety * cfl_star * h_min / c_max, with
  * h_min the shortest cell edge and c_max the largest wave speed. */

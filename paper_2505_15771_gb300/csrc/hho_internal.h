@@ -108,7 +108,30 @@ struct StageArgsT {
     T shot_src_w;
 };
 
-enum { MODE_TRACES = 0, MODE_STAGE = 1, MODE_APPLY = 2 };
+// MODE_RAW writes the rate before the per-cell material factors (and, in
+// solids, before the stress mixing): the derivative of the rate with respect
+// to those factors, used by the adjoint gradient.
+enum { MODE_TRACES = 0, MODE_STAGE = 1, MODE_APPLY = 2, MODE_RAW = 3 };
+
+// ERK plan (stage.cu): row i of the extended tableau (a_{s+1,:} = b) is the
+// partial sum P_i = U^{n-1} + dt sum_j a_ij k_j.
+enum { SRC_ZERO = -3, SRC_STATE = -2, SRC_X = -1 };   // >= 0: row buffer index
+struct TargetPlan {
+    int src, dst;
+    double a;
+};
+struct StagePlan {
+    int n_tgt;
+    TargetPlan t[MAX_TARGETS];
+};
+int build_plan(const hho_tableau* tab, std::vector<StagePlan>& plan, int* n_buf);
+
+// Launches one stage-kernel pass (FP64) over n_shots shots; and the receiver
+// kernel.  Defined in stage.cu, used by the adjoint driver.
+struct hho_ops;
+void launch_stage_f64(const hho_ops* ops, int mode, StageArgsT<double>& a, int n_shots, double t_src, void* stream);
+void launch_record_f64(const hho_ops* ops, const double* state, double* out, void* stream);
+int check_cuda(const char* what);
 
 struct hho_ops {
     int32_t k = 0, n = 0, f = 0;
@@ -162,6 +185,10 @@ struct hho_ops {
     int64_t host_work_size = 0;
     int64_t n_state = 0;
     int64_t trace_doubles = 0;    // one trace buffer (fluid + solid parts)
+    // adjoint support: interface coefficients of the operator with the
+    // coupling sign reversed, and per-class M0^-1 (n x n each)
+    double* d_if_coef_adj = nullptr;
+    double* d_cls_minv = nullptr;
     // host copies for the cost model
     std::vector<double> h_cls_dbl;
     std::vector<int32_t> h_cls_int, h_nb_f, h_nb_s;

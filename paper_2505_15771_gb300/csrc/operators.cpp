@@ -203,6 +203,21 @@ extern "C" int hho_tableau_erk(int32_t s, hho_tableau* t) {
 extern "C" int hho_operators_build(const hho_mesh* m, int32_t k, const double* rho, const double* lam,
                                    const double* mu, const double* kappa, const hho_params* params,
                                    hho_ops** out) {
+    return hho_operators_build_tau(m, k, rho, lam, mu, kappa, params, nullptr, out);
+}
+
+extern "C" int hho_ops_tau(const hho_ops* ops, double* h_tau) {
+    if (!ops || !h_tau) {
+        hho_set_error("hho_ops_tau: null pointer");
+        return HHO_EINVAL;
+    }
+    memcpy(h_tau, ops->tau.data(), sizeof(double) * ops->nc);
+    return HHO_OK;
+}
+
+extern "C" int hho_operators_build_tau(const hho_mesh* m, int32_t k, const double* rho, const double* lam,
+                                       const double* mu, const double* kappa, const hho_params* params,
+                                       const double* h_tau, hho_ops** out) {
     if (!m || !rho || !lam || !mu || !kappa || !out) {
         hho_set_error("hho_operators_build: null pointer");
         return HHO_EINVAL;
@@ -242,6 +257,13 @@ extern "C" int hho_operators_build(const hho_mesh* m, int32_t k, const double* r
             cmax[c] = cp;
         }
         if (P.tau_over_k) tau[c] /= k;
+        if (h_tau) {
+            if (!(h_tau[c] > 0.0)) {
+                hho_set_error("hho_operators_build_tau: tau[%lld] = %g must be positive", (long long)c, h_tau[c]);
+                return HHO_EINVAL;
+            }
+            tau[c] = h_tau[c];
+        }
     }
 
     hho_ops* ops = new (std::nothrow) hho_ops();
@@ -303,8 +325,13 @@ extern "C" int hho_operators_build(const hho_mesh* m, int32_t k, const double* r
             return HHO_EMESH;
         }
         ops->class_M0inv[cl] = M0inv;
+        // Class block: M0 (n x n, padded to a multiple of 4 entries), then per
+        // face [nx, ny, 0, 0 | Tr rows of nP | Lift rows of fP] with nP, fP the
+        // row lengths n, f rounded up to multiples of 4, so that every row
+        // starts on a 16-byte boundary (vector loads in the kernels).
         cls_doff[cl] = (int32_t)cls_dbl.size();
         for (double v : M0) cls_dbl.push_back(v);
+        while (cls_dbl.size() % 4) cls_dbl.push_back(0.0);
         for (int j = 0; j < nv; ++j) {
             int j1 = (j + 1) % nv;
             double ex = X[j1] - X[j], ey = Y[j1] - Y[j];
@@ -339,10 +366,21 @@ extern "C" int hho_operators_build(const hho_mesh* m, int32_t k, const double* r
             double tmax = 0.0, lmax = 0.0;
             for (double v : Tr) tmax = std::max(tmax, std::fabs(v));
             for (double v : Lift) lmax = std::max(lmax, std::fabs(v));
+            const int nP = (n + 3) / 4 * 4, fP = (f + 3) / 4 * 4;
             cls_dbl.push_back(nx);
             cls_dbl.push_back(ny);
-            for (double v : Tr) cls_dbl.push_back(std::fabs(v) < 1e-13 * tmax ? 0.0 : v);
-            for (double v : Lift) cls_dbl.push_back(std::fabs(v) < 1e-13 * lmax ? 0.0 : v);
+            cls_dbl.push_back(0.0);
+            cls_dbl.push_back(0.0);
+            for (int l = 0; l < f; ++l)
+                for (int i = 0; i < nP; ++i) {
+                    const double v = i < n ? Tr[l * n + i] : 0.0;
+                    cls_dbl.push_back(std::fabs(v) < 1e-13 * tmax ? 0.0 : v);
+                }
+            for (int i = 0; i < n; ++i)
+                for (int l = 0; l < fP; ++l) {
+                    const double v = l < f ? Lift[i * f + l] : 0.0;
+                    cls_dbl.push_back(std::fabs(v) < 1e-13 * lmax ? 0.0 : v);
+                }
         }
     }
 
@@ -357,8 +395,9 @@ extern "C" int hho_operators_build(const hho_mesh* m, int32_t k, const double* r
     for (int cl = 0; cl < NCL; ++cl) {
         if (cls_nf[cl] != 4) continue;
         const double want[4][2] = {{0.0, -1.0}, {1.0, 0.0}, {0.0, 1.0}, {-1.0, 0.0}};
-        const double* cd = &cls_dbl[cls_doff[cl] + n * n];
-        const int FS = 2 + 2 * f * n;
+        const int nP = (n + 3) / 4 * 4, fP = (f + 3) / 4 * 4;
+        const double* cd = &cls_dbl[cls_doff[cl] + (n * n + 3) / 4 * 4];
+        const int FS = 4 + f * nP + n * fP;
         bool ok = true;
         for (int j = 0; j < 4 && ok; ++j) {
             const double* fm = cd + j * FS;
@@ -368,8 +407,8 @@ extern "C" int hho_operators_build(const hho_mesh* m, int32_t k, const double* r
                     int e = (j % 2 == 0) ? EA[i] : EB[i];
                     bool tr_nz = e >= l && ((e - l) % 2) == 0;
                     bool li_nz = ((e + l) % 2) == 0;
-                    if (!tr_nz && fm[2 + l * n + i] != 0.0) ok = false;
-                    if (!li_nz && fm[2 + f * n + i * f + l] != 0.0) ok = false;
+                    if (!tr_nz && fm[4 + l * nP + i] != 0.0) ok = false;
+                    if (!li_nz && fm[4 + f * nP + i * fP + l] != 0.0) ok = false;
                 }
         }
         if (ok) cls_kind[cl] = KIND_RECT;
@@ -465,7 +504,7 @@ extern "C" int hho_operators_build(const hho_mesh* m, int32_t k, const double* r
     std::vector<int32_t> nb_f(SF, NB_BOUNDARY), nb_s(SS, NB_BOUNDARY);
     std::vector<double> beta_f(SF, 0.0), beta_s(SS, 0.0);
     std::vector<int32_t> if_nb;
-    std::vector<double> if_coef;
+    std::vector<double> if_coef, if_coef_adj;
     for (int64_t c = 0; c < nc; ++c) {
         int64_t b = m->cell_ptr[c];
         int nv = (int)(m->cell_ptr[c + 1] - b);
@@ -502,6 +541,14 @@ extern "C" int hho_operators_build(const hho_mesh* m, int32_t k, const double* r
                 hho_ops_destroy(ops);
                 return HHO_EMATERIAL;
             }
+            // the adjoint operator reverses the sign of the coupling block
+            double Amt[9] = {tau[cf], -nx, -ny, nx, tau[cs], 0.0, ny, 0.0, tau[cs]};
+            double Ait[9];
+            inverse3(Amt, Ait);
+            if (d == 0)
+                for (double v : {Ait[0], Ait[1], Ait[2], 0.0, 0.0, 0.0}) if_coef_adj.push_back(v);
+            else
+                for (double v : {Ait[4], Ait[5], Ait[7], Ait[8], Ait[3], Ait[6]}) if_coef_adj.push_back(v);
             int32_t r = (int32_t)if_nb.size();
             if_nb.push_back(other);
             if (d == 0)   // fluid side: p_F = a w_f + b_x w_sx + b_y w_sy
@@ -582,6 +629,13 @@ extern "C" int hho_operators_build(const hho_mesh* m, int32_t k, const double* r
     D.beta_f_f32 = dev_upload(ops, to_f32(beta_f), &err);
     D.beta_s_f32 = dev_upload(ops, to_f32(beta_s), &err);
     D.if_coef_f32 = dev_upload(ops, to_f32(if_coef), &err);
+    ops->d_if_coef_adj = dev_upload(ops, if_coef_adj, &err);
+    {
+        std::vector<double> minv;
+        for (int cl = 0; cl < NCL; ++cl)
+            for (double v : ops->class_M0inv[cl]) minv.push_back(v);
+        ops->d_cls_minv = dev_upload(ops, minv, &err);
+    }
     ops->d_dev2orig = dev_upload(ops, dev2orig, &err);
     ops->d_canon_off = dev_upload(ops, ops->canon_off, &err);
     ops->d_mass_f = dev_upload(ops, mass_f, &err);

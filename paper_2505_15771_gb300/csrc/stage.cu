@@ -52,7 +52,36 @@ template <int K>
 struct Dims {
     static constexpr int n = (K + 1) * (K + 2) / 2;
     static constexpr int f = K + 1;
-    static constexpr int FS = 2 + 2 * f * n;   // per-face stride in the class block
+    static constexpr int nP = (n + 3) / 4 * 4;            // padded row lengths (16-byte rows)
+    static constexpr int fP = (f + 3) / 4 * 4;
+    static constexpr int M0P = (n * n + 3) / 4 * 4;       // class mass block, padded
+    static constexpr int FS = 4 + f * nP + n * fP;        // per-face stride: [nx ny 0 0 | Tr | Lift]
+    static constexpr int TR = 4;                          // offset of Tr in a face block
+    static constexpr int LI = 4 + f * nP;                 // offset of Lift
+};
+
+// 16-byte vector loads of class-matrix rows (two doubles or four floats).
+template <class T>
+struct Vec16;
+template <>
+struct Vec16<double> {
+    static constexpr int w = 2;
+    __device__ static void load(const double* p, double* o) {
+        const double2 v = __ldg(reinterpret_cast<const double2*>(p));
+        o[0] = v.x;
+        o[1] = v.y;
+    }
+};
+template <>
+struct Vec16<float> {
+    static constexpr int w = 4;
+    __device__ static void load(const float* p, float* o) {
+        const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+        o[0] = v.x;
+        o[1] = v.y;
+        o[2] = v.z;
+        o[3] = v.w;
+    }
 };
 
 // Operator data in the arithmetic type T (FP64, or its FP32 copy).
@@ -150,29 +179,46 @@ struct RectFace {
     __host__ __device__ static constexpr bool lift_nz(int i, int l) { return ((e(i) + l) % 2) == 0; }
 };
 
-// y[l] = sum_i Tr[l][i] x[i] over the policy's pattern.
+// y[l] = sum_i Tr[l][i] x[i] over the policy's pattern.  Each row is read in
+// 16-byte chunks; a chunk with no entry in the pattern is not loaded.
 template <class T, int K, class P>
 __device__ __forceinline__ void trace_apply(const T* __restrict__ Tr, const T* x, T* y) {
-    constexpr int n = Dims<K>::n, f = Dims<K>::f;
+    constexpr int n = Dims<K>::n, f = Dims<K>::f, nP = Dims<K>::nP, w = Vec16<T>::w;
 #pragma unroll
     for (int l = 0; l < f; ++l) {
+        T row[nP];
+#pragma unroll
+        for (int c0 = 0; c0 < nP; c0 += w) {
+            bool need = false;
+#pragma unroll
+            for (int e = 0; e < w; ++e) need = need || (c0 + e < n && P::tr_nz(l, c0 + e));
+            if (need) Vec16<T>::load(Tr + l * nP + c0, row + c0);
+        }
         T acc = T(0);
 #pragma unroll
         for (int i = 0; i < n; ++i)
-            if (P::tr_nz(l, i)) acc = fma(__ldg(Tr + l * n + i), x[i], acc);
+            if (P::tr_nz(l, i)) acc = fma(row[i], x[i], acc);
         y[l] = acc;
     }
 }
-// y[i] = sum_l L[i][l] j[l] over the policy's pattern.
+// y[i] = sum_l L[i][l] j[l] over the policy's pattern (rows of fP entries).
 template <class T, int K, class P>
 __device__ __forceinline__ void lift_apply(const T* __restrict__ L, const T* j, T* y) {
-    constexpr int n = Dims<K>::n, f = Dims<K>::f;
+    constexpr int n = Dims<K>::n, f = Dims<K>::f, fP = Dims<K>::fP, w = Vec16<T>::w;
 #pragma unroll
     for (int i = 0; i < n; ++i) {
+        T row[fP];
+#pragma unroll
+        for (int c0 = 0; c0 < fP; c0 += w) {
+            bool need = false;
+#pragma unroll
+            for (int e = 0; e < w; ++e) need = need || (c0 + e < f && P::lift_nz(i, c0 + e));
+            if (need) Vec16<T>::load(L + i * fP + c0, row + c0);
+        }
         T acc = T(0);
 #pragma unroll
         for (int l = 0; l < f; ++l)
-            if (P::lift_nz(i, l)) acc = fma(__ldg(L + i * f + l), j[l], acc);
+            if (P::lift_nz(i, l)) acc = fma(row[l], j[l], acc);
         y[i] = acc;
     }
 }
@@ -285,7 +331,7 @@ __device__ __forceinline__ void fluid_face_rate(const StageArgsT<T>& A, const Ce
         }
     }
     T lv[n];
-    lift_apply<T, K, P>(fm + 2 + f * n, jmp, lv);
+    lift_apply<T, K, P>(fm + Dims<K>::LI, jmp, lv);
     if constexpr (P::rect) {
         axpy_sign<P::NX, n>(lv, kmx);
         axpy_sign<P::NY, n>(lv, kmy);
@@ -307,7 +353,7 @@ __device__ __forceinline__ void fluid_face_trace(const StageArgsT<T>& A, const C
     constexpr int n = Dims<K>::n, f = Dims<K>::f, FS = Dims<K>::FS;
     const DevOps& op = A.op;
     const T* fm = c.cd + j * FS;
-    const T* Tr = fm + 2;
+    const T* Tr = fm + Dims<K>::TR;
     const T* mx = U;
     const T* my = U + n;
     const T* p = U + 2 * n;
@@ -348,7 +394,7 @@ __device__ __forceinline__ void fluid_cell(const StageArgsT<T>& A, int q, int sh
     c.nF = __ldg(ci + CI_NF);
     c.npad = __ldg(ci + CI_NPAD);
     c.sbase = __ldg(ci + CI_SLOT);
-    c.cd = OpData<T>::cls(op) + __ldg(ci + CI_DOFF) + n * n;
+    c.cd = OpData<T>::cls(op) + __ldg(ci + CI_DOFF) + Dims<K>::M0P;
     c.N = op.Nf;
     c.SF = op.SF;
     c.SS = op.SS;
@@ -403,6 +449,12 @@ __device__ __forceinline__ void fluid_cell(const StageArgsT<T>& A, int q, int sh
 #pragma unroll
             for (int i = 0; i < n; ++i) kp[i] = fma(w, g[i], kp[i]);
         }
+        if constexpr (MODE == MODE_RAW) {
+            T* dst = A.tgt[0].dst + soff;
+#pragma unroll
+            for (int i = 0; i < 3 * n; ++i) dst[(size_t)i * c.N + q] = U[i];
+            return;
+        }
         const T sc[3] = {Am, Ap, T(0)};
         write_targets<3 * n, FluidGroups<n>>(A, c.N, soff, q, U, sc);
         if constexpr (MODE == MODE_APPLY) return;
@@ -456,7 +508,7 @@ __device__ __forceinline__ void solid_face_rate(const StageArgsT<T>& A, const Ce
             jy[l] = (l & 1) ? fma(-b1, wf, jy[l]) : fma(b1, wf, jy[l]);
         }
     }
-    const T* L = fm + 2 + f * n;
+    const T* L = fm + Dims<K>::LI;
     T lx[n], ly[n];
     lift_apply<T, K, P>(L, jx, lx);
     lift_apply<T, K, P>(L, jy, ly);
@@ -487,7 +539,7 @@ __device__ __forceinline__ void solid_face_trace(const StageArgsT<T>& A, const C
     constexpr int n = Dims<K>::n, f = Dims<K>::f, FS = Dims<K>::FS;
     const DevOps& op = A.op;
     const T* fm = c.cd + j * FS;
-    const T* Tr = fm + 2;
+    const T* Tr = fm + Dims<K>::TR;
     const T* sxx = U;
     const T* syy = U + n;
     const T* sxy = U + 2 * n;
@@ -559,7 +611,7 @@ __device__ __forceinline__ void solid_cell(const StageArgsT<T>& A, int q, int sh
     c.nF = __ldg(ci + CI_NF);
     c.npad = __ldg(ci + CI_NPAD);
     c.sbase = __ldg(ci + CI_SLOT);
-    c.cd = OpData<T>::cls(op) + __ldg(ci + CI_DOFF) + n * n;
+    c.cd = OpData<T>::cls(op) + __ldg(ci + CI_DOFF) + Dims<K>::M0P;
     c.N = op.Ns;
     c.SF = op.SF;
     c.SS = op.SS;
@@ -608,11 +660,13 @@ __device__ __forceinline__ void solid_cell(const StageArgsT<T>& A, int q, int sh
         }
         // stress rate = C e = c1 [(e_xx + r e_yy), (e_yy + r e_xx)], c3 e_xy; c1, c3 folded into targets
         const T r = __ldg(OpData<T>::scal_s(op) + SS_R * c.N + q);
+        if constexpr (MODE != MODE_RAW) {
 #pragma unroll
-        for (int i = 0; i < n; ++i) {
-            const T a = exx[i], b = eyy[i];
-            exx[i] = fma(r, b, a);
-            eyy[i] = fma(r, a, b);
+            for (int i = 0; i < n; ++i) {
+                const T a = exx[i], b = eyy[i];
+                exx[i] = fma(r, b, a);
+                eyy[i] = fma(r, a, b);
+            }
         }
         const T Av = __ldg(OpData<T>::scal_s(op) + SS_AV * c.N + q);
         for (int s = 0; s < A.n_src; ++s) {
@@ -634,6 +688,12 @@ __device__ __forceinline__ void solid_cell(const StageArgsT<T>& A, int q, int sh
                 kvx[i] = fma(w, g[i], kvx[i]);
                 kvy[i] = fma(w, g[n + i], kvy[i]);
             }
+        }
+        if constexpr (MODE == MODE_RAW) {
+            T* dst = A.tgt[0].dst + soff;
+#pragma unroll
+            for (int i = 0; i < 5 * n; ++i) dst[(size_t)i * c.N + q] = U[i];
+            return;
         }
         const T sc[3] = {__ldg(OpData<T>::scal_s(op) + SS_C1 * c.N + q), __ldg(OpData<T>::scal_s(op) + SS_C3 * c.N + q), Av};
         write_targets<5 * n, SolidGroups<n>>(A, c.N, soff, q, U, sc);
@@ -815,20 +875,7 @@ void launch_k(int k, const StageArgsT<T>& a, dim3 grid, cudaStream_t s) {
     else stage_kernel<T, 3, MODE><<<grid, 128, 0, s>>>(a);
 }
 
-// ---- ERK schedule ---------------------------------------------------------------
-// Row i of the extended tableau (a_{s+1,:} = b) is the partial sum
-// P_i = U^{n-1} + dt sum_j a_ij k_j.  Stage j computes k_j from P_j and
-// updates every later row with a nonzero a_ij; row j+1 becomes the next input.
-enum { SRC_ZERO = -3, SRC_STATE = -2, SRC_X = -1 };   // >= 0: row buffer index
-
-struct TargetPlan {
-    int src, dst;   // SRC_* / buffer index; dst SRC_STATE = d_state, SRC_X = stage buffer
-    double a;       // tableau coefficient (times dt at launch)
-};
-struct StagePlan {
-    int n_tgt;
-    TargetPlan t[MAX_TARGETS];
-};
+}  // namespace
 
 int build_plan(const hho_tableau* tab, std::vector<StagePlan>& plan, int* n_buf) {
     const int s = tab->s;
@@ -863,6 +910,8 @@ int build_plan(const hho_tableau* tab, std::vector<StagePlan>& plan, int* n_buf)
     *n_buf = nb;
     return HHO_OK;
 }
+
+namespace {
 
 int64_t n_energy_blocks(const hho_ops* ops) { return ((int64_t)ops->dev.Nf + ops->dev.Ns + 255) / 256 + 1; }
 
@@ -1354,6 +1403,66 @@ extern "C" int hho_erk_run_host(hho_ops* ops, const hho_tableau* tab, double t0,
     return HHO_OK;
 }
 
+extern "C" int hho_cfl_bracket(hho_ops* ops, const hho_tableau* tab, const double* d_state0, double T_f,
+                               int64_t N0, double eps, double delta, int64_t max_trials, double* d_state,
+                               double* d_work, int64_t* n_stable, int64_t* n_unstable, void* stream) {
+    if (!ops || !tab || !d_state0 || !d_state || !d_work || !n_stable || !n_unstable || !(T_f > 0.0) || N0 < 1 ||
+        !(eps > 0.0) || !(delta > 0.0) || max_trials < 1) {
+        hho_set_error("hho_cfl_bracket: bad arguments");
+        return HHO_EINVAL;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const int saved_src = ops->n_src, saved_shot = ops->n_shot_src;
+    ops->n_src = 0;        // Algorithm 1 runs without sources
+    ops->n_shot_src = 0;
+    int rc = HHO_OK;
+    int64_t N = N0, last = -1, first_unstable = -1;
+    for (int64_t trial = 0; trial < max_trials && N >= 1 && rc == HHO_OK; ++trial) {
+        const double dt = T_f / (double)N;
+        if (cudaMemcpyAsync(d_state, d_state0, sizeof(double) * ops->n_state, cudaMemcpyDeviceToDevice, st) !=
+            cudaSuccess) {
+            hho_set_error("hho_cfl_bracket: copy failed");
+            rc = HHO_ECUDA;
+            break;
+        }
+        double E0 = 0.0;
+        rc = hho_energy(ops, d_state, d_work, &E0, stream);
+        if (rc) break;
+        double Eprev = E0;
+        bool stable = true;
+        for (int64_t n = 0; n < N; ++n) {
+            rc = hho_erk_step(ops, tab, (double)n * dt, dt, 1, d_state, d_work, stream);
+            if (rc) break;
+            double E = 0.0;
+            rc = hho_energy(ops, d_state, d_work, &E, stream);
+            if (rc == HHO_EUNSTABLE) {   // non-finite energy: the trial is unstable
+                rc = HHO_OK;
+                stable = false;
+                break;
+            }
+            if (rc) break;
+            if ((E - E0) / E0 > eps || (E - Eprev) / Eprev > eps) {
+                stable = false;
+                break;
+            }
+            Eprev = E;
+        }
+        if (rc) break;
+        if (!stable) {
+            first_unstable = N;
+            break;
+        }
+        last = N;
+        int64_t dec = (int64_t)std::floor(delta * (double)N);
+        N -= dec < 1 ? 1 : dec;
+    }
+    ops->n_src = saved_src;
+    ops->n_shot_src = saved_shot;
+    *n_stable = last;
+    *n_unstable = first_unstable;
+    return rc;
+}
+
 // ---- energy without allocation ------------------------------------------------------
 // Block partial sums of hho_energy_static live in this fixed array instead of
 // a caller buffer.  Host code must not take its address directly (the host
@@ -1416,3 +1525,27 @@ extern "C" int hho_energy_static(hho_ops* ops, const double* d_state, double* d_
     sum_kernel<<<1, 256, 0, st>>>(partial, nblk, d_energy);
     return check_launch("hho_energy_static");
 }
+
+// ---- launchers for the adjoint driver (adjoint.cu) -----------------------------------
+void launch_stage_f64(const hho_ops* ops, int mode, StageArgsT<double>& a, int n_shots, double t_src, void* stream) {
+    const dim3 grid((ops->dev.Nf + ops->dev.Ns + 127) / 128, n_shots);
+    if (grid.x == 0) return;
+    a.state_stride = ops->n_state;
+    a.trace_stride = ops->trace_doubles;
+    if (mode == MODE_STAGE || mode == MODE_APPLY || mode == MODE_RAW) fill_sources<double>(ops, a, t_src, n_shots);
+    cudaStream_t st = (cudaStream_t)stream;
+    switch (mode) {
+        case MODE_TRACES: launch_k<double, MODE_TRACES>(ops->k, a, grid, st); break;
+        case MODE_STAGE: launch_k<double, MODE_STAGE>(ops->k, a, grid, st); break;
+        case MODE_APPLY: launch_k<double, MODE_APPLY>(ops->k, a, grid, st); break;
+        default: launch_k<double, MODE_RAW>(ops->k, a, grid, st); break;
+    }
+}
+
+void launch_record_f64(const hho_ops* ops, const double* state, double* out, void* stream) {
+    if (ops->n_rec == 0) return;
+    record_kernel<double><<<dim3((ops->n_rec + 63) / 64, 1), 64, 0, (cudaStream_t)stream>>>(
+        ops->dev, ops->n_rec, ops->d_rec_int, ops->d_rec_dbl, state, ops->n_state, out);
+}
+
+int check_cuda(const char* what) { return check_launch(what); }

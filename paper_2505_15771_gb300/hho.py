@@ -79,6 +79,8 @@ _SIGS = {
     "hho_profile_enable": (C.c_int, [_P, _I32]),
     "hho_profile_read": (C.c_int, [_P, C.POINTER(_D), C.POINTER(_I64)]),
     "hho_energy_static": (C.c_int, [_P, _P, _P, _P]),
+    "hho_cfl_bracket": (C.c_int, [_P, C.POINTER(Tableau), _P, _D, _I64, _D, _D, _I64, _P, _P, C.POINTER(_I64),
+                                  C.POINTER(_I64), _P]),
     "hho_batch_sizes": (C.c_int, [_P, C.POINTER(Tableau), _I32, _I32, C.POINTER(_I64), C.POINTER(_I64)]),
     "hho_batch_pack": (C.c_int, [_P, _I32, _I32, _P, _P, _P]),
     "hho_batch_unpack": (C.c_int, [_P, _I32, _I32, _P, _P, _P]),
@@ -302,3 +304,11 @@ def hho_batch_sources_set(ops, xy, direction, f0, t0, amp=1.0):
 def hho_batch_erk_step(ops, tab, n_shots, precision, t0, dt, nsteps, d_state, d_work, d_seismogram=None, stream=0):
     _check(lib().hho_batch_erk_step(ops, C.byref(tab), int(n_shots), int(precision), float(t0), float(dt),
                                     int(nsteps), d_state, d_work, d_seismogram, stream))
+
+
+def hho_cfl_bracket(ops, tab, d_state0, T_f, N0, eps, delta, max_trials, d_state, d_work, stream=0):
+    """Algorithm 1 of Sec. 5.1 on the GPU; returns (N_last_stable, N_first_unstable), -1 where absent."""
+    a, b = _I64(), _I64()
+    _check(lib().hho_cfl_bracket(ops, C.byref(tab), d_state0, float(T_f), int(N0), float(eps), float(delta),
+                                 int(max_trials), d_state, d_work, C.byref(a), C.byref(b), stream))
+    return a.value, b.value

@@ -464,3 +464,23 @@ def test_canonical_tables_hand_example():
     # canonical face 1 runs from vertex 1 to vertex 4: tangent (0,1), normal (1,0)
     _, _, L, n = M.face_geometry(m, 1)
     assert L == 1.0 and n.tolist() == [1.0, -0.0]
+
+
+def test_algorithm1_brackets_the_eigenvalue_limit():
+    """Algorithm 1 (Sec. 5.1) from random initial data: the last stable time
+    step lies within a few percent of the ERK4 eigenvalue stability limit of
+    the same operator (random data excites every mode)."""
+    from oracle import cfl as CF
+    md = synth.quad_grid(6, 3, -1.0, 1.0, 0.0, 1.0)
+    md.cell_domain = np.where(md.centroids_approx()[:, 0] < 0, 1, 0).astype(np.uint8)
+    nc = md.n_cells
+    sol = md.cell_domain == 1
+    S = system(md, 1, media=(np.ones(nc), np.where(sol, 1.0, 0.0), np.where(sol, 1.0, 0.0), np.ones(nc)))
+    st = E.Stepper(S)
+    dt_eig, _ = _stable_dt(S, 4, 1.0)
+    T_f = 300 * dt_eig
+    U0 = synth.random_state(S.nT, 8)
+    n_stable, n_unstable = CF.algorithm1(st, U0, T_f, N0=int(300 / 0.8))
+    dt_stable, dt_unstable = T_f / n_stable, T_f / n_unstable
+    assert dt_stable < dt_unstable
+    assert 0.93 * dt_eig <= dt_stable <= 1.03 * dt_eig, (dt_stable / dt_eig, dt_unstable / dt_eig)
