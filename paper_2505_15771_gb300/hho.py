@@ -61,6 +61,8 @@ _SIGS = {
     "hho_params_default": (None, [C.POINTER(Params)]),
     "hho_operators_build": (C.c_int, [_P, _I32, _P, _P, _P, _P, C.POINTER(Params), C.POINTER(_P)]),
     "hho_ops_destroy": (None, [_P]),
+    "hho_operators_build_tau": (C.c_int, [_P, _I32, _P, _P, _P, _P, C.POINTER(Params), _P, C.POINTER(_P)]),
+    "hho_ops_tau": (C.c_int, [_P, _P]),
     "hho_state_layout": (C.c_int, [_P, C.POINTER(Layout)]),
     "hho_state_pack": (C.c_int, [_P, _P, _P, _P]),
     "hho_state_unpack": (C.c_int, [_P, _P, _P, _P]),
@@ -182,6 +184,21 @@ def hho_operators_build(mesh, k, rho, lam, mu, kappa, params=None):
     out = _P()
     _check(lib().hho_operators_build(mesh, int(k), *[_ptr(a) for a in arrs], C.byref(p), C.byref(out)))
     return out
+
+
+def hho_operators_build_tau(mesh, k, rho, lam, mu, kappa, tau, params=None):
+    arrs = [_arr(a, np.float64) for a in (rho, lam, mu, kappa)]
+    t = None if tau is None else _arr(tau, np.float64)
+    p = hho_params_default() if params is None else params
+    out = _P()
+    _check(lib().hho_operators_build_tau(mesh, int(k), *[_ptr(a) for a in arrs], C.byref(p), _ptr(t), C.byref(out)))
+    return out
+
+
+def hho_ops_tau(ops, n_cells):
+    t = np.empty(n_cells, np.float64)
+    _check(lib().hho_ops_tau(ops, _ptr(t)))
+    return t
 
 
 def hho_ops_destroy(ops):
