@@ -162,6 +162,19 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- GPU run
+def replica_reduce(ms_local, units_local, world, dist=None, device=None):
+    """Whole-job timing of independent replicas: the slowest rank's time and
+    the units summed over ranks (value = units / time)."""
+    if world <= 1:
+        return ms_local, units_local
+    import torch
+    t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+    u = torch.tensor([units_local], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 def measured_traffic(k, cell_dofs):
     """DRAM bytes per stage launch from the committed ncu summary, if it was
     taken on the current stage kernel source (same sha256) and the same k;
@@ -323,12 +336,9 @@ def main():
     stage_ms, n_launch = hho.hho_profile_read(P.ops)
     hho.hho_profile_enable(P.ops, False)
     e_end = P.energy(state)
-    if world > 1:
-        t = torch.tensor([ms], device=P.dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
     per_rank_units = ndof * a.stages * a.steps
-    value = world * per_rank_units / (ms * 1e-3)
+    ms, total_units = replica_reduce(ms, per_rank_units, world, dist, P.dev)
+    value = total_units / (ms * 1e-3)
 
     # roofline of the stage kernel
     fp64_ops, bytes_min, bytes_kernel = hho.hho_stage_cost(P.ops, tab)

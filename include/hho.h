@@ -270,6 +270,32 @@ int hho_batch_erk_step(hho_ops* ops, const hho_tableau* tab, int32_t n_shots, in
                        double dt, int64_t nsteps, void* d_state, void* d_work, void* d_seismogram, void* stream);
 
 /* ------------------------------------------------------------------------- */
+/* Discrete adjoint (vector-Jacobian product of the receiver traces).         */
+/* ------------------------------------------------------------------------- */
+
+/* Doubles of device work that hho_adjoint_vjp needs: checkpoints every
+ * checkpoint_every steps, the stage values of one segment, the ERK work
+ * buffer and a few state-sized vectors. */
+int hho_adjoint_work_size(const hho_ops* ops, const hho_tableau* tab, int64_t nsteps, int64_t checkpoint_every,
+                          int64_t* n_doubles);
+
+/* Reverse mode through nsteps ERK steps (Eq. ERK_compact / Eq. ex_solve)
+ * from the device state d_state0 at time t0, with the sources and receivers
+ * set on ops.  d_cotangent (device, [nsteps][n_rec][5]) is dL/d of the
+ * traces that hho_erk_step_record writes after every step.  Outputs:
+ *   h_grad_cell[4 c + (0,1,2,3)] = dL/d(rho, kappa, lambda, mu) of cell c
+ *     (input order; kappa only in fluid cells, lambda and mu only in solid
+ *     cells), with the stabilisation weights tau held at their current values;
+ *   h_grad_wavelet (may be NULL): [nsteps][s][n_src] dL/dw at every stage time
+ *     t_{n-1} + c_j dt of every hho_sources_set source.
+ * The adjoint uses A^T = S M A' M^-1 S (S: sign flip of the dual fields, A':
+ * the stage operator with the interface coupling reversed) on the forward
+ * kernels; segments between checkpoints are recomputed.  Synchronises. */
+int hho_adjoint_vjp(hho_ops* ops, const hho_tableau* tab, double t0, double dt, int64_t nsteps,
+                    int64_t checkpoint_every, const double* d_state0, const double* d_cotangent, double* d_work,
+                    int64_t work_doubles, double* h_grad_cell, double* h_grad_wavelet, void* stream);
+
+/* ------------------------------------------------------------------------- */
 /* Sensors and energy (Sec. 5).                                               */
 /* ------------------------------------------------------------------------- */
 

@@ -60,6 +60,20 @@ def compliance(lam: float, mu: float, S: np.ndarray) -> np.ndarray:
     return (S - beta * np.trace(S) * np.eye(2)) / (2.0 * mu)
 
 
+def compliance_dlam(lam: float, mu: float, S: np.ndarray) -> np.ndarray:
+    """d/dlambda of compliance(lam, mu, S): -(dbeta/dlam) tr(S) I / (2 mu),
+    dbeta/dlam = mu / (2 (lam+mu)^2)."""
+    dbeta = mu / (2.0 * (lam + mu) ** 2)
+    return -dbeta * np.trace(S) * np.eye(2) / (2.0 * mu)
+
+
+def compliance_dmu(lam: float, mu: float, S: np.ndarray) -> np.ndarray:
+    """d/dmu of compliance(lam, mu, S), dbeta/dmu = -lam / (2 (lam+mu)^2)."""
+    beta = lam / (2.0 * (lam + mu))
+    dbeta = -lam / (2.0 * (lam + mu) ** 2)
+    return -dbeta * np.trace(S) * np.eye(2) / (2.0 * mu) - (S - beta * np.trace(S) * np.eye(2)) / (2.0 * mu ** 2)
+
+
 def sym_grad_coef(c: int, d: int, q: int) -> float:
     """grad_sym(phi e_d) : E_c = sum_q coef * d_q phi; returns the coef for q."""
     G = np.zeros((2, 2))
@@ -72,7 +86,7 @@ class System:
 
     def __init__(self, mesh: mmesh.Mesh, k: int, rho, lam, mu, kappa,
                  eta_f: float = 0.8, eta_s: float = 1.5, stab_speed: str = "cp",
-                 tau_over_k: bool = False):
+                 tau_over_k: bool = False, tau_override=None):
         if k < 1 or k > 3:
             raise ValueError("k must be 1, 2 or 3")
         self.mesh = mesh
@@ -102,6 +116,10 @@ class System:
                 tau[c] = eta_s * self.rho[c] * cs
             if tau_over_k:
                 tau[c] /= k
+        if tau_override is not None:
+            # stabilisation weights given explicitly (held fixed, e.g. while
+            # differentiating with respect to the materials)
+            tau = np.array(tau_override, dtype=np.float64)
         self.tau = tau
 
         n, f = self.n, self.f

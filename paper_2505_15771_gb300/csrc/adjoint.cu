@@ -1,0 +1,483 @@
+// Discrete adjoint of the ERK time stepping (vector-Jacobian product of the
+// receiver traces with respect to the materials and the source wavelet).
+//
+// Forward: k_i = A Y_i + w(t_i) g (A = -M^-1 K_cond, Eq. ex_solve), Y_i the
+// stage values of Eq. ERK_compact, U^n = U^{n-1} + dt sum_i b_i k_i, and the
+// traces d^n = R U^n (hho_record after every step).
+// Backward, for a cotangent G^n = dL/dd^n: lambda^n += R^T G^n, then for the
+// stages in reverse order
+//     mu_i = dt (b_i lambda^n + sum_{l>i} a_li nu_l),   nu_i = A^T mu_i,
+//     lambda^{n-1} = lambda^n + sum_i nu_i,
+//     dL/dtheta += mu_i^T dk_i/dtheta,   dL/dw(t_i) += mu_i^T g.
+// A^T is applied without a transposed kernel: the block structure of the
+// paper's system (Sec. 3.3) gives A^T = S M A' M^-1 S, where S flips the
+// signs of the dual fields (m, s) and A' is the same operator with the sign
+// of the interface coupling block reversed.  So A^T = mass kernel, forward
+// stage kernel on A' (traces + apply), mass kernel.
+//
+// Parameters: the per-cell factors of the inverse mass, theta = (1/(rho h),
+// kappa/h) in fluid cells and ((lambda+2mu)/h, lambda/(lambda+2mu), mu/h,
+// 1/(rho h)) in solid cells; dk/dtheta is the raw rate (MODE_RAW).  The
+// stabilisation weights tau (and with them the face coefficients) are held
+// fixed: the gradient is that of the discrete scheme with tau frozen at the
+// current model.  The host maps dL/dtheta to dL/d(rho, kappa, lambda, mu).
+//
+// Checkpointing: U is stored every `checkpoint_every` steps in the forward
+// pass; each segment is recomputed, keeping its stage values, before its
+// backward sweep.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "hho_internal.h"
+
+namespace {
+
+// out = S M in (inverse = false) or S M^-1 in (inverse = true); S = -1 on the
+// dual fields (m_x, m_y / s_xx, s_yy, s_xy), +1 on the primal fields.
+__global__ void mass_kernel(DevOps op, const double* __restrict__ mass_f, const double* __restrict__ mass_s,
+                            const double* __restrict__ cls_minv, const double* __restrict__ in,
+                            double* __restrict__ out, int inverse) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= op.Nf + op.Ns) return;
+    const bool fl = g < op.Nf;
+    const int q = fl ? g : g - op.Nf;
+    const int n = op.n;
+    const int cls = op.warp_class[(fl ? 0 : op.n_warps_f) + (q >> 5)];
+    const int* ci = op.cls_int + cls * CI_STRIDE;
+    if (q - ci[CI_START] >= ci[CI_COUNT]) return;
+    const double* Mat = inverse ? cls_minv + (size_t)cls * n * n : op.cls_dbl + ci[CI_DOFF];
+    const int N = fl ? op.Nf : op.Ns;
+    const size_t off = fl ? 0 : (size_t)3 * n * op.Nf;
+    const double* x = in + off;
+    double* y = out + off;
+    double u[10], r[10];
+    auto matvec = [&](int field) {
+        for (int i = 0; i < n; ++i) u[i] = x[(size_t)(field * n + i) * N + q];
+        for (int i = 0; i < n; ++i) {
+            double s = 0.0;
+            for (int j = 0; j < n; ++j) s = fma(Mat[i * n + j], u[j], s);
+            r[i] = s;
+        }
+    };
+    if (fl) {
+        const double cm = inverse ? 1.0 / mass_f[q] : mass_f[q];               // rho h^2
+        const double cp = inverse ? 1.0 / mass_f[N + q] : mass_f[N + q];       // h^2 / kappa
+        for (int fld = 0; fld < 3; ++fld) {
+            matvec(fld);
+            const double c = fld < 2 ? -cm : cp;                               // S: m negated
+            for (int i = 0; i < n; ++i) y[(size_t)(fld * n + i) * N + q] = c * r[i];
+        }
+    } else {
+        // s block: (h^2 D) (x) M0 with D = [[d0, d1, 0], [d1, d0, 0], [0, 0, d2]]
+        double d0 = mass_s[q], d1 = mass_s[N + q], d2 = mass_s[2 * N + q];
+        const double rv = inverse ? 1.0 / mass_s[3 * N + q] : mass_s[3 * N + q];
+        if (inverse) {
+            const double det = d0 * d0 - d1 * d1;
+            const double e0 = d0 / det, e1 = -d1 / det;
+            d0 = e0;
+            d1 = e1;
+            d2 = 1.0 / d2;
+        }
+        double t0[10], t1[10];
+        matvec(0);
+        for (int i = 0; i < n; ++i) t0[i] = r[i];
+        matvec(1);
+        for (int i = 0; i < n; ++i) t1[i] = r[i];
+        for (int i = 0; i < n; ++i) {
+            y[(size_t)(0 * n + i) * N + q] = -(d0 * t0[i] + d1 * t1[i]);
+            y[(size_t)(1 * n + i) * N + q] = -(d1 * t0[i] + d0 * t1[i]);
+        }
+        matvec(2);
+        for (int i = 0; i < n; ++i) y[(size_t)(2 * n + i) * N + q] = -d2 * r[i];
+        for (int fld = 3; fld < 5; ++fld) {
+            matvec(fld);
+            for (int i = 0; i < n; ++i) y[(size_t)(fld * n + i) * N + q] = rv * r[i];
+        }
+    }
+}
+
+// out = a x + b y over n values (x or y may be null: treated as zero; out may
+// alias x or y, each element is read before it is written by the same thread).
+__global__ void axpby_kernel(int64_t n, double a, const double* x, double b, const double* y, double* out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double v = 0.0;
+        if (x) v = a * x[i];
+        if (y) v = fma(b, y[i], v);
+        out[i] = v;
+    }
+}
+
+// lambda += R^T G for one time node: the transpose of record_kernel.  One
+// thread walks the receivers in order (deterministic sums).
+__global__ void inject_kernel(DevOps op, int n_rec, const int32_t* __restrict__ ri, const double* __restrict__ rd,
+                              const double* __restrict__ G, double* lam) {
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    const int n = op.n;
+    const int stride = 2 * n + 15;
+    double* lf = lam;
+    double* ls = lam + (size_t)3 * n * op.Nf;
+    for (int r = 0; r < n_rec; ++r) {
+        const double* d = rd + (size_t)r * stride;
+        const int kind = ri[4 * r], qf = ri[4 * r + 1], qs = ri[4 * r + 2];
+        const double* g = G + 5 * r;
+        auto add = [&](double* base, int N, int q, int field, const double* phi, double v) {
+            if (v == 0.0) return;
+            for (int i = 0; i < n; ++i) base[(size_t)(field * n + i) * N + q] += v * phi[i];
+        };
+        if (kind == 0) {   // [p, m_x, m_y]
+            add(lf, op.Nf, qf, 2, d, g[0]);
+            add(lf, op.Nf, qf, 0, d, g[1]);
+            add(lf, op.Nf, qf, 1, d, g[2]);
+        } else if (kind == 1) {   // [v_x, v_y, s_xx, s_yy, s_xy]
+            add(ls, op.Ns, qs, 3, d, g[0]);
+            add(ls, op.Ns, qs, 4, d, g[1]);
+            add(ls, op.Ns, qs, 0, d, g[2]);
+            add(ls, op.Ns, qs, 1, d, g[3]);
+            add(ls, op.Ns, qs, 2, d, g[4]);
+        } else {   // interface: [p_F, v_F] = Ai [w_f, w_sx, w_sy]
+            const double* pf = d;
+            const double* ps = d + n;
+            const double tf = d[2 * n], ts = d[2 * n + 1];
+            const double nfx = d[2 * n + 2], nfy = d[2 * n + 3], nsx = d[2 * n + 4], nsy = d[2 * n + 5];
+            const double* Ai = d + 2 * n + 6;
+            const double hf = Ai[0] * g[0] + Ai[3] * g[1] + Ai[6] * g[2];
+            const double hx = Ai[1] * g[0] + Ai[4] * g[1] + Ai[7] * g[2];
+            const double hy = Ai[2] * g[0] + Ai[5] * g[1] + Ai[8] * g[2];
+            add(lf, op.Nf, qf, 2, pf, tf * hf);
+            add(lf, op.Nf, qf, 0, pf, -nfx * hf);
+            add(lf, op.Nf, qf, 1, pf, -nfy * hf);
+            add(ls, op.Ns, qs, 3, ps, ts * hx);
+            add(ls, op.Ns, qs, 4, ps, ts * hy);
+            add(ls, op.Ns, qs, 0, ps, -nsx * hx);
+            add(ls, op.Ns, qs, 2, ps, -(nsy * hx + nsx * hy));
+            add(ls, op.Ns, qs, 1, ps, -nsy * hy);
+        }
+    }
+}
+
+// dL/dtheta += mu^T dk/dtheta with dk/dtheta from the raw rate (MODE_RAW).
+// grad: fluid [2][Nf] (1/(rho h), kappa/h), solid [4][Ns] (c1, r, c3, 1/(rho h)).
+__global__ void grad_kernel(DevOps op, const double* __restrict__ mu, const double* __restrict__ raw,
+                            double* __restrict__ grad_f, double* __restrict__ grad_s) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= op.Nf + op.Ns) return;
+    const bool fl = g < op.Nf;
+    const int q = fl ? g : g - op.Nf;
+    const int n = op.n;
+    const int cls = op.warp_class[(fl ? 0 : op.n_warps_f) + (q >> 5)];
+    const int* ci = op.cls_int + cls * CI_STRIDE;
+    if (q - ci[CI_START] >= ci[CI_COUNT]) return;
+    const int N = fl ? op.Nf : op.Ns;
+    const size_t off = fl ? 0 : (size_t)3 * n * op.Nf;
+    auto dot = [&](int fa, int fb) {
+        double s = 0.0;
+        for (int i = 0; i < n; ++i)
+            s = fma(mu[off + (size_t)(fa * n + i) * N + q], raw[off + (size_t)(fb * n + i) * N + q], s);
+        return s;
+    };
+    if (fl) {
+        grad_f[q] += dot(0, 0) + dot(1, 1);
+        grad_f[N + q] += dot(2, 2);
+    } else {
+        const double c1 = op.scal_s[SS_C1 * N + q], r = op.scal_s[SS_R * N + q];
+        const double sxx_exx = dot(0, 0), sxx_eyy = dot(0, 1), syy_exx = dot(1, 0), syy_eyy = dot(1, 1);
+        grad_s[q] += sxx_exx + r * sxx_eyy + syy_eyy + r * syy_exx;      // d/dc1
+        grad_s[N + q] += c1 * (sxx_eyy + syy_exx);                      // d/dr
+        grad_s[2 * N + q] += dot(2, 2);                                  // d/dc3
+        grad_s[3 * N + q] += dot(3, 3) + dot(4, 4);                      // d/d(1/(rho h))
+    }
+}
+
+// dL/dw for each point source: mu^T g over the source cell's coefficients
+// (the stage rate carries w(t) g, g the source's lifted load vector).
+struct SrcMeta {
+    int n;
+    int dom[MAX_SOURCES];
+    int q[MAX_SOURCES];
+};
+__global__ void wavelet_grad_kernel(DevOps op, SrcMeta meta, const double* __restrict__ g,
+                                    const double* __restrict__ mu, double* out) {
+    const int s = threadIdx.x;
+    if (s >= meta.n) return;
+    const int n = op.n;
+    const int q = meta.q[s];
+    double acc = 0.0;
+    if (meta.dom[s] == 0) {
+        for (int i = 0; i < n; ++i) acc = fma(mu[(size_t)(2 * n + i) * op.Nf + q], g[(size_t)s * 2 * n + i], acc);
+    } else {
+        const double* ms = mu + (size_t)3 * n * op.Nf;
+        for (int i = 0; i < n; ++i) {
+            acc = fma(ms[(size_t)(3 * n + i) * op.Ns + q], g[(size_t)s * 2 * n + i], acc);
+            acc = fma(ms[(size_t)(4 * n + i) * op.Ns + q], g[(size_t)s * 2 * n + n + i], acc);
+        }
+    }
+    out[s] = acc;
+}
+
+struct AdjBuffers {
+    int64_t S, T;           // state and trace sizes
+    double *ckpt, *stages, *erk_work, *lam, *mu, *x, *y, *nu, *acc, *pend, *raw, *tr, *grad_f, *grad_s, *wgrad;
+};
+
+int64_t adjoint_layout(const hho_ops* ops, const hho_tableau* tab, int64_t nsteps, int64_t C, AdjBuffers* b,
+                       double* base) {
+    const int s = tab->s;
+    const int64_t S = ops->n_state, T = ops->trace_doubles;
+    const int64_t n_ckpt = (nsteps + C - 1) / C + 1;
+    int64_t erk = 0;
+    hho_work_size(ops, tab, &erk);
+    int64_t off = 0;
+    auto take = [&](int64_t n) {
+        double* p = base ? base + off : nullptr;
+        off += (n + 31) / 32 * 32;
+        return p;
+    };
+    AdjBuffers B;
+    B.S = S;
+    B.T = T;
+    B.ckpt = take(n_ckpt * S);
+    B.stages = take(C * s * S);
+    B.erk_work = take(erk);
+    B.lam = take(S);
+    B.mu = take(S);
+    B.x = take(S);
+    B.y = take(S);
+    B.nu = take(S);
+    B.acc = take(S);
+    B.pend = take(s * S);
+    B.raw = take(S);
+    B.tr = take(T);
+    B.grad_f = take(2 * (int64_t)ops->dev.Nf);
+    B.grad_s = take(4 * (int64_t)ops->dev.Ns);
+    B.wgrad = take(nsteps * s * MAX_SOURCES);
+    if (b) *b = B;
+    return off;
+}
+
+int64_t grid1(int64_t n) {
+    int64_t g = (n + 255) / 256;
+    return g > 4096 ? 4096 : (g < 1 ? 1 : g);
+}
+
+}  // namespace
+
+extern "C" int hho_adjoint_work_size(const hho_ops* ops, const hho_tableau* tab, int64_t nsteps,
+                                     int64_t checkpoint_every, int64_t* n_doubles) {
+    if (!ops || !tab || !n_doubles || nsteps < 1 || checkpoint_every < 1) {
+        hho_set_error("hho_adjoint_work_size: bad arguments");
+        return HHO_EINVAL;
+    }
+    *n_doubles = adjoint_layout(ops, tab, nsteps, checkpoint_every, nullptr, nullptr);
+    return HHO_OK;
+}
+
+extern "C" int hho_adjoint_vjp(hho_ops* ops, const hho_tableau* tab, double t0, double dt, int64_t nsteps,
+                               int64_t checkpoint_every, const double* d_state0, const double* d_cotangent,
+                               double* d_work, int64_t work_doubles, double* h_grad_cell, double* h_grad_wavelet,
+                               void* stream) {
+    if (!ops || !tab || !d_state0 || !d_cotangent || !d_work || !h_grad_cell || nsteps < 1 || checkpoint_every < 1 ||
+        !std::isfinite(dt)) {
+        hho_set_error("hho_adjoint_vjp: bad arguments");
+        return HHO_EINVAL;
+    }
+    std::vector<StagePlan> plan;
+    int nb = 0;
+    if (build_plan(tab, plan, &nb) != HHO_OK) {
+        hho_set_error("hho_adjoint_vjp: unsupported tableau");
+        return HHO_EINVAL;
+    }
+    const int64_t C = checkpoint_every;
+    const int s = tab->s;
+    AdjBuffers B;
+    const int64_t need = adjoint_layout(ops, tab, nsteps, C, &B, d_work);
+    if (work_doubles < need) {
+        hho_set_error("hho_adjoint_vjp: work buffer has %lld doubles, needs %lld", (long long)work_doubles,
+                      (long long)need);
+        return HHO_EINVAL;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t S = B.S;
+    const int nthr = ops->dev.Nf + ops->dev.Ns;
+    const int cblk = (nthr + 127) / 128;
+    int rc = HHO_OK;
+    auto copy = [&](double* dst, const double* src, int64_t n) {
+        return cudaMemcpyAsync(dst, src, sizeof(double) * n, cudaMemcpyDeviceToDevice, st) == cudaSuccess;
+    };
+    // erk work split as in erk_run: [X][partial sums][2 traces]
+    double* X = B.erk_work;
+    double* bufs = B.erk_work + S;
+    double* trs[2] = {B.erk_work + S * (1 + nb), B.erk_work + S * (1 + nb) + ops->trace_doubles};
+    auto resolve = [&](int code, double* state) -> double* {
+        if (code == SRC_STATE) return state;
+        if (code == SRC_X) return X;
+        if (code == SRC_ZERO) return nullptr;
+        return bufs + S * code;
+    };
+    DevOps adj = ops->dev;
+    adj.if_coef = ops->d_if_coef_adj;
+
+    // ---- forward pass: checkpoints ------------------------------------------------
+    if (!copy(B.ckpt, d_state0, S)) {
+        hho_set_error("hho_adjoint_vjp: copy failed");
+        return HHO_ECUDA;
+    }
+    const int64_t n_ckpt = (nsteps + C - 1) / C;
+    for (int64_t c = 1; c < n_ckpt + 1 && c * C <= nsteps; ++c) {
+        if (!copy(B.ckpt + c * S, B.ckpt + (c - 1) * S, S)) return HHO_ECUDA;
+        rc = hho_erk_step(ops, tab, t0 + (double)((c - 1) * C) * dt, dt, C, B.ckpt + c * S, B.erk_work, stream);
+        if (rc) return rc;
+    }
+
+    // ---- backward sweep ---------------------------------------------------------------
+    axpby_kernel<<<grid1(S), 256, 0, st>>>(S, 0.0, nullptr, 0.0, nullptr, B.lam);
+    if (ops->dev.Nf > 0)
+        axpby_kernel<<<grid1(2 * (int64_t)ops->dev.Nf), 256, 0, st>>>(2 * (int64_t)ops->dev.Nf, 0.0, nullptr, 0.0,
+                                                                       nullptr, B.grad_f);
+    if (ops->dev.Ns > 0)
+        axpby_kernel<<<grid1(4 * (int64_t)ops->dev.Ns), 256, 0, st>>>(4 * (int64_t)ops->dev.Ns, 0.0, nullptr, 0.0,
+                                                                       nullptr, B.grad_s);
+    const int64_t n_segments = (nsteps + C - 1) / C;
+    for (int64_t seg = n_segments - 1; seg >= 0; --seg) {
+        const int64_t n0 = seg * C;                                   // segment starts at U^{n0}
+        const int64_t nst = (n0 + C <= nsteps) ? C : nsteps - n0;
+        // recompute the segment, keeping the stage values Y_{n,j} (stage j input)
+        double* U = B.x;   // running state
+        if (!copy(U, B.ckpt + seg * S, S)) return HHO_ECUDA;
+        StageArgsT<double> a;
+        memset(&a, 0, sizeof(a));
+        a.op = ops->dev;
+        a.inp = U;
+        a.tr_out = trs[0];
+        launch_stage_f64(ops, MODE_TRACES, a, 1, 0.0, false, stream);
+        int cur = 0;
+        for (int64_t m = 0; m < nst; ++m) {
+            const double tn = t0 + (double)(n0 + m) * dt;
+            for (int j = 0; j < s; ++j) {
+                double* Yj = B.stages + (m * s + j) * S;
+                if (!copy(Yj, j == 0 ? U : X, S)) return HHO_ECUDA;
+                const StagePlan& P = plan[j];
+                a.inp = (j == 0) ? U : X;
+                a.tr_in = trs[cur];
+                a.tr_out = trs[cur ^ 1];
+                a.n_tgt = P.n_tgt;
+                for (int t = 0; t < P.n_tgt; ++t) {
+                    a.tgt[t].src = resolve(P.t[t].src, U);
+                    a.tgt[t].dst = resolve(P.t[t].dst, U);
+                    a.tgt[t].coef = P.t[t].a * dt;
+                }
+                launch_stage_f64(ops, MODE_STAGE, a, 1, tn + tab->c[j] * dt, true, stream);
+                cur ^= 1;
+            }
+        }
+        rc = check_cuda("hho_adjoint_vjp (segment recompute)");
+        if (rc) return rc;
+        // backward through the segment
+        for (int64_t m = nst - 1; m >= 0; --m) {
+            const int64_t n = n0 + m + 1;                            // step n: U^{n-1} -> U^n
+            const double tn = t0 + (double)(n - 1) * dt;
+            if (ops->n_rec > 0)
+                inject_kernel<<<1, 32, 0, st>>>(ops->dev, ops->n_rec, ops->d_rec_int, ops->d_rec_dbl,
+                                                d_cotangent + (size_t)(n - 1) * 5 * ops->n_rec, B.lam);
+            if (!copy(B.acc, B.lam, S)) return HHO_ECUDA;
+            axpby_kernel<<<grid1(s * S), 256, 0, st>>>(s * S, 0.0, nullptr, 0.0, nullptr, B.pend);
+            for (int j = s - 1; j >= 0; --j) {
+                // mu_j = dt (b_j lambda + P_j)
+                axpby_kernel<<<grid1(S), 256, 0, st>>>(S, dt * tab->b[j], B.lam, dt, B.pend + j * S, B.mu);
+                // nu_j = A^T mu_j = S M A' M^-1 S mu_j
+                mass_kernel<<<cblk, 128, 0, st>>>(ops->dev, ops->d_mass_f, ops->d_mass_s, ops->d_cls_minv, B.mu, B.x,
+                                                  1);
+                StageArgsT<double> b;
+                memset(&b, 0, sizeof(b));
+                b.op = adj;
+                b.inp = B.x;
+                b.tr_out = B.tr;
+                launch_stage_f64(ops, MODE_TRACES, b, 1, 0.0, false, stream);
+                b.tr_in = B.tr;
+                b.tr_out = nullptr;
+                b.n_tgt = 1;
+                b.tgt[0].src = nullptr;
+                b.tgt[0].dst = B.y;
+                b.tgt[0].coef = 1.0;
+                launch_stage_f64(ops, MODE_APPLY, b, 1, 0.0, false, stream);
+                mass_kernel<<<cblk, 128, 0, st>>>(ops->dev, ops->d_mass_f, ops->d_mass_s, ops->d_cls_minv, B.y, B.nu,
+                                                  0);
+                axpby_kernel<<<grid1(S), 256, 0, st>>>(S, 1.0, B.acc, 1.0, B.nu, B.acc);
+                for (int l = 0; l < j; ++l)
+                    if (tab->a[j][l] != 0.0)
+                        axpby_kernel<<<grid1(S), 256, 0, st>>>(S, 1.0, B.pend + l * S, tab->a[j][l], B.nu,
+                                                               B.pend + l * S);
+                // parameter and wavelet gradients of stage j
+                const double* Yj = B.stages + (m * s + j) * S;
+                StageArgsT<double> r;
+                memset(&r, 0, sizeof(r));
+                r.op = ops->dev;
+                r.inp = Yj;
+                r.tr_out = B.tr;
+                launch_stage_f64(ops, MODE_TRACES, r, 1, 0.0, false, stream);
+                r.tr_in = B.tr;
+                r.tr_out = nullptr;
+                r.n_tgt = 1;
+                r.tgt[0].src = nullptr;
+                r.tgt[0].dst = B.raw;
+                r.tgt[0].coef = 1.0;
+                launch_stage_f64(ops, MODE_RAW, r, 1, tn + tab->c[j] * dt, true, stream);
+                grad_kernel<<<cblk, 128, 0, st>>>(ops->dev, B.mu, B.raw, B.grad_f, B.grad_s);
+                if (ops->n_src > 0 && h_grad_wavelet) {
+                    SrcMeta meta;
+                    meta.n = ops->n_src;
+                    for (int k2 = 0; k2 < ops->n_src; ++k2) {
+                        meta.dom[k2] = ops->src_dom[k2];
+                        meta.q[k2] = ops->src_q[k2];
+                    }
+                    wavelet_grad_kernel<<<1, 32, 0, st>>>(ops->dev, meta, ops->d_src_g, B.mu,
+                                                          B.wgrad + ((n - 1) * s + j) * MAX_SOURCES);
+                }
+                rc = check_cuda("hho_adjoint_vjp (backward stage)");
+                if (rc) return rc;
+            }
+            if (!copy(B.lam, B.acc, S)) return HHO_ECUDA;
+        }
+    }
+    // ---- gradients to the host, mapped to the materials ----------------------------------------
+    std::vector<double> gf(2 * (size_t)ops->dev.Nf), gs(4 * (size_t)ops->dev.Ns);
+    if ((!gf.empty() && cudaMemcpyAsync(gf.data(), B.grad_f, sizeof(double) * gf.size(), cudaMemcpyDeviceToHost, st) !=
+                            cudaSuccess) ||
+        (!gs.empty() && cudaMemcpyAsync(gs.data(), B.grad_s, sizeof(double) * gs.size(), cudaMemcpyDeviceToHost, st) !=
+                            cudaSuccess) ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+        hho_set_error("hho_adjoint_vjp: gradient copy failed");
+        return HHO_ECUDA;
+    }
+    if (ops->n_src > 0 && h_grad_wavelet) {
+        std::vector<double> wg((size_t)nsteps * s * MAX_SOURCES);
+        if (cudaMemcpy(wg.data(), B.wgrad, sizeof(double) * wg.size(), cudaMemcpyDeviceToHost) != cudaSuccess) {
+            hho_set_error("hho_adjoint_vjp: wavelet gradient copy failed");
+            return HHO_ECUDA;
+        }
+        for (int64_t n = 0; n < nsteps; ++n)
+            for (int j = 0; j < s; ++j)
+                for (int k2 = 0; k2 < ops->n_src; ++k2)
+                    h_grad_wavelet[(n * s + j) * ops->n_src + k2] = wg[(n * s + j) * MAX_SOURCES + k2];
+    }
+    const int Nf = ops->dev.Nf, Ns = ops->dev.Ns;
+    for (int64_t c = 0; c < ops->nc; ++c) {
+        double* o = h_grad_cell + 4 * c;   // [rho, kappa, lambda, mu]
+        o[0] = o[1] = o[2] = o[3] = 0.0;
+        const int q = ops->cell_pos[c];
+        const double h = ops->diam[c], rho = ops->rho[c];
+        if (ops->cell_dom[c] == 0) {
+            o[0] = gf[q] * (-1.0 / (rho * rho * h));                       // A_m = 1/(rho h)
+            o[1] = gf[Nf + q] / h;                                          // A_p = kappa/h
+        } else {
+            const double lam = ops->lam[c], mu = ops->mu[c], l2m = lam + 2.0 * mu;
+            const double gc1 = gs[q], gr = gs[Ns + q], gc3 = gs[2 * Ns + q], gav = gs[3 * Ns + q];
+            o[0] = gav * (-1.0 / (rho * rho * h));                          // A_v = 1/(rho h)
+            o[2] = gc1 / h + gr * (2.0 * mu / (l2m * l2m));                 // c1 = (lambda+2mu)/h, r = lambda/(lambda+2mu)
+            o[3] = gc1 * 2.0 / h + gr * (-2.0 * lam / (l2m * l2m)) + gc3 / h;   // c3 = mu/h
+        }
+    }
+    return HHO_OK;
+}

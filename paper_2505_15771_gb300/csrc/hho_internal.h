@@ -129,7 +129,8 @@ int build_plan(const hho_tableau* tab, std::vector<StagePlan>& plan, int* n_buf)
 // Launches one stage-kernel pass (FP64) over n_shots shots; and the receiver
 // kernel.  Defined in stage.cu, used by the adjoint driver.
 struct hho_ops;
-void launch_stage_f64(const hho_ops* ops, int mode, StageArgsT<double>& a, int n_shots, double t_src, void* stream);
+void launch_stage_f64(const hho_ops* ops, int mode, StageArgsT<double>& a, int n_shots, double t_src, bool sources,
+                      void* stream);
 void launch_record_f64(const hho_ops* ops, const double* state, double* out, void* stream);
 int check_cuda(const char* what);
 

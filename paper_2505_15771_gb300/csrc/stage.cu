@@ -428,6 +428,12 @@ __device__ __forceinline__ void fluid_cell(const StageArgsT<T>& A, int q, int sh
             fluid_face_rate<T, K, RectFace<1>>(A, c, 1, kmx, kmy, kp);
             fluid_face_rate<T, K, RectFace<2>>(A, c, 2, kmx, kmy, kp);
             fluid_face_rate<T, K, RectFace<3>>(A, c, 3, kmx, kmy, kp);
+        } else if (c.nF == 3) {   // triangles: faces unrolled so their loads can overlap
+#pragma unroll
+            for (int j = 0; j < 3; ++j) fluid_face_rate<T, K, GenericFace>(A, c, j, kmx, kmy, kp);
+        } else if (c.nF == 4) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) fluid_face_rate<T, K, GenericFace>(A, c, j, kmx, kmy, kp);
         } else {
 #pragma unroll 1
             for (int j = 0; j < c.nF; ++j) fluid_face_rate<T, K, GenericFace>(A, c, j, kmx, kmy, kp);
@@ -464,6 +470,9 @@ __device__ __forceinline__ void fluid_cell(const StageArgsT<T>& A, int q, int sh
         fluid_face_trace<T, K, RectFace<1>>(A, c, 1, U);
         fluid_face_trace<T, K, RectFace<2>>(A, c, 2, U);
         fluid_face_trace<T, K, RectFace<3>>(A, c, 3, U);
+    } else if (c.nF == 3) {
+#pragma unroll
+        for (int j = 0; j < 3; ++j) fluid_face_trace<T, K, GenericFace>(A, c, j, U);
     } else {
 #pragma unroll 1
         for (int j = 0; j < c.nF; ++j) fluid_face_trace<T, K, GenericFace>(A, c, j, U);
@@ -654,6 +663,12 @@ __device__ __forceinline__ void solid_cell(const StageArgsT<T>& A, int q, int sh
             solid_face_rate<T, K, RectFace<1>>(A, c, 1, exx, eyy, exy, kvx, kvy);
             solid_face_rate<T, K, RectFace<2>>(A, c, 2, exx, eyy, exy, kvx, kvy);
             solid_face_rate<T, K, RectFace<3>>(A, c, 3, exx, eyy, exy, kvx, kvy);
+        } else if (c.nF == 3) {
+#pragma unroll
+            for (int j = 0; j < 3; ++j) solid_face_rate<T, K, GenericFace>(A, c, j, exx, eyy, exy, kvx, kvy);
+        } else if (c.nF == 4) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) solid_face_rate<T, K, GenericFace>(A, c, j, exx, eyy, exy, kvx, kvy);
         } else {
 #pragma unroll 1
             for (int j = 0; j < c.nF; ++j) solid_face_rate<T, K, GenericFace>(A, c, j, exx, eyy, exy, kvx, kvy);
@@ -704,6 +719,9 @@ __device__ __forceinline__ void solid_cell(const StageArgsT<T>& A, int q, int sh
         solid_face_trace<T, K, RectFace<1>>(A, c, 1, U);
         solid_face_trace<T, K, RectFace<2>>(A, c, 2, U);
         solid_face_trace<T, K, RectFace<3>>(A, c, 3, U);
+    } else if (c.nF == 3) {
+#pragma unroll
+        for (int j = 0; j < 3; ++j) solid_face_trace<T, K, GenericFace>(A, c, j, U);
     } else {
 #pragma unroll 1
         for (int j = 0; j < c.nF; ++j) solid_face_trace<T, K, GenericFace>(A, c, j, U);
@@ -1527,12 +1545,20 @@ extern "C" int hho_energy_static(hho_ops* ops, const double* d_state, double* d_
 }
 
 // ---- launchers for the adjoint driver (adjoint.cu) -----------------------------------
-void launch_stage_f64(const hho_ops* ops, int mode, StageArgsT<double>& a, int n_shots, double t_src, void* stream) {
+void launch_stage_f64(const hho_ops* ops, int mode, StageArgsT<double>& a, int n_shots, double t_src, bool sources,
+                      void* stream) {
     const dim3 grid((ops->dev.Nf + ops->dev.Ns + 127) / 128, n_shots);
     if (grid.x == 0) return;
     a.state_stride = ops->n_state;
     a.trace_stride = ops->trace_doubles;
-    if (mode == MODE_STAGE || mode == MODE_APPLY || mode == MODE_RAW) fill_sources<double>(ops, a, t_src, n_shots);
+    if (sources) {
+        fill_sources<double>(ops, a, t_src, n_shots);
+    } else {
+        a.n_src = 0;
+        a.shot_src_q = nullptr;
+        a.shot_src_dom = nullptr;
+        a.shot_src_g = nullptr;
+    }
     cudaStream_t st = (cudaStream_t)stream;
     switch (mode) {
         case MODE_TRACES: launch_k<double, MODE_TRACES>(ops->k, a, grid, st); break;

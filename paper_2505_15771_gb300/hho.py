@@ -83,6 +83,8 @@ _SIGS = {
     "hho_energy_static": (C.c_int, [_P, _P, _P, _P]),
     "hho_cfl_bracket": (C.c_int, [_P, C.POINTER(Tableau), _P, _D, _I64, _D, _D, _I64, _P, _P, C.POINTER(_I64),
                                   C.POINTER(_I64), _P]),
+    "hho_adjoint_work_size": (C.c_int, [_P, C.POINTER(Tableau), _I64, _I64, C.POINTER(_I64)]),
+    "hho_adjoint_vjp": (C.c_int, [_P, C.POINTER(Tableau), _D, _D, _I64, _I64, _P, _P, _P, _I64, _P, _P, _P]),
     "hho_batch_sizes": (C.c_int, [_P, C.POINTER(Tableau), _I32, _I32, C.POINTER(_I64), C.POINTER(_I64)]),
     "hho_batch_pack": (C.c_int, [_P, _I32, _I32, _P, _P, _P]),
     "hho_batch_unpack": (C.c_int, [_P, _I32, _I32, _P, _P, _P]),
@@ -329,3 +331,20 @@ def hho_cfl_bracket(ops, tab, d_state0, T_f, N0, eps, delta, max_trials, d_state
     _check(lib().hho_cfl_bracket(ops, C.byref(tab), d_state0, float(T_f), int(N0), float(eps), float(delta),
                                  int(max_trials), d_state, d_work, C.byref(a), C.byref(b), stream))
     return a.value, b.value
+
+
+def hho_adjoint_work_size(ops, tab, nsteps, checkpoint_every):
+    n = _I64()
+    _check(lib().hho_adjoint_work_size(ops, C.byref(tab), int(nsteps), int(checkpoint_every), C.byref(n)))
+    return n.value
+
+
+def hho_adjoint_vjp(ops, tab, t0, dt, nsteps, checkpoint_every, d_state0, d_cotangent, d_work, work_doubles,
+                    n_cells, n_src=0, stream=0):
+    """Returns (grad_cell [n_cells, 4] = dL/d(rho, kappa, lambda, mu), grad_wavelet [nsteps, s, n_src] or None)."""
+    g = np.zeros((n_cells, 4), np.float64)
+    w = np.zeros((int(nsteps), tab.s, n_src), np.float64) if n_src > 0 else None
+    _check(lib().hho_adjoint_vjp(ops, C.byref(tab), float(t0), float(dt), int(nsteps), int(checkpoint_every),
+                                 d_state0, d_cotangent, d_work, int(work_doubles), _ptr(g),
+                                 None if w is None else _ptr(w), stream))
+    return g, w

@@ -1,0 +1,179 @@
+"""Discrete adjoint on the GPU (hho_adjoint_vjp) against the oracle's dense
+reverse mode and against central differences of the GPU forward traces.
+The stabilisation weights are held fixed (tau frozen at the model)."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import adjoint as ADJ
+from oracle import erk as E
+from tests.libutil import ensure_built, oracle_system
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+PTS = [(0.31, 0.2), (0.77, 0.41), (0.18, 0.5), (0.62, 0.5), (0.4, 0.8), (0.9, 0.66)]
+SRC = (0.55, 0.3)
+F0 = 6.0
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    ensure_built()
+    from paper_2505_15771_gb300 import hho, solver
+    return hho, solver
+
+
+def media(md, seed):
+    rng = np.random.default_rng(seed)
+    nc = md.n_cells
+    sol = md.cell_domain == 1
+    rho = 1 + rng.random(nc)
+    lam = np.where(sol, 3 + rng.random(nc), 0.0)
+    mu = np.where(sol, 2 + rng.random(nc), 0.0)
+    kap = np.where(sol, 0.0, 1 + rng.random(nc))
+    return rho, lam, mu, kap
+
+
+def gpu_problem(hho, md, k, med, tau=None):
+    mesh = hho.hho_mesh_create(md.xy, md.cell_ptr, md.cell_vtx, md.cell_domain)
+    ops = hho.hho_operators_build_tau(mesh, k, *med, tau)
+    hho.hho_mesh_destroy(mesh)
+    hho.hho_sources_set(ops, [SRC], [(0.0, 1.0)], [F0], [1.0 / F0], [1.0])
+    hho.hho_receivers_set(ops, PTS)
+    return ops
+
+
+def gpu_traces(hho, ops, U0, dt, nsteps, s=4):
+    tab = hho.hho_tableau_erk(s)
+    lay = hho.hho_state_layout(ops)
+    c = torch.as_tensor(U0).cuda()
+    x = torch.zeros(lay.n_state, dtype=torch.float64, device="cuda")
+    hho.hho_state_pack(ops, c.data_ptr(), x.data_ptr())
+    work = torch.empty(hho.hho_work_size(ops, tab), dtype=torch.float64, device="cuda")
+    seis = torch.zeros((nsteps, len(PTS), 5), dtype=torch.float64, device="cuda")
+    hho.hho_erk_step_record(ops, tab, 0.0, dt, nsteps, x.data_ptr(), work.data_ptr(), seis.data_ptr())
+    return seis.cpu().numpy()
+
+
+def gpu_vjp(hho, ops, U0, dt, nsteps, G, nc, s=4, ckpt=5):
+    tab = hho.hho_tableau_erk(s)
+    lay = hho.hho_state_layout(ops)
+    c = torch.as_tensor(U0).cuda()
+    x0 = torch.zeros(lay.n_state, dtype=torch.float64, device="cuda")
+    hho.hho_state_pack(ops, c.data_ptr(), x0.data_ptr())
+    nw = hho.hho_adjoint_work_size(ops, tab, nsteps, ckpt)
+    work = torch.empty(nw, dtype=torch.float64, device="cuda")
+    g = torch.as_tensor(G.reshape(nsteps, len(PTS), 5)).cuda().contiguous()
+    return hho.hho_adjoint_vjp(ops, tab, 0.0, dt, nsteps, ckpt, x0.data_ptr(), g.data_ptr(), work.data_ptr(), nw,
+                               nc, n_src=1)
+
+
+@pytest.mark.parametrize("k,s", [(1, 4), (2, 3)])
+def test_adjoint_matches_oracle(lib, k, s):
+    """Material gradients dL/d(rho, kappa, lambda, mu) and wavelet gradients
+    dL/dw(t_i) of L = <G, traces> agree with the oracle's dense reverse mode."""
+    hho, solver = lib
+    md = synth.quad_grid(6, 6)
+    med = media(md, 1)
+    Sy = oracle_system(md, k, med)
+    st = E.Stepper(Sy)
+    load, _ = Sy.point_load(*SRC, direction=(0.0, 1.0))
+    dense = ADJ.DenseAdjoint(st, PTS, load, lambda t: synth.ricker(t, F0))
+    nsteps, dt = 17, 0.004
+    rng = np.random.default_rng(7)
+    U0 = synth.random_state(Sy.nT, 5)
+    G = rng.standard_normal((nsteps, len(PTS) * 5))
+    tr_ref, _ = dense.run(U0, 0.0, dt, nsteps, "erk%d" % s)
+    ops = gpu_problem(hho, md, k, med)
+    try:
+        tr = gpu_traces(hho, ops, U0, dt, nsteps, s)
+        assert np.linalg.norm(tr.reshape(nsteps, -1) - tr_ref) <= 1e-12 * np.linalg.norm(tr_ref)
+        g_ref, w_ref = dense.vjp(U0, 0.0, dt, nsteps, G, "erk%d" % s)
+        g, w = gpu_vjp(hho, ops, U0, dt, nsteps, G, md.n_cells, s)
+    finally:
+        hho.hho_ops_destroy(ops)
+    eg = np.linalg.norm(g - g_ref) / np.linalg.norm(g_ref)
+    ew = np.linalg.norm(w[:, :, 0] - w_ref) / np.linalg.norm(w_ref)
+    print("k=%d ERK%d gradient rel err %.3e wavelet %.3e" % (k, s, eg, ew))
+    assert eg <= 1e-10 and ew <= 1e-10
+
+
+def test_adjoint_matches_finite_differences(lib):
+    """<grad, delta> against central differences of L = <G, traces> computed
+    with the GPU forward, tau frozen (hho_operators_build_tau), on 6 seeded
+    random material directions: relative error <= 1e-6."""
+    hho, solver = lib
+    md = synth.quad_grid(8, 8)
+    med = media(md, 2)
+    nc = md.n_cells
+    nsteps, dt = 30, 0.003
+    rng = np.random.default_rng(11)
+    base = gpu_problem(hho, md, 2, med)
+    tau = hho.hho_ops_tau(base, nc)
+    lay = hho.hho_state_layout(base)
+    U0 = synth.random_state(lay.n_canonical, 3)
+    G = rng.standard_normal((nsteps, len(PTS) * 5))
+    g, _ = gpu_vjp(hho, base, U0, dt, nsteps, G, nc, 4, ckpt=7)
+    hho.hho_ops_destroy(base)
+    rho, lam, mu, kap = med
+    worst = 0.0
+    for trial in range(6):
+        d = rng.standard_normal((nc, 4)) * np.stack([rho, kap, lam, mu], axis=1) * 0.05
+        eps = 1e-5
+
+        def L(sign):
+            ops = gpu_problem(hho, md, 2, (rho + sign * eps * d[:, 0], lam + sign * eps * d[:, 2],
+                                           mu + sign * eps * d[:, 3], kap + sign * eps * d[:, 1]), tau)
+            try:
+                tr = gpu_traces(hho, ops, U0, dt, nsteps)
+            finally:
+                hho.hho_ops_destroy(ops)
+            return float(np.sum(tr.reshape(nsteps, -1) * G))
+        fd = (L(1) - L(-1)) / (2 * eps)
+        an = float(np.sum(g * d))
+        worst = max(worst, abs(fd - an) / abs(fd))
+    print("adjoint vs central differences, worst rel err %.3e" % worst)
+    assert worst <= 1e-6
+
+
+def test_autograd_traces_misfit(lib):
+    """torch.autograd.Function: L = 1/2 |traces - observed|^2; backward gives
+    dL/d(rho, lambda, mu, kappa, amplitude) through the GPU adjoint; checked
+    against central differences (tau frozen) in a random direction."""
+    hho, solver = lib
+    from paper_2505_15771_gb300.autograd import TraceModel, Traces
+    md = synth.quad_grid(6, 6)
+    rho, lam, mu, kap = media(md, 4)
+    nsteps, dt = 20, 0.004
+    model = TraceModel(md, 1, SRC, (0.0, 1.0), F0, PTS, dt, nsteps, stages=4, checkpoint_every=6)
+    lay_probe = gpu_problem(hho, md, 1, (rho, lam, mu, kap))
+    U0 = 0.1 * synth.random_state(hho.hho_state_layout(lay_probe).n_canonical, 9)
+    tau = hho.hho_ops_tau(lay_probe, md.n_cells)
+    hho.hho_ops_destroy(lay_probe)
+    rng = np.random.default_rng(5)
+    obs = torch.as_tensor(rng.standard_normal((nsteps, len(PTS), 5))).cuda()
+    T = [torch.tensor(v, dtype=torch.float64, requires_grad=True) for v in (rho, lam, mu, kap)]
+    amp = torch.tensor(1.0, dtype=torch.float64, requires_grad=True)
+    tr = Traces.apply(T[0], T[1], T[2], T[3], amp, model, U0)
+    loss = 0.5 * ((tr - obs) ** 2).sum()
+    loss.backward()
+    d = rng.standard_normal((md.n_cells, 4)) * np.stack([rho, lam, mu, kap], axis=1) * 0.05
+    da = 0.3
+    an = sum(float(np.sum(T[j].grad.numpy() * d[:, j])) for j in range(4)) + float(amp.grad) * da
+    eps = 1e-6
+    obs_np = obs.cpu().numpy()
+
+    def L(sign):
+        ops = model.build(rho + sign * eps * d[:, 0], lam + sign * eps * d[:, 1], mu + sign * eps * d[:, 2],
+                          kap + sign * eps * d[:, 3], 1.0 + sign * eps * da, tau)
+        try:
+            t = gpu_traces(hho, ops, U0, dt, nsteps)
+        finally:
+            hho.hho_ops_destroy(ops)
+        return 0.5 * float(np.sum((t - obs_np) ** 2))
+    fd = (L(1) - L(-1)) / (2 * eps)
+    print("autograd vs central differences: %.12e %.12e" % (an, fd))
+    assert abs(fd - an) <= 1e-6 * abs(fd)

@@ -484,3 +484,54 @@ def test_algorithm1_brackets_the_eigenvalue_limit():
     dt_stable, dt_unstable = T_f / n_stable, T_f / n_unstable
     assert dt_stable < dt_unstable
     assert 0.93 * dt_eig <= dt_stable <= 1.03 * dt_eig, (dt_stable / dt_eig, dt_unstable / dt_eig)
+
+
+def test_compliance_derivatives_match_finite_differences():
+    """The analytic derivatives of the plane-strain compliance used by the
+    oracle's adjoint equal central differences of the compliance."""
+    Sm = np.array([[1.3, -0.4], [-0.4, 0.7]])
+    lam, mu, e = 8.05, 7.225, 1e-6
+    dl = (A.compliance(lam + e, mu, Sm) - A.compliance(lam - e, mu, Sm)) / (2 * e)
+    dm = (A.compliance(lam, mu + e, Sm) - A.compliance(lam, mu - e, Sm)) / (2 * e)
+    assert np.allclose(A.compliance_dlam(lam, mu, Sm), dl, rtol=1e-7, atol=1e-12)
+    assert np.allclose(A.compliance_dmu(lam, mu, Sm), dm, rtol=1e-7, atol=1e-12)
+
+
+def test_dense_adjoint_matches_finite_differences():
+    """The oracle's reverse mode (with tau frozen) against central differences
+    of the forward traces in random material directions."""
+    from oracle import adjoint as ADJ
+    md = synth.quad_grid(4, 4)
+    rng = np.random.default_rng(3)
+    nc = md.n_cells
+    sol = md.cell_domain == 1
+    rho = 1 + rng.random(nc)
+    lam = np.where(sol, 3 + rng.random(nc), 0.0)
+    mu = np.where(sol, 2 + rng.random(nc), 0.0)
+    kap = np.where(sol, 0.0, 1 + rng.random(nc))
+    S0 = system(md, 1, media=(rho, lam, mu, kap))
+    tau = S0.tau.copy()
+    pts = [(0.3, 0.2), (0.6, 0.7), (0.4, 0.5)]
+    src = (0.55, 0.3)
+
+    def build(r, l, m_, k_):
+        S = system(md, 1, media=(r, l, m_, k_), tau_override=tau)
+        st = E.Stepper(S)
+        load, _ = S.point_load(*src, direction=(0.0, 1.0))
+        return ADJ.DenseAdjoint(st, pts, load, lambda t: synth.ricker(t, 5.0))
+    U0 = synth.random_state(S0.nT, 2)
+    nsteps, dt = 12, 0.01
+    G = rng.standard_normal((nsteps, len(pts) * 5))
+    base = build(rho, lam, mu, kap)
+    grad, _ = base.vjp(U0, 0.0, dt, nsteps, G)
+    for trial in range(3):
+        d = rng.standard_normal((nc, 4)) * np.stack([rho, kap, lam, mu], axis=1) * 0.1
+        eps = 1e-6
+        def J(sign):
+            adj = build(rho + sign * eps * d[:, 0], lam + sign * eps * d[:, 2], mu + sign * eps * d[:, 3],
+                        kap + sign * eps * d[:, 1])
+            tr, _ = adj.run(U0, 0.0, dt, nsteps)
+            return float(np.sum(tr.reshape(nsteps, -1) * G))
+        fd = (J(1) - J(-1)) / (2 * eps)
+        an = float(np.sum(grad[:, [0, 1, 2, 3]] * d))
+        assert abs(fd - an) <= 1e-6 * abs(fd), (fd, an)
