@@ -428,12 +428,6 @@ __device__ __forceinline__ void fluid_cell(const StageArgsT<T>& A, int q, int sh
             fluid_face_rate<T, K, RectFace<1>>(A, c, 1, kmx, kmy, kp);
             fluid_face_rate<T, K, RectFace<2>>(A, c, 2, kmx, kmy, kp);
             fluid_face_rate<T, K, RectFace<3>>(A, c, 3, kmx, kmy, kp);
-        } else if (c.nF == 3) {   // triangles: faces unrolled so their loads can overlap
-#pragma unroll
-            for (int j = 0; j < 3; ++j) fluid_face_rate<T, K, GenericFace>(A, c, j, kmx, kmy, kp);
-        } else if (c.nF == 4) {
-#pragma unroll
-            for (int j = 0; j < 4; ++j) fluid_face_rate<T, K, GenericFace>(A, c, j, kmx, kmy, kp);
         } else {
 #pragma unroll 1
             for (int j = 0; j < c.nF; ++j) fluid_face_rate<T, K, GenericFace>(A, c, j, kmx, kmy, kp);
@@ -470,9 +464,6 @@ __device__ __forceinline__ void fluid_cell(const StageArgsT<T>& A, int q, int sh
         fluid_face_trace<T, K, RectFace<1>>(A, c, 1, U);
         fluid_face_trace<T, K, RectFace<2>>(A, c, 2, U);
         fluid_face_trace<T, K, RectFace<3>>(A, c, 3, U);
-    } else if (c.nF == 3) {
-#pragma unroll
-        for (int j = 0; j < 3; ++j) fluid_face_trace<T, K, GenericFace>(A, c, j, U);
     } else {
 #pragma unroll 1
         for (int j = 0; j < c.nF; ++j) fluid_face_trace<T, K, GenericFace>(A, c, j, U);
@@ -663,12 +654,6 @@ __device__ __forceinline__ void solid_cell(const StageArgsT<T>& A, int q, int sh
             solid_face_rate<T, K, RectFace<1>>(A, c, 1, exx, eyy, exy, kvx, kvy);
             solid_face_rate<T, K, RectFace<2>>(A, c, 2, exx, eyy, exy, kvx, kvy);
             solid_face_rate<T, K, RectFace<3>>(A, c, 3, exx, eyy, exy, kvx, kvy);
-        } else if (c.nF == 3) {
-#pragma unroll
-            for (int j = 0; j < 3; ++j) solid_face_rate<T, K, GenericFace>(A, c, j, exx, eyy, exy, kvx, kvy);
-        } else if (c.nF == 4) {
-#pragma unroll
-            for (int j = 0; j < 4; ++j) solid_face_rate<T, K, GenericFace>(A, c, j, exx, eyy, exy, kvx, kvy);
         } else {
 #pragma unroll 1
             for (int j = 0; j < c.nF; ++j) solid_face_rate<T, K, GenericFace>(A, c, j, exx, eyy, exy, kvx, kvy);
@@ -719,9 +704,6 @@ __device__ __forceinline__ void solid_cell(const StageArgsT<T>& A, int q, int sh
         solid_face_trace<T, K, RectFace<1>>(A, c, 1, U);
         solid_face_trace<T, K, RectFace<2>>(A, c, 2, U);
         solid_face_trace<T, K, RectFace<3>>(A, c, 3, U);
-    } else if (c.nF == 3) {
-#pragma unroll
-        for (int j = 0; j < 3; ++j) solid_face_trace<T, K, GenericFace>(A, c, j, U);
     } else {
 #pragma unroll 1
         for (int j = 0; j < c.nF; ++j) solid_face_trace<T, K, GenericFace>(A, c, j, U);

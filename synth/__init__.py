@@ -276,6 +276,36 @@ def hybrid_c3(n_shots, nx=1360, ny=680, k=3):
     return dict(mesh=md, media=media, k=k, sources=srcs, f0=10.0, receivers=rec, h=1.0 / ny)
 
 
+def gaussian_anomaly(md: MeshData, centre, radius, amplitude):
+    """Per-cell multiplicative factor 1 + amplitude exp(-|x - centre|^2 / radius^2)."""
+    cen = md.centroids_approx()
+    r2 = (cen[:, 0] - centre[0]) ** 2 + (cen[:, 1] - centre[1]) ** 2
+    return 1.0 + amplitude * np.exp(-r2 / radius ** 2)
+
+
+def adjoint_c4(n=256, k=2, n_shots=8, n_rec=128):
+    """Two-layer medium on [0,1]^2, 256 x 256 quads, solid below y = 0.5
+    (rho 2.5, vp 3.0, vs 1.7), water above (rho 1, c 1.5).  The true model has
+    a +10 % Gaussian anomaly in v_S (radius 0.06) at a seeded solid point
+    (seed 4, y in [0.3, 0.45]); the current model is the smooth background.
+    n_shots Ricker point forces (f0 = 30) at seeded solid points (seeds 5,
+    6, ...; y in [0.3, 0.45]) and n_rec receivers on the interface y = 0.5,
+    so that 800 CFL-limited steps (t = 0.11) record the scattered field."""
+    md = quad_grid(n, n, 0.0, 1.0, 0.0, 1.0, 0.5)
+    bg = layered_media(md)
+    c = seeded_point(4, 0.2, 0.8, 0.3, 0.45, margin=0.0)
+    f = gaussian_anomaly(md, c, 0.06, 0.10)
+    rho = bg[0]
+    sol = md.cell_domain == SOLID
+    vp = np.where(sol, 3.0, 0.0)
+    vs = np.where(sol, 1.7 * f, 0.0)
+    lam_t, mu_t = lame_from_speeds(rho, vp, vs)
+    true = (rho, np.where(sol, lam_t, 0.0), np.where(sol, mu_t, 0.0), bg[3])
+    srcs = [seeded_point(5 + s, 0.05, 0.95, 0.3, 0.45, margin=0.0) for s in range(n_shots)]
+    rec = receivers_on_line(n_rec, 0.0, 1.0, 0.5)
+    return dict(mesh=md, true=true, background=bg, k=k, sources=srcs, receivers=rec, f0=30.0, anomaly_centre=c)
+
+
 def bilayer_c2(nx=1024, ny=512, k=2):
     """[0,2]x[0,1] quads, solid below y = 0.5 with a seeded +-20 % random field
     (vp, vs share g1 seed 1, rho g2 seed 2), water above; 256 receivers at y = 0.75."""
