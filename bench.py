@@ -47,6 +47,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--k", type=int, default=2)
+    ap.add_argument("--arith", default="f64", choices=["f64", "f32x2"],
+                    help="arithmetic of the headline stage path: FP64 instructions, or double-float pairs "
+                         "(FP64-class accuracy on the FP32 pipes)")
     ap.add_argument("--stages", type=int, default=4)
     ap.add_argument("--nx", type=int, default=1024)
     ap.add_argument("--ny", type=int, default=512)
@@ -55,9 +58,13 @@ def parse():
     ap.add_argument("--shots", type=int, default=16, help="shots of the batched (NEXT-1) measurement")
     ap.add_argument("--batch-precision", default="f32", choices=["f32", "f64"])
     ap.add_argument("--batch-steps", type=int, default=10)
-    ap.add_argument("--batch-nx", type=int, default=1360)
-    ap.add_argument("--batch-ny", type=int, default=680)
+    ap.add_argument("--batch-workload", default="c3", choices=["c3", "c5"],
+                    help="c3: 1360x680 hybrid quads/triangles, k=3; c5: basin section with hanging nodes, k=2")
+    ap.add_argument("--batch-nx", type=int, default=None, help="default 1360 (c3) or 2860 (c5)")
+    ap.add_argument("--batch-ny", type=int, default=None, help="default 680 (c3) or 715 (c5)")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--adjoint-steps", type=int, default=800, help="steps of the adjoint (NEXT-2) measurement")
+    ap.add_argument("--no-adjoint", action="store_true")
     return ap.parse_args()
 
 
@@ -175,19 +182,26 @@ def replica_reduce(ms_local, units_local, world, dist=None, device=None):
     return float(t.item()), float(u.item())
 
 
-def measured_traffic(k, cell_dofs):
-    """DRAM bytes per stage launch from the committed ncu summary, if it was
-    taken on the current stage kernel source (same sha256) and the same k;
-    scaled from the captured case by cell DOFs.  None otherwise."""
+def stage_source_sha():
+    """sha256 of the stage kernel sources (stage.cu, then f2x.cuh)."""
     import hashlib
+    h = hashlib.sha256()
+    for f in ("stage.cu", "f2x.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2505_15771_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
+
+
+def measured_traffic(k, cell_dofs, arith="f64"):
+    """DRAM bytes per stage launch from the committed ncu summary, if it was
+    taken on the current stage kernel sources (same sha256), the same k and
+    arithmetic; scaled from the captured case by cell DOFs.  None otherwise."""
     path = os.path.join(ROOT, "profiles", "stage_kernel_traffic.json")
     if not os.path.exists(path):
         return None
     rec = json.load(open(path))
-    src = open(os.path.join(ROOT, "paper_2505_15771_gb300", "csrc", "stage.cu"), "rb").read()
-    if rec.get("stage_cu_sha256") != hashlib.sha256(src).hexdigest():
+    if rec.get("stage_sources_sha256") != stage_source_sha():
         return None
-    entry = rec.get("k%d" % k)
+    entry = rec.get(("k%d" % k) if arith == "f64" else ("%s_k%d" % (arith, k)))
     if not entry:
         return None
     return entry["dram_bytes_per_launch_per_cell_dof"] * cell_dofs
@@ -213,13 +227,27 @@ def measure_batched(a, torch, hho, solver, hbm_peak):
     import synth
     S = a.shots
     prec = hho.HHO_F32 if a.batch_precision == "f32" else hho.HHO_F64
-    w = synth.hybrid_c3(S, nx=a.batch_nx, ny=a.batch_ny, k=3)
+    if a.batch_workload == "c5":
+        w = synth.basin_c5(nx=a.batch_nx, ny=a.batch_ny, n_shots=S)
+        kk = w["k"]
+        desc = ("basin section 20x5 km on %dx%d coarse squares (4x-refined spline basin, hanging-node polygons, "
+                "triangles along the basin floor), k=%d, ERK4, water over bedrock with a graded sedimentary basin, "
+                "one Ricker point force (f0=15) per shot at a seeded solid point, %d seabed receivers recorded every "
+                "step" % (a.batch_nx, a.batch_ny, kk, len(w["receivers"])))
+        cfl = CFL_TRIANGLES_ERK4_K3
+    else:
+        w = synth.hybrid_c3(S, nx=a.batch_nx, ny=a.batch_ny, k=3)
+        kk = 3
+        desc = ("hybrid %dx%d on [0,2]x[0,1] (quads below y=0.7, triangles above), k=3, ERK4, random-field solid "
+                "under water, one Ricker point force per shot at a seeded solid point, 256 receivers recorded every "
+                "step" % (a.batch_nx, a.batch_ny))
+        cfl = CFL_TRIANGLES_ERK4_K3
     md = w["mesh"]
-    P = solver.Problem(md, w["media"], 3)
-    P.set_shot_sources(w["sources"], [(0.0, 1.0)] * S, 10.0)
+    P = solver.Problem(md, w["media"], kk)
+    P.set_shot_sources(w["sources"], [(0.0, 1.0)] * S, w["f0"])
     P.set_receivers(w["receivers"])
     tab = hho.hho_tableau_erk(4)
-    dt = hho.hho_cfl_dt(P.ops, CFL_TRIANGLES_ERK4_K3, 0.9)
+    dt = hho.hho_cfl_dt(P.ops, cfl, 0.9)
     ndof = P.layout.n_canonical
     state, work = P.batch_buffers(4, S, prec)
     steps = max(1, a.batch_steps)
@@ -258,21 +286,80 @@ def measure_batched(a, torch, hho, solver, hbm_peak):
     avg = stage_ms * 1e-3 / max(nl, 1)
     out = {"metric": "shot-cell-DOF updates/s per ERK stage", "value": value, "unit": "shot-cell-DOF-stage/s",
            "precision": a.batch_precision, "shots": S, "steps": steps, "ms_per_step": ms / steps,
-           "workload": "hybrid %dx%d on [0,2]x[0,1] (quads below y=0.7, triangles above), "
-                       "k=3, ERK4, random-field solid under water, one Ricker point force per shot at a seeded "
-                       "solid point, 256 receivers recorded every step" % (a.batch_nx, a.batch_ny),
+           "workload": desc,
            "cells": int(md.n_cells), "cell_dofs": int(ndof), "dt": dt, "seismograms_finite": finite,
            "fp64_single_shot_same_mesh": v64, "speedup_vs_sequential_fp64": value / v64,
            "roofline": {"bound": "hbm", "achieved": per_launch / avg / 1e9, "peak": hbm_peak, "unit": "GB/s",
                         "frac": per_launch / avg / 1e9 / hbm_peak,
                         "algorithmic_bytes_per_launch": per_launch, "avg_launch_ms": avg * 1e3,
-                        "kernel": "stage_kernel<%s,3,1>" % ("float" if prec == hho.HHO_F32 else "double")}}
+                        "kernel": "stage_kernel<%s,%d,1>" % ("float" if prec == hho.HHO_F32 else "double", kk)}}
     P.close()
+    return out
+
+
+def measure_adjoint(a, torch, hho):
+    """Discrete adjoint on the 256 x 256 two-layer workload (k = 2, ERK4,
+    800 steps, checkpoints every 50, 128 interface receivers): one shot's
+    misfit gradient w.r.t. every cell's (rho, kappa, lambda, mu), timed with
+    CUDA events against the forward run with trace recording."""
+    import synth
+    w = synth.adjoint_c4()
+    md = w["mesh"]
+    nc = md.n_cells
+    k, nsteps, ckpt = w["k"], a.adjoint_steps, 50
+    stream = torch.cuda.current_stream()
+    tab = hho.hho_tableau_erk(4)
+    mesh = hho.hho_mesh_create(md.xy, md.cell_ptr, md.cell_vtx, md.cell_domain)
+    ops = hho.hho_operators_build(mesh, k, *w["background"])
+    hho.hho_mesh_destroy(mesh)
+    hho.hho_sources_set(ops, [w["sources"][0]], [(0.0, 1.0)], [w["f0"]], [1.0 / w["f0"]], [1.0])
+    hho.hho_receivers_set(ops, w["receivers"])
+    dt = hho.hho_cfl_dt(ops, CFL_SQUARES_ERK4[k], 0.9)
+    lay = hho.hho_state_layout(ops)
+    x = torch.zeros(lay.n_state, dtype=torch.float64, device="cuda")
+    wk = torch.empty(hho.hho_work_size(ops, tab), dtype=torch.float64, device="cuda")
+    seis = torch.zeros((nsteps, len(w["receivers"]), 5), dtype=torch.float64, device="cuda")
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    hho.hho_erk_step_record(ops, tab, 0.0, dt, min(nsteps, 3), x.data_ptr(), wk.data_ptr(), seis.data_ptr(),
+                            stream.cuda_stream)
+    x.zero_()
+    torch.cuda.synchronize()
+    e[0].record(stream)
+    hho.hho_erk_step_record(ops, tab, 0.0, dt, nsteps, x.data_ptr(), wk.data_ptr(), seis.data_ptr(),
+                            stream.cuda_stream)
+    e[1].record(stream)
+    torch.cuda.synchronize()
+    fwd_ms = e[0].elapsed_time(e[1])
+    g = (0.01 * seis).contiguous()   # cotangent: a residual of 1 % of the traces
+    x0 = torch.zeros_like(x)
+    nw = hho.hho_adjoint_work_size(ops, tab, nsteps, ckpt)
+    aw = torch.empty(nw, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    e[2].record(stream)
+    grad, _ = hho.hho_adjoint_vjp(ops, tab, 0.0, dt, nsteps, ckpt, x0.data_ptr(), g.data_ptr(), aw.data_ptr(), nw,
+                                  nc, n_src=1, stream=stream.cuda_stream)
+    e[3].record(stream)
+    torch.cuda.synchronize()
+    adj_ms = e[2].elapsed_time(e[3])
+    ndof = lay.n_canonical
+    out = {"metric": "adjoint cell-DOF-stages/s (forward-equivalent work / gradient time)",
+           "value": ndof * 4 * nsteps / (adj_ms * 1e-3), "unit": "cell-DOF-stage/s",
+           "workload": "256x256 quads, two-layer (water over solid), k=2, ERK4, %d steps, checkpoints every %d, "
+                       "one Ricker shot, 128 interface receivers, gradient w.r.t. per-cell rho/kappa/lambda/mu"
+                       % (nsteps, ckpt),
+           "cells": int(nc), "cell_dofs": int(ndof), "steps": nsteps, "gradient_ms": adj_ms,
+           "forward_record_ms": fwd_ms, "adjoint_over_forward": adj_ms / fwd_ms,
+           "gradient_finite": bool(np.isfinite(grad).all()), "dtype": "f64"}
+    hho.hho_ops_destroy(ops)
     return out
 
 
 def main():
     a = parse()
+    if a.batch_nx is None:
+        a.batch_nx = 2860 if a.batch_workload == "c5" else 1360
+    if a.batch_ny is None:
+        a.batch_ny = 715 if a.batch_workload == "c5" else 680
     if a.impl == "reference":
         run_reference(a)
         return
@@ -296,6 +383,8 @@ def main():
     P = solver.Problem(md, media, a.k)
     P.set_sources([w["source"]], [(0.0, 1.0)], 10.0)
     P.set_receivers(w["receivers"])
+    ARITH = {"f64": hho.HHO_F64, "f32x2": hho.HHO_F32X2}
+    P.set_arithmetic(ARITH[a.arith])
     tab = hho.hho_tableau_erk(a.stages)
     # CFL-limited dt (Eq. CFL): 0.9 x the ERK4 eigenvalue limit of the stage
     # operator on squares (c# dt / h = 0.233, 0.122, 0.082 for k = 1, 2, 3)
@@ -350,6 +439,11 @@ def main():
     if os.path.exists(pk):
         peaks = json.load(open(pk))
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    hbm_view = {"algorithmic_bytes_per_launch": bytes_min / a.stages,
+                "achieved_gbs": bytes_min / a.stages / avg_launch_s / 1e9,
+                "peak_gbs": hbm_peak, "frac": bytes_min / a.stages / avg_launch_s / 1e9 / hbm_peak,
+                "kernel_design_bytes_per_launch": bytes_kernel / a.stages,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in peaks else "fallback"}
     roofline = {
         "bound": "alu",
         "achieved": ops_per_launch / avg_launch_s / 1e12,
@@ -361,12 +455,39 @@ def main():
         "avg_launch_ms": avg_launch_s * 1e3,
         "launches_timed": n_launch,
         "peak_source": "live DFMA probe (libhho_probe.so), best of 3",
-        "hbm_view": {"algorithmic_bytes_per_launch": bytes_min / a.stages,
-                     "achieved_gbs": bytes_min / a.stages / avg_launch_s / 1e9,
-                     "peak_gbs": hbm_peak, "frac": bytes_min / a.stages / avg_launch_s / 1e9 / hbm_peak,
-                     "kernel_design_bytes_per_launch": bytes_kernel / a.stages,
-                     "peak_source": "MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in peaks else "fallback"},
+        "hbm_view": hbm_view,
     }
+    if a.arith == "f32x2":
+        # double-float: no FP64 instruction in the stage kernel; the bound is
+        # HBM traffic (the FP64-equivalent lane-op rate is kept as a view)
+        alu_view = {k2: roofline[k2] for k2 in ("achieved", "peak", "unit", "frac", "peak_source")}
+        alu_view["note"] = "FP64-equivalent lane-ops of the cost model per second, against the FP64 DFMA probe"
+        roofline = {"bound": "hbm", "achieved": hbm_view["achieved_gbs"], "peak": hbm_peak, "unit": "GB/s",
+                    "frac": hbm_view["frac"], "traffic": measured_traffic(a.k, ndof, "f32x2"),
+                    "kernel": "stage_kernel<f2x,%d,1>" % a.k, "avg_launch_ms": avg_launch_s * 1e3,
+                    "launches_timed": n_launch, "peak_source": hbm_view["peak_source"],
+                    "algorithmic_bytes_per_launch": hbm_view["algorithmic_bytes_per_launch"],
+                    "alu_view": alu_view}
+
+    # the other arithmetic on the same workload, for comparison
+    other_name = "f64" if a.arith == "f32x2" else "f32x2"
+    P.set_arithmetic(ARITH[other_name])
+    run(3, 0.0)
+    torch.cuda.synchronize()
+    hho.hho_profile_enable(P.ops, True)
+    o0 = torch.cuda.Event(enable_timing=True)
+    o1 = torch.cuda.Event(enable_timing=True)
+    o0.record(stream)
+    run(a.steps, 3 * dt)
+    o1.record(stream)
+    torch.cuda.synchronize()
+    o_stage_ms, o_n = hho.hho_profile_read(P.ops)
+    hho.hho_profile_enable(P.ops, False)
+    other_arith = {"arith": other_name, "value": ndof * a.stages * a.steps / (o0.elapsed_time(o1) * 1e-3),
+                   "unit": UNIT, "avg_launch_ms": o_stage_ms / max(o_n, 1),
+                   "hbm_frac": bytes_min / a.stages / (o_stage_ms * 1e-3 / max(o_n, 1)) / 1e9 / hbm_peak}
+    P.set_arithmetic(ARITH[a.arith])
+    state.zero_()
 
     # end to end through the host-buffer entry point (pinned host state)
     e2e = None
@@ -397,19 +518,23 @@ def main():
         del state, work, seis
         torch.cuda.empty_cache()
         batched = measure_batched(a, torch, hho, solver, hbm_peak)
+    adjoint = None
+    if rank == 0 and not a.no_adjoint:
+        torch.cuda.empty_cache()
+        adjoint = measure_adjoint(a, torch, hho)
 
     launches = 1 + a.stages * a.steps + a.steps      # trace init + stages + receiver records
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
                 "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "vs_baseline": None, "dtype": a.arith, "data": "synthetic",
                 "config": {"workload": workload_name(a), "cells": int(md.n_cells), "cell_dofs": int(ndof),
                            "k": a.k, "tableau": "erk%d" % a.stages, "dt": dt,
                            "l2": "inputs larger than L2 (state %.0f MB, work %.0f MB per GPU)" % (state_mb, work_mb),
                            "parallelism": "replicas" if world > 1 else "single GPU",
                            "energy_after_warmup": e_warm, "energy_after_timed": e_end},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
-                "batched": batched}
+                "other_arith": other_arith, "batched": batched, "adjoint": adjoint}
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()

@@ -188,8 +188,19 @@ typedef struct {
 int hho_tableau_erk(int32_t s, hho_tableau* out);
 
 /* Size in doubles of the caller-owned work buffer that hho_erk_step needs
- * for this tableau (stage vector, partial sums, two trace buffers). */
+ * for this tableau (stage vector, partial sums, two trace buffers, energy
+ * scratch, and room for a double-float copy of the state). */
 int hho_work_size(const hho_ops* ops, const hho_tableau* tab, int64_t* n_doubles);
+
+/* Arithmetic of hho_erk_step, hho_erk_step_record, hho_erk_run_host and
+ * hho_apply on this operator: HHO_F64 (default, FP64 instructions) or
+ * HHO_F32X2 (double-float pairs on the FP32 pipes, about 48 significant bits;
+ * see HHO_F32X2 below).  With HHO_F32X2 the FP64 device state is split into a
+ * pair copy inside d_work at the start of each call and rounded back at the
+ * end; the stage operator itself is unchanged (Eq. ex_solve).  HHO_EINVAL
+ * for other values.  No counterpart in the paper: GB300 issues FP64 at a
+ * small fraction of its FP32 rate. */
+int hho_set_arithmetic(hho_ops* ops, int32_t arith);
 
 /* Point sources with a Ricker wavelet
  * w(t) = amp (1 - 2 pi^2 f0^2 (t - t0)^2) exp(-pi^2 f0^2 (t - t0)^2):
@@ -240,6 +251,10 @@ int hho_apply(hho_ops* ops, double t, const double* d_state, double* d_rate, dou
 
 #define HHO_F64 0   /* state, traces and arithmetic in FP64 */
 #define HHO_F32 1   /* state, traces and arithmetic in FP32; operators built in FP64 and rounded */
+#define HHO_F32X2 2 /* double-float: every value a pair of FP32 numbers hi + lo (about 48
+                       significant bits, 8 bytes), arithmetic by error-free transforms on
+                       the FP32 pipes; operators built in FP64 and split into pairs;
+                       seismograms in FP64 */
 
 /* Element counts (of the precision's type) of a batched state
  * (n_shots x n_state, shot-major) and of the work buffer hho_batch_erk_step

@@ -110,52 +110,57 @@ __global__ void axpby_kernel(int64_t n, double a, const double* x, double b, con
     }
 }
 
-// lambda += R^T G for one time node: the transpose of record_kernel.  One
-// thread walks the receivers in order (deterministic sums).
-__global__ void inject_kernel(DevOps op, int n_rec, const int32_t* __restrict__ ri, const double* __restrict__ rd,
-                              const double* __restrict__ G, double* lam) {
-    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+// lambda += R^T G for one time node: the transpose of record_kernel.  Block t
+// owns the t-th cell read by the receivers; thread (field, i) adds the
+// contributions of that cell's receivers to lambda[field, i] in increasing
+// receiver order, so each entry receives the same sums in the same order as a
+// walk over the receivers one by one.  blockDim >= 5 n.
+__global__ void inject_kernel(DevOps op, int n_inj, const int32_t* __restrict__ inj, const int32_t* __restrict__ ri,
+                              const double* __restrict__ rd, const double* __restrict__ G, double* lam) {
+    const int t = blockIdx.x;
     const int n = op.n;
+    const int fld = threadIdx.x / n, i = threadIdx.x - fld * n;
+    if (t >= n_inj) return;
+    const int dom = inj[n_inj + 1 + 2 * t], q = inj[n_inj + 1 + 2 * t + 1];
+    if (fld >= (dom == 0 ? 3 : 5)) return;
+    const int32_t* recs = inj + 3 * n_inj + 1;
     const int stride = 2 * n + 15;
-    double* lf = lam;
-    double* ls = lam + (size_t)3 * n * op.Nf;
-    for (int r = 0; r < n_rec; ++r) {
+    const int N = dom == 0 ? op.Nf : op.Ns;
+    double* base = dom == 0 ? lam : lam + (size_t)3 * n * op.Nf;
+    const size_t idx = (size_t)(fld * n + i) * N + q;
+    double acc = base[idx];
+    for (int e = inj[t]; e < inj[t + 1]; ++e) {
+        const int r = recs[e];
         const double* d = rd + (size_t)r * stride;
-        const int kind = ri[4 * r], qf = ri[4 * r + 1], qs = ri[4 * r + 2];
+        const int kind = ri[4 * r];
         const double* g = G + 5 * r;
-        auto add = [&](double* base, int N, int q, int field, const double* phi, double v) {
-            if (v == 0.0) return;
-            for (int i = 0; i < n; ++i) base[(size_t)(field * n + i) * N + q] += v * phi[i];
-        };
-        if (kind == 0) {   // [p, m_x, m_y]
-            add(lf, op.Nf, qf, 2, d, g[0]);
-            add(lf, op.Nf, qf, 0, d, g[1]);
-            add(lf, op.Nf, qf, 1, d, g[2]);
+        double v;
+        const double* phi = d;
+        if (kind == 0) {          // [p, m_x, m_y]
+            v = fld == 2 ? g[0] : (fld == 0 ? g[1] : g[2]);
         } else if (kind == 1) {   // [v_x, v_y, s_xx, s_yy, s_xy]
-            add(ls, op.Ns, qs, 3, d, g[0]);
-            add(ls, op.Ns, qs, 4, d, g[1]);
-            add(ls, op.Ns, qs, 0, d, g[2]);
-            add(ls, op.Ns, qs, 1, d, g[3]);
-            add(ls, op.Ns, qs, 2, d, g[4]);
-        } else {   // interface: [p_F, v_F] = Ai [w_f, w_sx, w_sy]
-            const double* pf = d;
-            const double* ps = d + n;
+            v = fld == 3 ? g[0] : fld == 4 ? g[1] : fld == 0 ? g[2] : fld == 1 ? g[3] : g[4];
+        } else {                  // interface: [p_F, v_F] = Ai [w_f, w_sx, w_sy]
             const double tf = d[2 * n], ts = d[2 * n + 1];
             const double nfx = d[2 * n + 2], nfy = d[2 * n + 3], nsx = d[2 * n + 4], nsy = d[2 * n + 5];
             const double* Ai = d + 2 * n + 6;
-            const double hf = Ai[0] * g[0] + Ai[3] * g[1] + Ai[6] * g[2];
-            const double hx = Ai[1] * g[0] + Ai[4] * g[1] + Ai[7] * g[2];
-            const double hy = Ai[2] * g[0] + Ai[5] * g[1] + Ai[8] * g[2];
-            add(lf, op.Nf, qf, 2, pf, tf * hf);
-            add(lf, op.Nf, qf, 0, pf, -nfx * hf);
-            add(lf, op.Nf, qf, 1, pf, -nfy * hf);
-            add(ls, op.Ns, qs, 3, ps, ts * hx);
-            add(ls, op.Ns, qs, 4, ps, ts * hy);
-            add(ls, op.Ns, qs, 0, ps, -nsx * hx);
-            add(ls, op.Ns, qs, 2, ps, -(nsy * hx + nsx * hy));
-            add(ls, op.Ns, qs, 1, ps, -nsy * hy);
+            if (dom == 0) {
+                const double hf = Ai[0] * g[0] + Ai[3] * g[1] + Ai[6] * g[2];
+                v = fld == 2 ? tf * hf : (fld == 0 ? -nfx * hf : -nfy * hf);
+            } else {
+                const double hx = Ai[1] * g[0] + Ai[4] * g[1] + Ai[7] * g[2];
+                const double hy = Ai[2] * g[0] + Ai[5] * g[1] + Ai[8] * g[2];
+                phi = d + n;
+                v = fld == 3 ? ts * hx
+                    : fld == 4 ? ts * hy
+                    : fld == 0 ? -nsx * hx
+                    : fld == 2 ? -(nsy * hx + nsx * hy)
+                               : -nsy * hy;
+            }
         }
+        if (v != 0.0) acc += v * phi[i];
     }
+    base[idx] = acc;
 }
 
 // dL/dtheta += mu^T dk/dtheta with dk/dtheta from the raw rate (MODE_RAW).
@@ -378,9 +383,10 @@ extern "C" int hho_adjoint_vjp(hho_ops* ops, const hho_tableau* tab, double t0, 
         for (int64_t m = nst - 1; m >= 0; --m) {
             const int64_t n = n0 + m + 1;                            // step n: U^{n-1} -> U^n
             const double tn = t0 + (double)(n - 1) * dt;
-            if (ops->n_rec > 0)
-                inject_kernel<<<1, 32, 0, st>>>(ops->dev, ops->n_rec, ops->d_rec_int, ops->d_rec_dbl,
-                                                d_cotangent + (size_t)(n - 1) * 5 * ops->n_rec, B.lam);
+            if (ops->n_inj > 0)
+                inject_kernel<<<ops->n_inj, (5 * ops->n + 31) / 32 * 32, 0, st>>>(
+                    ops->dev, ops->n_inj, ops->d_inj, ops->d_rec_int, ops->d_rec_dbl,
+                    d_cotangent + (size_t)(n - 1) * 5 * ops->n_rec, B.lam);
             if (!copy(B.acc, B.lam, S)) return HHO_ECUDA;
             axpby_kernel<<<grid1(s * S), 256, 0, st>>>(s * S, 0.0, nullptr, 0.0, nullptr, B.pend);
             for (int j = s - 1; j >= 0; --j) {

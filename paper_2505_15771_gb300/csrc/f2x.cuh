@@ -1,0 +1,102 @@
+// Double-float ("double-word") arithmetic on the FP32 pipes.
+//
+// A value is the unevaluated sum hi + lo of two FP32 numbers with
+// hi = RN(hi + lo), about 48 significant bits: FP64-class accuracy for the
+// stage operator at FP32 issue rates (GB300 runs FP32 at roughly 60x its
+// FP64 rate).  The building blocks are the error-free transforms
+//   TwoSum   (Knuth, TAOCP vol. 2): s + t = a + b exactly,
+//   Fast2Sum (Dekker 1971): the same for |a| >= |b|,
+//   TwoProd  with FMA: p + e = a * b exactly,
+// and the double-word operations analysed by Joldes, Muller and Popescu,
+// "Tight and rigorous error bounds for basic building blocks of double-word
+// arithmetic", ACM TOMS 44(2), 2017:
+//   add: SloppyDWPlusDW (TwoSum of the high parts, plain sum of the low
+//        parts, Fast2Sum renormalisation);
+//   mul: DWTimesDW with FMA (the xl * yl term dropped);
+//   fma: the DWTimesDW product left unnormalised and added as in add;
+//   div: one Newton-style correction of the FP32 quotient (Dekker 1971).
+// No step relies on FMA contraction of a separate multiply and add: where
+// the exact product error is needed the FMA is explicit.  The type is a plain
+// pair so that arrays of it have the layout of FP64 arrays (8 bytes a value).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "hho_internal.h"
+
+__device__ __forceinline__ f2x f2x_fast_two_sum(float a, float b) {
+    const float s = a + b;
+    const float z = s - a;
+    return f2x{s, b - z};
+}
+
+__device__ __forceinline__ f2x f2x_two_sum(float a, float b) {
+    const float s = a + b;
+    const float ap = s - b;
+    const float bp = s - ap;
+    return f2x{s, (a - ap) + (b - bp)};
+}
+
+__device__ __forceinline__ f2x operator+(f2x x, f2x y) {
+    const f2x s = f2x_two_sum(x.hi, y.hi);
+    const float w = s.lo + (x.lo + y.lo);
+    return f2x_fast_two_sum(s.hi, w);
+}
+__device__ __forceinline__ f2x operator-(f2x x) { return f2x{-x.hi, -x.lo}; }
+__device__ __forceinline__ f2x operator-(f2x x, f2x y) { return x + (-y); }
+__device__ __forceinline__ f2x& operator+=(f2x& x, f2x y) { return x = x + y; }
+__device__ __forceinline__ f2x& operator-=(f2x& x, f2x y) { return x = x - y; }
+
+__device__ __forceinline__ f2x operator*(f2x x, f2x y) {
+    const float p = x.hi * y.hi;
+    float e = fmaf(x.hi, y.hi, -p);
+    e = fmaf(x.hi, y.lo, e);
+    e = fmaf(x.lo, y.hi, e);
+    return f2x_fast_two_sum(p, e);
+}
+
+// x * y + z
+__device__ __forceinline__ f2x fma(f2x x, f2x y, f2x z) {
+    const float p = x.hi * y.hi;
+    float e = fmaf(x.hi, y.hi, -p);
+    e = fmaf(x.hi, y.lo, e);
+    e = fmaf(x.lo, y.hi, e);
+    const f2x s = f2x_two_sum(p, z.hi);
+    const float w = s.lo + (e + z.lo);
+    return f2x_fast_two_sum(s.hi, w);
+}
+
+// c * x and c * x + z for an FP32 constant c (the exact small integers of
+// the polynomial derivatives)
+__device__ __forceinline__ f2x mulc(float c, f2x x) {
+    const float p = c * x.hi;
+    float e = fmaf(c, x.hi, -p);
+    e = fmaf(c, x.lo, e);
+    return f2x_fast_two_sum(p, e);
+}
+__device__ __forceinline__ f2x fmac(float c, f2x x, f2x z) {
+    const float p = c * x.hi;
+    float e = fmaf(c, x.hi, -p);
+    e = fmaf(c, x.lo, e);
+    const f2x s = f2x_two_sum(p, z.hi);
+    const float w = s.lo + (e + z.lo);
+    return f2x_fast_two_sum(s.hi, w);
+}
+
+__device__ __forceinline__ f2x operator/(f2x x, f2x y) {
+    const float q = x.hi / y.hi;
+    const f2x r = x - mulc(q, y);
+    return f2x_fast_two_sum(q, r.hi / y.hi);
+}
+
+// Read-only load of a pair (one 8-byte load).
+__device__ __forceinline__ f2x __ldg(const f2x* p) {
+    const float2 v = __ldg(reinterpret_cast<const float2*>(p));
+    return f2x(v.x, v.y);
+}
+
+// Scalar helpers shared by the FP64, FP32 and double-float instantiations.
+__device__ __forceinline__ double mulc(float c, double x) { return (double)c * x; }
+__device__ __forceinline__ float mulc(float c, float x) { return c * x; }
+__device__ __forceinline__ double fmac(float c, double x, double z) { return fma((double)c, x, z); }
+__device__ __forceinline__ float fmac(float c, float x, float z) { return fmaf(c, x, z); }

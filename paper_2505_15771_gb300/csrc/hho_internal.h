@@ -9,6 +9,25 @@
 
 void hho_set_error(const char* fmt, ...);
 
+#if defined(__CUDACC__)
+#define HHO_HD __host__ __device__
+#else
+#define HHO_HD
+#endif
+
+// A double-float value hi + lo: two FP32 numbers with hi = RN(hi + lo),
+// about 48 significant bits (arithmetic in f2x.cuh).  8 bytes: arrays of it
+// have the layout of FP64 arrays.
+struct alignas(8) f2x {
+    float hi, lo;
+    f2x() = default;
+    HHO_HD constexpr f2x(float h, float l) : hi(h), lo(l) {}
+    HHO_HD constexpr explicit f2x(int v) : hi((float)v), lo(0.0f) {}
+    // split of an FP64 value: hi = RN(v), lo = RN(v - hi) (v - hi is exact)
+    HHO_HD explicit f2x(double v) : hi((float)v), lo((float)(v - (double)(float)v)) {}
+    HHO_HD explicit operator double() const { return (double)hi + (double)lo; }
+};
+
 // Face types (Sec. 3.1 face sets).
 enum { FT_FLUID = 0, FT_SOLID = 1, FT_IFACE = 2, FT_BND_FLUID = 3, FT_BND_SOLID = 4 };
 
@@ -43,6 +62,7 @@ struct DevOps {
     int32_t Nf, Ns;          // padded cell slots per domain (multiples of 32)
     int32_t SF, SS;          // face-side slots per domain
     int32_t n_warps_f, n_warps_s;
+    int32_t max_nf;              // most faces of any class
     const int32_t* warp_class;   // [n_warps_f + n_warps_s]
     const int32_t* cls_int;      // [n_classes][CI_STRIDE]
     const double* cls_dbl;       // class matrices, see operators.cpp
@@ -61,6 +81,13 @@ struct DevOps {
     const float* beta_f_f32;
     const float* beta_s_f32;
     const float* if_coef_f32;
+    // double-float copies, for the double-float path
+    const f2x* cls_x;
+    const f2x* scal_f_x;
+    const f2x* scal_s_x;
+    const f2x* beta_f_x;
+    const f2x* beta_s_x;
+    const f2x* if_coef_x;
 };
 
 // Fluid scalars: A_m = 1/(rho h), A_p = kappa/h, tau.  Solid: c1 = (lambda+2mu)/h,
@@ -159,6 +186,12 @@ struct hho_ops {
     std::vector<uint8_t> poly_dom;
     std::vector<int64_t> face_cells, cell_faces;
     std::vector<int32_t> face_type, face_local;
+    std::vector<int64_t> iface_faces;                 // the fluid-solid interface faces
+    // point location: uniform bucket grid over the cells' bounding boxes,
+    // each bucket listing its cells in increasing order
+    int32_t loc_gx = 0, loc_gy = 0;
+    double loc_x0 = 0.0, loc_y0 = 0.0, loc_dx = 1.0, loc_dy = 1.0;
+    std::vector<int64_t> loc_ptr, loc_ids;
     // per-shot sources of the batched path
     int32_t n_shot_src = 0;
     int32_t* d_shot_src_dom = nullptr;
@@ -167,6 +200,10 @@ struct hho_ops {
     float* d_shot_src_g32 = nullptr;
     double shot_f0 = 0.0, shot_t0 = 0.0, shot_amp = 0.0;
     float* d_src_g32 = nullptr;
+    f2x* d_src_gx = nullptr;
+    f2x* d_shot_src_gx = nullptr;
+    // arithmetic of the single-shot stepping entry points (HHO_F64 or HHO_F32X2)
+    int32_t arith = HHO_F64;
     // sources
     int32_t n_src = 0;
     int32_t src_dom[MAX_SOURCES], src_q[MAX_SOURCES];
@@ -176,6 +213,11 @@ struct hho_ops {
     int32_t n_rec = 0;
     int32_t* d_rec_int = nullptr;
     double* d_rec_dbl = nullptr;
+    // transpose of recording (adjoint): the cells the receivers read, each with
+    // its receivers in increasing order.  One int block:
+    // [ptr: n_inj + 1][cell: 2 n_inj (domain, position)][receiver ids]
+    int32_t n_inj = 0;
+    int32_t* d_inj = nullptr;
     // energy
     double* d_mass_f = nullptr;   // per fluid cell: rho h^2, h^2/kappa
     double* d_mass_s = nullptr;   // per solid cell: h^2 * compliance (3), rho h^2

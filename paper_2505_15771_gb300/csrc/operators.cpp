@@ -24,6 +24,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <new>
 #include <vector>
 
@@ -164,6 +165,65 @@ bool point_in_cell(const std::vector<double>& xy, const int64_t* vtx, int nv, do
         if (cr < -1e-12 * scale * scale) return false;
     }
     return true;
+}
+
+// Bucket grid for locate(): about one bucket per cell over the mesh's
+// bounding box; each cell is listed in every bucket its bounding box
+// (enlarged by 1e-9 of its size, beyond point_in_cell's tolerance) meets.
+void build_locator(hho_ops* ops) {
+    const int64_t nc = ops->nc;
+    ops->loc_gx = ops->loc_gy = 0;
+    if (nc <= 0) return;
+    std::vector<double> bb((size_t)4 * nc);
+    double X0 = 1e300, X1 = -1e300, Y0 = 1e300, Y1 = -1e300;
+    for (int64_t c = 0; c < nc; ++c) {
+        double xmin = 1e300, xmax = -1e300, ymin = 1e300, ymax = -1e300;
+        for (int64_t e = ops->poly_ptr[c]; e < ops->poly_ptr[c + 1]; ++e) {
+            const double px = ops->poly_xy[2 * ops->poly_vtx[e]], py = ops->poly_xy[2 * ops->poly_vtx[e] + 1];
+            xmin = std::min(xmin, px); xmax = std::max(xmax, px);
+            ymin = std::min(ymin, py); ymax = std::max(ymax, py);
+        }
+        const double pad = 1e-9 * std::max(xmax - xmin, ymax - ymin);
+        bb[4 * c + 0] = xmin - pad; bb[4 * c + 1] = xmax + pad;
+        bb[4 * c + 2] = ymin - pad; bb[4 * c + 3] = ymax + pad;
+        X0 = std::min(X0, bb[4 * c]); X1 = std::max(X1, bb[4 * c + 1]);
+        Y0 = std::min(Y0, bb[4 * c + 2]); Y1 = std::max(Y1, bb[4 * c + 3]);
+    }
+    const double W = std::max(X1 - X0, 1e-300), H = std::max(Y1 - Y0, 1e-300);
+    const double target = (double)std::min<int64_t>(nc, (int64_t)1 << 22);
+    int64_t gx = std::max<int64_t>(1, std::min<int64_t>(1 << 14, (int64_t)std::llround(std::sqrt(target * W / H))));
+    int64_t gy = std::max<int64_t>(1, std::min<int64_t>(1 << 14, (int64_t)std::llround(target / (double)gx)));
+    ops->loc_gx = (int32_t)gx;
+    ops->loc_gy = (int32_t)gy;
+    ops->loc_x0 = X0;
+    ops->loc_y0 = Y0;
+    ops->loc_dx = W / (double)gx;
+    ops->loc_dy = H / (double)gy;
+    auto range = [&](double lo, double hi, double o, double d, int64_t g, int64_t* a, int64_t* b) {
+        *a = std::min<int64_t>(std::max<int64_t>((int64_t)std::floor((lo - o) / d), 0), g - 1);
+        *b = std::min<int64_t>(std::max<int64_t>((int64_t)std::floor((hi - o) / d), 0), g - 1);
+    };
+    std::vector<int64_t> cnt((size_t)gx * gy + 1, 0);
+    for (int pass = 0; pass < 2; ++pass) {
+        if (pass == 1) {
+            for (size_t i = 1; i < cnt.size(); ++i) cnt[i] += cnt[i - 1];
+            ops->loc_ptr.assign(cnt.size(), 0);
+            for (size_t i = 1; i < cnt.size(); ++i) ops->loc_ptr[i] = cnt[i - 1];
+            ops->loc_ids.assign((size_t)cnt.back(), 0);
+            cnt.assign(ops->loc_ptr.begin(), ops->loc_ptr.end());
+        }
+        for (int64_t c = 0; c < nc; ++c) {
+            int64_t ax, bx, ay, by;
+            range(bb[4 * c], bb[4 * c + 1], X0, ops->loc_dx, gx, &ax, &bx);
+            range(bb[4 * c + 2], bb[4 * c + 3], Y0, ops->loc_dy, gy, &ay, &by);
+            for (int64_t j = ay; j <= by; ++j)
+                for (int64_t i = ax; i <= bx; ++i) {
+                    const int64_t k = j * gx + i;
+                    if (pass == 0) ++cnt[k];
+                    else ops->loc_ids[(size_t)cnt[k]++] = c;
+                }
+        }
+    }
 }
 
 }  // namespace
@@ -585,6 +645,9 @@ extern "C" int hho_operators_build_tau(const hho_mesh* m, int32_t k, const doubl
     ops->cell_faces = m->cell_faces;
     ops->face_type = m->face_type;
     ops->face_local = m->face_local;
+    for (int64_t F = 0; F < (int64_t)m->face_type.size(); ++F)
+        if (m->face_type[F] == FT_IFACE) ops->iface_faces.push_back(F);
+    build_locator(ops);
     double hmin = 1e300, cm = 0.0;
     for (int64_t c = 0; c < nc; ++c) {
         int64_t b = m->cell_ptr[c];
@@ -611,6 +674,9 @@ extern "C" int hho_operators_build_tau(const hho_mesh* m, int32_t k, const doubl
     D.SS = SS;
     D.n_warps_f = Nf / 32;
     D.n_warps_s = Ns / 32;
+    D.max_nf = 0;
+    for (int32_t cl = 0; cl < (int32_t)(cls_int.size() / CI_STRIDE); ++cl)
+        D.max_nf = std::max(D.max_nf, cls_int[(size_t)cl * CI_STRIDE + CI_NF]);
     D.warp_class = dev_upload(ops, warp_class, &err);
     D.cls_int = dev_upload(ops, cls_int, &err);
     D.cls_dbl = dev_upload(ops, cls_dbl, &err);
@@ -629,6 +695,17 @@ extern "C" int hho_operators_build_tau(const hho_mesh* m, int32_t k, const doubl
     D.beta_f_f32 = dev_upload(ops, to_f32(beta_f), &err);
     D.beta_s_f32 = dev_upload(ops, to_f32(beta_s), &err);
     D.if_coef_f32 = dev_upload(ops, to_f32(if_coef), &err);
+    auto to_x = [](const std::vector<double>& v) {
+        std::vector<f2x> o(v.size());
+        for (size_t i = 0; i < v.size(); ++i) o[i] = f2x(v[i]);
+        return o;
+    };
+    D.cls_x = dev_upload(ops, to_x(cls_dbl), &err);
+    D.scal_f_x = dev_upload(ops, to_x(scal_f), &err);
+    D.scal_s_x = dev_upload(ops, to_x(scal_s), &err);
+    D.beta_f_x = dev_upload(ops, to_x(beta_f), &err);
+    D.beta_s_x = dev_upload(ops, to_x(beta_s), &err);
+    D.if_coef_x = dev_upload(ops, to_x(if_coef), &err);
     ops->d_if_coef_adj = dev_upload(ops, if_coef_adj, &err);
     {
         std::vector<double> minv;
@@ -660,11 +737,14 @@ extern "C" void hho_ops_destroy(hho_ops* ops) {
     for (void* p : ops->allocations) cudaFree(p);
     if (ops->d_src_g) cudaFree(ops->d_src_g);
     if (ops->d_src_g32) cudaFree(ops->d_src_g32);
+    if (ops->d_src_gx) cudaFree(ops->d_src_gx);
+    if (ops->d_shot_src_gx) cudaFree(ops->d_shot_src_gx);
     if (ops->d_shot_src_dom) cudaFree(ops->d_shot_src_dom);
     if (ops->d_shot_src_q) cudaFree(ops->d_shot_src_q);
     if (ops->d_shot_src_g) cudaFree(ops->d_shot_src_g);
     if (ops->d_shot_src_g32) cudaFree(ops->d_shot_src_g32);
     if (ops->d_rec_int) cudaFree(ops->d_rec_int);
+    if (ops->d_inj) cudaFree(ops->d_inj);
     if (ops->d_rec_dbl) cudaFree(ops->d_rec_dbl);
     if (ops->d_host_state) cudaFree(ops->d_host_state);
     if (ops->d_host_canon) cudaFree(ops->d_host_canon);
@@ -690,8 +770,19 @@ extern "C" int hho_state_layout(const hho_ops* ops, hho_layout* out) {
 }
 
 // Lowest-index cell containing the point (boundary inclusive), or -1.
+// The lowest-numbered cell containing (x, y), or -1.  Candidates come from
+// the point's bucket (every cell whose slightly enlarged bounding box meets
+// the bucket), tested in increasing order: the same answer as testing every
+// cell in order.
 static int64_t locate(const hho_ops* ops, double x, double y) {
-    for (int64_t c = 0; c < ops->nc; ++c) {
+    if (ops->loc_gx <= 0 || !std::isfinite(x) || !std::isfinite(y)) return -1;
+    const double fx = std::floor((x - ops->loc_x0) / ops->loc_dx), fy = std::floor((y - ops->loc_y0) / ops->loc_dy);
+    if (fx < -1.0 || fy < -1.0 || fx > ops->loc_gx || fy > ops->loc_gy) return -1;
+    const int64_t bx = std::min<int64_t>(std::max<int64_t>((int64_t)fx, 0), ops->loc_gx - 1);
+    const int64_t by = std::min<int64_t>(std::max<int64_t>((int64_t)fy, 0), ops->loc_gy - 1);
+    const int64_t bk = by * ops->loc_gx + bx;
+    for (int64_t e = ops->loc_ptr[bk]; e < ops->loc_ptr[bk + 1]; ++e) {
+        const int64_t c = ops->loc_ids[e];
         int64_t b = ops->poly_ptr[c];
         int nv = (int)(ops->poly_ptr[c + 1] - b);
         if (point_in_cell(ops->poly_xy, &ops->poly_vtx[b], nv, x, y)) return c;
@@ -751,15 +842,23 @@ extern "C" int hho_sources_set(hho_ops* ops, int32_t n_src, const double* xy, co
         cudaFree(ops->d_src_g32);
         ops->d_src_g32 = nullptr;
     }
+    if (ops->d_src_gx) {
+        cudaFree(ops->d_src_gx);
+        ops->d_src_gx = nullptr;
+    }
     ops->n_src = 0;
     if (n_src > 0) {
         std::vector<float> g32(g.begin(), g.end());
+        std::vector<f2x> gx(g.size());
+        for (size_t i = 0; i < g.size(); ++i) gx[i] = f2x(g[i]);
         if (cudaMalloc((void**)&ops->d_src_g, sizeof(double) * g.size()) != cudaSuccess ||
-            cudaMalloc((void**)&ops->d_src_g32, sizeof(float) * g.size()) != cudaSuccess) {
+            cudaMalloc((void**)&ops->d_src_g32, sizeof(float) * g.size()) != cudaSuccess ||
+            cudaMalloc((void**)&ops->d_src_gx, sizeof(f2x) * g.size()) != cudaSuccess) {
             hho_set_error("hho_sources_set: device allocation failed");
             return HHO_ENOMEM;
         }
         if (cudaMemcpy(ops->d_src_g, g.data(), sizeof(double) * g.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(ops->d_src_gx, gx.data(), sizeof(f2x) * g.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
             cudaMemcpy(ops->d_src_g32, g32.data(), sizeof(float) * g.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
             hho_set_error("hho_sources_set: upload failed");
             return HHO_ECUDA;
@@ -785,9 +884,8 @@ extern "C" int hho_receivers_set(hho_ops* ops, int32_t n_rec, const double* xy) 
         double x = xy[2 * r], y = xy[2 * r + 1];
         // interface face containing the point?
         int64_t found = -1;
-        int64_t nF = (int64_t)ops->face_type.size();
-        for (int64_t F = 0; F < nF && found < 0; ++F) {
-            if (ops->face_type[F] != FT_IFACE) continue;
+        for (size_t e = 0; e < ops->iface_faces.size() && found < 0; ++e) {
+            const int64_t F = ops->iface_faces[e];
             int64_t c0 = ops->face_cells[2 * F];
             int j = ops->face_local[2 * F];
             int64_t b = ops->poly_ptr[c0];
@@ -834,20 +932,46 @@ extern "C" int hho_receivers_set(hho_ops* ops, int32_t n_rec, const double* xy) 
         ri[r * 4 + 2] = ops->cell_pos[c];
         cell_basis_at(ops, c, x, y, d);
     }
+    // cells read by the receivers (an interface receiver reads two), each with
+    // its receivers in increasing order
+    std::map<std::pair<int32_t, int32_t>, std::vector<int32_t>> reads;
+    for (int r = 0; r < n_rec; ++r) {
+        const int kind = ri[r * 4 + 0];
+        if (kind == 0 || kind == 2) reads[{0, ri[r * 4 + 1]}].push_back(r);
+        if (kind == 1 || kind == 2) reads[{1, ri[r * 4 + 2]}].push_back(r);
+    }
+    std::vector<int32_t> inj;
+    {
+        const int32_t nt = (int32_t)reads.size();
+        inj.assign((size_t)3 * nt + 1, 0);
+        int32_t t = 0;
+        for (const auto& kv : reads) {
+            inj[t + 1] = inj[t] + (int32_t)kv.second.size();
+            inj[nt + 1 + 2 * t] = kv.first.first;
+            inj[nt + 1 + 2 * t + 1] = kv.first.second;
+            inj.insert(inj.end(), kv.second.begin(), kv.second.end());
+            ++t;
+        }
+    }
     if (ops->d_rec_int) { cudaFree(ops->d_rec_int); ops->d_rec_int = nullptr; }
     if (ops->d_rec_dbl) { cudaFree(ops->d_rec_dbl); ops->d_rec_dbl = nullptr; }
+    if (ops->d_inj) { cudaFree(ops->d_inj); ops->d_inj = nullptr; }
     ops->n_rec = 0;
+    ops->n_inj = 0;
     if (n_rec > 0) {
         if (cudaMalloc((void**)&ops->d_rec_int, sizeof(int32_t) * ri.size()) != cudaSuccess ||
-            cudaMalloc((void**)&ops->d_rec_dbl, sizeof(double) * rd.size()) != cudaSuccess) {
+            cudaMalloc((void**)&ops->d_rec_dbl, sizeof(double) * rd.size()) != cudaSuccess ||
+            cudaMalloc((void**)&ops->d_inj, sizeof(int32_t) * inj.size()) != cudaSuccess) {
             hho_set_error("hho_receivers_set: device allocation failed");
             return HHO_ENOMEM;
         }
         if (cudaMemcpy(ops->d_rec_int, ri.data(), sizeof(int32_t) * ri.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
-            cudaMemcpy(ops->d_rec_dbl, rd.data(), sizeof(double) * rd.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+            cudaMemcpy(ops->d_rec_dbl, rd.data(), sizeof(double) * rd.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(ops->d_inj, inj.data(), sizeof(int32_t) * inj.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
             hho_set_error("hho_receivers_set: upload failed");
             return HHO_ECUDA;
         }
+        ops->n_inj = (int32_t)reads.size();
     }
     ops->n_rec = n_rec;
     return HHO_OK;
@@ -898,21 +1022,25 @@ extern "C" int hho_batch_sources_set(hho_ops* ops, int32_t n_shots, const double
         q[s] = ops->cell_pos[c];
     }
     for (void** p : {(void**)&ops->d_shot_src_dom, (void**)&ops->d_shot_src_q, (void**)&ops->d_shot_src_g,
-                     (void**)&ops->d_shot_src_g32}) {
+                     (void**)&ops->d_shot_src_g32, (void**)&ops->d_shot_src_gx}) {
         if (*p) cudaFree(*p);
         *p = nullptr;
     }
     ops->n_shot_src = 0;
     if (n_shots == 0) return HHO_OK;
     std::vector<float> g32(g.begin(), g.end());
+    std::vector<f2x> gx(g.size());
+    for (size_t i = 0; i < g.size(); ++i) gx[i] = f2x(g[i]);
     if (cudaMalloc((void**)&ops->d_shot_src_dom, sizeof(int32_t) * n_shots) != cudaSuccess ||
         cudaMalloc((void**)&ops->d_shot_src_q, sizeof(int32_t) * n_shots) != cudaSuccess ||
         cudaMalloc((void**)&ops->d_shot_src_g, sizeof(double) * g.size()) != cudaSuccess ||
-        cudaMalloc((void**)&ops->d_shot_src_g32, sizeof(float) * g.size()) != cudaSuccess) {
+        cudaMalloc((void**)&ops->d_shot_src_g32, sizeof(float) * g.size()) != cudaSuccess ||
+        cudaMalloc((void**)&ops->d_shot_src_gx, sizeof(f2x) * g.size()) != cudaSuccess) {
         hho_set_error("hho_batch_sources_set: device allocation failed");
         return HHO_ENOMEM;
     }
-    if (cudaMemcpy(ops->d_shot_src_dom, dom.data(), sizeof(int32_t) * n_shots, cudaMemcpyHostToDevice) != cudaSuccess ||
+    if (cudaMemcpy(ops->d_shot_src_gx, gx.data(), sizeof(f2x) * g.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(ops->d_shot_src_dom, dom.data(), sizeof(int32_t) * n_shots, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(ops->d_shot_src_q, q.data(), sizeof(int32_t) * n_shots, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(ops->d_shot_src_g, g.data(), sizeof(double) * g.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(ops->d_shot_src_g32, g32.data(), sizeof(float) * g.size(), cudaMemcpyHostToDevice) != cudaSuccess) {

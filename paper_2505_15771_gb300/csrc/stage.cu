@@ -35,6 +35,7 @@
 #include <mutex>
 #include <vector>
 
+#include "f2x.cuh"
 #include "hho_internal.h"
 
 namespace {
@@ -84,7 +85,18 @@ struct Vec16<float> {
     }
 };
 
-// Operator data in the arithmetic type T (FP64, or its FP32 copy).
+template <>
+struct Vec16<f2x> {
+    static constexpr int w = 2;
+    __device__ static void load(const f2x* p, f2x* o) {
+        const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+        o[0] = f2x(v.x, v.y);
+        o[1] = f2x(v.z, v.w);
+    }
+};
+
+// Operator data in the arithmetic type T (FP64, its FP32 copy, or its
+// double-float copy).
 template <class T>
 struct OpData;
 template <>
@@ -106,6 +118,16 @@ struct OpData<float> {
     __device__ static const float* if_coef(const DevOps& o) { return o.if_coef_f32; }
 };
 
+template <>
+struct OpData<f2x> {
+    __device__ static const f2x* cls(const DevOps& o) { return o.cls_x; }
+    __device__ static const f2x* scal_f(const DevOps& o) { return o.scal_f_x; }
+    __device__ static const f2x* scal_s(const DevOps& o) { return o.scal_s_x; }
+    __device__ static const f2x* beta_f(const DevOps& o) { return o.beta_f_x; }
+    __device__ static const f2x* beta_s(const DevOps& o) { return o.beta_s_x; }
+    __device__ static const f2x* if_coef(const DevOps& o) { return o.if_coef_x; }
+};
+
 // d/dX of a polynomial in the scaled-monomial basis (exact, compile-time sparse).
 template <class T, int K>
 __device__ __forceinline__ void ddx(const T* u, T* out) {
@@ -114,7 +136,7 @@ __device__ __forceinline__ void ddx(const T* u, T* out) {
         const int a = ea(i), b = eb(i);
         if (a + 1 + b <= K) {
             const int s = eidx(a + 1, b);
-            out[i] = (a == 0) ? u[s] : T(a + 1) * u[s];
+            out[i] = (a == 0) ? u[s] : mulc(float(a + 1), u[s]);
         } else {
             out[i] = T(0);
         }
@@ -127,7 +149,7 @@ __device__ __forceinline__ void ddy(const T* u, T* out) {
         const int a = ea(i), b = eb(i);
         if (a + b + 1 <= K) {
             const int s = eidx(a, b + 1);
-            out[i] = (b == 0) ? u[s] : T(b + 1) * u[s];
+            out[i] = (b == 0) ? u[s] : mulc(float(b + 1), u[s]);
         } else {
             out[i] = T(0);
         }
@@ -141,7 +163,7 @@ __device__ __forceinline__ void add_ddx(const T* u, T* out) {
         const int a = ea(i), b = eb(i);
         if (a + 1 + b <= K) {
             const int s = eidx(a + 1, b);
-            out[i] = (a == 0) ? out[i] + u[s] : fma(T(a + 1), u[s], out[i]);
+            out[i] = (a == 0) ? out[i] + u[s] : fmac(float(a + 1), u[s], out[i]);
         }
     }
 }
@@ -152,7 +174,7 @@ __device__ __forceinline__ void add_ddy(const T* u, T* out) {
         const int a = ea(i), b = eb(i);
         if (a + b + 1 <= K) {
             const int s = eidx(a, b + 1);
-            out[i] = (b == 0) ? out[i] + u[s] : fma(T(b + 1), u[s], out[i]);
+            out[i] = (b == 0) ? out[i] + u[s] : fmac(float(b + 1), u[s], out[i]);
         }
     }
 }
@@ -821,9 +843,9 @@ __global__ void sum_kernel(const double* __restrict__ partial, int np, double* o
 // Receivers: fluid [p, m_x, m_y, 0, 0]; solid [v_x, v_y, s_xx, s_yy, s_xy];
 // interface [p_F, v_Fx, v_Fy, 0, 0] from the pointwise face solve.
 // y = shot: state shot stride n_state, output shot stride 5 n_rec.
-template <class T>
+template <class T, class TO = T>
 __global__ void record_kernel(DevOps op, int n_rec, const int32_t* __restrict__ ri, const double* __restrict__ rd,
-                              const T* __restrict__ state, int64_t n_state, T* out) {
+                              const T* __restrict__ state, int64_t n_state, TO* out) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n_rec) return;
     const int n = op.n;
@@ -864,8 +886,8 @@ __global__ void record_kernel(DevOps op, int n_rec, const int32_t* __restrict__ 
         o[1] = Ai[3] * wf + Ai[4] * wsx + Ai[5] * wsy;
         o[2] = Ai[6] * wf + Ai[7] * wsx + Ai[8] * wsy;
     }
-    T* ob = out + (size_t)blockIdx.y * 5 * n_rec + 5 * r;
-    for (int j = 0; j < 5; ++j) ob[j] = T(o[j]);
+    TO* ob = out + (size_t)blockIdx.y * 5 * n_rec + 5 * r;
+    for (int j = 0; j < 5; ++j) ob[j] = TO(o[j]);
 }
 
 template <class T, int MODE>
@@ -936,12 +958,16 @@ template <>
 const double* src_g_of<double>(const hho_ops* ops) { return ops->d_src_g; }
 template <>
 const float* src_g_of<float>(const hho_ops* ops) { return ops->d_src_g32; }
+template <>
+const f2x* src_g_of<f2x>(const hho_ops* ops) { return ops->d_src_gx; }
 template <class T>
 const T* shot_g_of(const hho_ops* ops);
 template <>
 const double* shot_g_of<double>(const hho_ops* ops) { return ops->d_shot_src_g; }
 template <>
 const float* shot_g_of<float>(const hho_ops* ops) { return ops->d_shot_src_g32; }
+template <>
+const f2x* shot_g_of<f2x>(const hho_ops* ops) { return ops->d_shot_src_gx; }
 
 template <class T>
 void fill_sources(const hho_ops* ops, StageArgsT<T>& a, double t, int n_shots) {
@@ -978,15 +1004,26 @@ extern "C" int hho_work_size(const hho_ops* ops, const hho_tableau* tab, int64_t
         hho_set_error("hho_work_size: unsupported tableau");
         return HHO_EINVAL;
     }
-    *out = ops->n_state * (1 + nb) + 2 * ops->trace_doubles + n_energy_blocks(ops) + 8;
+    *out = ops->n_state * (2 + nb) + 2 * ops->trace_doubles + n_energy_blocks(ops) + 8;
     return HHO_OK;
 }
 
 // Time stepping for n_shots states of element type T.  Work layout (elements
 // of T): [X: S n_state][partial sums: nb S n_state][traces: 2 x S trace].
 template <class T>
+struct SeisOf {   // element type of recorded traces: the state's, FP64 for double-float
+    using type = T;
+};
+template <>
+struct SeisOf<f2x> {
+    using type = double;
+};
+
+template <class T>
 static int erk_run(hho_ops* ops, const hho_tableau* tab, double t0, double dt, int64_t nsteps, int n_shots,
-                   T* d_state, T* d_work, T* d_seis, void* stream, const char* who) {
+                   T* d_state, T* d_work, void* d_seis_v, void* stream, const char* who) {
+    using TS = typename SeisOf<T>::type;
+    TS* d_seis = (TS*)d_seis_v;
     if (!ops || !tab || !d_state || !d_work || nsteps < 0 || n_shots < 1 || n_shots > 65535 || !std::isfinite(dt) ||
         !std::isfinite(t0)) {
         hho_set_error("%s: bad arguments", who);
@@ -1048,7 +1085,7 @@ static int erk_run(hho_ops* ops, const hho_tableau* tab, double t0, double dt, i
             cur ^= 1;
         }
         if (d_seis && ops->n_rec > 0) {
-            record_kernel<T><<<dim3((ops->n_rec + 63) / 64, n_shots), 64, 0, st>>>(
+            record_kernel<T, TS><<<dim3((ops->n_rec + 63) / 64, n_shots), 64, 0, st>>>(
                 ops->dev, ops->n_rec, ops->d_rec_int, ops->d_rec_dbl, d_state, ops->n_state,
                 d_seis + (size_t)step * 5 * ops->n_rec * n_shots);
             rc = check_launch(who);
@@ -1058,9 +1095,61 @@ static int erk_run(hho_ops* ops, const hho_tableau* tab, double t0, double dt, i
     return HHO_OK;
 }
 
+// Doubles of the FP64 work layout [X][partial sums][2 traces][energy scratch];
+// hho_work_size adds one state of double-float pairs after it.
+static int64_t work_f64_part(const hho_ops* ops, int nb) {
+    return ops->n_state * (1 + nb) + 2 * ops->trace_doubles + n_energy_blocks(ops) + 8;
+}
+
+namespace {
+__global__ void to_pairs_kernel(const double* __restrict__ x, f2x* __restrict__ y, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = f2x(x[i]);
+}
+__global__ void from_pairs_kernel(const f2x* __restrict__ x, double* __restrict__ y, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = double(x[i]);
+}
+int pairs_grid(int64_t n) { return (int)std::min<int64_t>((n + 255) / 256, 152 * 16); }
+}  // namespace
+
+// Single-shot stepping: FP64, or double-float on a pair copy of the state
+// kept at the end of the work buffer (converted in and out once per call).
+static int erk_single(hho_ops* ops, const hho_tableau* tab, double t0, double dt, int64_t nsteps, double* d_state,
+                      double* d_work, double* d_seis, void* stream, const char* who) {
+    if (!ops || ops->arith != HHO_F32X2)
+        return erk_run<double>(ops, tab, t0, dt, nsteps, 1, d_state, d_work, d_seis, stream, who);
+    std::vector<StagePlan> plan;
+    int nb = 0;
+    if (!tab || !d_state || !d_work || build_plan(tab, plan, &nb) != HHO_OK) {
+        hho_set_error("%s: bad arguments", who);
+        return HHO_EINVAL;
+    }
+    if (nsteps <= 0 || ops->n_state == 0)
+        return erk_run<f2x>(ops, tab, t0, dt, nsteps, 1, (f2x*)d_state, (f2x*)d_work, d_seis, stream, who);
+    cudaStream_t st = (cudaStream_t)stream;
+    f2x* ux = (f2x*)(d_work + work_f64_part(ops, nb));
+    to_pairs_kernel<<<pairs_grid(ops->n_state), 256, 0, st>>>(d_state, ux, ops->n_state);
+    int rc = check_launch(who);
+    if (rc) return rc;
+    rc = erk_run<f2x>(ops, tab, t0, dt, nsteps, 1, ux, (f2x*)d_work, d_seis, stream, who);
+    if (rc) return rc;
+    from_pairs_kernel<<<pairs_grid(ops->n_state), 256, 0, st>>>(ux, d_state, ops->n_state);
+    return check_launch(who);
+}
+
+extern "C" int hho_set_arithmetic(hho_ops* ops, int32_t arith) {
+    if (!ops || (arith != HHO_F64 && arith != HHO_F32X2)) {
+        hho_set_error("hho_set_arithmetic: arith must be HHO_F64 or HHO_F32X2");
+        return HHO_EINVAL;
+    }
+    ops->arith = arith;
+    return HHO_OK;
+}
+
 extern "C" int hho_erk_step(hho_ops* ops, const hho_tableau* tab, double t0, double dt, int64_t nsteps,
                             double* d_state, double* d_work, void* stream) {
-    return erk_run<double>(ops, tab, t0, dt, nsteps, 1, d_state, d_work, nullptr, stream, "hho_erk_step");
+    return erk_single(ops, tab, t0, dt, nsteps, d_state, d_work, nullptr, stream, "hho_erk_step");
 }
 
 extern "C" int hho_erk_step_record(hho_ops* ops, const hho_tableau* tab, double t0, double dt, int64_t nsteps,
@@ -1069,14 +1158,15 @@ extern "C" int hho_erk_step_record(hho_ops* ops, const hho_tableau* tab, double 
         hho_set_error("hho_erk_step_record: null seismogram buffer");
         return HHO_EINVAL;
     }
-    return erk_run<double>(ops, tab, t0, dt, nsteps, 1, d_state, d_work, d_seismogram, stream, "hho_erk_step_record");
+    return erk_single(ops, tab, t0, dt, nsteps, d_state, d_work, d_seismogram, stream, "hho_erk_step_record");
 }
 
 // ---- batched shots -----------------------------------------------------------------
 
 static bool batch_args_ok(const hho_ops* ops, int32_t n_shots, int32_t precision, const char* who) {
-    if (!ops || n_shots < 1 || n_shots > 65535 || (precision != HHO_F64 && precision != HHO_F32)) {
-        hho_set_error("%s: bad arguments (1 <= n_shots <= 65535, precision HHO_F64 or HHO_F32)", who);
+    if (!ops || n_shots < 1 || n_shots > 65535 ||
+        (precision != HHO_F64 && precision != HHO_F32 && precision != HHO_F32X2)) {
+        hho_set_error("%s: bad arguments (1 <= n_shots <= 65535, precision HHO_F64, HHO_F32 or HHO_F32X2)", who);
         return false;
     }
     return true;
@@ -1112,6 +1202,9 @@ extern "C" int hho_batch_pack(const hho_ops* ops, int32_t n_shots, int32_t preci
     if (precision == HHO_F64)
         pack_kernel<double><<<grid, 128, 0, st>>>(ops->d_dev2orig, ops->d_canon_off, ops->dev.Nf, ops->dev.Ns, ops->n,
                                                   ops->n_canonical, ops->n_state, d_canonical, (double*)d_state);
+    else if (precision == HHO_F32X2)
+        pack_kernel<f2x><<<grid, 128, 0, st>>>(ops->d_dev2orig, ops->d_canon_off, ops->dev.Nf, ops->dev.Ns, ops->n,
+                                               ops->n_canonical, ops->n_state, d_canonical, (f2x*)d_state);
     else
         pack_kernel<float><<<grid, 128, 0, st>>>(ops->d_dev2orig, ops->d_canon_off, ops->dev.Nf, ops->dev.Ns, ops->n,
                                                  ops->n_canonical, ops->n_state, d_canonical, (float*)d_state);
@@ -1131,6 +1224,9 @@ extern "C" int hho_batch_unpack(const hho_ops* ops, int32_t n_shots, int32_t pre
     if (precision == HHO_F64)
         unpack_kernel<double><<<grid, 128, 0, st>>>(ops->d_dev2orig, ops->d_canon_off, ops->dev.Nf, ops->dev.Ns, ops->n,
                                                     ops->n_canonical, ops->n_state, (const double*)d_state, d_canonical);
+    else if (precision == HHO_F32X2)
+        unpack_kernel<f2x><<<grid, 128, 0, st>>>(ops->d_dev2orig, ops->d_canon_off, ops->dev.Nf, ops->dev.Ns, ops->n,
+                                                 ops->n_canonical, ops->n_state, (const f2x*)d_state, d_canonical);
     else
         unpack_kernel<float><<<grid, 128, 0, st>>>(ops->d_dev2orig, ops->d_canon_off, ops->dev.Nf, ops->dev.Ns, ops->n,
                                                    ops->n_canonical, ops->n_state, (const float*)d_state, d_canonical);
@@ -1146,10 +1242,13 @@ extern "C" int hho_batch_erk_step(hho_ops* ops, const hho_tableau* tab, int32_t 
         return HHO_EINVAL;
     }
     if (precision == HHO_F64)
-        return erk_run<double>(ops, tab, t0, dt, nsteps, n_shots, (double*)d_state, (double*)d_work,
-                               (double*)d_seismogram, stream, "hho_batch_erk_step");
-    return erk_run<float>(ops, tab, t0, dt, nsteps, n_shots, (float*)d_state, (float*)d_work, (float*)d_seismogram,
-                          stream, "hho_batch_erk_step");
+        return erk_run<double>(ops, tab, t0, dt, nsteps, n_shots, (double*)d_state, (double*)d_work, d_seismogram,
+                               stream, "hho_batch_erk_step");
+    if (precision == HHO_F32X2)
+        return erk_run<f2x>(ops, tab, t0, dt, nsteps, n_shots, (f2x*)d_state, (f2x*)d_work, d_seismogram, stream,
+                            "hho_batch_erk_step");
+    return erk_run<float>(ops, tab, t0, dt, nsteps, n_shots, (float*)d_state, (float*)d_work, d_seismogram, stream,
+                          "hho_batch_erk_step");
 }
 
 extern "C" int hho_profile_enable(hho_ops* ops, int32_t on) {
@@ -1268,6 +1367,31 @@ extern "C" int hho_stage_cost(const hho_ops* ops, const hho_tableau* tab, int64_
     return HHO_OK;
 }
 
+template <class T>
+static int apply_t(hho_ops* ops, double t, const T* d_state, T* d_rate, T* d_traces, cudaStream_t st) {
+    const dim3 grid((ops->dev.Nf + ops->dev.Ns + 127) / 128, 1);
+    if (grid.x == 0) return HHO_OK;
+    StageArgsT<T> a;
+    memset(&a, 0, sizeof(a));
+    a.op = ops->dev;
+    a.state_stride = ops->n_state;
+    a.trace_stride = ops->trace_doubles;
+    a.inp = d_state;
+    a.tr_out = d_traces;
+    launch_k<T, MODE_TRACES>(ops->k, a, grid, st);
+    int rc = check_launch("hho_apply (trace kernel)");
+    if (rc) return rc;
+    a.tr_in = d_traces;
+    a.tr_out = nullptr;
+    a.n_tgt = 1;
+    a.tgt[0].src = nullptr;
+    a.tgt[0].dst = d_rate;
+    a.tgt[0].coef = T(1.0);
+    fill_sources<T>(ops, a, t, 1);
+    launch_k<T, MODE_APPLY>(ops->k, a, grid, st);
+    return check_launch("hho_apply (stage kernel)");
+}
+
 extern "C" int hho_apply(hho_ops* ops, double t, const double* d_state, double* d_rate, double* d_work,
                          void* stream) {
     if (!ops || !d_state || !d_rate || !d_work) {
@@ -1275,27 +1399,19 @@ extern "C" int hho_apply(hho_ops* ops, double t, const double* d_state, double* 
         return HHO_EINVAL;
     }
     cudaStream_t st = (cudaStream_t)stream;
-    const dim3 grid((ops->dev.Nf + ops->dev.Ns + 127) / 128, 1);
-    if (grid.x == 0) return HHO_OK;
-    StageArgsT<double> a;
-    memset(&a, 0, sizeof(a));
-    a.op = ops->dev;
-    a.state_stride = ops->n_state;
-    a.trace_stride = ops->trace_doubles;
-    a.inp = d_state;
-    a.tr_out = d_work;
-    launch_k<double, MODE_TRACES>(ops->k, a, grid, st);
-    int rc = check_launch("hho_apply (trace kernel)");
+    if (ops->arith != HHO_F32X2) return apply_t<double>(ops, t, d_state, d_rate, d_work, st);
+    // double-float: [traces][state pairs][rate pairs] inside the work buffer
+    if (ops->n_state == 0) return HHO_OK;
+    f2x* tr = (f2x*)d_work;
+    f2x* ux = (f2x*)(d_work + ops->trace_doubles);
+    f2x* rx = ux + ops->n_state;
+    to_pairs_kernel<<<pairs_grid(ops->n_state), 256, 0, st>>>(d_state, ux, ops->n_state);
+    int rc = check_launch("hho_apply");
     if (rc) return rc;
-    a.tr_in = d_work;
-    a.tr_out = nullptr;
-    a.n_tgt = 1;
-    a.tgt[0].src = nullptr;
-    a.tgt[0].dst = d_rate;
-    a.tgt[0].coef = 1.0;
-    fill_sources<double>(ops, a, t, 1);
-    launch_k<double, MODE_APPLY>(ops->k, a, grid, st);
-    return check_launch("hho_apply (stage kernel)");
+    rc = apply_t<f2x>(ops, t, ux, rx, tr, st);
+    if (rc) return rc;
+    from_pairs_kernel<<<pairs_grid(ops->n_state), 256, 0, st>>>(rx, d_rate, ops->n_state);
+    return check_launch("hho_apply");
 }
 
 extern "C" int hho_state_pack(const hho_ops* ops, const double* d_canonical, double* d_state, void* stream) {

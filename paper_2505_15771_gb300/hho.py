@@ -18,7 +18,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libhho.so")
 
-HHO_F64, HHO_F32 = 0, 1
+HHO_F64, HHO_F32, HHO_F32X2 = 0, 1, 2
 HHO_OK, HHO_EINVAL, HHO_EMESH, HHO_EMATERIAL, HHO_EDEGREE, HHO_ECFL, HHO_EUNSTABLE, HHO_ECUDA, HHO_ENOMEM = range(9)
 
 
@@ -70,6 +70,7 @@ _SIGS = {
     "hho_work_size": (C.c_int, [_P, C.POINTER(Tableau), C.POINTER(_I64)]),
     "hho_sources_set": (C.c_int, [_P, _I32, _P, _P, _P, _P, _P]),
     "hho_erk_step": (C.c_int, [_P, C.POINTER(Tableau), _D, _D, _I64, _P, _P, _P]),
+    "hho_set_arithmetic": (C.c_int, [_P, _I32]),
     "hho_erk_run_host": (C.c_int, [_P, C.POINTER(Tableau), _D, _D, _I64, _P, _P]),
     "hho_apply": (C.c_int, [_P, _D, _P, _P, _P, _P]),
     "hho_receivers_set": (C.c_int, [_P, _I32, _P]),
@@ -238,6 +239,11 @@ def hho_sources_set(ops, xy, direction, f0, t0, amp):
     d = _arr(direction, np.float64).reshape(-1, 2)
     a = [_arr(v, np.float64).reshape(-1) for v in (f0, t0, amp)]
     _check(lib().hho_sources_set(ops, xy.shape[0], _ptr(xy), _ptr(d), *[_ptr(v) for v in a]))
+
+
+def hho_set_arithmetic(ops, arith):
+    """HHO_F64 (default) or HHO_F32X2 (double-float) for the single-shot stepping calls."""
+    _check(lib().hho_set_arithmetic(ops, int(arith)))
 
 
 def hho_erk_step(ops, tab, t0, dt, nsteps, d_state, d_work, stream=0):

@@ -107,17 +107,26 @@ class Problem:
         return hho.hho_energy(self.ops, state.data_ptr(), self.work(2).data_ptr(), _stream(stream))
 
     # ---- batched shots ---------------------------------------------------------------
+    @staticmethod
+    def _elem_dtype(precision):
+        # HHO_F32X2 pairs occupy 8 bytes an element: float64 tensors serve as raw storage
+        return torch.float32 if precision == hho.HHO_F32 else torch.float64
+
+    def set_arithmetic(self, arith):
+        """hho.HHO_F64 or hho.HHO_F32X2 for step / apply / run_host."""
+        hho.hho_set_arithmetic(self.ops, arith)
+
     def batch_buffers(self, s, n_shots, precision=hho.HHO_F64):
         tab = hho.hho_tableau_erk(s)
         ns, nw = hho.hho_batch_sizes(self.ops, tab, n_shots, precision)
-        dt = torch.float64 if precision == hho.HHO_F64 else torch.float32
+        dt = self._elem_dtype(precision)
         return (torch.zeros(ns, dtype=dt, device=self.dev), torch.empty(nw, dtype=dt, device=self.dev))
 
     def batch_to_device(self, canonicals, precision=hho.HHO_F64, stream=None):
         """canonicals: [n_shots, n_canonical] host array -> batched device state."""
         c = torch.as_tensor(np.ascontiguousarray(canonicals, dtype=np.float64)).to(self.dev)
         S = c.shape[0]
-        dt = torch.float64 if precision == hho.HHO_F64 else torch.float32
+        dt = self._elem_dtype(precision)
         st = torch.zeros(S * self.layout.n_state, dtype=dt, device=self.dev)
         hho.hho_batch_pack(self.ops, S, precision, c.data_ptr(), st.data_ptr(), _stream(stream))
         return st

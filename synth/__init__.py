@@ -306,6 +306,140 @@ def adjoint_c4(n=256, k=2, n_shots=8, n_rec=128):
     return dict(mesh=md, true=true, background=bg, k=k, sources=srcs, receivers=rec, f0=30.0, anomaly_centre=c)
 
 
+# Boundary slots of a coarse cell on the 4x finer lattice, counter-clockwise
+# from the bottom-left corner: corners 0, 4, 8, 12; slots 1-3 bottom, 5-7
+# right, 9-11 top, 13-15 left (the possible hanging nodes).
+_SLOT_OFF = np.array([(0, 0), (1, 0), (2, 0), (3, 0), (4, 0), (4, 1), (4, 2), (4, 3),
+                      (4, 4), (3, 4), (2, 4), (1, 4), (0, 4), (0, 3), (0, 2), (0, 1)], dtype=np.int64)
+_SLOT_SIDE = np.array([-1, 0, 0, 0, -1, 1, 1, 1, -1, 2, 2, 2, -1, 3, 3, 3])
+# slot lists of the polygons a coarse cell can become
+_POLY_SLOTS = {
+    "quad": list(range(16)),
+    "tri_d0_a": [0, 1, 2, 3, 4, 5, 6, 7, 8],          # split along bottom-left -> top-right
+    "tri_d0_b": [0, 8, 9, 10, 11, 12, 13, 14, 15],
+    "tri_d1_a": [0, 1, 2, 3, 4, 12, 13, 14, 15],      # split along bottom-right -> top-left
+    "tri_d1_b": [4, 5, 6, 7, 8, 9, 10, 11, 12],
+}
+
+
+def basin_floor(seed, xa, xb, n_ctrl=7, dmin=0.3, dmax=0.8):
+    """Seeded basin depth d(x) >= 0: a clamped cubic spline through n_ctrl
+    equally spaced control points on [xa, xb] (zero at both ends, interior
+    depths uniform in [dmin, dmax]); zero outside (xa, xb)."""
+    from scipy.interpolate import CubicSpline
+    rng = np.random.default_rng(seed)
+    xc = np.linspace(xa, xb, n_ctrl)
+    dc = np.concatenate([[0.0], dmin + (dmax - dmin) * rng.random(n_ctrl - 2), [0.0]])
+    cs = CubicSpline(xc, dc, bc_type="clamped")
+
+    def depth(x):
+        x = np.asarray(x, dtype=np.float64)
+        d = np.where((x > xa) & (x < xb), cs(np.clip(x, xa, xb)), 0.0)
+        return np.maximum(d, 0.0)
+    return depth
+
+
+def basin_mesh(nx, ny, x0, x1, y0, y1, y_sea, depth):
+    """Coarse nx x ny squares; those whose centre lies in the basin
+    (y_sea - depth(x) < y < y_sea) are refined 4 x 4; their unrefined
+    neighbours keep the shared sides' 3 hanging nodes as vertices (7- to
+    13-vertex polygons); unrefined solid cells crossed by the basin floor are
+    split into two triangles (diagonal along the floor's slope), hanging nodes
+    included.  Cells: plain/hanging coarse cells row by row, then the
+    triangles, then the fine squares in fine-lattice row order."""
+    hx, hy = (x1 - x0) / nx, (y1 - y0) / ny
+    FX = 4 * nx + 1
+    J, I = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+    xl, yb = x0 + I * hx, y0 + J * hy
+    xc, yc = xl + 0.5 * hx, yb + 0.5 * hy
+    floor_c = y_sea - depth(xc)
+    refined = (depth(xc) > 0) & (yc > floor_c) & (yc < y_sea)
+    fl, fm, fr = y_sea - depth(xl), floor_c, y_sea - depth(xl + hx)
+    lo = np.minimum(np.minimum(fl, fm), fr)
+    hi = np.maximum(np.maximum(fl, fm), fr)
+    touches = (depth(xl) > 0) | (depth(xc) > 0) | (depth(xl + hx) > 0)
+    split = ~refined & touches & (yb + hy <= y_sea) & (lo < yb + hy) & (hi > yb)
+    diag1 = (fr - fl) < 0            # floor rising to the left: split bottom-right -> top-left
+    pad = np.zeros((ny + 2, nx + 2), dtype=bool)
+    pad[1:-1, 1:-1] = refined
+    hang = np.stack([pad[:-2, 1:-1], pad[1:-1, 2:], pad[2:, 1:-1], pad[1:-1, :-2]], axis=-1) & ~refined[..., None]
+    # fine-lattice vertex ids of each coarse cell's 16 boundary slots
+    base = (4 * J)[..., None] * FX + (4 * I)[..., None]
+    slot_vid = base + _SLOT_OFF[:, 1] * FX + _SLOT_OFF[:, 0]          # (ny, nx, 16)
+    slot_on = np.where(_SLOT_SIDE < 0, True, False)[None, None, :] | \
+        np.take_along_axis(hang, np.clip(_SLOT_SIDE, 0, 3)[None, None, :].repeat(ny, 0).repeat(nx, 1), axis=2) & \
+        (_SLOT_SIDE >= 0)[None, None, :]
+    ptr_parts, vtx_parts = [], []
+
+    def emit(mask_cells, slots):
+        sv = slot_vid[mask_cells][:, slots]
+        so = slot_on[mask_cells][:, slots]
+        ptr_parts.append(so.sum(axis=1))
+        vtx_parts.append(sv[so])
+
+    emit(~refined & ~split, _POLY_SLOTS["quad"])
+    if split.any():
+        # the two triangles of each split cell, in cell order
+        for a_key, b_key, m in (("tri_d0_a", "tri_d0_b", split & ~diag1), ("tri_d1_a", "tri_d1_b", split & diag1)):
+            if not m.any():
+                continue
+            sa, sb = _POLY_SLOTS[a_key], _POLY_SLOTS[b_key]
+            va, oa = slot_vid[m][:, sa], slot_on[m][:, sa]
+            vb, ob = slot_vid[m][:, sb], slot_on[m][:, sb]
+            cnt = np.stack([oa.sum(1), ob.sum(1)], axis=1).ravel()
+            v = np.concatenate([va, vb], axis=1)
+            o = np.concatenate([oa, ob], axis=1)
+            ptr_parts.append(cnt)
+            vtx_parts.append(v[o])
+    # fine squares of the refined cells, fine-lattice row order
+    fJ, fI = np.nonzero(np.repeat(np.repeat(refined, 4, axis=0), 4, axis=1))
+    a = fJ.astype(np.int64) * FX + fI
+    ptr_parts.append(np.full(len(a), 4))
+    vtx_parts.append(np.stack([a, a + 1, a + FX + 1, a + FX], axis=1).ravel())
+    counts = np.concatenate(ptr_parts).astype(np.int64)
+    vtx = np.concatenate(vtx_parts).astype(np.int64)
+    used, inv = np.unique(vtx, return_inverse=True)
+    xy = np.stack([x0 + (used % FX) * (hx / 4), y0 + (used // FX) * (hy / 4)], axis=1)
+    cell_ptr = np.zeros(len(counts) + 1, dtype=np.int64)
+    cell_ptr[1:] = np.cumsum(counts)
+    md = MeshData(xy=xy, cell_ptr=cell_ptr, cell_vtx=inv.astype(np.int64), cell_domain=np.zeros(len(counts), np.uint8))
+    cen = md.centroids_approx()
+    md.cell_domain = np.where(cen[:, 1] < y_sea, SOLID, FLUID).astype(np.uint8)
+    return md
+
+
+def basin_c5(nx=2860, ny=715, k=2, n_shots=32, n_rec=512):
+    """A 20 x 5 km section (units km, s): water (rho 1.0, c 1.5) above the
+    seabed y = 4, bedrock below (rho 2.7, vp 5.5, vs 3.2) holding a
+    sedimentary basin between x = 6 and 14 km whose floor is a seeded spline
+    (seed 8, depth 0.3-0.8 km).  Basin media grow linearly with the relative
+    depth z in [0, 1] below the seabed: vs 0.4 + 0.4 z, vp 1.6 + 0.4 z,
+    rho 1.8 + 0.3 z.  Mesh: basin_mesh on nx x ny squares (2860 x 715: about
+    3.3 M cells).  n_shots Ricker point forces (f0 = 15 Hz) at seeded solid
+    points (seed 9) with x in [4, 16], y in [3.2, 3.95]; n_rec receivers on the
+    seabed."""
+    x0, x1, y0, y1, y_sea = 0.0, 20.0, 0.0, 5.0, 4.0
+    depth = basin_floor(8, 6.0, 14.0)
+    md = basin_mesh(nx, ny, x0, x1, y0, y1, y_sea, depth)
+    cen = md.centroids_approx()
+    d = depth(cen[:, 0])
+    sol = md.cell_domain == SOLID
+    in_basin = sol & (d > 0) & (cen[:, 1] > y_sea - d)
+    z = np.clip((y_sea - cen[:, 1]) / np.where(d > 0, d, 1.0), 0.0, 1.0)
+    rho = np.where(sol, np.where(in_basin, 1.8 + 0.3 * z, 2.7), 1.0)
+    vp = np.where(in_basin, 1.6 + 0.4 * z, 5.5)
+    vs = np.where(in_basin, 0.4 + 0.4 * z, 3.2)
+    ls, ms = lame_from_speeds(rho, vp, vs)
+    lam = np.where(sol, ls, 0.0)
+    mu = np.where(sol, ms, 0.0)
+    kappa = np.where(sol, 0.0, 1.0 * 1.5 ** 2)
+    rng = np.random.default_rng(9)
+    srcs = [(4.0 + 12.0 * rng.random(), 3.2 + 0.75 * rng.random()) for _ in range(n_shots)]
+    rec = receivers_on_line(n_rec, x0, x1, y_sea)
+    return dict(mesh=md, media=(rho, lam, mu, kappa), k=k, sources=srcs, f0=15.0, receivers=rec,
+                in_basin=in_basin, depth=depth)
+
+
 def bilayer_c2(nx=1024, ny=512, k=2):
     """[0,2]x[0,1] quads, solid below y = 0.5 with a seeded +-20 % random field
     (vp, vs share g1 seed 1, rho g2 seed 2), water above; 256 receivers at y = 0.75."""

@@ -51,10 +51,15 @@ def cases():
         ("hybrid_k3", synth.hybrid_grid(6, 6, 0.0, 1.0, 0.0, 1.0, 0.7, 0.5), 3, 8),
         ("periodic_k2", synth.quad_grid(4, 10, 0.0, 0.4, -0.5, 0.5, y_interface=0.0, periodic_x=True), 2, None),
         ("random_media_k1", synth.quad_grid(7, 7, 0.0, 1.0, 0.0, 1.0, 0.45), 1, 9),
+        # the basin section at 40 x 10 coarse cells: 4x-refined squares, 7- and
+        # 9-vertex hanging-node polygons, triangles along the basin floor
+        ("basin_k2", synth.basin_c5(nx=40, ny=10)["mesh"], 2, "basin"),
     ]
 
 
 def media_for(md, seed):
+    if seed == "basin":
+        return synth.basin_c5(nx=40, ny=10)["media"]
     return synth.layered_media(md) if seed is None else random_media(md, seed)
 
 
@@ -75,14 +80,14 @@ def test_rate_operator_parity(lib, name, md, k, seed):
 
 
 @pytest.mark.parametrize("s", [2, 3, 4])
-@pytest.mark.parametrize("name,md,k,seed", [cases()[1], cases()[3], cases()[4]])
+@pytest.mark.parametrize("name,md,k,seed", [cases()[1], cases()[3], cases()[4], cases()[7]])
 def test_erk_steps_parity(lib, name, md, k, seed, s):
     """A few ERK(s) steps (Eq. ERK_compact) at a stable dt."""
     media = media_for(md, seed)
     S = oracle_system(md, k, media)
     st = E.Stepper(S)
     U = synth.random_state(S.nT, 7)
-    dt = 0.02 / (k * k)
+    dt = 0.02 / (k * k) * (0.4 if name == "basin_k2" else 1.0)   # basin: h/c_max is 0.4x the unit meshes'
     ref = st.step(U, 0.0, dt, "erk%d" % s, 5)
     P = lib.Problem(md, media, k)
     x = P.to_device(U)
