@@ -11,13 +11,20 @@
 // "Tight and rigorous error bounds for basic building blocks of double-word
 // arithmetic", ACM TOMS 44(2), 2017:
 //   add: SloppyDWPlusDW (TwoSum of the high parts, plain sum of the low
-//        parts, Fast2Sum renormalisation);
+//        parts);
 //   mul: DWTimesDW with FMA (the xl * yl term dropped);
-//   fma: the DWTimesDW product left unnormalised and added as in add;
+//   fma: the DWTimesDW product added as in add;
 //   div: one Newton-style correction of the FP32 quotient (Dekker 1971).
-// No step relies on FMA contraction of a separate multiply and add: where
-// the exact product error is needed the FMA is explicit.  The type is a plain
-// pair so that arrays of it have the layout of FP64 arrays (8 bytes a value).
+// Results are left unnormalised: the final Fast2Sum of those algorithms is
+// deferred to norm(), which the kernels apply where a value is stored.  An
+// unnormalised pair is still the exact sum hi + lo with |lo| of the order of
+// u |operands| (u = 2^-24), so every later operation keeps its absolute error
+// at O(u^2) times the magnitudes involved, as with renormalised pairs; the
+// saving is three instructions per operation and a shorter dependency chain
+// through each accumulator.  No step relies on FMA contraction of a separate
+// multiply and add: where the exact product error is needed the FMA is
+// explicit.  The type is a plain pair so that arrays of it have the layout of
+// FP64 arrays (8 bytes a value).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -40,7 +47,7 @@ __device__ __forceinline__ f2x f2x_two_sum(float a, float b) {
 __device__ __forceinline__ f2x operator+(f2x x, f2x y) {
     const f2x s = f2x_two_sum(x.hi, y.hi);
     const float w = s.lo + (x.lo + y.lo);
-    return f2x_fast_two_sum(s.hi, w);
+    return f2x{s.hi, w};
 }
 __device__ __forceinline__ f2x operator-(f2x x) { return f2x{-x.hi, -x.lo}; }
 __device__ __forceinline__ f2x operator-(f2x x, f2x y) { return x + (-y); }
@@ -52,7 +59,7 @@ __device__ __forceinline__ f2x operator*(f2x x, f2x y) {
     float e = fmaf(x.hi, y.hi, -p);
     e = fmaf(x.hi, y.lo, e);
     e = fmaf(x.lo, y.hi, e);
-    return f2x_fast_two_sum(p, e);
+    return f2x{p, e};
 }
 
 // x * y + z
@@ -63,7 +70,7 @@ __device__ __forceinline__ f2x fma(f2x x, f2x y, f2x z) {
     e = fmaf(x.lo, y.hi, e);
     const f2x s = f2x_two_sum(p, z.hi);
     const float w = s.lo + (e + z.lo);
-    return f2x_fast_two_sum(s.hi, w);
+    return f2x{s.hi, w};
 }
 
 // c * x and c * x + z for an FP32 constant c (the exact small integers of
@@ -72,7 +79,7 @@ __device__ __forceinline__ f2x mulc(float c, f2x x) {
     const float p = c * x.hi;
     float e = fmaf(c, x.hi, -p);
     e = fmaf(c, x.lo, e);
-    return f2x_fast_two_sum(p, e);
+    return f2x{p, e};
 }
 __device__ __forceinline__ f2x fmac(float c, f2x x, f2x z) {
     const float p = c * x.hi;
@@ -80,13 +87,14 @@ __device__ __forceinline__ f2x fmac(float c, f2x x, f2x z) {
     e = fmaf(c, x.lo, e);
     const f2x s = f2x_two_sum(p, z.hi);
     const float w = s.lo + (e + z.lo);
-    return f2x_fast_two_sum(s.hi, w);
+    return f2x{s.hi, w};
 }
 
 __device__ __forceinline__ f2x operator/(f2x x, f2x y) {
+    y = f2x_fast_two_sum(y.hi, y.lo);
     const float q = x.hi / y.hi;
     const f2x r = x - mulc(q, y);
-    return f2x_fast_two_sum(q, r.hi / y.hi);
+    return f2x_fast_two_sum(q, (r.hi + r.lo) / y.hi);
 }
 
 // Read-only load of a pair (one 8-byte load).
@@ -95,7 +103,12 @@ __device__ __forceinline__ f2x __ldg(const f2x* p) {
     return f2x(v.x, v.y);
 }
 
+// Renormalised pair (hi = RN(hi + lo)), applied where a value is stored.
+__device__ __forceinline__ f2x norm(f2x x) { return f2x_fast_two_sum(x.hi, x.lo); }
+
 // Scalar helpers shared by the FP64, FP32 and double-float instantiations.
+__device__ __forceinline__ double norm(double x) { return x; }
+__device__ __forceinline__ float norm(float x) { return x; }
 __device__ __forceinline__ double mulc(float c, double x) { return (double)c * x; }
 __device__ __forceinline__ float mulc(float c, float x) { return c * x; }
 __device__ __forceinline__ double fmac(float c, double x, double z) { return fma((double)c, x, z); }

@@ -182,21 +182,23 @@ __device__ __forceinline__ void add_ddy(const T* u, T* out) {
 // ---- face policies ---------------------------------------------------------------
 // GenericFace: any polygon face; normals and class matrices read at run time,
 // every matrix entry used (no run-time tests on floating-point values).
-// RectFace<J>: face J of an axis-aligned rectangle (J = 0 bottom, 1 right,
-// 2 top, 3 left); normals and the parity sparsity of Tr and Lift are
-// compile-time constants, entries outside the pattern are never loaded.
+// RectAxis<A>: the faces of an axis-aligned rectangle with one orientation,
+// A = 0 horizontal (faces 0 bottom and 2 top, normal (0, s)), A = 1 vertical
+// (faces 1 right and 3 left, normal (s, 0)); the sign s = +-1 is a run-time
+// argument, the parity sparsity of Tr and Lift is compile-time and entries
+// outside the pattern are never loaded.  One body per orientation, looped
+// over its two faces, keeps the kernel's instruction footprint small.
 struct GenericFace {
     static constexpr bool rect = false;
-    static constexpr int NX = 0, NY = 0;
+    static constexpr bool horiz = false;
     __host__ __device__ static constexpr bool tr_nz(int, int) { return true; }
     __host__ __device__ static constexpr bool lift_nz(int, int) { return true; }
 };
-template <int J>
-struct RectFace {
+template <int AX>
+struct RectAxis {
     static constexpr bool rect = true;
-    static constexpr int NX = (J == 1) ? 1 : (J == 3 ? -1 : 0);
-    static constexpr int NY = (J == 0) ? -1 : (J == 2 ? 1 : 0);
-    __host__ __device__ static constexpr int e(int i) { return (J % 2 == 0) ? ea(i) : eb(i); }
+    static constexpr bool horiz = AX == 0;
+    __host__ __device__ static constexpr int e(int i) { return horiz ? ea(i) : eb(i); }
     __host__ __device__ static constexpr bool tr_nz(int l, int i) { return e(i) >= l && ((e(i) - l) % 2) == 0; }
     __host__ __device__ static constexpr bool lift_nz(int i, int l) { return ((e(i) + l) % 2) == 0; }
 };
@@ -244,16 +246,24 @@ __device__ __forceinline__ void lift_apply(const T* __restrict__ L, const T* j, 
         y[i] = acc;
     }
 }
-// y += s * x for a compile-time sign s in {-1, 0, 1}
-template <int S, int NN, class T>
-__device__ __forceinline__ void axpy_sign(const T* x, T* y) {
-    if constexpr (S == 1) {
+// Rectangle faces: one body per orientation looped over its two faces
+// (compact code: the double-float kernel is bound by instruction fetch
+// otherwise), or the four faces unrolled with constant signs (the FP64 and
+// FP32 kernels schedule better fully unrolled).
+template <class T>
+struct RectLoop {
+    static constexpr bool value = false;
+};
+template <>
+struct RectLoop<f2x> {
+    static constexpr bool value = true;
+};
+
+// y += s * x for a run-time sign s = +-1
+template <int NN, class T>
+__device__ __forceinline__ void add_signed(const T* x, T* y, int s) {
 #pragma unroll
-        for (int i = 0; i < NN; ++i) y[i] += x[i];
-    } else if constexpr (S == -1) {
-#pragma unroll
-        for (int i = 0; i < NN; ++i) y[i] -= x[i];
-    }
+    for (int i = 0; i < NN; ++i) y[i] += (s > 0) ? x[i] : -x[i];
 }
 
 template <int NV, class T>
@@ -275,10 +285,10 @@ __device__ __forceinline__ void write_targets(const StageArgsT<T>& A, int N, siz
         if (G.src) {
             const T* src = G.src + off;
 #pragma unroll
-            for (int i = 0; i < NV; ++i) dst[(size_t)i * N + q] = fma(c[GRP::g(i)], k[i], src[(size_t)i * N + q]);
+            for (int i = 0; i < NV; ++i) dst[(size_t)i * N + q] = norm(fma(c[GRP::g(i)], k[i], src[(size_t)i * N + q]));
         } else {
 #pragma unroll
-            for (int i = 0; i < NV; ++i) dst[(size_t)i * N + q] = c[GRP::g(i)] * k[i];
+            for (int i = 0; i < NV; ++i) dst[(size_t)i * N + q] = norm(c[GRP::g(i)] * k[i]);
         }
     }
     const TargetT<T> G = A.tgt[0];
@@ -288,13 +298,13 @@ __device__ __forceinline__ void write_targets(const StageArgsT<T>& A, int N, siz
         const T* src = G.src + off;
 #pragma unroll
         for (int i = 0; i < NV; ++i) {
-            k[i] = fma(c[GRP::g(i)], k[i], src[(size_t)i * N + q]);
+            k[i] = norm(fma(c[GRP::g(i)], k[i], src[(size_t)i * N + q]));
             dst[(size_t)i * N + q] = k[i];
         }
     } else {
 #pragma unroll
         for (int i = 0; i < NV; ++i) {
-            k[i] = c[GRP::g(i)] * k[i];
+            k[i] = norm(c[GRP::g(i)] * k[i]);
             dst[(size_t)i * N + q] = k[i];
         }
     }
@@ -324,8 +334,8 @@ struct CellCtx {
 // Lift the face jump of one face into the raw rate accumulators
 // (kmx, kmy: grad p part; kp: div m part, tau folded).
 template <class T, int K, class P>
-__device__ __forceinline__ void fluid_face_rate(const StageArgsT<T>& A, const CellCtx<T>& c, int j, T* kmx, T* kmy,
-                                                T* kp) {
+__device__ __forceinline__ void fluid_face_rate(const StageArgsT<T>& A, const CellCtx<T>& c, int j, int sg, T* kmx,
+                                                T* kmy, T* kp) {
     constexpr int n = Dims<K>::n, f = Dims<K>::f, FS = Dims<K>::FS;
     const DevOps& op = A.op;
     const T* fm = c.cd + j * FS;
@@ -355,8 +365,7 @@ __device__ __forceinline__ void fluid_face_rate(const StageArgsT<T>& A, const Ce
     T lv[n];
     lift_apply<T, K, P>(fm + Dims<K>::LI, jmp, lv);
     if constexpr (P::rect) {
-        axpy_sign<P::NX, n>(lv, kmx);
-        axpy_sign<P::NY, n>(lv, kmy);
+        add_signed<n>(lv, P::horiz ? kmy : kmx, sg);
     } else {
         const T nx = __ldg(fm), ny = __ldg(fm + 1);
 #pragma unroll
@@ -371,7 +380,8 @@ __device__ __forceinline__ void fluid_face_rate(const StageArgsT<T>& A, const Ce
 
 // Publish w = tau p|_F - (m.n)|_F and omega = alpha w - p|_F for one face.
 template <class T, int K, class P>
-__device__ __forceinline__ void fluid_face_trace(const StageArgsT<T>& A, const CellCtx<T>& c, int j, const T* U) {
+__device__ __forceinline__ void fluid_face_trace(const StageArgsT<T>& A, const CellCtx<T>& c, int j, int sg,
+                                                 const T* U) {
     constexpr int n = Dims<K>::n, f = Dims<K>::f, FS = Dims<K>::FS;
     const DevOps& op = A.op;
     const T* fm = c.cd + j * FS;
@@ -382,8 +392,7 @@ __device__ __forceinline__ void fluid_face_trace(const StageArgsT<T>& A, const C
     T tp[f], tm[f];
     trace_apply<T, K, P>(Tr, p, tp);
     if constexpr (P::rect) {
-        if constexpr (P::NX != 0) trace_apply<T, K, P>(Tr, mx, tm);
-        else trace_apply<T, K, P>(Tr, my, tm);
+        trace_apply<T, K, P>(Tr, P::horiz ? my : mx, tm);
     } else {
         const T nx = __ldg(fm), ny = __ldg(fm + 1);
         T mn[n];
@@ -391,15 +400,15 @@ __device__ __forceinline__ void fluid_face_trace(const StageArgsT<T>& A, const C
         for (int i = 0; i < n; ++i) mn[i] = fma(nx, mx[i], ny * my[i]);
         trace_apply<T, K, P>(Tr, mn, tm);
     }
-    constexpr int sgn = P::rect ? (P::NX + P::NY) : 1;   // rect: tm holds the unsigned trace
+    const int sgn = P::rect ? sg : 1;   // rect: tm holds the unsigned trace
     const int slot = c.sbase + j * c.npad + c.lq;
     const int nb = __ldg(op.nb_f + slot);
     const T al = (nb >= NB_BOUNDARY) ? __ldg(OpData<T>::beta_f(op) + slot) : __ldg(OpData<T>::if_coef(op) + 6 * (-2 - nb));
 #pragma unroll
     for (int l = 0; l < f; ++l) {
-        const T w = (sgn > 0) ? fma(c.tau, tp[l], -tm[l]) : fma(c.tau, tp[l], tm[l]);
-        c.trf_out[(size_t)l * c.SF + slot] = w;
-        c.trf_out[(size_t)(f + l) * c.SF + slot] = fma(al, w, -tp[l]);
+        const T w = fma(c.tau, tp[l], (sgn > 0) ? -tm[l] : tm[l]);
+        c.trf_out[(size_t)l * c.SF + slot] = norm(w);
+        c.trf_out[(size_t)(f + l) * c.SF + slot] = norm(fma(al, w, -tp[l]));
     }
 }
 
@@ -446,13 +455,22 @@ __device__ __forceinline__ void fluid_cell(const StageArgsT<T>& A, int q, int sh
             add_ddy<T, K>(u, kp);
         }
         if (rect) {
-            fluid_face_rate<T, K, RectFace<0>>(A, c, 0, kmx, kmy, kp);
-            fluid_face_rate<T, K, RectFace<1>>(A, c, 1, kmx, kmy, kp);
-            fluid_face_rate<T, K, RectFace<2>>(A, c, 2, kmx, kmy, kp);
-            fluid_face_rate<T, K, RectFace<3>>(A, c, 3, kmx, kmy, kp);
+            // faces 0 (s = -1) and 2 (s = +1) are horizontal, 1 (s = +1) and 3 (s = -1) vertical
+            if constexpr (RectLoop<T>::value) {
+#pragma unroll 1
+                for (int h = 0; h < 2; ++h) fluid_face_rate<T, K, RectAxis<0>>(A, c, 2 * h, 2 * h - 1, kmx, kmy, kp);
+#pragma unroll 1
+                for (int v = 0; v < 2; ++v)
+                    fluid_face_rate<T, K, RectAxis<1>>(A, c, 1 + 2 * v, 1 - 2 * v, kmx, kmy, kp);
+            } else {
+                fluid_face_rate<T, K, RectAxis<0>>(A, c, 0, -1, kmx, kmy, kp);
+                fluid_face_rate<T, K, RectAxis<1>>(A, c, 1, 1, kmx, kmy, kp);
+                fluid_face_rate<T, K, RectAxis<0>>(A, c, 2, 1, kmx, kmy, kp);
+                fluid_face_rate<T, K, RectAxis<1>>(A, c, 3, -1, kmx, kmy, kp);
+            }
         } else {
 #pragma unroll 1
-            for (int j = 0; j < c.nF; ++j) fluid_face_rate<T, K, GenericFace>(A, c, j, kmx, kmy, kp);
+            for (int j = 0; j < c.nF; ++j) fluid_face_rate<T, K, GenericFace>(A, c, j, 1, kmx, kmy, kp);
         }
         const T Am = __ldg(OpData<T>::scal_f(op) + SF_AM * c.N + q), Ap = __ldg(OpData<T>::scal_f(op) + SF_AP * c.N + q);
         // Point sources: the stored vector is kappa/h^2 M0^-1 phi(x_s); the
@@ -474,7 +492,7 @@ __device__ __forceinline__ void fluid_cell(const StageArgsT<T>& A, int q, int sh
         if constexpr (MODE == MODE_RAW) {
             T* dst = A.tgt[0].dst + soff;
 #pragma unroll
-            for (int i = 0; i < 3 * n; ++i) dst[(size_t)i * c.N + q] = U[i];
+            for (int i = 0; i < 3 * n; ++i) dst[(size_t)i * c.N + q] = norm(U[i]);
             return;
         }
         const T sc[3] = {Am, Ap, T(0)};
@@ -482,13 +500,20 @@ __device__ __forceinline__ void fluid_cell(const StageArgsT<T>& A, int q, int sh
         if constexpr (MODE == MODE_APPLY) return;
     }
     if (rect) {
-        fluid_face_trace<T, K, RectFace<0>>(A, c, 0, U);
-        fluid_face_trace<T, K, RectFace<1>>(A, c, 1, U);
-        fluid_face_trace<T, K, RectFace<2>>(A, c, 2, U);
-        fluid_face_trace<T, K, RectFace<3>>(A, c, 3, U);
+        if constexpr (RectLoop<T>::value) {
+#pragma unroll 1
+            for (int h = 0; h < 2; ++h) fluid_face_trace<T, K, RectAxis<0>>(A, c, 2 * h, 2 * h - 1, U);
+#pragma unroll 1
+            for (int v = 0; v < 2; ++v) fluid_face_trace<T, K, RectAxis<1>>(A, c, 1 + 2 * v, 1 - 2 * v, U);
+        } else {
+            fluid_face_trace<T, K, RectAxis<0>>(A, c, 0, -1, U);
+            fluid_face_trace<T, K, RectAxis<1>>(A, c, 1, 1, U);
+            fluid_face_trace<T, K, RectAxis<0>>(A, c, 2, 1, U);
+            fluid_face_trace<T, K, RectAxis<1>>(A, c, 3, -1, U);
+        }
     } else {
 #pragma unroll 1
-        for (int j = 0; j < c.nF; ++j) fluid_face_trace<T, K, GenericFace>(A, c, j, U);
+        for (int j = 0; j < c.nF; ++j) fluid_face_trace<T, K, GenericFace>(A, c, j, 1, U);
     }
 }
 
@@ -496,8 +521,8 @@ __device__ __forceinline__ void fluid_cell(const StageArgsT<T>& A, int q, int sh
 // Lift one face's velocity jump into the raw accumulators: e (strain rate,
 // symmetric-gradient part) and kv (div s part, tau folded).
 template <class T, int K, class P>
-__device__ __forceinline__ void solid_face_rate(const StageArgsT<T>& A, const CellCtx<T>& c, int j, T* exx, T* eyy,
-                                                T* exy, T* kvx, T* kvy) {
+__device__ __forceinline__ void solid_face_rate(const StageArgsT<T>& A, const CellCtx<T>& c, int j, int sg, T* exx,
+                                                T* eyy, T* exy, T* kvx, T* kvy) {
     constexpr int n = Dims<K>::n, f = Dims<K>::f, FS = Dims<K>::FS;
     const DevOps& op = A.op;
     const T* fm = c.cd + j * FS;
@@ -535,10 +560,13 @@ __device__ __forceinline__ void solid_face_rate(const StageArgsT<T>& A, const Ce
     lift_apply<T, K, P>(L, jx, lx);
     lift_apply<T, K, P>(L, jy, ly);
     if constexpr (P::rect) {
-        axpy_sign<P::NX, n>(lx, exx);
-        axpy_sign<P::NX, n>(ly, exy);
-        axpy_sign<P::NY, n>(ly, eyy);
-        axpy_sign<P::NY, n>(lx, exy);
+        if constexpr (P::horiz) {
+            add_signed<n>(ly, eyy, sg);
+            add_signed<n>(lx, exy, sg);
+        } else {
+            add_signed<n>(lx, exx, sg);
+            add_signed<n>(ly, exy, sg);
+        }
     } else {
         const T nx = __ldg(fm), ny = __ldg(fm + 1);
 #pragma unroll
@@ -557,7 +585,8 @@ __device__ __forceinline__ void solid_face_rate(const StageArgsT<T>& A, const Ce
 
 // Publish w = tau v|_F - (s n)|_F and omega = alpha w - v|_F for one face.
 template <class T, int K, class P>
-__device__ __forceinline__ void solid_face_trace(const StageArgsT<T>& A, const CellCtx<T>& c, int j, const T* U) {
+__device__ __forceinline__ void solid_face_trace(const StageArgsT<T>& A, const CellCtx<T>& c, int j, int sg,
+                                                 const T* U) {
     constexpr int n = Dims<K>::n, f = Dims<K>::f, FS = Dims<K>::FS;
     const DevOps& op = A.op;
     const T* fm = c.cd + j * FS;
@@ -572,7 +601,7 @@ __device__ __forceinline__ void solid_face_trace(const StageArgsT<T>& A, const C
     trace_apply<T, K, P>(Tr, vy, tvy);
     if constexpr (P::rect) {
         // s n = (nx s_xx + ny s_xy, nx s_xy + ny s_yy) with one of nx, ny = +-1
-        if constexpr (P::NX != 0) {
+        if constexpr (!P::horiz) {
             trace_apply<T, K, P>(Tr, sxx, tsx);
             trace_apply<T, K, P>(Tr, sxy, tsy);
         } else {
@@ -590,7 +619,7 @@ __device__ __forceinline__ void solid_face_trace(const StageArgsT<T>& A, const C
         trace_apply<T, K, P>(Tr, snx, tsx);
         trace_apply<T, K, P>(Tr, sny, tsy);
     }
-    constexpr int sgn = P::rect ? (P::NX + P::NY) : 1;
+    const int sgn = P::rect ? sg : 1;
     const int slot = c.sbase + j * c.npad + c.lq;
     const int nb = __ldg(op.nb_s + slot);
     T* TWS = c.trs_out;
@@ -598,24 +627,24 @@ __device__ __forceinline__ void solid_face_trace(const StageArgsT<T>& A, const C
         const T be = __ldg(OpData<T>::beta_s(op) + slot);
 #pragma unroll
         for (int l = 0; l < f; ++l) {
-            const T wx = (sgn > 0) ? fma(c.tau, tvx[l], -tsx[l]) : fma(c.tau, tvx[l], tsx[l]);
-            const T wy = (sgn > 0) ? fma(c.tau, tvy[l], -tsy[l]) : fma(c.tau, tvy[l], tsy[l]);
-            TWS[(size_t)l * c.SS + slot] = wx;
-            TWS[(size_t)(f + l) * c.SS + slot] = wy;
-            TWS[(size_t)(2 * f + l) * c.SS + slot] = fma(be, wx, -tvx[l]);
-            TWS[(size_t)(3 * f + l) * c.SS + slot] = fma(be, wy, -tvy[l]);
+            const T wx = fma(c.tau, tvx[l], (sgn > 0) ? -tsx[l] : tsx[l]);
+            const T wy = fma(c.tau, tvy[l], (sgn > 0) ? -tsy[l] : tsy[l]);
+            TWS[(size_t)l * c.SS + slot] = norm(wx);
+            TWS[(size_t)(f + l) * c.SS + slot] = norm(wy);
+            TWS[(size_t)(2 * f + l) * c.SS + slot] = norm(fma(be, wx, -tvx[l]));
+            TWS[(size_t)(3 * f + l) * c.SS + slot] = norm(fma(be, wy, -tvy[l]));
         }
     } else {
         const T* co = OpData<T>::if_coef(op) + 6 * (-2 - nb);
         const T a00 = __ldg(co), a01 = __ldg(co + 1), a10 = __ldg(co + 2), a11 = __ldg(co + 3);
 #pragma unroll
         for (int l = 0; l < f; ++l) {
-            const T wx = (sgn > 0) ? fma(c.tau, tvx[l], -tsx[l]) : fma(c.tau, tvx[l], tsx[l]);
-            const T wy = (sgn > 0) ? fma(c.tau, tvy[l], -tsy[l]) : fma(c.tau, tvy[l], tsy[l]);
-            TWS[(size_t)l * c.SS + slot] = wx;
-            TWS[(size_t)(f + l) * c.SS + slot] = wy;
-            TWS[(size_t)(2 * f + l) * c.SS + slot] = fma(a00, wx, fma(a01, wy, -tvx[l]));
-            TWS[(size_t)(3 * f + l) * c.SS + slot] = fma(a10, wx, fma(a11, wy, -tvy[l]));
+            const T wx = fma(c.tau, tvx[l], (sgn > 0) ? -tsx[l] : tsx[l]);
+            const T wy = fma(c.tau, tvy[l], (sgn > 0) ? -tsy[l] : tsy[l]);
+            TWS[(size_t)l * c.SS + slot] = norm(wx);
+            TWS[(size_t)(f + l) * c.SS + slot] = norm(wy);
+            TWS[(size_t)(2 * f + l) * c.SS + slot] = norm(fma(a00, wx, fma(a01, wy, -tvx[l])));
+            TWS[(size_t)(3 * f + l) * c.SS + slot] = norm(fma(a10, wx, fma(a11, wy, -tvy[l])));
         }
     }
 }
@@ -672,13 +701,22 @@ __device__ __forceinline__ void solid_cell(const StageArgsT<T>& A, int q, int sh
             add_ddx<T, K>(u, kvy);
         }
         if (rect) {
-            solid_face_rate<T, K, RectFace<0>>(A, c, 0, exx, eyy, exy, kvx, kvy);
-            solid_face_rate<T, K, RectFace<1>>(A, c, 1, exx, eyy, exy, kvx, kvy);
-            solid_face_rate<T, K, RectFace<2>>(A, c, 2, exx, eyy, exy, kvx, kvy);
-            solid_face_rate<T, K, RectFace<3>>(A, c, 3, exx, eyy, exy, kvx, kvy);
+            if constexpr (RectLoop<T>::value) {
+#pragma unroll 1
+                for (int h = 0; h < 2; ++h)
+                    solid_face_rate<T, K, RectAxis<0>>(A, c, 2 * h, 2 * h - 1, exx, eyy, exy, kvx, kvy);
+#pragma unroll 1
+                for (int v = 0; v < 2; ++v)
+                    solid_face_rate<T, K, RectAxis<1>>(A, c, 1 + 2 * v, 1 - 2 * v, exx, eyy, exy, kvx, kvy);
+            } else {
+                solid_face_rate<T, K, RectAxis<0>>(A, c, 0, -1, exx, eyy, exy, kvx, kvy);
+                solid_face_rate<T, K, RectAxis<1>>(A, c, 1, 1, exx, eyy, exy, kvx, kvy);
+                solid_face_rate<T, K, RectAxis<0>>(A, c, 2, 1, exx, eyy, exy, kvx, kvy);
+                solid_face_rate<T, K, RectAxis<1>>(A, c, 3, -1, exx, eyy, exy, kvx, kvy);
+            }
         } else {
 #pragma unroll 1
-            for (int j = 0; j < c.nF; ++j) solid_face_rate<T, K, GenericFace>(A, c, j, exx, eyy, exy, kvx, kvy);
+            for (int j = 0; j < c.nF; ++j) solid_face_rate<T, K, GenericFace>(A, c, j, 1, exx, eyy, exy, kvx, kvy);
         }
         // stress rate = C e = c1 [(e_xx + r e_yy), (e_yy + r e_xx)], c3 e_xy; c1, c3 folded into targets
         const T r = __ldg(OpData<T>::scal_s(op) + SS_R * c.N + q);
@@ -714,7 +752,7 @@ __device__ __forceinline__ void solid_cell(const StageArgsT<T>& A, int q, int sh
         if constexpr (MODE == MODE_RAW) {
             T* dst = A.tgt[0].dst + soff;
 #pragma unroll
-            for (int i = 0; i < 5 * n; ++i) dst[(size_t)i * c.N + q] = U[i];
+            for (int i = 0; i < 5 * n; ++i) dst[(size_t)i * c.N + q] = norm(U[i]);
             return;
         }
         const T sc[3] = {__ldg(OpData<T>::scal_s(op) + SS_C1 * c.N + q), __ldg(OpData<T>::scal_s(op) + SS_C3 * c.N + q), Av};
@@ -722,13 +760,20 @@ __device__ __forceinline__ void solid_cell(const StageArgsT<T>& A, int q, int sh
         if constexpr (MODE == MODE_APPLY) return;
     }
     if (rect) {
-        solid_face_trace<T, K, RectFace<0>>(A, c, 0, U);
-        solid_face_trace<T, K, RectFace<1>>(A, c, 1, U);
-        solid_face_trace<T, K, RectFace<2>>(A, c, 2, U);
-        solid_face_trace<T, K, RectFace<3>>(A, c, 3, U);
+        if constexpr (RectLoop<T>::value) {
+#pragma unroll 1
+            for (int h = 0; h < 2; ++h) solid_face_trace<T, K, RectAxis<0>>(A, c, 2 * h, 2 * h - 1, U);
+#pragma unroll 1
+            for (int v = 0; v < 2; ++v) solid_face_trace<T, K, RectAxis<1>>(A, c, 1 + 2 * v, 1 - 2 * v, U);
+        } else {
+            solid_face_trace<T, K, RectAxis<0>>(A, c, 0, -1, U);
+            solid_face_trace<T, K, RectAxis<1>>(A, c, 1, 1, U);
+            solid_face_trace<T, K, RectAxis<0>>(A, c, 2, 1, U);
+            solid_face_trace<T, K, RectAxis<1>>(A, c, 3, -1, U);
+        }
     } else {
 #pragma unroll 1
-        for (int j = 0; j < c.nF; ++j) solid_face_trace<T, K, GenericFace>(A, c, j, U);
+        for (int j = 0; j < c.nF; ++j) solid_face_trace<T, K, GenericFace>(A, c, j, 1, U);
     }
 }
 
