@@ -168,6 +168,21 @@ int hho_state_layout(const hho_ops* ops, hho_layout* out);
 int hho_state_pack(const hho_ops* ops, const double* d_canonical, double* d_state, void* stream);
 int hho_state_unpack(const hho_ops* ops, const double* d_state, double* d_canonical, void* stream);
 
+/* Initial fields, L2-projected onto the cell spaces P^k(T) (host, FP64).
+ *   HHO_FIELD_RICKER: the Ricker pulse of Sec. 5.2, Eq. ricker_ic, on the
+ *     fluid dual variable m:
+ *       m_0(x, y) = theta exp(-pi^2 r^2 / lambda^2) (x - x_c, y - y_c),
+ *       r^2 = (x - x_c)^2 + (y - y_c)^2,
+ *     params = {x_c, y_c, theta, lambda} (n_params = 4); every other field
+ *     (p, and all solid fields) is zero.
+ * Writes the whole canonical vector h_canonical (n_canonical doubles, host):
+ * per cell M0^-1 of the moments (f, phi_i)_T computed with a collapsed
+ * Gauss-Legendre rule of 16 x 16 points on each triangle of the cell's fan
+ * from its centroid.  HHO_EINVAL for an unknown kind or bad params.  No
+ * device work. */
+#define HHO_FIELD_RICKER 0
+int hho_project_field(const hho_ops* ops, int32_t kind, const double* params, int32_t n_params, double* h_canonical);
+
 /* ------------------------------------------------------------------------- */
 /* Time stepping (Sec. 4.2: Eq. ERK_compact, face elimination Eq. ex_solve,   */
 /* tableaux Eq. ERK).                                                         */

@@ -977,6 +977,70 @@ extern "C" int hho_receivers_set(hho_ops* ops, int32_t n_rec, const double* xy) 
     return HHO_OK;
 }
 
+extern "C" int hho_project_field(const hho_ops* ops, int32_t kind, const double* params, int32_t n_params,
+                                 double* h_canonical) {
+    if (!ops || !h_canonical || !params || kind != HHO_FIELD_RICKER || n_params != 4 || !(params[3] > 0.0) ||
+        !std::isfinite(params[0]) || !std::isfinite(params[1]) || !std::isfinite(params[2])) {
+        hho_set_error("hho_project_field: bad arguments (kind HHO_FIELD_RICKER, params {x_c, y_c, theta, lambda > 0})");
+        return HHO_EINVAL;
+    }
+    const double xc = params[0], yc = params[1], theta = params[2], lam = params[3];
+    const int n = ops->n;
+    std::vector<int> EA, EB;
+    exponents(ops->k, EA, EB);
+    std::vector<double> gx, gw;
+    gauss_legendre(16, gx, gw);
+    std::fill(h_canonical, h_canonical + ops->n_canonical, 0.0);
+    std::vector<double> phi(n), mx(n), my(n), X, Y;
+    for (int64_t c = 0; c < ops->nc; ++c) {
+        if (ops->poly_dom[c] != 0) continue;   // the pulse lives on the fluid unknown m
+        const int64_t b = ops->poly_ptr[c];
+        const int nv = (int)(ops->poly_ptr[c + 1] - b);
+        const double h = ops->diam[c], cx = ops->centroid[2 * c], cy = ops->centroid[2 * c + 1];
+        X.assign(nv, 0.0);
+        Y.assign(nv, 0.0);
+        for (int i = 0; i < nv; ++i) {
+            X[i] = (ops->poly_xy[2 * ops->poly_vtx[b + i]] - cx) / h;
+            Y[i] = (ops->poly_xy[2 * ops->poly_vtx[b + i] + 1] - cy) / h;
+        }
+        std::fill(mx.begin(), mx.end(), 0.0);
+        std::fill(my.begin(), my.end(), 0.0);
+        // moments in the scaled coordinates X = (x - x_T)/h: M0 = h^2 M0_ref
+        // and (f, phi)_T = h^2 (f, phi)_ref, so M0^-1 (f, phi)_T = M0_ref^-1 (f, phi)_ref
+        for (int t = 0; t < nv; ++t) {
+            const int t1 = (t + 1) % nv;
+            const double ax = X[t], ay = Y[t], bx = X[t1] - X[t], by = Y[t1] - Y[t];
+            const double det = ax * by - ay * bx;
+            for (size_t iu = 0; iu < gx.size(); ++iu)
+                for (size_t iv = 0; iv < gx.size(); ++iv) {
+                    const double u = 0.5 * (gx[iu] + 1.0), v = 0.5 * (gx[iv] + 1.0);
+                    const double wt = 0.25 * gw[iu] * gw[iv] * u * det;
+                    const double Xp = u * ax + u * v * bx, Yp = u * ay + u * v * by;
+                    const double x = cx + h * Xp, y = cy + h * Yp;
+                    const double r2 = (x - xc) * (x - xc) + (y - yc) * (y - yc);
+                    const double g = theta * std::exp(-M_PI * M_PI * r2 / (lam * lam));
+                    basis_values(EA, EB, Xp, Yp, phi.data());
+                    for (int i = 0; i < n; ++i) {
+                        mx[i] += wt * g * (x - xc) * phi[i];
+                        my[i] += wt * g * (y - yc) * phi[i];
+                    }
+                }
+        }
+        const std::vector<double>& Mi = ops->class_M0inv[ops->cell_class_of[c]];
+        double* out = h_canonical + ops->canon_off[c];   // fluid block [m_x | m_y | p]
+        for (int i = 0; i < n; ++i) {
+            double sx = 0.0, sy = 0.0;
+            for (int q = 0; q < n; ++q) {
+                sx += Mi[i * n + q] * mx[q];
+                sy += Mi[i * n + q] * my[q];
+            }
+            out[i] = sx;
+            out[n + i] = sy;
+        }
+    }
+    return HHO_OK;
+}
+
 extern "C" int hho_cfl_dt(const hho_ops* ops, double cfl_star, double safety, double* dt_out) {
     if (!ops || !dt_out || !(cfl_star > 0.0) || !(safety > 0.0)) {
         hho_set_error("hho_cfl_dt: bad arguments");

@@ -203,6 +203,34 @@ struct RectAxis {
     __host__ __device__ static constexpr bool lift_nz(int i, int l) { return ((e(i) + l) % 2) == 0; }
 };
 
+// Class matrices of the double-float kernel are read from a per-warp copy in
+// shared memory (its many FP32 instructions per matrix entry would otherwise
+// wait on L1 misses: the streamed state and traces evict the class rows); the
+// FP64 and FP32 kernels read them through the read-only data path.
+template <class T>
+struct ClsSmem {
+    static constexpr bool value = false;
+};
+template <>
+struct ClsSmem<f2x> {
+    static constexpr bool value = true;
+};
+template <class T>
+__device__ __forceinline__ void cls_row(const T* p, T* o) {
+    if constexpr (ClsSmem<T>::value) {
+        const float4 v = *reinterpret_cast<const float4*>(p);   // two pairs
+        o[0] = T(v.x, v.y);
+        o[1] = T(v.z, v.w);
+    } else {
+        Vec16<T>::load(p, o);
+    }
+}
+template <class T>
+__device__ __forceinline__ T cls_val(const T* p) {
+    if constexpr (ClsSmem<T>::value) return *p;
+    else return __ldg(p);
+}
+
 // y[l] = sum_i Tr[l][i] x[i] over the policy's pattern.  Each row is read in
 // 16-byte chunks; a chunk with no entry in the pattern is not loaded.
 template <class T, int K, class P>
@@ -216,7 +244,7 @@ __device__ __forceinline__ void trace_apply(const T* __restrict__ Tr, const T* x
             bool need = false;
 #pragma unroll
             for (int e = 0; e < w; ++e) need = need || (c0 + e < n && P::tr_nz(l, c0 + e));
-            if (need) Vec16<T>::load(Tr + l * nP + c0, row + c0);
+            if (need) cls_row<T>(Tr + l * nP + c0, row + c0);
         }
         T acc = T(0);
 #pragma unroll
@@ -237,7 +265,7 @@ __device__ __forceinline__ void lift_apply(const T* __restrict__ L, const T* j, 
             bool need = false;
 #pragma unroll
             for (int e = 0; e < w; ++e) need = need || (c0 + e < f && P::lift_nz(i, c0 + e));
-            if (need) Vec16<T>::load(L + i * fP + c0, row + c0);
+            if (need) cls_row<T>(L + i * fP + c0, row + c0);
         }
         T acc = T(0);
 #pragma unroll
@@ -367,7 +395,7 @@ __device__ __forceinline__ void fluid_face_rate(const StageArgsT<T>& A, const Ce
     if constexpr (P::rect) {
         add_signed<n>(lv, P::horiz ? kmy : kmx, sg);
     } else {
-        const T nx = __ldg(fm), ny = __ldg(fm + 1);
+        const T nx = cls_val(fm), ny = cls_val(fm + 1);
 #pragma unroll
         for (int i = 0; i < n; ++i) {
             kmx[i] = fma(nx, lv[i], kmx[i]);
@@ -394,7 +422,7 @@ __device__ __forceinline__ void fluid_face_trace(const StageArgsT<T>& A, const C
     if constexpr (P::rect) {
         trace_apply<T, K, P>(Tr, P::horiz ? my : mx, tm);
     } else {
-        const T nx = __ldg(fm), ny = __ldg(fm + 1);
+        const T nx = cls_val(fm), ny = cls_val(fm + 1);
         T mn[n];
 #pragma unroll
         for (int i = 0; i < n; ++i) mn[i] = fma(nx, mx[i], ny * my[i]);
@@ -413,7 +441,7 @@ __device__ __forceinline__ void fluid_face_trace(const StageArgsT<T>& A, const C
 }
 
 template <class T, int K, int MODE>
-__device__ __forceinline__ void fluid_cell(const StageArgsT<T>& A, int q, int shot) {
+__device__ __forceinline__ void fluid_cell(const StageArgsT<T>& A, int q, int shot, const T* cd_smem) {
     constexpr int n = Dims<K>::n, f = Dims<K>::f;
     const DevOps& op = A.op;
     const int cls = __ldg(op.warp_class + (q >> 5));
@@ -425,7 +453,7 @@ __device__ __forceinline__ void fluid_cell(const StageArgsT<T>& A, int q, int sh
     c.nF = __ldg(ci + CI_NF);
     c.npad = __ldg(ci + CI_NPAD);
     c.sbase = __ldg(ci + CI_SLOT);
-    c.cd = OpData<T>::cls(op) + __ldg(ci + CI_DOFF) + Dims<K>::M0P;
+    c.cd = ClsSmem<T>::value ? cd_smem : OpData<T>::cls(op) + __ldg(ci + CI_DOFF) + Dims<K>::M0P;
     c.N = op.Nf;
     c.SF = op.SF;
     c.SS = op.SS;
@@ -568,7 +596,7 @@ __device__ __forceinline__ void solid_face_rate(const StageArgsT<T>& A, const Ce
             add_signed<n>(ly, exy, sg);
         }
     } else {
-        const T nx = __ldg(fm), ny = __ldg(fm + 1);
+        const T nx = cls_val(fm), ny = cls_val(fm + 1);
 #pragma unroll
         for (int i = 0; i < n; ++i) {
             exx[i] = fma(nx, lx[i], exx[i]);
@@ -609,7 +637,7 @@ __device__ __forceinline__ void solid_face_trace(const StageArgsT<T>& A, const C
             trace_apply<T, K, P>(Tr, syy, tsy);
         }
     } else {
-        const T nx = __ldg(fm), ny = __ldg(fm + 1);
+        const T nx = cls_val(fm), ny = cls_val(fm + 1);
         T snx[n], sny[n];
 #pragma unroll
         for (int i = 0; i < n; ++i) {
@@ -650,7 +678,7 @@ __device__ __forceinline__ void solid_face_trace(const StageArgsT<T>& A, const C
 }
 
 template <class T, int K, int MODE>
-__device__ __forceinline__ void solid_cell(const StageArgsT<T>& A, int q, int shot) {
+__device__ __forceinline__ void solid_cell(const StageArgsT<T>& A, int q, int shot, const T* cd_smem) {
     constexpr int n = Dims<K>::n, f = Dims<K>::f;
     const DevOps& op = A.op;
     const int cls = __ldg(op.warp_class + op.n_warps_f + (q >> 5));
@@ -662,7 +690,7 @@ __device__ __forceinline__ void solid_cell(const StageArgsT<T>& A, int q, int sh
     c.nF = __ldg(ci + CI_NF);
     c.npad = __ldg(ci + CI_NPAD);
     c.sbase = __ldg(ci + CI_SLOT);
-    c.cd = OpData<T>::cls(op) + __ldg(ci + CI_DOFF) + Dims<K>::M0P;
+    c.cd = ClsSmem<T>::value ? cd_smem : OpData<T>::cls(op) + __ldg(ci + CI_DOFF) + Dims<K>::M0P;
     c.N = op.Ns;
     c.SF = op.SF;
     c.SS = op.SS;
@@ -777,15 +805,60 @@ __device__ __forceinline__ void solid_cell(const StageArgsT<T>& A, int q, int sh
     }
 }
 
-// Grid: x over the padded cells of both domains, y over shots.
+// Resident blocks per SM asked of the register allocator (128 threads a
+// block): 2 blocks allow 255 registers, 3 allow 168, 4 allow 128, 5 allow 96,
+// 6 allow 80, 8 allow 64.  The stage kernels are bound by load latency, so
+// occupancy pays even at the price of spills to L1-resident local memory;
+// the values are the fastest of a sweep on the 1024 x 512 bilayer (and, for
+// FP32, the 1.2 M-cell hybrid mesh) on GB300.
+template <class T, int K>
+struct MinBlocks;
+template <int K>
+struct MinBlocks<double, K> {
+    static constexpr int value = K == 1 ? 8 : (K == 2 ? 8 : 5);
+};
+template <int K>
+struct MinBlocks<float, K> {
+    static constexpr int value = K == 1 ? 8 : (K == 2 ? 8 : 8);
+};
+template <int K>
+struct MinBlocks<f2x, K> {
+    static constexpr int value = K == 1 ? 8 : (K == 2 ? 8 : 5);
+};
+
+// Dynamic shared memory of a stage block: the per-warp class copies
+// (max_nf face blocks of Dims<K>::FS values per warp) when ClsSmem<T>.
+template <class T, int K>
+size_t stage_smem_bytes(int max_nf) {
+    return ClsSmem<T>::value ? sizeof(T) * (128 / 32) * (size_t)max_nf * Dims<K>::FS : 0;
+}
+
+// Grid: x over the padded cells of both domains (fluid warps, then solid
+// warps; a warp lies in one class), y over shots; 128 threads.
 template <class T, int K, int MODE>
-__global__ void __launch_bounds__(128) stage_kernel(const StageArgsT<T> A) {
+__global__ void __launch_bounds__(128, MinBlocks<T, K>::value) stage_kernel(const StageArgsT<T> A) {
     const int gq = blockIdx.x * blockDim.x + threadIdx.x;
     const int shot = blockIdx.y;
+    const T* cd = nullptr;
+    if constexpr (ClsSmem<T>::value) {
+        extern __shared__ __align__(16) unsigned char stage_smem[];
+        constexpr int FS = Dims<K>::FS;
+        const int gw = gq >> 5;
+        if (gw >= A.op.n_warps_f + A.op.n_warps_s) return;   // the whole warp is past the last class
+        T* dst = reinterpret_cast<T*>(stage_smem) + (threadIdx.x >> 5) * A.op.max_nf * FS;
+        const int* ci = A.op.cls_int + __ldg(A.op.warp_class + gw) * CI_STRIDE;
+        const int nv = __ldg(ci + CI_NF) * FS * (int)sizeof(T) / 16;
+        const float4* src =
+            reinterpret_cast<const float4*>(OpData<T>::cls(A.op) + __ldg(ci + CI_DOFF) + Dims<K>::M0P);
+        float4* d4 = reinterpret_cast<float4*>(dst);
+        for (int e = threadIdx.x & 31; e < nv; e += 32) d4[e] = __ldg(src + e);
+        __syncwarp();
+        cd = dst;
+    }
     if (gq < A.op.Nf)
-        fluid_cell<T, K, MODE>(A, gq, shot);
+        fluid_cell<T, K, MODE>(A, gq, shot, cd);
     else if (gq < A.op.Nf + A.op.Ns)
-        solid_cell<T, K, MODE>(A, gq - A.op.Nf, shot);
+        solid_cell<T, K, MODE>(A, gq - A.op.Nf, shot, cd);
 }
 
 // canonical (AoS, input cell order, FP64) <-> device layout (SoA by class, T);
@@ -935,11 +1008,27 @@ __global__ void record_kernel(DevOps op, int n_rec, const int32_t* __restrict__ 
     for (int j = 0; j < 5; ++j) ob[j] = TO(o[j]);
 }
 
+template <class T, int K, int MODE>
+void launch_kk(const StageArgsT<T>& a, dim3 grid, cudaStream_t s) {
+    const size_t smem = stage_smem_bytes<T, K>(a.op.max_nf);
+    if (smem > 48 * 1024) {
+        // the opt-in is per function and device; remember the largest size set
+        static size_t opted[64] = {};
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (dev < 0 || dev >= 64 || opted[dev] < smem) {
+            cudaFuncSetAttribute(stage_kernel<T, K, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (dev >= 0 && dev < 64) opted[dev] = smem;
+        }
+    }
+    stage_kernel<T, K, MODE><<<grid, 128, smem, s>>>(a);
+}
+
 template <class T, int MODE>
 void launch_k(int k, const StageArgsT<T>& a, dim3 grid, cudaStream_t s) {
-    if (k == 1) stage_kernel<T, 1, MODE><<<grid, 128, 0, s>>>(a);
-    else if (k == 2) stage_kernel<T, 2, MODE><<<grid, 128, 0, s>>>(a);
-    else stage_kernel<T, 3, MODE><<<grid, 128, 0, s>>>(a);
+    if (k == 1) launch_kk<T, 1, MODE>(a, grid, s);
+    else if (k == 2) launch_kk<T, 2, MODE>(a, grid, s);
+    else launch_kk<T, 3, MODE>(a, grid, s);
 }
 
 }  // namespace

@@ -19,6 +19,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libhho.so")
 
 HHO_F64, HHO_F32, HHO_F32X2 = 0, 1, 2
+HHO_FIELD_RICKER = 0
 HHO_OK, HHO_EINVAL, HHO_EMESH, HHO_EMATERIAL, HHO_EDEGREE, HHO_ECFL, HHO_EUNSTABLE, HHO_ECUDA, HHO_ENOMEM = range(9)
 
 
@@ -66,6 +67,7 @@ _SIGS = {
     "hho_state_layout": (C.c_int, [_P, C.POINTER(Layout)]),
     "hho_state_pack": (C.c_int, [_P, _P, _P, _P]),
     "hho_state_unpack": (C.c_int, [_P, _P, _P, _P]),
+    "hho_project_field": (C.c_int, [_P, _I32, _P, _I32, _P]),
     "hho_tableau_erk": (C.c_int, [_I32, C.POINTER(Tableau)]),
     "hho_work_size": (C.c_int, [_P, C.POINTER(Tableau), C.POINTER(_I64)]),
     "hho_sources_set": (C.c_int, [_P, _I32, _P, _P, _P, _P, _P]),
@@ -202,6 +204,15 @@ def hho_ops_tau(ops, n_cells):
     t = np.empty(n_cells, np.float64)
     _check(lib().hho_ops_tau(ops, _ptr(t)))
     return t
+
+
+def hho_project_field(ops, kind, params):
+    """Canonical FP64 vector (host) of an initial field projected onto the cell spaces."""
+    lay = hho_state_layout(ops)
+    out = np.empty(lay.n_canonical, np.float64)
+    p = np.ascontiguousarray(params, dtype=np.float64)
+    _check(lib().hho_project_field(ops, int(kind), _ptr(p), len(p), _ptr(out)))
+    return out
 
 
 def hho_ops_destroy(ops):

@@ -440,6 +440,46 @@ def basin_c5(nx=2860, ny=715, k=2, n_shots=32, n_rec=512):
                 in_basin=in_basin, depth=depth)
 
 
+def ricker_academic(n=64, k=2):
+    """Sec. 5.2.1 (academic properties): L = H = 1, fluid (rho 1, c_P 1) over
+    solid (rho 1, c_P sqrt 3, c_S 1), so lambda = mu = kappa = 1; n x n
+    squares.  The paper puts the pulse at x_c = 0 and the interface sensor at
+    x = -0.3, so the domain is read as x in (-L/2, L/2): fluid y in (0, 0.5),
+    solid y in (-0.5, 0).  Initial Ricker pulse on m (Eq. ricker_ic) at
+    (0, 0.125) with theta = 1, lambda = c_P^f / f_c = 0.1 (f_c = 10); no
+    source term; T_f = 1.  Sensors S^f, S^s read off the figure of the
+    domain, S^i = (-0.3, 0) from the text."""
+    md = quad_grid(n, n, -0.5, 0.5, -0.5, 0.5, y_interface=0.0)
+    sol = md.cell_domain == SOLID
+    nc = md.n_cells
+    rho = np.ones(nc)
+    lam = np.where(sol, 1.0, 0.0)     # rho (c_P^2 - 2 c_S^2) = 3 - 2
+    mu = np.where(sol, 1.0, 0.0)
+    kappa = np.where(sol, 0.0, 1.0)
+    return dict(mesh=md, media=(rho, lam, mu, kappa), k=k, pulse=(0.0, 0.125, 1.0, 0.1),
+                sensors=[(-0.25, 0.15), (-0.25, -0.25), (-0.3, 0.0)], T_f=1.0, c_max=np.sqrt(3.0), h=1.0 / n)
+
+
+def granite_water(h=0.025, k=2):
+    """Sec. 5.2.2 (granite under water) in km, s and g/cm^3: L = 3.8, fluid
+    height 1 (rho 1.025, c_P 1.5), solid height 1.6 (rho 2.69, c_P 6, c_S 3),
+    domain x in (-1.9, 1.9), y in (-1.6, 1); squares of side h (25 m: the
+    paper's 23.6 m does not divide the layer heights).  Pulse on m (Eq.
+    ricker_ic) at (0, 0.2) with theta = 1, lambda = 1.5 / 10 = 0.15;
+    T_f = 0.5.  The paper shows snapshots only; the sensors here are our own
+    (fluid, solid, interface, 0.5 km left of the pulse)."""
+    nx, ny = int(round(3.8 / h)), int(round(2.6 / h))
+    md = quad_grid(nx, ny, -1.9, 1.9, -1.6, 1.0, y_interface=0.0)
+    sol = md.cell_domain == SOLID
+    rho = np.where(sol, 2.69, 1.025)
+    ls, ms = lame_from_speeds(2.69, 6.0, 3.0)
+    lam = np.where(sol, ls, 0.0)
+    mu = np.where(sol, ms, 0.0)
+    kappa = np.where(sol, 0.0, 1.025 * 1.5 ** 2)
+    return dict(mesh=md, media=(rho, lam, mu, kappa), k=k, pulse=(0.0, 0.2, 1.0, 0.15),
+                sensors=[(-0.5, 0.2), (-0.5, -0.3), (-0.5, 0.0)], T_f=0.5, c_max=6.0, h=h)
+
+
 def bilayer_c2(nx=1024, ny=512, k=2):
     """[0,2]x[0,1] quads, solid below y = 0.5 with a seeded +-20 % random field
     (vp, vs share g1 seed 1, rho g2 seed 2), water above; 256 receivers at y = 0.75."""
