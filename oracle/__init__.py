@@ -22,6 +22,9 @@ geophysical media using hybrid high-order methods on general meshes"):
 * ``erk``       -- the ERK tableaux (Eq. ERK) and the time step of Sec. 4.2
                    ("ERK_compact" with the face elimination "ex_solve"), done
                    with generic global sparse solves.
+* ``sdirk``     -- the SDIRK tableaux (Eq. SDIRK) and the implicit step of
+                   Sec. 4.1 (Eq. SDIRK_compact, Eq. cp_dirk) on the full
+                   non-condensed system with a generic sparse LU.
 * ``diagnostics`` -- discrete energy (Sec. 5.1), stabilisation dissipation,
                    sensor evaluation.
 

@@ -466,8 +466,8 @@ def granite_water(h=0.025, k=2):
     domain x in (-1.9, 1.9), y in (-1.6, 1); squares of side h (25 m: the
     paper's 23.6 m does not divide the layer heights).  Pulse on m (Eq.
     ricker_ic) at (0, 0.2) with theta = 1, lambda = 1.5 / 10 = 0.15;
-    T_f = 0.5.  The paper shows snapshots only; the sensors here are our own
-    (fluid, solid, interface, 0.5 km left of the pulse)."""
+    T_f = 0.5.  Sensors S^f = (-0.5, 0.2), S^s = (-1.0, -0.5) and
+    S^i = (-0.4, 0) as printed with the run's sensor table."""
     nx, ny = int(round(3.8 / h)), int(round(2.6 / h))
     md = quad_grid(nx, ny, -1.9, 1.9, -1.6, 1.0, y_interface=0.0)
     sol = md.cell_domain == SOLID
@@ -477,7 +477,7 @@ def granite_water(h=0.025, k=2):
     mu = np.where(sol, ms, 0.0)
     kappa = np.where(sol, 0.0, 1.025 * 1.5 ** 2)
     return dict(mesh=md, media=(rho, lam, mu, kappa), k=k, pulse=(0.0, 0.2, 1.0, 0.15),
-                sensors=[(-0.5, 0.2), (-0.5, -0.3), (-0.5, 0.0)], T_f=0.5, c_max=6.0, h=h)
+                sensors=[(-0.5, 0.2), (-1.0, -0.5), (-0.4, 0.0)], T_f=0.5, c_max=6.0, h=h)
 
 
 def bilayer_c2(nx=1024, ny=512, k=2):
