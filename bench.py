@@ -65,6 +65,7 @@ def parse():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--adjoint-steps", type=int, default=800, help="steps of the adjoint (NEXT-2) measurement")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-sdirk", action="store_true")
     return ap.parse_args()
 
 
@@ -354,6 +355,48 @@ def measure_adjoint(a, torch, hho):
     return out
 
 
+def measure_sdirk(a, torch, hho, solver):
+    """Implicit SDIRK(3,4) (matrix-free GMRES on the stage systems) against
+    ERK4 over the same simulated time on the bilayer at 256 x 128, k = 2:
+    SDIRK at 4 x the ERK4 square CFL step, tol 1e-8, restart 20."""
+    import synth
+    w = synth.bilayer_c2(nx=256, ny=128, k=2)
+    P = solver.Problem(w["mesh"], w["media"], 2)
+    P.set_sources([w["source"]], [(0.0, 1.0)], 10.0)
+    n = P.layout.n_canonical
+    dt_erk = hho.hho_cfl_dt(P.ops, CFL_SQUARES_ERK4[2], 0.9)
+    ratio, n_sdirk = 4, 4
+    x = P.to_device(np.zeros(n))
+    P.sdirk_step(x, 3, 0.0, ratio * dt_erk, 1, tol=1e-8, restart=20, max_iter=5000)   # warm-up
+    P.step(x, 4, 0.0, dt_erk, 3)
+    x.zero_()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    its = P.sdirk_step(x, 3, 0.0, ratio * dt_erk, n_sdirk, tol=1e-8, restart=20, max_iter=5000)
+    torch.cuda.synchronize()
+    t_sd = time.perf_counter() - t0
+    e_sd = P.energy(x)
+    y = P.to_device(np.zeros(n))
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    P.step(y, 4, 0.0, dt_erk, ratio * n_sdirk)
+    e1.record()
+    torch.cuda.synchronize()
+    t_erk = e0.elapsed_time(e1) * 1e-3
+    diff = float(torch.linalg.vector_norm(x - y) / torch.linalg.vector_norm(y))
+    stages = 3 * n_sdirk
+    out = {"metric": "wall time for the same simulated interval, SDIRK(3,4) vs ERK4",
+           "workload": "bilayer 256x128 on [0,2]x[0,1], k=2, Ricker source, SDIRK(3,4) dt = %d x ERK4 dt, "
+                       "%d SDIRK steps, GMRES tol 1e-8 restart 20, FP64" % (ratio, n_sdirk),
+           "cell_dofs": int(n), "sdirk_wall_s": t_sd, "erk4_s": t_erk, "sdirk_over_erk4": t_sd / t_erk,
+           "gmres_applications": int(its), "applications_per_stage": its / stages,
+           "rel_diff_vs_erk4": diff, "energy_sdirk": e_sd,
+           "note": "wall clock (GMRES synchronises once per Krylov vector); no preconditioner"}
+    P.close()
+    return out
+
+
 def main():
     a = parse()
     if a.batch_nx is None:
@@ -518,6 +561,10 @@ def main():
         del state, work, seis
         torch.cuda.empty_cache()
         batched = measure_batched(a, torch, hho, solver, hbm_peak)
+    sdirk = None
+    if rank == 0 and not a.no_sdirk:
+        torch.cuda.empty_cache()
+        sdirk = measure_sdirk(a, torch, hho, solver)
     adjoint = None
     if rank == 0 and not a.no_adjoint:
         torch.cuda.empty_cache()
@@ -535,7 +582,7 @@ def main():
                            "parallelism": "replicas" if world > 1 else "single GPU",
                            "energy_after_warmup": e_warm, "energy_after_timed": e_end},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
-                "other_arith": other_arith, "batched": batched, "adjoint": adjoint}
+                "other_arith": other_arith, "batched": batched, "adjoint": adjoint, "sdirk": sdirk}
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()

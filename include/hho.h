@@ -49,6 +49,7 @@ extern "C" {
 #define HHO_EUNSTABLE  6  /* non-finite or growing energy detected on the host      */
 #define HHO_ECUDA      7  /* a CUDA runtime call failed                             */
 #define HHO_ENOMEM     8  /* host or device allocation failed                       */
+#define HHO_ENOCONV    9  /* an implicit stage solve missed its tolerance           */
 
 typedef struct hho_mesh hho_mesh;
 typedef struct hho_ops hho_ops;
@@ -256,6 +257,40 @@ int hho_erk_run_host(hho_ops* ops, const hho_tableau* tab, double t0, double dt,
  * d_work: at least hho_work_size(ops, ERK2) doubles. */
 int hho_apply(hho_ops* ops, double t, const double* d_state, double* d_rate, double* d_work,
               void* stream);
+
+/* ------------------------------------------------------------------------- */
+/* Implicit stepping: SDIRK (Sec. 4.1, Eq. SDIRK_compact, Eq. cp_dirk).        */
+/* ------------------------------------------------------------------------- */
+
+/* Fills *out with an SDIRK tableau (lower triangular a, constant diagonal
+ * a_*): s = 1 the implicit midpoint rule (a_* = 1/2); s = 2 Eq. SDIRK's
+ * 2-stage tableau as printed (a_* = 1/4, order 2); s = 3 Eq. SDIRK's
+ * SDIRK(3,4) (nu = cos(pi/18)/sqrt 3 + 1/2, xi = 1/(6 (2 nu - 1)^2));
+ * s = 23 the order-3 2-stage member a_* = (3 + sqrt 3)/6.  HHO_EINVAL
+ * otherwise. */
+int hho_tableau_sdirk(int32_t s, hho_tableau* out);
+
+/* Doubles of the caller-owned device work buffer hho_sdirk_step needs for
+ * this tableau and GMRES restart length (1 <= restart <= 64). */
+int hho_sdirk_work_size(const hho_ops* ops, const hho_tableau* tab, int32_t restart, int64_t* n_doubles);
+
+/* Advances d_state (device layout, FP64, in/out) by nsteps SDIRK steps.
+ * Every stage of Eq. cp_dirk keeps K_FT U_T + K_F U_F = 0, so its cell part
+ * is (I - a_* dt J) Y_i = U^{n-1} + dt sum_{j<i} a_ij k_j + a_* dt M^-1 F(t_i)
+ * with J = -M^-1 (K_T - K_TF K_F^-1 K_FT) and k_j = J Y_j + M^-1 F(t_j); the
+ * last stage is U^n = U^{n-1} + dt sum_j b_j k_j.  Each stage system is
+ * solved matrix-free by restarted GMRES (restart vectors, at most max_iter
+ * operator applications per stage) to ||r|| <= tol ||rhs||; the operator is
+ * the stage kernel of hho_erk_step in FP64 (hho_set_arithmetic does not
+ * apply).  h_iterations (host, may be NULL) receives the total number of
+ * operator applications inside GMRES.  Synchronises the stream once per
+ * Krylov vector (the Hessenberg matrix and the Givens rotations live on the
+ * host).  HHO_ENOCONV if a stage misses tol within max_iter (d_state then
+ * holds the steps completed so far); HHO_EINVAL for a tableau that is not
+ * lower triangular with a constant positive diagonal. */
+int hho_sdirk_step(hho_ops* ops, const hho_tableau* tab, double t0, double dt, int64_t nsteps, double tol,
+                   int32_t restart, int32_t max_iter, double* d_state, double* d_work, int64_t* h_iterations,
+                   void* stream);
 
 /* ------------------------------------------------------------------------- */
 /* Batched shots: S independent states (right-hand sides, e.g. one point     */

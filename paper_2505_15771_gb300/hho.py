@@ -20,7 +20,8 @@ LIB_PATH = os.path.join(_HERE, "libhho.so")
 
 HHO_F64, HHO_F32, HHO_F32X2 = 0, 1, 2
 HHO_FIELD_RICKER = 0
-HHO_OK, HHO_EINVAL, HHO_EMESH, HHO_EMATERIAL, HHO_EDEGREE, HHO_ECFL, HHO_EUNSTABLE, HHO_ECUDA, HHO_ENOMEM = range(9)
+(HHO_OK, HHO_EINVAL, HHO_EMESH, HHO_EMATERIAL, HHO_EDEGREE, HHO_ECFL, HHO_EUNSTABLE, HHO_ECUDA, HHO_ENOMEM,
+ HHO_ENOCONV) = range(10)
 
 
 class HHOError(RuntimeError):
@@ -73,6 +74,10 @@ _SIGS = {
     "hho_sources_set": (C.c_int, [_P, _I32, _P, _P, _P, _P, _P]),
     "hho_erk_step": (C.c_int, [_P, C.POINTER(Tableau), _D, _D, _I64, _P, _P, _P]),
     "hho_set_arithmetic": (C.c_int, [_P, _I32]),
+    "hho_tableau_sdirk": (C.c_int, [_I32, C.POINTER(Tableau)]),
+    "hho_sdirk_work_size": (C.c_int, [_P, C.POINTER(Tableau), _I32, C.POINTER(_I64)]),
+    "hho_sdirk_step": (C.c_int, [_P, C.POINTER(Tableau), _D, _D, _I64, _D, _I32, _I32, _P, _P, C.POINTER(_I64),
+                                 _P]),
     "hho_erk_run_host": (C.c_int, [_P, C.POINTER(Tableau), _D, _D, _I64, _P, _P]),
     "hho_apply": (C.c_int, [_P, _D, _P, _P, _P, _P]),
     "hho_receivers_set": (C.c_int, [_P, _I32, _P]),
@@ -250,6 +255,27 @@ def hho_sources_set(ops, xy, direction, f0, t0, amp):
     d = _arr(direction, np.float64).reshape(-1, 2)
     a = [_arr(v, np.float64).reshape(-1) for v in (f0, t0, amp)]
     _check(lib().hho_sources_set(ops, xy.shape[0], _ptr(xy), _ptr(d), *[_ptr(v) for v in a]))
+
+
+def hho_tableau_sdirk(s):
+    """SDIRK tableau: s = 1, 2 (as printed), 3 (SDIRK(3,4)) or 23 (order-3 2-stage)."""
+    t = Tableau()
+    _check(lib().hho_tableau_sdirk(int(s), C.byref(t)))
+    return t
+
+
+def hho_sdirk_work_size(ops, tab, restart):
+    n = _I64()
+    _check(lib().hho_sdirk_work_size(ops, C.byref(tab), int(restart), C.byref(n)))
+    return n.value
+
+
+def hho_sdirk_step(ops, tab, t0, dt, nsteps, tol, restart, max_iter, d_state, d_work, stream=0):
+    """Returns the number of GMRES operator applications."""
+    its = _I64()
+    _check(lib().hho_sdirk_step(ops, C.byref(tab), float(t0), float(dt), int(nsteps), float(tol), int(restart),
+                                int(max_iter), _ptr(d_state), _ptr(d_work), C.byref(its), _ptr(stream)))
+    return its.value
 
 
 def hho_set_arithmetic(ops, arith):

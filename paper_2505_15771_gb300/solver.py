@@ -92,6 +92,16 @@ class Problem:
         tab = hho.hho_tableau_erk(s)
         hho.hho_erk_step(self.ops, tab, t0, dt, nsteps, state.data_ptr(), self.work(tab).data_ptr(), _stream(stream))
 
+    def sdirk_step(self, state, s, t0, dt, nsteps, tol=1e-12, restart=40, max_iter=2000, stream=None):
+        """Implicit SDIRK steps (hho_sdirk_step); returns the GMRES operator applications."""
+        tab = hho.hho_tableau_sdirk(s)
+        n = hho.hho_sdirk_work_size(self.ops, tab, restart)
+        key = ("sdirk", s, restart)
+        if key not in self._work or self._work[key].numel() < n:
+            self._work[key] = torch.empty(n, dtype=torch.float64, device=self.dev)
+        return hho.hho_sdirk_step(self.ops, tab, t0, dt, nsteps, tol, restart, max_iter, state.data_ptr(),
+                                  self._work[key].data_ptr(), _stream(stream))
+
     def apply(self, state, t=0.0, stream=None):
         rate = self.empty_state()
         hho.hho_apply(self.ops, t, state.data_ptr(), rate.data_ptr(), self.work(2).data_ptr(), _stream(stream))
