@@ -218,6 +218,28 @@ int hho_work_size(const hho_ops* ops, const hho_tableau* tab, int64_t* n_doubles
  * small fraction of its FP32 rate. */
 int hho_set_arithmetic(hho_ops* ops, int32_t arith);
 
+/* How the ERK loops of hho_erk_step, hho_erk_step_record, hho_erk_run_host
+ * and hho_batch_erk_step issue their kernels:
+ *   HHO_LAUNCH_STREAM: each stage, record and trace kernel launched on the
+ *     caller's stream, with the stage times computed on the host;
+ *   HHO_LAUNCH_GRAPH: one step (its stage kernels, the receiver record and a
+ *     clock increment) captured once as a CUDA graph on a stream of ops and
+ *     replayed on the caller's stream for every step; the stage times and the
+ *     Ricker wavelets come from a clock in device memory, so the replayed
+ *     kernels have identical arguments.  The graph is captured again when the
+ *     arguments of a step change (buffers, tableau, dt, sources, receivers);
+ *   HHO_LAUNCH_AUTO (default): graphs when a stage grid has at most 2048
+ *     blocks (about 260,000 cells x shots) and a call has at least 8 steps,
+ *     where launch overhead matters, else stream launches.
+ * Stage profiling (hho_profile_enable) always uses stream launches.  Device
+ * and host evaluate the wavelet's exponential separately, so the two modes
+ * agree to rounding (about 1e-16 relative), not bit for bit.  HHO_EINVAL for
+ * other values.  No counterpart in the paper. */
+#define HHO_LAUNCH_STREAM 0
+#define HHO_LAUNCH_GRAPH  1
+#define HHO_LAUNCH_AUTO   2
+int hho_set_launch_mode(hho_ops* ops, int32_t mode);
+
 /* Point sources with a Ricker wavelet
  * w(t) = amp (1 - 2 pi^2 f0^2 (t - t0)^2) exp(-pi^2 f0^2 (t - t0)^2):
  * in a solid cell a point force along h_dir (load vector w(t) phi_i(x_s) e_dir

@@ -102,6 +102,13 @@ constexpr int32_t NB_BOUNDARY = -1;
 constexpr int MAX_TARGETS = 4;
 constexpr int MAX_SOURCES = 8;
 
+// Simulation clock read by graph-replayed stage kernels: the time of stage
+// j of step n of a call is (t0 + n dt) + c_j dt.
+struct StageClock {
+    double t0;
+    int64_t step;
+};
+
 template <class T>
 struct TargetT {
     const T* src;   // nullptr: zero
@@ -133,6 +140,12 @@ struct StageArgsT {
     const int32_t* shot_src_q;
     const T* shot_src_g;             // [shots][2][n]
     T shot_src_w;
+    // graph replay: with clock set the stage time comes from the device clock
+    // and the wavelets are evaluated in the kernel from these parameters
+    const StageClock* clock;
+    double dt, c_stage;
+    double src_f0[MAX_SOURCES], src_t0[MAX_SOURCES], src_amp[MAX_SOURCES];
+    double shot_f0, shot_t0, shot_amp;
 };
 
 // MODE_RAW writes the rate before the per-cell material factors (and, in
@@ -204,6 +217,15 @@ struct hho_ops {
     f2x* d_shot_src_gx = nullptr;
     // arithmetic of the single-shot stepping entry points (HHO_F64 or HHO_F32X2)
     int32_t arith = HHO_F64;
+    // launch mode of the ERK loops and the captured steps (stage.cu)
+    int32_t launch_mode = HHO_LAUNCH_AUTO;
+    StageClock* d_clock = nullptr;
+    void* cap_stream = nullptr;                      // cudaStream_t used for capture
+    struct StepGraph {
+        std::vector<unsigned char> key;              // byte image of the step's kernel arguments
+        void* exec = nullptr;                        // cudaGraphExec_t
+    };
+    std::vector<StepGraph> graphs;
     // sources
     int32_t n_src = 0;
     int32_t src_dom[MAX_SOURCES], src_q[MAX_SOURCES];

@@ -674,6 +674,10 @@ extern "C" int hho_operators_build_tau(const hho_mesh* m, int32_t k, const doubl
     D.SS = SS;
     D.n_warps_f = Nf / 32;
     D.n_warps_s = Ns / 32;
+    {
+        std::vector<StageClock> clk(1, StageClock{0.0, 0});
+        ops->d_clock = dev_upload(ops, clk, &err);
+    }
     D.max_nf = 0;
     for (int32_t cl = 0; cl < (int32_t)(cls_int.size() / CI_STRIDE); ++cl)
         D.max_nf = std::max(D.max_nf, cls_int[(size_t)cl * CI_STRIDE + CI_NF]);
@@ -750,6 +754,9 @@ extern "C" void hho_ops_destroy(hho_ops* ops) {
     if (ops->d_host_canon) cudaFree(ops->d_host_canon);
     if (ops->d_host_work) cudaFree(ops->d_host_work);
     for (void* e : ops->prof_events) cudaEventDestroy((cudaEvent_t)e);
+    for (auto& g : ops->graphs)
+        if (g.exec) cudaGraphExecDestroy((cudaGraphExec_t)g.exec);
+    if (ops->cap_stream) cudaStreamDestroy((cudaStream_t)ops->cap_stream);
     delete ops;
 }
 

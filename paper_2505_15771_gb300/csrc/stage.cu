@@ -358,6 +358,31 @@ struct CellCtx {
     T* trs_out;
 };
 
+// ---- point-source wavelets ----------------------------------------------------------
+// Ricker wavelet amp (1 - 2 a^2) exp(-a^2), a = pi f0 (t - t0), at the stage
+// time.  With a device clock (graph replay) the time is (t0 + n dt) + c dt
+// formed with rounded operations in the host's order, and the wavelet is
+// evaluated here; otherwise the host's values are used.
+__device__ __forceinline__ double stage_time(const StageClock* clk, double dt, double c) {
+    const double tn = __dadd_rn(clk->t0, __dmul_rn((double)clk->step, dt));
+    return __dadd_rn(tn, __dmul_rn(c, dt));
+}
+__device__ __forceinline__ double ricker_dev(double t, double f0, double t0, double amp) {
+    const double a = __dmul_rn(__dmul_rn(M_PI, f0), __dadd_rn(t, -t0));
+    const double a2 = __dmul_rn(a, a);
+    return __dmul_rn(__dmul_rn(amp, __dadd_rn(1.0, -__dmul_rn(2.0, a2))), exp(-a2));
+}
+template <class T>
+__device__ __forceinline__ T src_value(const StageArgsT<T>& A, int s) {
+    if (!A.clock) return A.src_w[s];
+    return T(ricker_dev(stage_time(A.clock, A.dt, A.c_stage), A.src_f0[s], A.src_t0[s], A.src_amp[s]));
+}
+template <class T>
+__device__ __forceinline__ T shot_src_value(const StageArgsT<T>& A) {
+    if (!A.clock) return A.shot_src_w;
+    return T(ricker_dev(stage_time(A.clock, A.dt, A.c_stage), A.shot_f0, A.shot_t0, A.shot_amp));
+}
+
 // ---- fluid cells -------------------------------------------------------------------
 // Lift the face jump of one face into the raw rate accumulators
 // (kmx, kmy: grad p part; kp: div m part, tau folded).
@@ -505,14 +530,14 @@ __device__ __forceinline__ void fluid_cell(const StageArgsT<T>& A, int q, int sh
         // raw rate is multiplied by A_p = kappa/h in the targets.
         for (int s = 0; s < A.n_src; ++s) {
             if (A.src_dom[s] == 0 && A.src_q[s] == q) {
-                const T w = A.src_w[s] / Ap;
+                const T w = src_value(A, s) / Ap;
                 const T* g = A.src_g + (size_t)s * 2 * n;
 #pragma unroll
                 for (int i = 0; i < n; ++i) kp[i] = fma(w, g[i], kp[i]);
             }
         }
         if (A.shot_src_q && A.shot_src_dom[shot] == 0 && A.shot_src_q[shot] == q) {
-            const T w = A.shot_src_w / Ap;
+            const T w = shot_src_value(A) / Ap;
             const T* g = A.shot_src_g + (size_t)shot * 2 * n;
 #pragma unroll
             for (int i = 0; i < n; ++i) kp[i] = fma(w, g[i], kp[i]);
@@ -759,7 +784,7 @@ __device__ __forceinline__ void solid_cell(const StageArgsT<T>& A, int q, int sh
         const T Av = __ldg(OpData<T>::scal_s(op) + SS_AV * c.N + q);
         for (int s = 0; s < A.n_src; ++s) {
             if (A.src_dom[s] == 1 && A.src_q[s] == q) {
-                const T w = A.src_w[s] / Av;
+                const T w = src_value(A, s) / Av;
                 const T* g = A.src_g + (size_t)s * 2 * n;
 #pragma unroll
                 for (int i = 0; i < n; ++i) {
@@ -769,7 +794,7 @@ __device__ __forceinline__ void solid_cell(const StageArgsT<T>& A, int q, int sh
             }
         }
         if (A.shot_src_q && A.shot_src_dom[shot] == 1 && A.shot_src_q[shot] == q) {
-            const T w = A.shot_src_w / Av;
+            const T w = shot_src_value(A) / Av;
             const T* g = A.shot_src_g + (size_t)shot * 2 * n;
 #pragma unroll
             for (int i = 0; i < n; ++i) {
@@ -963,7 +988,8 @@ __global__ void sum_kernel(const double* __restrict__ partial, int np, double* o
 // y = shot: state shot stride n_state, output shot stride 5 n_rec.
 template <class T, class TO = T>
 __global__ void record_kernel(DevOps op, int n_rec, const int32_t* __restrict__ ri, const double* __restrict__ rd,
-                              const T* __restrict__ state, int64_t n_state, TO* out) {
+                              const T* __restrict__ state, int64_t n_state, TO* out,
+                              const StageClock* clock = nullptr) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n_rec) return;
     const int n = op.n;
@@ -1004,6 +1030,8 @@ __global__ void record_kernel(DevOps op, int n_rec, const int32_t* __restrict__ 
         o[1] = Ai[3] * wf + Ai[4] * wsx + Ai[5] * wsy;
         o[2] = Ai[6] * wf + Ai[7] * wsx + Ai[8] * wsy;
     }
+    // with a device clock (graph replay) out is the trace base, offset by the step
+    if (clock) out += (size_t)clock->step * 5 * n_rec * gridDim.y;
     TO* ob = out + (size_t)blockIdx.y * 5 * n_rec + 5 * r;
     for (int j = 0; j < 5; ++j) ob[j] = TO(o[j]);
 }
@@ -1142,6 +1170,41 @@ extern "C" int hho_work_size(const hho_ops* ops, const hho_tableau* tab, int64_t
     return HHO_OK;
 }
 
+namespace {
+__global__ void clock_set_kernel(StageClock* c, double t0) {
+    c->t0 = t0;
+    c->step = 0;
+}
+__global__ void clock_advance_kernel(StageClock* c) { c->step += 1; }
+
+// Sources for a stage evaluated from the device clock (graph replay).
+template <class T>
+void fill_sources_clock(const hho_ops* ops, StageArgsT<T>& a, double c_stage, double dt, int n_shots) {
+    fill_sources<T>(ops, a, 0.0, n_shots);   // cells, vectors and pointers
+    for (int s = 0; s < MAX_SOURCES; ++s) a.src_w[s] = T(0);
+    a.shot_src_w = T(0);
+    a.clock = ops->d_clock;
+    a.dt = dt;
+    a.c_stage = c_stage;
+    for (int s = 0; s < ops->n_src; ++s) {
+        a.src_f0[s] = ops->src_f0[s];
+        a.src_t0[s] = ops->src_t0[s];
+        a.src_amp[s] = ops->src_amp[s];
+    }
+    if (a.shot_src_q) {
+        a.shot_f0 = ops->shot_f0;
+        a.shot_t0 = ops->shot_t0;
+        a.shot_amp = ops->shot_amp;
+    }
+}
+
+template <class V>
+void append_bytes(std::vector<unsigned char>& key, const V& v) {
+    const unsigned char* p = reinterpret_cast<const unsigned char*>(&v);
+    key.insert(key.end(), p, p + sizeof(V));
+}
+}  // namespace
+
 // Time stepping for n_shots states of element type T.  Work layout (elements
 // of T): [X: S n_state][partial sums: nb S n_state][traces: 2 x S trace].
 template <class T>
@@ -1192,10 +1255,98 @@ static int erk_run(hho_ops* ops, const hho_tableau* tab, double t0, double dt, i
     a.inp = d_state;
     a.tr_out = tr[0];
     a.n_tgt = 0;
+    const bool use_graph =
+        !ops->prof_on && ops->d_clock &&
+        (ops->launch_mode == HHO_LAUNCH_GRAPH ||
+         (ops->launch_mode == HHO_LAUNCH_AUTO && (int64_t)grid.x * n_shots <= 2048 && nsteps >= 8));
     launch_k<T, MODE_TRACES>(ops->k, a, grid, st);
     int rc = check_launch(who);
     if (rc) return rc;
     int cur = 0;
+    if (use_graph) {
+        // One step = its stage kernels, the receiver record and the clock
+        // increment, captured once per distinct set of arguments (two sets
+        // when an odd stage count alternates the trace buffers) and replayed.
+        clock_set_kernel<<<1, 1, 0, st>>>(ops->d_clock, t0);
+        rc = check_launch(who);
+        if (rc) return rc;
+        const bool rec = d_seis && ops->n_rec > 0;
+        const dim3 rgrid((ops->n_rec + 63) / 64, n_shots);
+        cudaGraphExec_t execs[2] = {nullptr, nullptr};
+        for (int par = 0; par < ((tab->s & 1) ? 2 : 1); ++par) {
+            std::vector<StageArgsT<T>> args(tab->s);
+            int c2 = par;
+            std::vector<unsigned char> key;
+            append_bytes(key, (int)sizeof(T));
+            append_bytes(key, grid);
+            for (int j = 0; j < tab->s; ++j) {
+                StageArgsT<T>& b = args[j];
+                b = a;
+                const StagePlan& P = plan[j];
+                b.inp = (j == 0) ? d_state : X;
+                b.tr_in = tr[c2];
+                b.tr_out = tr[c2 ^ 1];
+                b.n_tgt = P.n_tgt;
+                for (int t = 0; t < P.n_tgt; ++t) {
+                    b.tgt[t].src = resolve(P.t[t].src);
+                    b.tgt[t].dst = resolve(P.t[t].dst);
+                    b.tgt[t].coef = T(P.t[t].a * dt);
+                }
+                fill_sources_clock<T>(ops, b, tab->c[j], dt, n_shots);
+                append_bytes(key, b);
+                c2 ^= 1;
+            }
+            append_bytes(key, rec ? (const void*)d_seis : nullptr);
+            append_bytes(key, ops->d_rec_int);
+            append_bytes(key, ops->d_rec_dbl);
+            append_bytes(key, ops->n_rec);
+            cudaGraphExec_t found = nullptr;
+            for (auto& g : ops->graphs)
+                if (g.key == key) found = (cudaGraphExec_t)g.exec;
+            if (!found) {
+                if (!ops->cap_stream) {
+                    cudaStream_t cs;
+                    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
+                        hho_set_error("%s: capture stream creation failed", who);
+                        return HHO_ECUDA;
+                    }
+                    ops->cap_stream = (void*)cs;
+                }
+                cudaStream_t cs = (cudaStream_t)ops->cap_stream;
+                cudaGraph_t graph = nullptr;
+                if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+                    hho_set_error("%s: stream capture failed to start", who);
+                    return HHO_ECUDA;
+                }
+                for (int j = 0; j < tab->s; ++j) launch_k<T, MODE_STAGE>(ops->k, args[j], grid, cs);
+                if (rec)
+                    record_kernel<T, TS><<<rgrid, 64, 0, cs>>>(ops->dev, ops->n_rec, ops->d_rec_int, ops->d_rec_dbl,
+                                                             d_state, ops->n_state, d_seis, ops->d_clock);
+                clock_advance_kernel<<<1, 1, 0, cs>>>(ops->d_clock);
+                const cudaError_t ce = cudaStreamEndCapture(cs, &graph);
+                if (ce != cudaSuccess || !graph || cudaGraphInstantiate(&found, graph, 0) != cudaSuccess) {
+                    if (graph) cudaGraphDestroy(graph);
+                    cudaGetLastError();
+                    hho_set_error("%s: step graph capture or instantiation failed", who);
+                    return HHO_ECUDA;
+                }
+                cudaGraphDestroy(graph);
+                if (ops->graphs.size() >= 8) {
+                    cudaGraphExecDestroy((cudaGraphExec_t)ops->graphs.front().exec);
+                    ops->graphs.erase(ops->graphs.begin());
+                }
+                ops->graphs.push_back({key, (void*)found});
+            }
+            execs[par] = found;
+        }
+        for (int64_t step = 0; step < nsteps; ++step) {
+            if (cudaGraphLaunch(execs[(tab->s & 1) ? (int)(step & 1) : 0], st) != cudaSuccess) {
+                hho_set_error("%s: graph launch failed", who);
+                return HHO_ECUDA;
+            }
+        }
+        return check_launch(who);
+    }
     for (int64_t step = 0; step < nsteps; ++step) {
         const double tn = t0 + (double)step * dt;
         for (int j = 0; j < tab->s; ++j) {
@@ -1270,6 +1421,15 @@ static int erk_single(hho_ops* ops, const hho_tableau* tab, double t0, double dt
     if (rc) return rc;
     from_pairs_kernel<<<pairs_grid(ops->n_state), 256, 0, st>>>(ux, d_state, ops->n_state);
     return check_launch(who);
+}
+
+extern "C" int hho_set_launch_mode(hho_ops* ops, int32_t mode) {
+    if (!ops || (mode != HHO_LAUNCH_STREAM && mode != HHO_LAUNCH_GRAPH && mode != HHO_LAUNCH_AUTO)) {
+        hho_set_error("hho_set_launch_mode: mode must be HHO_LAUNCH_STREAM, HHO_LAUNCH_GRAPH or HHO_LAUNCH_AUTO");
+        return HHO_EINVAL;
+    }
+    ops->launch_mode = mode;
+    return HHO_OK;
 }
 
 extern "C" int hho_set_arithmetic(hho_ops* ops, int32_t arith) {

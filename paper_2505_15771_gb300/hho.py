@@ -20,6 +20,7 @@ LIB_PATH = os.path.join(_HERE, "libhho.so")
 
 HHO_F64, HHO_F32, HHO_F32X2 = 0, 1, 2
 HHO_FIELD_RICKER = 0
+HHO_LAUNCH_STREAM, HHO_LAUNCH_GRAPH, HHO_LAUNCH_AUTO = 0, 1, 2
 (HHO_OK, HHO_EINVAL, HHO_EMESH, HHO_EMATERIAL, HHO_EDEGREE, HHO_ECFL, HHO_EUNSTABLE, HHO_ECUDA, HHO_ENOMEM,
  HHO_ENOCONV) = range(10)
 
@@ -74,6 +75,7 @@ _SIGS = {
     "hho_sources_set": (C.c_int, [_P, _I32, _P, _P, _P, _P, _P]),
     "hho_erk_step": (C.c_int, [_P, C.POINTER(Tableau), _D, _D, _I64, _P, _P, _P]),
     "hho_set_arithmetic": (C.c_int, [_P, _I32]),
+    "hho_set_launch_mode": (C.c_int, [_P, _I32]),
     "hho_tableau_sdirk": (C.c_int, [_I32, C.POINTER(Tableau)]),
     "hho_sdirk_work_size": (C.c_int, [_P, C.POINTER(Tableau), _I32, C.POINTER(_I64)]),
     "hho_sdirk_step": (C.c_int, [_P, C.POINTER(Tableau), _D, _D, _I64, _D, _I32, _I32, _P, _P, C.POINTER(_I64),
@@ -276,6 +278,11 @@ def hho_sdirk_step(ops, tab, t0, dt, nsteps, tol, restart, max_iter, d_state, d_
     _check(lib().hho_sdirk_step(ops, C.byref(tab), float(t0), float(dt), int(nsteps), float(tol), int(restart),
                                 int(max_iter), _ptr(d_state), _ptr(d_work), C.byref(its), _ptr(stream)))
     return its.value
+
+
+def hho_set_launch_mode(ops, mode):
+    """HHO_LAUNCH_STREAM, HHO_LAUNCH_GRAPH or HHO_LAUNCH_AUTO (default) for the ERK loops."""
+    _check(lib().hho_set_launch_mode(ops, int(mode)))
 
 
 def hho_set_arithmetic(ops, arith):

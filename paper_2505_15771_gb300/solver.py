@@ -122,6 +122,10 @@ class Problem:
         # HHO_F32X2 pairs occupy 8 bytes an element: float64 tensors serve as raw storage
         return torch.float32 if precision == hho.HHO_F32 else torch.float64
 
+    def set_launch_mode(self, mode):
+        """hho.HHO_LAUNCH_STREAM, HHO_LAUNCH_GRAPH or HHO_LAUNCH_AUTO for step / batch_step / run_host."""
+        hho.hho_set_launch_mode(self.ops, mode)
+
     def set_arithmetic(self, arith):
         """hho.HHO_F64 or hho.HHO_F32X2 for step / apply / run_host."""
         hho.hho_set_arithmetic(self.ops, arith)
