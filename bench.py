@@ -56,7 +56,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--shots", type=int, default=16, help="shots of the batched (NEXT-1) measurement")
-    ap.add_argument("--batch-precision", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--batch-precision", default="f32", choices=["f32", "f64", "f32x2"])
     ap.add_argument("--batch-steps", type=int, default=10)
     ap.add_argument("--batch-workload", default="c3", choices=["c3", "c5"],
                     help="c3: 1360x680 hybrid quads/triangles, k=3; c5: basin section with hanging nodes, k=2")
@@ -227,7 +227,7 @@ def measure_batched(a, torch, hho, solver, hbm_peak):
     on the same mesh (the "S sequential FP64 runs" comparison)."""
     import synth
     S = a.shots
-    prec = hho.HHO_F32 if a.batch_precision == "f32" else hho.HHO_F64
+    prec = {"f32": hho.HHO_F32, "f64": hho.HHO_F64, "f32x2": hho.HHO_F32X2}[a.batch_precision]
     if a.batch_workload == "c5":
         w = synth.basin_c5(nx=a.batch_nx, ny=a.batch_ny, n_shots=S)
         kk = w["k"]
@@ -253,7 +253,7 @@ def measure_batched(a, torch, hho, solver, hbm_peak):
     state, work = P.batch_buffers(4, S, prec)
     steps = max(1, a.batch_steps)
     seis = torch.empty((max(steps, 3), S, len(w["receivers"]), 5),
-                       dtype=torch.float32 if prec == hho.HHO_F32 else torch.float64, device=P.dev)
+                       dtype=torch.float32 if prec == hho.HHO_F32 else torch.float64, device=P.dev)   # FP64 for f32x2
     stream = torch.cuda.current_stream()
     P.batch_step(state, work, S, 4, 0.0, dt, 3, precision=prec, seismogram=seis)
     torch.cuda.synchronize()
@@ -293,7 +293,8 @@ def measure_batched(a, torch, hho, solver, hbm_peak):
            "roofline": {"bound": "hbm", "achieved": per_launch / avg / 1e9, "peak": hbm_peak, "unit": "GB/s",
                         "frac": per_launch / avg / 1e9 / hbm_peak,
                         "algorithmic_bytes_per_launch": per_launch, "avg_launch_ms": avg * 1e3,
-                        "kernel": "stage_kernel<%s,%d,1>" % ("float" if prec == hho.HHO_F32 else "double", kk)}}
+                        "kernel": "stage_kernel<%s,%d,1>" % ({hho.HHO_F32: "float", hho.HHO_F64: "double",
+                                                               hho.HHO_F32X2: "f2x"}[prec], kk)}}
     P.close()
     return out
 
