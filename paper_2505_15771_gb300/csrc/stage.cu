@@ -358,6 +358,69 @@ struct CellCtx {
     T* trs_out;
 };
 
+// ---- L2 prefetch hints -------------------------------------------------------------
+// A stage thread reads its cell's state, its faces' own traces, its
+// neighbours' traces and the targets' sources in about twenty dependent
+// rounds, and with 64 registers it cannot hold more of them in flight.
+// Prefetch hints take no register and bring the lines of later rounds into
+// L2 early.  Mask bits: 1 state, 2 own traces and face tables, 4 neighbour
+// traces, 8 target sources, all at the start of the cell; 16 target sources
+// and 32 neighbour traces just before the face loop.
+template <class T>
+struct L2Prefetch {
+    static constexpr int mask = 0;
+};
+template <>
+struct L2Prefetch<float> {
+    static constexpr int mask = 51;
+};
+template <>
+struct L2Prefetch<f2x> {
+    static constexpr int mask = 0;
+};
+
+__device__ __forceinline__ void pf_l2(const void* p) { asm volatile("prefetch.L2 [%0];" ::"l"(p)); }
+
+// The warp's 32-element runs base + a * stride (a < narr), spread over the
+// lanes: every 128-byte line a run touches, unaligned runs included.
+template <class E>
+__device__ __forceinline__ void pf_runs(const E* base, size_t stride, int narr, int lane) {
+    constexpr int BYTES = 32 * (int)sizeof(E), LINES = BYTES / 128 + 1;
+    for (int e = lane; e < narr * LINES; e += 32) {
+        const int a = e / LINES, m = e - a * LINES;
+        pf_l2(reinterpret_cast<const char*>(base + (size_t)a * stride) + min(m * 128, BYTES - 1));
+    }
+}
+
+// WHERE 0: at the start of the cell; 1: before the face loop.  NV state
+// values per cell, NW published traces per face slot (w first, then omega).
+template <class T, int NV, int NW, int WHERE, bool TARGETS>
+__device__ __forceinline__ void prefetch_cell(const StageArgsT<T>& A, const CellCtx<T>& c, size_t soff, const T* tr,
+                                              int S, const int* nbt, const T* bet, int nfaces) {
+    constexpr int PF = L2Prefetch<T>::mask;
+    const int lane = c.q & 31;
+    if constexpr (WHERE == 0 && (PF & 1)) pf_runs(A.inp + soff + (c.q - lane), c.N, NV, lane);
+    if constexpr (WHERE == 0 && (PF & 2)) {
+        for (int j = 0; j < nfaces; ++j) {
+            const int s0 = c.sbase + j * c.npad + c.lq - lane;
+            pf_runs(tr + (size_t)NW * S + s0, S, NW, lane);
+            pf_runs(nbt + s0, 0, 1, lane);
+            pf_runs(bet + s0, 0, 1, lane);
+        }
+    }
+    if constexpr ((WHERE == 0 && (PF & 4)) || (WHERE == 1 && (PF & 32))) {
+        for (int j = 0; j < nfaces; ++j) {
+            const int nb = __ldg(nbt + c.sbase + j * c.npad + c.lq);
+            if (nb >= 0)
+                for (int l = 0; l < NW; ++l) pf_l2(tr + (size_t)l * S + nb);
+        }
+    }
+    if constexpr (TARGETS && ((WHERE == 0 && (PF & 8)) || (WHERE == 1 && (PF & 16)))) {
+        for (int t = 0; t < A.n_tgt; ++t)
+            if (A.tgt[t].src) pf_runs(A.tgt[t].src + soff + (c.q - lane), c.N, NV, lane);
+    }
+}
+
 // ---- point-source wavelets ----------------------------------------------------------
 // Ricker wavelet amp (1 - 2 a^2) exp(-a^2), a = pi f0 (t - t0), at the stage
 // time.  With a device clock (graph replay) the time is (t0 + n dt) + c dt
@@ -497,6 +560,9 @@ __device__ __forceinline__ void fluid_cell(const StageArgsT<T>& A, int q, int sh
         T* kmx = U;
         T* kmy = U + n;
         T* kp = U + 2 * n;
+        if constexpr (L2Prefetch<T>::mask != 0)
+            prefetch_cell<T, 3 * n, f, 0, MODE != MODE_RAW>(A, c, soff, c.trf_in, c.SF, op.nb_f,
+                                                            OpData<T>::beta_f(op), rect ? 4 : c.nF);
         {
             T u[n];
             load_state<n>(A.inp + soff, c.N, q, 2 * n, u);      // p
@@ -507,6 +573,9 @@ __device__ __forceinline__ void fluid_cell(const StageArgsT<T>& A, int q, int sh
             load_state<n>(A.inp + soff, c.N, q, n, u);          // m_y
             add_ddy<T, K>(u, kp);
         }
+        if constexpr (L2Prefetch<T>::mask != 0)
+            prefetch_cell<T, 3 * n, f, 1, MODE != MODE_RAW>(A, c, soff, c.trf_in, c.SF, op.nb_f,
+                                                            OpData<T>::beta_f(op), rect ? 4 : c.nF);
         if (rect) {
             // faces 0 (s = -1) and 2 (s = +1) are horizontal, 1 (s = +1) and 3 (s = -1) vertical
             if constexpr (RectLoop<T>::value) {
@@ -737,6 +806,9 @@ __device__ __forceinline__ void solid_cell(const StageArgsT<T>& A, int q, int sh
         T* exy = U + 2 * n;
         T* kvx = U + 3 * n;
         T* kvy = U + 4 * n;
+        if constexpr (L2Prefetch<T>::mask != 0)
+            prefetch_cell<T, 5 * n, 2 * f, 0, MODE != MODE_RAW>(A, c, soff, c.trs_in, c.SS, op.nb_s,
+                                                                OpData<T>::beta_s(op), rect ? 4 : c.nF);
         {
             T u[n];
             load_state<n>(inp, c.N, q, 3 * n, u);    // v_x
@@ -753,6 +825,9 @@ __device__ __forceinline__ void solid_cell(const StageArgsT<T>& A, int q, int sh
             add_ddy<T, K>(u, kvx);
             add_ddx<T, K>(u, kvy);
         }
+        if constexpr (L2Prefetch<T>::mask != 0)
+            prefetch_cell<T, 5 * n, 2 * f, 1, MODE != MODE_RAW>(A, c, soff, c.trs_in, c.SS, op.nb_s,
+                                                                OpData<T>::beta_s(op), rect ? 4 : c.nF);
         if (rect) {
             if constexpr (RectLoop<T>::value) {
 #pragma unroll 1
