@@ -287,6 +287,27 @@ struct RectLoop<f2x> {
     static constexpr bool value = true;
 };
 
+// Where a stage thread keeps its 3n (fluid) or 5n (solid) accumulators.  In
+// registers they do not fit the 64-register budget of 8 resident blocks and
+// spill to local memory, whose footprint (over 400 bytes a thread) exceeds
+// L1.  With AccSmem the block's dynamic shared memory holds them instead,
+// thread-major with an odd stride in elements (no bank conflicts).  That
+// makes the FP32 kernel about 20 % faster at k = 3 (still 8 blocks); for
+// 8-byte values the shared memory allows only 6 blocks, which left the
+// double-float kernel unchanged and slowed the FP64 one.
+template <class T, int K>
+struct AccSmem {
+    static constexpr bool value = false;
+};
+template <int K>
+struct AccSmem<float, K> {
+    static constexpr bool value = K >= 2;
+};
+template <int K>
+__host__ __device__ constexpr int acc_stride() {
+    return (5 * Dims<K>::n) | 1;
+}
+
 // y += s * x for a run-time sign s = +-1
 template <int NN, class T>
 __device__ __forceinline__ void add_signed(const T* x, T* y, int s) {
@@ -365,14 +386,17 @@ struct CellCtx {
 // Prefetch hints take no register and bring the lines of later rounds into
 // L2 early.  Mask bits: 1 state, 2 own traces and face tables, 4 neighbour
 // traces, 8 target sources, all at the start of the cell; 16 target sources
-// and 32 neighbour traces just before the face loop.
+// and 32 neighbour traces just before the face loop.  The FP32 kernel gains
+// about 20 % from them (mask 50, the best of a sweep on GB300); for 8-byte
+// values every mask was slower, the lines in flight evicting one another
+// from L2 before use.
 template <class T>
 struct L2Prefetch {
     static constexpr int mask = 0;
 };
 template <>
 struct L2Prefetch<float> {
-    static constexpr int mask = 51;
+    static constexpr int mask = 50;
 };
 template <>
 struct L2Prefetch<f2x> {
@@ -529,7 +553,7 @@ __device__ __forceinline__ void fluid_face_trace(const StageArgsT<T>& A, const C
 }
 
 template <class T, int K, int MODE>
-__device__ __forceinline__ void fluid_cell(const StageArgsT<T>& A, int q, int shot, const T* cd_smem) {
+__device__ __forceinline__ void fluid_cell(const StageArgsT<T>& A, int q, int shot, const T* cd_smem, T* acc_smem) {
     constexpr int n = Dims<K>::n, f = Dims<K>::f;
     const DevOps& op = A.op;
     const int cls = __ldg(op.warp_class + (q >> 5));
@@ -553,7 +577,8 @@ __device__ __forceinline__ void fluid_cell(const StageArgsT<T>& A, int q, int sh
     c.trs_out = A.tr_out + toff + (size_t)2 * f * c.SF;
     const size_t soff = (size_t)shot * A.state_stride;
     const bool rect = __ldg(ci + CI_KIND) == KIND_RECT;
-    T U[3 * n];   // [m_x | m_y | p]
+    T Ureg[AccSmem<T, K>::value ? 1 : 3 * n];
+    T* U = AccSmem<T, K>::value ? acc_smem : Ureg;   // [m_x | m_y | p]
     if constexpr (MODE == MODE_TRACES) {
         load_state<3 * n>(A.inp + soff, c.N, q, 0, U);
     } else {
@@ -772,7 +797,7 @@ __device__ __forceinline__ void solid_face_trace(const StageArgsT<T>& A, const C
 }
 
 template <class T, int K, int MODE>
-__device__ __forceinline__ void solid_cell(const StageArgsT<T>& A, int q, int shot, const T* cd_smem) {
+__device__ __forceinline__ void solid_cell(const StageArgsT<T>& A, int q, int shot, const T* cd_smem, T* acc_smem) {
     constexpr int n = Dims<K>::n, f = Dims<K>::f;
     const DevOps& op = A.op;
     const int cls = __ldg(op.warp_class + op.n_warps_f + (q >> 5));
@@ -797,7 +822,8 @@ __device__ __forceinline__ void solid_cell(const StageArgsT<T>& A, int q, int sh
     const bool rect = __ldg(ci + CI_KIND) == KIND_RECT;
     const size_t soff = (size_t)shot * A.state_stride + (size_t)3 * n * op.Nf;
     const T* inp = A.inp + soff;
-    T U[5 * n];   // [s_xx | s_yy | s_xy | v_x | v_y]
+    T Ureg[AccSmem<T, K>::value ? 1 : 5 * n];
+    T* U = AccSmem<T, K>::value ? acc_smem : Ureg;   // [s_xx | s_yy | s_xy | v_x | v_y]
     if constexpr (MODE == MODE_TRACES) {
         load_state<5 * n>(inp, c.N, q, 0, U);
     } else {
@@ -929,8 +955,12 @@ struct MinBlocks<f2x, K> {
 // Dynamic shared memory of a stage block: the per-warp class copies
 // (max_nf face blocks of Dims<K>::FS values per warp) when ClsSmem<T>.
 template <class T, int K>
-size_t stage_smem_bytes(int max_nf) {
+__host__ __device__ size_t stage_cls_smem_bytes(int max_nf) {
     return ClsSmem<T>::value ? sizeof(T) * (128 / 32) * (size_t)max_nf * Dims<K>::FS : 0;
+}
+template <class T, int K>
+size_t stage_smem_bytes(int max_nf) {
+    return stage_cls_smem_bytes<T, K>(max_nf) + (AccSmem<T, K>::value ? sizeof(T) * 128 * acc_stride<K>() : 0);
 }
 
 // Grid: x over the padded cells of both domains (fluid warps, then solid
@@ -940,8 +970,11 @@ __global__ void __launch_bounds__(128, MinBlocks<T, K>::value) stage_kernel(cons
     const int gq = blockIdx.x * blockDim.x + threadIdx.x;
     const int shot = blockIdx.y;
     const T* cd = nullptr;
+    extern __shared__ __align__(16) unsigned char stage_smem[];
+    T* acc = nullptr;
+    if constexpr (AccSmem<T, K>::value)
+        acc = reinterpret_cast<T*>(stage_smem + stage_cls_smem_bytes<T, K>(A.op.max_nf)) + threadIdx.x * acc_stride<K>();
     if constexpr (ClsSmem<T>::value) {
-        extern __shared__ __align__(16) unsigned char stage_smem[];
         constexpr int FS = Dims<K>::FS;
         const int gw = gq >> 5;
         if (gw >= A.op.n_warps_f + A.op.n_warps_s) return;   // the whole warp is past the last class
@@ -956,9 +989,9 @@ __global__ void __launch_bounds__(128, MinBlocks<T, K>::value) stage_kernel(cons
         cd = dst;
     }
     if (gq < A.op.Nf)
-        fluid_cell<T, K, MODE>(A, gq, shot, cd);
+        fluid_cell<T, K, MODE>(A, gq, shot, cd, acc);
     else if (gq < A.op.Nf + A.op.Ns)
-        solid_cell<T, K, MODE>(A, gq - A.op.Nf, shot, cd);
+        solid_cell<T, K, MODE>(A, gq - A.op.Nf, shot, cd, acc);
 }
 
 // canonical (AoS, input cell order, FP64) <-> device layout (SoA by class, T);
@@ -1122,6 +1155,18 @@ void launch_kk(const StageArgsT<T>& a, dim3 grid, cudaStream_t s) {
         if (dev < 0 || dev >= 64 || opted[dev] < smem) {
             cudaFuncSetAttribute(stage_kernel<T, K, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (dev >= 0 && dev < 64) opted[dev] = smem;
+        }
+    }
+    if constexpr (AccSmem<T, K>::value) {
+        // the accumulators need the largest shared-memory carveout for the
+        // resident blocks the register budget allows
+        static bool carved[64] = {};
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (dev < 0 || dev >= 64 || !carved[dev]) {
+            cudaFuncSetAttribute(stage_kernel<T, K, MODE>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared);
+            if (dev >= 0 && dev < 64) carved[dev] = true;
         }
     }
     stage_kernel<T, K, MODE><<<grid, 128, smem, s>>>(a);
