@@ -292,9 +292,11 @@ struct RectLoop<f2x> {
 // spill to local memory, whose footprint (over 400 bytes a thread) exceeds
 // L1.  With AccSmem the block's dynamic shared memory holds them instead,
 // thread-major with an odd stride in elements (no bank conflicts).  That
-// makes the FP32 kernel about 20 % faster at k = 3 (still 8 blocks); for
-// 8-byte values the shared memory allows only 6 blocks, which left the
-// double-float kernel unchanged and slowed the FP64 one.
+// makes the FP32 kernel about 20 % faster at k = 3 (still 8 blocks).  For
+// 8-byte values the shared memory allows at most 6 blocks: the double-float
+// k = 2 kernel at 5 blocks (96 registers, no spills) with prefetched target
+// sources is 7 % faster than with 8 blocks and spills; the FP64 kernel, bound
+// by its FP64 pipe, and double-float k = 3 (4 blocks) gain nothing.
 template <class T, int K>
 struct AccSmem {
     static constexpr bool value = false;
@@ -302,6 +304,10 @@ struct AccSmem {
 template <int K>
 struct AccSmem<float, K> {
     static constexpr bool value = K >= 2;
+};
+template <int K>
+struct AccSmem<f2x, K> {
+    static constexpr bool value = K == 2;
 };
 template <int K>
 __host__ __device__ constexpr int acc_stride() {
@@ -387,20 +393,21 @@ struct CellCtx {
 // L2 early.  Mask bits: 1 state, 2 own traces and face tables, 4 neighbour
 // traces, 8 target sources, all at the start of the cell; 16 target sources
 // and 32 neighbour traces just before the face loop.  The FP32 kernel gains
-// about 20 % from them (mask 50, the best of a sweep on GB300); for 8-byte
-// values every mask was slower, the lines in flight evicting one another
-// from L2 before use.
-template <class T>
+// about 20 % from them (mask 50, the best of a sweep on GB300).  The 8-byte
+// kernels with register accumulators (spilled) lost with every mask; the
+// double-float k = 2 kernel with shared-memory accumulators gains 7 % from
+// prefetching the target sources (mask 16).
+template <class T, int K>
 struct L2Prefetch {
     static constexpr int mask = 0;
 };
-template <>
-struct L2Prefetch<float> {
+template <int K>
+struct L2Prefetch<float, K> {
     static constexpr int mask = 50;
 };
-template <>
-struct L2Prefetch<f2x> {
-    static constexpr int mask = 0;
+template <int K>
+struct L2Prefetch<f2x, K> {
+    static constexpr int mask = K == 2 ? 16 : 0;
 };
 
 __device__ __forceinline__ void pf_l2(const void* p) { asm volatile("prefetch.L2 [%0];" ::"l"(p)); }
@@ -418,10 +425,10 @@ __device__ __forceinline__ void pf_runs(const E* base, size_t stride, int narr, 
 
 // WHERE 0: at the start of the cell; 1: before the face loop.  NV state
 // values per cell, NW published traces per face slot (w first, then omega).
-template <class T, int NV, int NW, int WHERE, bool TARGETS>
+template <class T, int K, int NV, int NW, int WHERE, bool TARGETS>
 __device__ __forceinline__ void prefetch_cell(const StageArgsT<T>& A, const CellCtx<T>& c, size_t soff, const T* tr,
                                               int S, const int* nbt, const T* bet, int nfaces) {
-    constexpr int PF = L2Prefetch<T>::mask;
+    constexpr int PF = L2Prefetch<T, K>::mask;
     const int lane = c.q & 31;
     if constexpr (WHERE == 0 && (PF & 1)) pf_runs(A.inp + soff + (c.q - lane), c.N, NV, lane);
     if constexpr (WHERE == 0 && (PF & 2)) {
@@ -585,8 +592,8 @@ __device__ __forceinline__ void fluid_cell(const StageArgsT<T>& A, int q, int sh
         T* kmx = U;
         T* kmy = U + n;
         T* kp = U + 2 * n;
-        if constexpr (L2Prefetch<T>::mask != 0)
-            prefetch_cell<T, 3 * n, f, 0, MODE != MODE_RAW>(A, c, soff, c.trf_in, c.SF, op.nb_f,
+        if constexpr (L2Prefetch<T, K>::mask != 0)
+            prefetch_cell<T, K, 3 * n, f, 0, MODE != MODE_RAW>(A, c, soff, c.trf_in, c.SF, op.nb_f,
                                                             OpData<T>::beta_f(op), rect ? 4 : c.nF);
         {
             T u[n];
@@ -598,8 +605,8 @@ __device__ __forceinline__ void fluid_cell(const StageArgsT<T>& A, int q, int sh
             load_state<n>(A.inp + soff, c.N, q, n, u);          // m_y
             add_ddy<T, K>(u, kp);
         }
-        if constexpr (L2Prefetch<T>::mask != 0)
-            prefetch_cell<T, 3 * n, f, 1, MODE != MODE_RAW>(A, c, soff, c.trf_in, c.SF, op.nb_f,
+        if constexpr (L2Prefetch<T, K>::mask != 0)
+            prefetch_cell<T, K, 3 * n, f, 1, MODE != MODE_RAW>(A, c, soff, c.trf_in, c.SF, op.nb_f,
                                                             OpData<T>::beta_f(op), rect ? 4 : c.nF);
         if (rect) {
             // faces 0 (s = -1) and 2 (s = +1) are horizontal, 1 (s = +1) and 3 (s = -1) vertical
@@ -832,8 +839,8 @@ __device__ __forceinline__ void solid_cell(const StageArgsT<T>& A, int q, int sh
         T* exy = U + 2 * n;
         T* kvx = U + 3 * n;
         T* kvy = U + 4 * n;
-        if constexpr (L2Prefetch<T>::mask != 0)
-            prefetch_cell<T, 5 * n, 2 * f, 0, MODE != MODE_RAW>(A, c, soff, c.trs_in, c.SS, op.nb_s,
+        if constexpr (L2Prefetch<T, K>::mask != 0)
+            prefetch_cell<T, K, 5 * n, 2 * f, 0, MODE != MODE_RAW>(A, c, soff, c.trs_in, c.SS, op.nb_s,
                                                                 OpData<T>::beta_s(op), rect ? 4 : c.nF);
         {
             T u[n];
@@ -851,8 +858,8 @@ __device__ __forceinline__ void solid_cell(const StageArgsT<T>& A, int q, int sh
             add_ddy<T, K>(u, kvx);
             add_ddx<T, K>(u, kvy);
         }
-        if constexpr (L2Prefetch<T>::mask != 0)
-            prefetch_cell<T, 5 * n, 2 * f, 1, MODE != MODE_RAW>(A, c, soff, c.trs_in, c.SS, op.nb_s,
+        if constexpr (L2Prefetch<T, K>::mask != 0)
+            prefetch_cell<T, K, 5 * n, 2 * f, 1, MODE != MODE_RAW>(A, c, soff, c.trs_in, c.SS, op.nb_s,
                                                                 OpData<T>::beta_s(op), rect ? 4 : c.nF);
         if (rect) {
             if constexpr (RectLoop<T>::value) {
@@ -934,9 +941,11 @@ __device__ __forceinline__ void solid_cell(const StageArgsT<T>& A, int q, int sh
 // Resident blocks per SM asked of the register allocator (128 threads a
 // block): 2 blocks allow 255 registers, 3 allow 168, 4 allow 128, 5 allow 96,
 // 6 allow 80, 8 allow 64.  The stage kernels are bound by load latency, so
-// occupancy pays even at the price of spills to L1-resident local memory;
-// the values are the fastest of a sweep on the 1024 x 512 bilayer (and, for
-// FP32, the 1.2 M-cell hybrid mesh) on GB300.
+// occupancy pays even at the price of spills to local memory; where the
+// accumulators sit in shared memory (AccSmem) the shared memory may cap the
+// resident blocks below this count.  The values are the fastest of sweeps
+// on the 1024 x 512 bilayer (and, for FP32, the 1.2 M-cell hybrid mesh) on
+// GB300.
 template <class T, int K>
 struct MinBlocks;
 template <int K>
@@ -949,7 +958,7 @@ struct MinBlocks<float, K> {
 };
 template <int K>
 struct MinBlocks<f2x, K> {
-    static constexpr int value = K == 1 ? 8 : (K == 2 ? 8 : 5);
+    static constexpr int value = K == 1 ? 8 : (K == 2 ? 5 : 5);
 };
 
 // Dynamic shared memory of a stage block: the per-warp class copies
