@@ -361,8 +361,8 @@ int hho_batch_erk_step(hho_ops* ops, const hho_tableau* tab, int32_t n_shots, in
 /* ------------------------------------------------------------------------- */
 
 /* Doubles of device work that hho_adjoint_vjp needs: checkpoints every
- * checkpoint_every steps, the stage values of one segment, the ERK work
- * buffer and a few state-sized vectors. */
+ * checkpoint_every steps, the stage values of one segment with their face
+ * traces, the ERK work buffer and a few state-sized vectors. */
 int hho_adjoint_work_size(const hho_ops* ops, const hho_tableau* tab, int64_t nsteps, int64_t checkpoint_every,
                           int64_t* n_doubles);
 

@@ -23,8 +23,8 @@
 // current model.  The host maps dL/dtheta to dL/d(rho, kappa, lambda, mu).
 //
 // Checkpointing: U is stored every `checkpoint_every` steps in the forward
-// pass; each segment is recomputed, keeping its stage values, before its
-// backward sweep.
+// pass; each segment is recomputed, keeping its stage values and their face
+// traces, before its backward sweep.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -35,11 +35,33 @@
 
 namespace {
 
-// out = S M in (inverse = false) or S M^-1 in (inverse = true); S = -1 on the
-// dual fields (m_x, m_y / s_xx, s_yy, s_xy), +1 on the primal fields.
+constexpr int MAX_STAGES = 6;   // the largest tableau build_plan accepts
+
+// The operand of the mass kernel: in = a1 in1 + a2 in2 (in2 may be null),
+// rounded as axpby_kernel does; stored to `keep` when that is not null.
+struct MassIn {
+    const double* in1;
+    double a1;
+    const double* in2;
+    double a2;
+    double* keep;
+};
+// Where the result v = S M in (or S M^-1 in) goes: `out` (may be null), and
+// the ERK adjoint accumulations acc += v, pend[l] += a[l] v.
+struct MassOut {
+    double* out;
+    double* acc;
+    int n_pend;
+    double* pend[MAX_STAGES];
+    double a[MAX_STAGES];
+};
+
+// v = S M in (inverse = 0) or S M^-1 in (inverse = 1) per cell; S = -1 on the
+// dual fields (m_x, m_y / s_xx, s_yy, s_xy), +1 on the primal fields.  One
+// thread per cell; the operand combination and the accumulations of the
+// adjoint stage recursion are fused in (MassIn, MassOut).
 __global__ void mass_kernel(DevOps op, const double* __restrict__ mass_f, const double* __restrict__ mass_s,
-                            const double* __restrict__ cls_minv, const double* __restrict__ in,
-                            double* __restrict__ out, int inverse) {
+                            const double* __restrict__ cls_minv, MassIn I, MassOut O, int inverse) {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= op.Nf + op.Ns) return;
     const bool fl = g < op.Nf;
@@ -51,16 +73,27 @@ __global__ void mass_kernel(DevOps op, const double* __restrict__ mass_f, const 
     const double* Mat = inverse ? cls_minv + (size_t)cls * n * n : op.cls_dbl + ci[CI_DOFF];
     const int N = fl ? op.Nf : op.Ns;
     const size_t off = fl ? 0 : (size_t)3 * n * op.Nf;
-    const double* x = in + off;
-    double* y = out + off;
+    auto idx = [&](int field, int i) { return off + (size_t)(field * n + i) * N + q; };
     double u[10], r[10];
     auto matvec = [&](int field) {
-        for (int i = 0; i < n; ++i) u[i] = x[(size_t)(field * n + i) * N + q];
+        for (int i = 0; i < n; ++i) {
+            const size_t e = idx(field, i);
+            double v = I.a1 * I.in1[e];
+            if (I.in2) v = fma(I.a2, I.in2[e], v);
+            if (I.keep) I.keep[e] = v;
+            u[i] = v;
+        }
         for (int i = 0; i < n; ++i) {
             double s = 0.0;
             for (int j = 0; j < n; ++j) s = fma(Mat[i * n + j], u[j], s);
             r[i] = s;
         }
+    };
+    auto emit = [&](int field, int i, double v) {
+        const size_t e = idx(field, i);
+        if (O.out) O.out[e] = v;
+        if (O.acc) O.acc[e] = O.acc[e] + v;
+        for (int l = 0; l < O.n_pend; ++l) O.pend[l][e] = fma(O.a[l], v, O.pend[l][e]);
     };
     if (fl) {
         const double cm = inverse ? 1.0 / mass_f[q] : mass_f[q];               // rho h^2
@@ -68,7 +101,7 @@ __global__ void mass_kernel(DevOps op, const double* __restrict__ mass_f, const 
         for (int fld = 0; fld < 3; ++fld) {
             matvec(fld);
             const double c = fld < 2 ? -cm : cp;                               // S: m negated
-            for (int i = 0; i < n; ++i) y[(size_t)(fld * n + i) * N + q] = c * r[i];
+            for (int i = 0; i < n; ++i) emit(fld, i, c * r[i]);
         }
     } else {
         // s block: (h^2 D) (x) M0 with D = [[d0, d1, 0], [d1, d0, 0], [0, 0, d2]]
@@ -87,14 +120,14 @@ __global__ void mass_kernel(DevOps op, const double* __restrict__ mass_f, const 
         matvec(1);
         for (int i = 0; i < n; ++i) t1[i] = r[i];
         for (int i = 0; i < n; ++i) {
-            y[(size_t)(0 * n + i) * N + q] = -(d0 * t0[i] + d1 * t1[i]);
-            y[(size_t)(1 * n + i) * N + q] = -(d1 * t0[i] + d0 * t1[i]);
+            emit(0, i, -(d0 * t0[i] + d1 * t1[i]));
+            emit(1, i, -(d1 * t0[i] + d0 * t1[i]));
         }
         matvec(2);
-        for (int i = 0; i < n; ++i) y[(size_t)(2 * n + i) * N + q] = -d2 * r[i];
+        for (int i = 0; i < n; ++i) emit(2, i, -d2 * r[i]);
         for (int fld = 3; fld < 5; ++fld) {
             matvec(fld);
-            for (int i = 0; i < n; ++i) y[(size_t)(fld * n + i) * N + q] = rv * r[i];
+            for (int i = 0; i < n; ++i) emit(fld, i, rv * r[i]);
         }
     }
 }
@@ -224,7 +257,7 @@ __global__ void wavelet_grad_kernel(DevOps op, SrcMeta meta, const double* __res
 
 struct AdjBuffers {
     int64_t S, T;           // state and trace sizes
-    double *ckpt, *stages, *erk_work, *lam, *mu, *x, *y, *nu, *acc, *pend, *raw, *tr, *grad_f, *grad_s, *wgrad;
+    double *ckpt, *stages, *stage_tr, *erk_work, *lam, *mu, *x, *y, *acc, *pend, *raw, *tr, *grad_f, *grad_s, *wgrad;
 };
 
 int64_t adjoint_layout(const hho_ops* ops, const hho_tableau* tab, int64_t nsteps, int64_t C, AdjBuffers* b,
@@ -244,13 +277,13 @@ int64_t adjoint_layout(const hho_ops* ops, const hho_tableau* tab, int64_t nstep
     B.S = S;
     B.T = T;
     B.ckpt = take(n_ckpt * S);
-    B.stages = take(C * s * S);
+    B.stages = take((C * s + 1) * S);     // stage inputs of a segment, then its end state
+    B.stage_tr = take((C * s + 1) * T);   // their face traces
     B.erk_work = take(erk);
     B.lam = take(S);
     B.mu = take(S);
     B.x = take(S);
     B.y = take(S);
-    B.nu = take(S);
     B.acc = take(S);
     B.pend = take(s * S);
     B.raw = take(S);
@@ -311,16 +344,11 @@ extern "C" int hho_adjoint_vjp(hho_ops* ops, const hho_tableau* tab, double t0, 
     auto copy = [&](double* dst, const double* src, int64_t n) {
         return cudaMemcpyAsync(dst, src, sizeof(double) * n, cudaMemcpyDeviceToDevice, st) == cudaSuccess;
     };
-    // erk work split as in erk_run: [X][partial sums][2 traces]
-    double* X = B.erk_work;
+    // the ERK partial-sum buffers of the segment recompute, laid out as in
+    // erk_run ([X][partial sums][2 traces]; X and the traces live in the
+    // segment store here)
     double* bufs = B.erk_work + S;
-    double* trs[2] = {B.erk_work + S * (1 + nb), B.erk_work + S * (1 + nb) + ops->trace_doubles};
-    auto resolve = [&](int code, double* state) -> double* {
-        if (code == SRC_STATE) return state;
-        if (code == SRC_X) return X;
-        if (code == SRC_ZERO) return nullptr;
-        return bufs + S * code;
-    };
+    auto partial = [&](int code) -> double* { return code == SRC_ZERO ? nullptr : bufs + S * code; };
     DevOps adj = ops->dev;
     adj.if_coef = ops->d_if_coef_adj;
 
@@ -348,33 +376,37 @@ extern "C" int hho_adjoint_vjp(hho_ops* ops, const hho_tableau* tab, double t0, 
     for (int64_t seg = n_segments - 1; seg >= 0; --seg) {
         const int64_t n0 = seg * C;                                   // segment starts at U^{n0}
         const int64_t nst = (n0 + C <= nsteps) ? C : nsteps - n0;
-        // recompute the segment, keeping the stage values Y_{n,j} (stage j input)
-        double* U = B.x;   // running state
-        if (!copy(U, B.ckpt + seg * S, S)) return HHO_ECUDA;
+        // Recompute the segment.  Stage j of step m reads its input Y_{m,j}
+        // and that input's face traces from slot m s + j of the segment store
+        // and writes the next stage input (slot m s + j + 1, or the next
+        // step's state in slot (m + 1) s) with its traces straight into the
+        // store: no copies, and the backward sweep needs no trace launch for
+        // the forward stage values.
+        auto Y = [&](int64_t m, int j) { return B.stages + (m * s + j) * S; };
+        auto TY = [&](int64_t m, int j) { return B.stage_tr + (m * s + j) * B.T; };
+        if (!copy(Y(0, 0), B.ckpt + seg * S, S)) return HHO_ECUDA;
         StageArgsT<double> a;
         memset(&a, 0, sizeof(a));
         a.op = ops->dev;
-        a.inp = U;
-        a.tr_out = trs[0];
+        a.inp = Y(0, 0);
+        a.tr_out = TY(0, 0);
         launch_stage_f64(ops, MODE_TRACES, a, 1, 0.0, false, stream);
-        int cur = 0;
         for (int64_t m = 0; m < nst; ++m) {
             const double tn = t0 + (double)(n0 + m) * dt;
             for (int j = 0; j < s; ++j) {
-                double* Yj = B.stages + (m * s + j) * S;
-                if (!copy(Yj, j == 0 ? U : X, S)) return HHO_ECUDA;
                 const StagePlan& P = plan[j];
-                a.inp = (j == 0) ? U : X;
-                a.tr_in = trs[cur];
-                a.tr_out = trs[cur ^ 1];
+                const bool last = j + 1 == s;
+                a.inp = Y(m, j);
+                a.tr_in = TY(m, j);
+                a.tr_out = last ? TY(m + 1, 0) : TY(m, j + 1);
                 a.n_tgt = P.n_tgt;
                 for (int t = 0; t < P.n_tgt; ++t) {
-                    a.tgt[t].src = resolve(P.t[t].src, U);
-                    a.tgt[t].dst = resolve(P.t[t].dst, U);
+                    const int sc = P.t[t].src, dc = P.t[t].dst;
+                    a.tgt[t].src = sc == SRC_STATE ? Y(m, 0) : partial(sc);
+                    a.tgt[t].dst = dc == SRC_STATE ? Y(m + 1, 0) : dc == SRC_X ? Y(m, j + 1) : partial(dc);
                     a.tgt[t].coef = P.t[t].a * dt;
                 }
                 launch_stage_f64(ops, MODE_STAGE, a, 1, tn + tab->c[j] * dt, true, stream);
-                cur ^= 1;
             }
         }
         rc = check_cuda("hho_adjoint_vjp (segment recompute)");
@@ -390,11 +422,13 @@ extern "C" int hho_adjoint_vjp(hho_ops* ops, const hho_tableau* tab, double t0, 
             if (!copy(B.acc, B.lam, S)) return HHO_ECUDA;
             axpby_kernel<<<grid1(s * S), 256, 0, st>>>(s * S, 0.0, nullptr, 0.0, nullptr, B.pend);
             for (int j = s - 1; j >= 0; --j) {
-                // mu_j = dt (b_j lambda + P_j)
-                axpby_kernel<<<grid1(S), 256, 0, st>>>(S, dt * tab->b[j], B.lam, dt, B.pend + j * S, B.mu);
-                // nu_j = A^T mu_j = S M A' M^-1 S mu_j
-                mass_kernel<<<cblk, 128, 0, st>>>(ops->dev, ops->d_mass_f, ops->d_mass_s, ops->d_cls_minv, B.mu, B.x,
-                                                  1);
+                // mu_j = dt (b_j lambda + P_j), x = M^-1 S mu_j
+                const MassIn mi = {B.lam, dt * tab->b[j], B.pend + j * S, dt, B.mu};
+                MassOut mo;
+                memset(&mo, 0, sizeof(mo));
+                mo.out = B.x;
+                mass_kernel<<<cblk, 128, 0, st>>>(ops->dev, ops->d_mass_f, ops->d_mass_s, ops->d_cls_minv, mi, mo, 1);
+                // nu_j = S M A' x, accumulated into acc and the pending sums P_l (l < j)
                 StageArgsT<double> b;
                 memset(&b, 0, sizeof(b));
                 b.op = adj;
@@ -408,22 +442,22 @@ extern "C" int hho_adjoint_vjp(hho_ops* ops, const hho_tableau* tab, double t0, 
                 b.tgt[0].dst = B.y;
                 b.tgt[0].coef = 1.0;
                 launch_stage_f64(ops, MODE_APPLY, b, 1, 0.0, false, stream);
-                mass_kernel<<<cblk, 128, 0, st>>>(ops->dev, ops->d_mass_f, ops->d_mass_s, ops->d_cls_minv, B.y, B.nu,
-                                                  0);
-                axpby_kernel<<<grid1(S), 256, 0, st>>>(S, 1.0, B.acc, 1.0, B.nu, B.acc);
+                const MassIn ni = {B.y, 1.0, nullptr, 0.0, nullptr};
+                MassOut no;
+                memset(&no, 0, sizeof(no));
+                no.acc = B.acc;
                 for (int l = 0; l < j; ++l)
-                    if (tab->a[j][l] != 0.0)
-                        axpby_kernel<<<grid1(S), 256, 0, st>>>(S, 1.0, B.pend + l * S, tab->a[j][l], B.nu,
-                                                               B.pend + l * S);
-                // parameter and wavelet gradients of stage j
-                const double* Yj = B.stages + (m * s + j) * S;
+                    if (tab->a[j][l] != 0.0) {
+                        no.pend[no.n_pend] = B.pend + l * S;
+                        no.a[no.n_pend++] = tab->a[j][l];
+                    }
+                mass_kernel<<<cblk, 128, 0, st>>>(ops->dev, ops->d_mass_f, ops->d_mass_s, ops->d_cls_minv, ni, no, 0);
+                // parameter and wavelet gradients of stage j (the forward traces of Y_{m,j} are stored)
                 StageArgsT<double> r;
                 memset(&r, 0, sizeof(r));
                 r.op = ops->dev;
-                r.inp = Yj;
-                r.tr_out = B.tr;
-                launch_stage_f64(ops, MODE_TRACES, r, 1, 0.0, false, stream);
-                r.tr_in = B.tr;
+                r.inp = Y(m, j);
+                r.tr_in = TY(m, j);
                 r.tr_out = nullptr;
                 r.n_tgt = 1;
                 r.tgt[0].src = nullptr;
