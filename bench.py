@@ -8,7 +8,8 @@ time step: every stage kernel plus the receiver recording.
 Metric: cell-DOF updates per second per ERK stage =
 cell DOFs x stages x steps / time.  `value` is device-timed with inputs
 resident in HBM; `e2e` is the same metric through hho_erk_run_host with the
-state in pinned host memory (host<->device copies inside every step).
+state in pinned host memory (every step reads it from and writes it back to
+host memory inside the timed region).
 
 Roofline: the stage kernel is bound by FP64 arithmetic on this part (FP64
 FMA rate measured live by the probe kernel), reported as "bound": "alu"
@@ -592,7 +593,9 @@ def main():
         el = time.perf_counter() - t0
         e2e = {"value": world * ndof * a.stages * ne / el, "unit": UNIT, "h2d_bytes_per_step": 8 * ndof,
                "d2h_bytes_per_step": 8 * ndof, "steps": ne,
-               "path": "hho_erk_run_host: pinned H2D, pack, 1 ERK step, unpack, D2H, stream sync"}
+               "path": "hho_erk_run_host on a pinned host buffer: the pack kernel reads the canonical state from "
+                       "host memory (NVLink-C2C), 1 ERK step, the unpack kernel writes it back to host memory, "
+                       "stream sync"}
 
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:

@@ -266,11 +266,15 @@ int hho_erk_step(hho_ops* ops, const hho_tableau* tab, double t0, double dt, int
 int hho_erk_step_record(hho_ops* ops, const hho_tableau* tab, double t0, double dt, int64_t nsteps,
                         double* d_state, double* d_work, double* d_seismogram, void* stream);
 
-/* Same as hho_erk_step, end to end from host memory: copies the canonical
- * host vector h_canonical (n_canonical doubles; pinned memory recommended) to
- * the device, packs it, steps, unpacks and copies it back, and synchronises
- * the stream.  The device buffers it needs are allocated on the first call
- * and kept with ops. */
+/* Same as hho_erk_step, end to end from host memory: the canonical host
+ * vector h_canonical (n_canonical doubles) is packed into the device layout,
+ * stepped, unpacked back into h_canonical, and the stream is synchronised.
+ * Pinned host memory (cudaHostAlloc, or a pinned torch tensor) mapped into
+ * the device's address space is read and written by the pack kernels
+ * directly; other host memory is staged through a device copy.  Both give
+ * the same bits as hho_state_pack, hho_erk_step and hho_state_unpack.  The
+ * device buffers it needs are allocated on the first call and kept with
+ * ops. */
 int hho_erk_run_host(hho_ops* ops, const hho_tableau* tab, double t0, double dt, int64_t nsteps,
                      double* h_canonical, void* stream);
 

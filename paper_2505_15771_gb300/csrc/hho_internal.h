@@ -187,6 +187,8 @@ struct hho_ops {
     int64_t n_canonical = 0;
     int32_t* d_dev2orig = nullptr;             // [Nf + Ns]: original cell id or -1 (padding)
     int64_t* d_canon_off = nullptr;            // [nc]
+    int32_t* d_cell_dom = nullptr;             // [nc]: 0 fluid, 1 solid
+    int32_t* d_cell_pos = nullptr;             // [nc]: device position within the cell's domain
     double c_max = 0.0, h_min = 0.0;
     // host-side per-cell data kept for sources/receivers
     std::vector<double> centroid, diam, rho, tau;

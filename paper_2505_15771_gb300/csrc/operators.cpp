@@ -719,6 +719,8 @@ extern "C" int hho_operators_build_tau(const hho_mesh* m, int32_t k, const doubl
     }
     ops->d_dev2orig = dev_upload(ops, dev2orig, &err);
     ops->d_canon_off = dev_upload(ops, ops->canon_off, &err);
+    ops->d_cell_dom = dev_upload(ops, ops->cell_dom, &err);
+    ops->d_cell_pos = dev_upload(ops, ops->cell_pos, &err);
     ops->d_mass_f = dev_upload(ops, mass_f, &err);
     ops->d_mass_s = dev_upload(ops, mass_s, &err);
     if (err != HHO_OK) {

@@ -1041,6 +1041,76 @@ __global__ void unpack_kernel(const int32_t* __restrict__ dev2orig, const int64_
     for (int i = 0; i < nv; ++i) cv[i] = double(st[(size_t)i * N + q]);
 }
 
+// Canonical vector in host memory (pinned, mapped into the device's address
+// space) <-> device-layout state of type T.  A block of 64 threads takes 64
+// consecutive canonical cells, whose values form one contiguous run: the run
+// crosses the host link in coalesced 8-byte accesses (eight in flight per
+// thread) and is reordered through shared memory, one thread per cell on the
+// device side.  Padding slots of the state are not touched.
+constexpr int STAGED_CELLS = 64;
+template <class T>
+__global__ void __launch_bounds__(STAGED_CELLS) pack_host_kernel(const int32_t* __restrict__ cell_dom,
+                                                                 const int32_t* __restrict__ cell_pos,
+                                                                 const int64_t* __restrict__ canon_off, int nc,
+                                                                 int64_t n_canon, int Nf, int Ns, int n,
+                                                                 const double* __restrict__ canon,
+                                                                 T* __restrict__ state) {
+    extern __shared__ double run[];
+    const int c0 = blockIdx.x * STAGED_CELLS;
+    const int c1 = min(c0 + STAGED_CELLS, nc);
+    const int64_t e0 = canon_off[c0];
+    const int len = (int)((c1 < nc ? canon_off[c1] : n_canon) - e0);
+    constexpr int U = 8;
+    for (int b = 0; b < len; b += U * STAGED_CELLS) {
+        double v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int e = b + u * STAGED_CELLS + threadIdx.x;
+            v[u] = e < len ? canon[e0 + e] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int e = b + u * STAGED_CELLS + threadIdx.x;
+            if (e < len) run[e] = v[u];
+        }
+    }
+    __syncthreads();
+    const int c = c0 + threadIdx.x;
+    if (c >= c1) return;
+    const bool fl = cell_dom[c] == 0;
+    const int q = cell_pos[c];
+    const int N = fl ? Nf : Ns;
+    T* st = state + (fl ? 0 : (size_t)3 * n * Nf);
+    const double* v = run + (canon_off[c] - e0);
+    const int nv = (fl ? 3 : 5) * n;
+    for (int i = 0; i < nv; ++i) st[(size_t)i * N + q] = T(v[i]);
+}
+template <class T>
+__global__ void __launch_bounds__(STAGED_CELLS) unpack_host_kernel(const int32_t* __restrict__ cell_dom,
+                                                                   const int32_t* __restrict__ cell_pos,
+                                                                   const int64_t* __restrict__ canon_off, int nc,
+                                                                   int64_t n_canon, int Nf, int Ns, int n,
+                                                                   const T* __restrict__ state,
+                                                                   double* __restrict__ canon) {
+    extern __shared__ double run[];
+    const int c0 = blockIdx.x * STAGED_CELLS;
+    const int c1 = min(c0 + STAGED_CELLS, nc);
+    const int64_t e0 = canon_off[c0];
+    const int len = (int)((c1 < nc ? canon_off[c1] : n_canon) - e0);
+    const int c = c0 + threadIdx.x;
+    if (c < c1) {
+        const bool fl = cell_dom[c] == 0;
+        const int q = cell_pos[c];
+        const int N = fl ? Nf : Ns;
+        const T* st = state + (fl ? 0 : (size_t)3 * n * Nf);
+        double* v = run + (canon_off[c] - e0);
+        const int nv = (fl ? 3 : 5) * n;
+        for (int i = 0; i < nv; ++i) v[i] = double(st[(size_t)i * N + q]);
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < len; e += STAGED_CELLS) canon[e0 + e] = run[e];
+}
+
 // Energy 1/2 U^T M U (Sec. 5.1) with M = h^2 (material) x M0_ref per cell.
 template <int K>
 __global__ void __launch_bounds__(256) energy_kernel(DevOps op, const double* __restrict__ state,
@@ -1552,6 +1622,50 @@ static int erk_single(hho_ops* ops, const hho_tableau* tab, double t0, double dt
     return check_launch(who);
 }
 
+// hho_erk_run_host on a pinned, mapped host buffer: the state is packed
+// from the host buffer straight into the arithmetic's device state (the
+// double-float pair copy, or the FP64 state), stepped, and unpacked
+// straight back, with no device copy of the canonical vector.
+static int erk_run_mapped(hho_ops* ops, const hho_tableau* tab, double t0, double dt, int64_t nsteps,
+                          double* m_canonical, cudaStream_t st) {
+    const char* who = "hho_erk_run_host";
+    std::vector<StagePlan> plan;
+    int nb = 0;
+    if (build_plan(tab, plan, &nb) != HHO_OK) {
+        hho_set_error("%s: unsupported tableau", who);
+        return HHO_EINVAL;
+    }
+    const int nc = (int)ops->nc;
+    if (nc == 0) return HHO_OK;
+    const int blocks = (nc + STAGED_CELLS - 1) / STAGED_CELLS;
+    const size_t smem = sizeof(double) * STAGED_CELLS * 5 * ops->n;
+    const bool pairs = ops->arith == HHO_F32X2;
+    void* dst = pairs ? (void*)(ops->d_host_work + work_f64_part(ops, nb)) : (void*)ops->d_host_state;
+    if (pairs)
+        pack_host_kernel<f2x><<<blocks, STAGED_CELLS, smem, st>>>(ops->d_cell_dom, ops->d_cell_pos, ops->d_canon_off, nc,
+                                                                   ops->n_canonical, ops->dev.Nf, ops->dev.Ns, ops->n,
+                                                                   m_canonical, (f2x*)dst);
+    else
+        pack_host_kernel<double><<<blocks, STAGED_CELLS, smem, st>>>(ops->d_cell_dom, ops->d_cell_pos, ops->d_canon_off,
+                                                                      nc, ops->n_canonical, ops->dev.Nf, ops->dev.Ns,
+                                                                      ops->n, m_canonical, (double*)dst);
+    int rc = check_launch(who);
+    if (rc) return rc;
+    rc = pairs ? erk_run<f2x>(ops, tab, t0, dt, nsteps, 1, (f2x*)dst, (f2x*)ops->d_host_work, nullptr, st, who)
+               : erk_run<double>(ops, tab, t0, dt, nsteps, 1, (double*)dst, ops->d_host_work, nullptr, st, who);
+    if (rc) return rc;
+    if (pairs)
+        unpack_host_kernel<f2x><<<blocks, STAGED_CELLS, smem, st>>>(ops->d_cell_dom, ops->d_cell_pos, ops->d_canon_off,
+                                                                     nc, ops->n_canonical, ops->dev.Nf, ops->dev.Ns,
+                                                                     ops->n, (const f2x*)dst, m_canonical);
+    else
+        unpack_host_kernel<double><<<blocks, STAGED_CELLS, smem, st>>>(ops->d_cell_dom, ops->d_cell_pos,
+                                                                        ops->d_canon_off, nc, ops->n_canonical,
+                                                                        ops->dev.Nf, ops->dev.Ns, ops->n,
+                                                                        (const double*)dst, m_canonical);
+    return check_launch(who);
+}
+
 extern "C" int hho_set_launch_mode(hho_ops* ops, int32_t mode) {
     if (!ops || (mode != HHO_LAUNCH_STREAM && mode != HHO_LAUNCH_GRAPH && mode != HHO_LAUNCH_AUTO)) {
         hho_set_error("hho_set_launch_mode: mode must be HHO_LAUNCH_STREAM, HHO_LAUNCH_GRAPH or HHO_LAUNCH_AUTO");
@@ -1912,6 +2026,7 @@ extern "C" int hho_erk_run_host(hho_ops* ops, const hho_tableau* tab, double t0,
             return HHO_ENOMEM;
         }
     }
+    cudaStream_t st = (cudaStream_t)stream;
     if (ops->host_work_size < wsz) {
         if (ops->d_host_work) cudaFree(ops->d_host_work);
         ops->d_host_work = nullptr;
@@ -1920,8 +2035,28 @@ extern "C" int hho_erk_run_host(hho_ops* ops, const hho_tableau* tab, double t0,
             return HHO_ENOMEM;
         }
         ops->host_work_size = wsz;
+        // the mapped path leaves padding slots of its states unwritten
+        if (cudaMemsetAsync(ops->d_host_work, 0, sizeof(double) * wsz, st) != cudaSuccess ||
+            cudaMemsetAsync(ops->d_host_state, 0, sizeof(double) * ops->n_state, st) != cudaSuccess) {
+            hho_set_error("hho_erk_run_host: device memset failed");
+            return HHO_ECUDA;
+        }
     }
-    cudaStream_t st = (cudaStream_t)stream;
+    // A pinned host buffer mapped into the device's address space is read
+    // and written by the pack kernels directly (over NVLink-C2C on GB300);
+    // any other host memory goes through a staging copy.
+    cudaPointerAttributes pa;
+    if (cudaPointerGetAttributes(&pa, h_canonical) == cudaSuccess && pa.type == cudaMemoryTypeHost &&
+        pa.devicePointer) {
+        rc = erk_run_mapped(ops, tab, t0, dt, nsteps, (double*)pa.devicePointer, st);
+        if (rc) return rc;
+        if (cudaStreamSynchronize(st) != cudaSuccess) {
+            hho_set_error("hho_erk_run_host: %s", cudaGetErrorString(cudaGetLastError()));
+            return HHO_ECUDA;
+        }
+        return HHO_OK;
+    }
+    cudaGetLastError();   // an unregistered pointer leaves an error on some drivers
     if (cudaMemcpyAsync(ops->d_host_canon, h_canonical, sizeof(double) * ops->n_canonical, cudaMemcpyHostToDevice,
                         st) != cudaSuccess) {
         hho_set_error("hho_erk_run_host: host-to-device copy failed");
