@@ -53,5 +53,34 @@ def build(verbose=False):
     return LIB
 
 
+def build_stage_variant(tuning_header: str, out_dir: str) -> str:
+    """Builds <out_dir>/libhho.so with stage.cu compiled against the given
+    stage_tuning.h text (a candidate of tune.py) and the other translation
+    units taken from the in-tree build, which must exist."""
+    objs = [os.path.join(OBJ, s + ".o") for s in SOURCES if s not in ("stage.cu", "probe.cu")]
+    missing = [o for o in objs if not os.path.exists(o)]
+    if missing:
+        raise RuntimeError("in-tree objects missing (%s); run build() first" % ", ".join(missing))
+    src = os.path.join(out_dir, "csrc")
+    os.makedirs(src, exist_ok=True)
+    for f in os.listdir(CSRC):
+        if f.endswith((".cu", ".cuh", ".h", ".cpp")):
+            with open(os.path.join(CSRC, f), "rb") as a, open(os.path.join(src, f), "wb") as b:
+                b.write(a.read())
+    with open(os.path.join(src, "stage_tuning.h"), "w") as f:
+        f.write(tuning_header)
+    obj = os.path.join(out_dir, "stage.cu.o")
+    flags = [x for x in FLAGS if x != "-I" + CSRC] + ["-I" + src]
+    r = subprocess.run([NVCC] + ARCH + flags + ["-c", os.path.join(src, "stage.cu"), "-o", obj],
+                       capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError("nvcc failed for the stage variant in %s:\n%s" % (out_dir, r.stderr))
+    lib = os.path.join(out_dir, "libhho.so")
+    r = subprocess.run([NVCC] + ARCH + ["-shared", "-o", lib, obj] + objs, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError("link failed for the stage variant in %s:\n%s" % (out_dir, r.stderr))
+    return lib
+
+
 if __name__ == "__main__":
     print(build(verbose="-v" in sys.argv))

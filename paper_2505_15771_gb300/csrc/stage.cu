@@ -37,6 +37,7 @@
 
 #include "f2x.cuh"
 #include "hho_internal.h"
+#include "stage_tuning.h"
 
 namespace {
 
@@ -297,17 +298,23 @@ struct RectLoop<f2x> {
 // k = 2 kernel at 5 blocks (96 registers, no spills) with prefetched target
 // sources is 7 % faster than with 8 blocks and spills; the FP64 kernel, bound
 // by its FP64 pipe, and double-float k = 3 (4 blocks) gain nothing.
+template <class T>
+struct Tuned;
+template <>
+struct Tuned<double> {
+    static constexpr StageTuning t = TUNED_F64;
+};
+template <>
+struct Tuned<float> {
+    static constexpr StageTuning t = TUNED_F32;
+};
+template <>
+struct Tuned<f2x> {
+    static constexpr StageTuning t = TUNED_F2X;
+};
 template <class T, int K>
 struct AccSmem {
-    static constexpr bool value = false;
-};
-template <int K>
-struct AccSmem<float, K> {
-    static constexpr bool value = K >= 2;
-};
-template <int K>
-struct AccSmem<f2x, K> {
-    static constexpr bool value = K == 2;
+    static constexpr bool value = Tuned<T>::t.acc_smem[K - 1] != 0;
 };
 template <int K>
 __host__ __device__ constexpr int acc_stride() {
@@ -399,15 +406,7 @@ struct CellCtx {
 // prefetching the target sources (mask 16).
 template <class T, int K>
 struct L2Prefetch {
-    static constexpr int mask = 0;
-};
-template <int K>
-struct L2Prefetch<float, K> {
-    static constexpr int mask = 50;
-};
-template <int K>
-struct L2Prefetch<f2x, K> {
-    static constexpr int mask = K == 2 ? 16 : 0;
+    static constexpr int mask = Tuned<T>::t.prefetch[K - 1];
 };
 
 __device__ __forceinline__ void pf_l2(const void* p) { asm volatile("prefetch.L2 [%0];" ::"l"(p)); }
@@ -947,18 +946,8 @@ __device__ __forceinline__ void solid_cell(const StageArgsT<T>& A, int q, int sh
 // on the 1024 x 512 bilayer (and, for FP32, the 1.2 M-cell hybrid mesh) on
 // GB300.
 template <class T, int K>
-struct MinBlocks;
-template <int K>
-struct MinBlocks<double, K> {
-    static constexpr int value = K == 1 ? 8 : (K == 2 ? 8 : 5);
-};
-template <int K>
-struct MinBlocks<float, K> {
-    static constexpr int value = K == 1 ? 8 : (K == 2 ? 8 : 8);
-};
-template <int K>
-struct MinBlocks<f2x, K> {
-    static constexpr int value = K == 1 ? 8 : (K == 2 ? 5 : 5);
+struct MinBlocks {
+    static constexpr int value = Tuned<T>::t.min_blocks[K - 1];
 };
 
 // Dynamic shared memory of a stage block: the per-warp class copies

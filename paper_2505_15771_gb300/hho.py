@@ -16,7 +16,9 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libhho.so")
+# HHO_LIB names another build of the library (tune.py times its candidate
+# builds this way); by default the in-tree one is loaded.
+LIB_PATH = os.environ.get("HHO_LIB") or os.path.join(_HERE, "libhho.so")
 
 HHO_F64, HHO_F32, HHO_F32X2 = 0, 1, 2
 HHO_FIELD_RICKER = 0

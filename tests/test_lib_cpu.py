@@ -102,3 +102,24 @@ def test_tableaux_match_oracle(hho, s):
             assert t.a[i][j] == Aext[i, j]
         assert t.b[i] == b[i] and t.c[i] == c[i]
     _expect(hho, hho.HHO_EINVAL, hho.hho_tableau_erk, 5)
+
+
+def test_tuning_tables_round_trip():
+    """The tuner reads the stage_tuning.h tables the stage kernels compile
+    against, and rewriting them with one entry changed touches that entry
+    only."""
+    from paper_2505_15771_gb300 import tune
+    text = open(tune.HEADER).read()
+    tables = tune.read_tables(text)
+    assert tune.write_tables(text, tables) == text
+    for arith in ("f64", "f32", "f2x"):
+        t = tables[arith]
+        assert all(len(t[f]) == 3 for f in tune.FIELDS)
+        assert all(m in (2, 3, 4, 5, 6, 8, 10, 12) for m in t["min_blocks"])
+        assert all(a in (0, 1) for a in t["acc_smem"])
+        assert all(0 <= p < 64 for p in t["prefetch"])
+    new = tune.with_entry(tables, "f2x", 2, {"min_blocks": 6, "acc_smem": 0, "prefetch": 48})
+    back = tune.read_tables(tune.write_tables(text, new))
+    assert back["f2x"]["min_blocks"][1] == 6 and back["f2x"]["prefetch"][1] == 48
+    assert back["f64"] == tables["f64"] and back["f32"] == tables["f32"]
+    assert back["f2x"]["min_blocks"][0] == tables["f2x"]["min_blocks"][0]
