@@ -39,7 +39,7 @@ from . import build as B
 
 HEADER = os.path.join(B.CSRC, "stage_tuning.h")
 TABLE = {"f64": "TUNED_F64", "f32": "TUNED_F32", "f2x": "TUNED_F2X"}
-AXES = {"min_blocks": [4, 5, 6, 8], "acc_smem": [0, 1], "prefetch": [0, 16, 48, 50]}
+AXES = {"min_blocks": [4, 5, 6, 8, 10, 12], "acc_smem": [0, 1], "prefetch": [0, 16, 48, 50]}
 FIELDS = ("min_blocks", "acc_smem", "prefetch")
 
 
