@@ -123,3 +123,20 @@ def test_tuning_tables_round_trip():
     assert back["f2x"]["min_blocks"][1] == 6 and back["f2x"]["prefetch"][1] == 48
     assert back["f64"] == tables["f64"] and back["f32"] == tables["f32"]
     assert back["f2x"]["min_blocks"][0] == tables["f2x"]["min_blocks"][0]
+
+
+def test_tuner_candidate_build_is_a_complete_library(hho, tmp_path):
+    """A tuner candidate (stage.cu rebuilt against a changed tuning table and
+    linked with the in-tree objects) loads and exports every entry point of
+    include/hho.h."""
+    import ctypes
+    from paper_2505_15771_gb300 import build, tune
+    text = open(tune.HEADER).read()
+    t = tune.with_entry(tune.read_tables(text), "f2x", 2, {"min_blocks": 6, "acc_smem": 0, "prefetch": 48})
+    path = build.build_stage_variant(tune.write_tables(text, t), str(tmp_path))
+    src = open(ROOT + "/include/hho.h").read()
+    declared = sorted(set(re.findall(r"\b(hho_[a-z_0-9]+)\s*\(", src)))
+    lib = ctypes.CDLL(path)
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert "TUNED_F2X = {{8, 6, 5}, {0, 0, 0}, {0, 48, 0}}" in open(tmp_path / "csrc" / "stage_tuning.h").read()
