@@ -185,10 +185,11 @@ def replica_reduce(ms_local, units_local, world, dist=None, device=None):
 
 
 def stage_source_sha():
-    """sha256 of the stage kernel sources (stage.cu, then f2x.cuh)."""
+    """sha256 of the stage kernel sources (stage.cu, f2x.cuh, then the tuning
+    table stage_tuning.h)."""
     import hashlib
     h = hashlib.sha256()
-    for f in ("stage.cu", "f2x.cuh"):
+    for f in ("stage.cu", "f2x.cuh", "stage_tuning.h"):
         h.update(open(os.path.join(ROOT, "paper_2505_15771_gb300", "csrc", f), "rb").read())
     return h.hexdigest()
 
