@@ -22,7 +22,7 @@ directly from the defining integrals:
   on interface faces;
 * source vectors as load vectors (f, q)_T and (f^s, w)_T.
 
-Readings of the paper taken here (each listed in the design doc):
+Readings of the paper taken here:
 
 * Signs of the dual variables: the weak form (Eq. HHO1/HHO2) is used, i.e.
   d/dt m = g(p) and d/dt s = C g_sym(v).  The printed block matrix carries the

@@ -7,8 +7,8 @@ oracle and the GPU library consume.
 
 Workload shapes follow the paper's academic bilayer (Sec. 5.2: fluid over
 solid, flat interface) and its basin case (Sec. 5.3: water over a solid with a
-sedimentary basin); the exact sizes are the synthetic stand-ins documented in
-the design doc, because the paper's meshes, gmsh files and SEM3D traces are not
+sedimentary basin); the sizes are synthetic stand-ins with the paper's
+shapes, because the paper's meshes, gmsh files and SEM3D traces are not
 available.
 """
 from __future__ import annotations

@@ -1,6 +1,6 @@
 """GPU parity: the CUDA stage path (through the C ABI) against the CPU oracle.
 
-Bar (the benchmark spec): relative L2 <= 1e-12 in FP64 over all cell DOFs in the
+Bar: relative L2 <= 1e-12 in FP64 over all cell DOFs in the
 canonical layout, and on receiver traces.  Each test states its tolerance.
 """
 import json
