@@ -54,13 +54,22 @@ __global__ void multidot_kernel(const double* __restrict__ V, int64_t stride, in
     }
 }
 
-// out[l] = sum over blocks of partial[b * nv + l], blocks in order.
+// out[l] = sum over blocks of partial[b * nv + l]: block l; thread t adds
+// b = t, t + 256, ... in increasing order, then a fixed tree over the
+// threads.  (A single dependent chain over the 608 partials took about
+// 50 us a call on GB300, whose FP64 add latency is long.)
 __global__ void sum_partials_kernel(const double* __restrict__ partial, int nb, int nv, double* __restrict__ out) {
-    const int l = blockIdx.x * blockDim.x + threadIdx.x;
-    if (l >= nv) return;
+    __shared__ double sh[RED_THREADS];
+    const int l = blockIdx.x;
     double s = 0.0;
-    for (int b = 0; b < nb; ++b) s += partial[(size_t)b * nv + l];
-    out[l] = s;
+    for (int b = threadIdx.x; b < nb; b += RED_THREADS) s += partial[(size_t)b * nv + l];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = RED_THREADS / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[l] = sh[0];
 }
 
 // y = alpha y + beta sum_l coef[l] V_l  (coef in device memory; y may be
@@ -218,7 +227,7 @@ void apply_op(hho_ops* ops, const double* v, double* out, double* tr, double a_d
 // dst[l] = V_l . w for l < nv, on the device (no synchronisation)
 void dots_dev(const SdirkWork& W, const double* V, int nv, const double* w, double* dst, cudaStream_t st) {
     multidot_kernel<<<RED_BLOCKS, RED_THREADS, 0, st>>>(V, W.n, nv, w, W.n, W.partial);
-    sum_partials_kernel<<<1, 64, 0, st>>>(W.partial, RED_BLOCKS, nv, dst);
+    sum_partials_kernel<<<nv, RED_THREADS, 0, st>>>(W.partial, RED_BLOCKS, nv, dst);
 }
 
 // the same, copied to the host (synchronises)
