@@ -34,22 +34,30 @@ constexpr int RED_THREADS = 256;
 constexpr int MAX_RESTART = 64;
 
 // partial[b * nv + l] = block b's share of sum_i V_l[i] w[i], l < nv
-// (V_l = V + l * stride); grid-stride order and a fixed tree reduction.
+// (V_l = V + l * stride).  Four vectors per pass over i (independent FP64
+// chains), then one fixed tree over the block for the four sums.
+constexpr int MD_W = 4;
 __global__ void multidot_kernel(const double* __restrict__ V, int64_t stride, int nv, const double* __restrict__ w,
                                 int64_t n, double* __restrict__ partial) {
-    __shared__ double sh[RED_THREADS];
-    for (int l = 0; l < nv; ++l) {
-        const double* v = V + (size_t)l * stride;
-        double acc = 0.0;
-        for (int64_t i = blockIdx.x * (int64_t)RED_THREADS + threadIdx.x; i < n; i += (int64_t)gridDim.x * RED_THREADS)
-            acc = fma(v[i], w[i], acc);
-        sh[threadIdx.x] = acc;
+    __shared__ double sh[MD_W][RED_THREADS];
+    for (int l0 = 0; l0 < nv; l0 += MD_W) {
+        const int nl = min(MD_W, nv - l0);
+        double acc[MD_W] = {0.0, 0.0, 0.0, 0.0};
+        for (int64_t i = blockIdx.x * (int64_t)RED_THREADS + threadIdx.x; i < n; i += (int64_t)gridDim.x * RED_THREADS) {
+            const double wi = w[i];
+#pragma unroll
+            for (int l = 0; l < MD_W; ++l)
+                if (l < nl) acc[l] = fma(V[(size_t)(l0 + l) * stride + i], wi, acc[l]);
+        }
+#pragma unroll
+        for (int l = 0; l < MD_W; ++l) sh[l][threadIdx.x] = acc[l];
         __syncthreads();
         for (int o = RED_THREADS / 2; o > 0; o >>= 1) {
-            if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+            if ((int)threadIdx.x < o)
+                for (int l = 0; l < nl; ++l) sh[l][threadIdx.x] += sh[l][threadIdx.x + o];
             __syncthreads();
         }
-        if (threadIdx.x == 0) partial[(size_t)blockIdx.x * nv + l] = sh[0];
+        if ((int)threadIdx.x < nl) partial[(size_t)blockIdx.x * nv + l0 + threadIdx.x] = sh[threadIdx.x][0];
         __syncthreads();
     }
 }
