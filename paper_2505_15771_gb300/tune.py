@@ -126,8 +126,16 @@ def measure(lib, arith, k, workload, steps, warmup):
 
 # ---- search ----------------------------------------------------------------------------
 
-def tune(arith, k, workload, steps=20, warmup=3, passes=1, jobs=4, log=print):
-    base_text = open(HEADER).read()
+def tune(arith, k, workload, steps=20, warmup=3, passes=1, jobs=4, log=print, header_text=None, build_fn=None,
+         measure_fn=None):
+    """Coordinate descent over AXES from the table's current (arith, k)
+    entry.  Returns (best entry, {(min_blocks, acc_smem, prefetch): rate},
+    tables).  build_fn(header_text, out_dir) -> library path and
+    measure_fn(library, arith, k, workload, steps, warmup) -> rate default to
+    a candidate build and a timing in a fresh process."""
+    base_text = header_text if header_text is not None else open(HEADER).read()
+    build_fn = build_fn or B.build_stage_variant
+    measure_fn = measure_fn or measure
     tables = read_tables(base_text)
     best = {f: tables[arith][f][k - 1] for f in FIELDS}
     results = {}
@@ -135,7 +143,7 @@ def tune(arith, k, workload, steps=20, warmup=3, passes=1, jobs=4, log=print):
     with tempfile.TemporaryDirectory(prefix="hho_tune_") as tmp:
         def build(entry):
             d = os.path.join(tmp, "mb%d_acc%d_pf%d" % key(entry))
-            return B.build_stage_variant(write_tables(base_text, with_entry(tables, arith, k, entry)), d)
+            return build_fn(write_tables(base_text, with_entry(tables, arith, k, entry)), d)
 
         for _ in range(passes):
             for axis in FIELDS:
@@ -144,7 +152,7 @@ def tune(arith, k, workload, steps=20, warmup=3, passes=1, jobs=4, log=print):
                 with concurrent.futures.ThreadPoolExecutor(max_workers=jobs) as ex:
                     libs = list(ex.map(build, cands))
                 for c, lib in zip(cands, libs):
-                    results[key(c)] = measure(lib, arith, k, workload, steps, warmup)
+                    results[key(c)] = measure_fn(lib, arith, k, workload, steps, warmup)
                     log("  %-40s %.4e" % ("min_blocks=%d acc_smem=%d prefetch=%d" % key(c), results[key(c)]))
                 best = max((dict(zip(FIELDS, kk)) for kk in results), key=lambda e: results[key(e)])
     return best, results, tables

@@ -140,3 +140,52 @@ def test_tuner_candidate_build_is_a_complete_library(hho, tmp_path):
     for name in declared:
         assert hasattr(lib, name), name
     assert "TUNED_F2X = {{8, 6, 5}, {0, 0, 0}, {0, 48, 0}}" in open(tmp_path / "csrc" / "stage_tuning.h").read()
+
+
+def test_tuner_coordinate_descent_on_a_synthetic_landscape():
+    """The tuner's search, with the build and the timing replaced by a
+    synthetic rate surface: each candidate build sees the header with only
+    the tuned entry changed, one pass reaches the optimum of a separable
+    surface, and on a coupled one a second pass moves past the first pass's
+    point, without timing any candidate twice."""
+    from paper_2505_15771_gb300 import tune
+    text = open(tune.HEADER).read()
+    tables = tune.read_tables(text)
+    seen = {}
+
+    def build(header, out_dir):
+        t = tune.read_tables(header)
+        assert t["f64"] == tables["f64"] and t["f32"] == tables["f32"]
+        e = (t["f2x"]["min_blocks"][1], t["f2x"]["acc_smem"][1], t["f2x"]["prefetch"][1])
+        assert t["f2x"]["min_blocks"][0] == tables["f2x"]["min_blocks"][0]
+        return e
+
+    def separable(e, *_):
+        seen[e] = seen.get(e, 0) + 1
+        mb, acc, pf = e
+        return 100.0 - (mb - 6) ** 2 + 3.0 * acc - abs(pf - 48) / 16.0
+
+    best, res, _ = tune.tune("f2x", 2, "bilayer", log=lambda *a: None, header_text=text, build_fn=build,
+                             measure_fn=separable)
+    assert (best["min_blocks"], best["acc_smem"], best["prefetch"]) == (6, 1, 48)
+    assert all(v == 1 for v in seen.values())
+
+    # coupled: the best block count moves from 8 to 5 once the accumulators
+    # are in shared memory, which only the second pass can see
+    seen.clear()
+
+    def coupled(e, *_):
+        seen[e] = seen.get(e, 0) + 1
+        mb, acc, pf = e
+        return 50.0 - abs(mb - (5 if acc else 8)) + 4.0 * acc + (1.0 if pf == 16 else 0.0)
+
+    start = tune.write_tables(text, tune.with_entry(tables, "f2x", 2, {"min_blocks": 8, "acc_smem": 0,
+                                                                        "prefetch": 0}))
+    b1, _, _ = tune.tune("f2x", 2, "bilayer", log=lambda *a: None, header_text=start, build_fn=build,
+                         measure_fn=coupled)
+    assert (b1["min_blocks"], b1["acc_smem"], b1["prefetch"]) == (8, 1, 16)
+    seen.clear()
+    b2, res, _ = tune.tune("f2x", 2, "bilayer", passes=2, log=lambda *a: None, header_text=start, build_fn=build,
+                           measure_fn=coupled)
+    assert (b2["min_blocks"], b2["acc_smem"], b2["prefetch"]) == (5, 1, 16)
+    assert all(v == 1 for v in seen.values()) and len(seen) == len(res)
