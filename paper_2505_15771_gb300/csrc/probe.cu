@@ -1,5 +1,6 @@
-// FP64 FMA throughput probe: the denominator of the FP64 (ALU) roofline.
-// Eight independent FMA chains per thread, 8 blocks of 256 threads per SM.
+// FMA throughput probes: the denominators of the ALU rooflines (FP64 for the
+// FP64 stage kernels; FP32 for the double-float and FP32 ones).  Eight
+// independent FMA chains per thread, 8 blocks of 256 threads per SM.
 #include <cuda_runtime.h>
 
 __global__ void dfma_probe_kernel(double* out, int iters, double a, double b) {
@@ -28,6 +29,45 @@ extern "C" int hho_probe_dfma_rate(int iters, int reps, double* fma_per_s) {
     for (int r = 0; r < reps; ++r) {
         cudaEventRecord(e0);
         dfma_probe_kernel<<<blocks, threads>>>(out, iters, 1.0000001, 1e-9);
+        cudaEventRecord(e1);
+        if (cudaEventSynchronize(e1) != cudaSuccess) { rc = 1; break; }
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        const double rate = (double)blocks * threads * iters * 8 / (ms * 1e-3);
+        if (rate > best) best = rate;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(out);
+    *fma_per_s = best;
+    return rc;
+}
+
+__global__ void ffma_probe_kernel(float* out, int iters, float a, float b) {
+    float x0 = threadIdx.x, x1 = x0 + 1, x2 = x0 + 2, x3 = x0 + 3, x4 = x0 + 4, x5 = x0 + 5, x6 = x0 + 6, x7 = x0 + 7;
+    for (int i = 0; i < iters; ++i) {
+        x0 = fmaf(x0, a, b); x1 = fmaf(x1, a, b); x2 = fmaf(x2, a, b); x3 = fmaf(x3, a, b);
+        x4 = fmaf(x4, a, b); x5 = fmaf(x5, a, b); x6 = fmaf(x6, a, b); x7 = fmaf(x7, a, b);
+    }
+    out[blockIdx.x * blockDim.x + threadIdx.x] = x0 + x1 + x2 + x3 + x4 + x5 + x6 + x7;
+}
+
+// The same for FP32 FMAs: best rate in FP32 FMA lane-operations per second.
+extern "C" int hho_probe_ffma_rate(int iters, int reps, double* fma_per_s) {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 1;
+    const int blocks = sms * 8, threads = 256;
+    float* out = nullptr;
+    if (cudaMalloc(&out, sizeof(float) * blocks * threads) != cudaSuccess) return 1;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    double best = 0.0;
+    int rc = 0;
+    for (int r = 0; r < reps; ++r) {
+        cudaEventRecord(e0);
+        ffma_probe_kernel<<<blocks, threads>>>(out, iters, 1.0000001f, 1e-9f);
         cudaEventRecord(e1);
         if (cudaEventSynchronize(e1) != cudaSuccess) { rc = 1; break; }
         float ms = 0.0f;

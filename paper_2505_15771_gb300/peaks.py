@@ -1,0 +1,29 @@
+"""Measured ALU ceilings of the GPU: FP64 and FP32 FMA throughput from the
+probes in libhho_probe.so (eight independent FMA chains per thread, eight
+256-thread blocks per SM, best of several runs), printed as FMA lane-ops/s
+and TFLOP/s (FMA = 2 flops).
+
+    python -m paper_2505_15771_gb300.peaks
+"""
+import ctypes
+import json
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def rates(iters=4000, reps=5):
+    lib = ctypes.CDLL(os.path.join(_HERE, "libhho_probe.so"))
+    out = {}
+    for name, fn, it in (("fp64", "hho_probe_dfma_rate", iters), ("fp32", "hho_probe_ffma_rate", 16 * iters)):
+        f = getattr(lib, fn)
+        f.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
+        r = ctypes.c_double()
+        if f(it, reps, ctypes.byref(r)) != 0:
+            raise RuntimeError("%s failed" % fn)
+        out[name] = {"fma_lane_ops_per_s": r.value, "tflops": 2.0 * r.value / 1e12}
+    return out
+
+
+if __name__ == "__main__":
+    print(json.dumps(rates(), indent=1))
