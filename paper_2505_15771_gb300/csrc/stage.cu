@@ -25,8 +25,11 @@
 // (Eq. ERK_compact with a_{s+1,j} = b_j); and publishes w, omega of the new
 // stage value for the next stage (double-buffered traces).
 //
-// Arithmetic is FP64 for the single-shot path; the batched path runs the same
-// kernels in FP64 or FP32 (shots on blockIdx.y).
+// The kernels are templated on the arithmetic: FP64; double-float pairs on
+// the FP32 pipes (f2x.cuh, FP64-class accuracy, the single-shot default of
+// the benchmark); FP32 for batched shots (shots on blockIdx.y).  Their
+// launch parameters (resident blocks, accumulator placement, prefetch hints)
+// come from the table in stage_tuning.h.
 #include <cuda_runtime.h>
 
 #include <algorithm>
