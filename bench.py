@@ -67,6 +67,10 @@ def parse():
     ap.add_argument("--adjoint-steps", type=int, default=800, help="steps of the adjoint (NEXT-2) measurement")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-sdirk", action="store_true")
+    ap.add_argument("--traffic-record", nargs=2, metavar=("CSV_K2", "CSV_K3"), default=None,
+                    help="write profiles/stage_kernel_traffic.json from two ncu CSV logs (dram bytes of the stage "
+                         "launches on the 768x384 k=2 and 640x320 k=3 bilayers; commands in "
+                         "profiles/stage_kernel_traffic_bilayer.md) and exit; needs no GPU")
     return ap.parse_args()
 
 
@@ -208,6 +212,52 @@ def measured_traffic(k, cell_dofs, arith="f64"):
     if not entry:
         return None
     return entry["dram_bytes_per_launch_per_cell_dof"] * cell_dofs
+
+
+def write_traffic_record(csv_k2, csv_k3):
+    """profiles/stage_kernel_traffic.json from ncu --csv logs of
+    dram__bytes_read.sum, dram__bytes_write.sum and gpu__time_duration.sum:
+    per arithmetic and k, the mean over the captured ERK stage launches
+    (stage_kernel<T, k, 1>) divided by the captured case's cell DOFs, keyed
+    by the current stage sources."""
+    import csv
+    import collections
+    scale = {"byte": 1.0, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "ns": 1e-3, "us": 1.0, "usecond": 1.0,
+             "msecond": 1e3, "ms": 1e3}
+    out = {}
+    # captured cases: 768x384 at k = 2 and 640x320 at k = 3, half fluid (3n) and half solid (5n) cells
+    for path, k, case in ((csv_k2, 2, (768, 384)), (csv_k3, 3, (640, 320))):
+        n = (k + 1) * (k + 2) // 2
+        dofs = case[0] * case[1] * 0.5 * (3 + 5) * n
+        rows = [r for r in csv.reader(open(path)) if len(r) > 10]
+        hdr, data = rows[0], rows[1:]
+        ki, mi, vi, ui, ii = (hdr.index(c) for c in ("Kernel Name", "Metric Name", "Metric Value", "Metric Unit", "ID"))
+        per = collections.defaultdict(dict)
+        for r in data:
+            per[(r[ii], r[ki])][r[mi]] = float(r[vi].replace(",", "")) * scale.get(r[ui], 1.0)
+        by_kernel = collections.defaultdict(list)
+        for (_, name), m in per.items():
+            if (", %d, 1>" % k) in name:
+                by_kernel[name].append(m)
+        for name, ms in by_kernel.items():
+            b = [m["dram__bytes_read.sum"] + m["dram__bytes_write.sum"] for m in ms]
+            t = [m["gpu__time_duration.sum"] for m in ms]
+            key = ("k%d" % k) if "double" in name else ("f32x2_k%d" % k)
+            out[key] = {"captured": "bilayer %dx%d, %d cell DOFs, %d stage launches" % (case[0], case[1], dofs,
+                                                                                       len(ms)),
+                        "dram_bytes_per_launch_mean": sum(b) / len(b),
+                        "dram_bytes_per_launch_per_cell_dof": sum(b) / len(b) / dofs,
+                        "kernel_time_us_mean_under_ncu": sum(t) / len(t)}
+    rec = {"stage_sources_sha256": stage_source_sha(),
+           "note": "ncu dram__bytes_read.sum + dram__bytes_write.sum of the ERK stage launches (stage_kernel<T,k,1>), "
+                   "mean over the captured launches, divided by the cell DOFs of the captured case; bench.py scales "
+                   "by the workload's cell DOFs (one thread per cell, class-sorted SoA: traffic grows in "
+                   "proportion). Keys: k<k> FP64 kernel, f32x2_k<k> double-float kernel. Written by bench.py "
+                   "--traffic-record; commands in profiles/stage_kernel_traffic_bilayer.md."}
+    rec.update(out)
+    with open(os.path.join(ROOT, "profiles", "stage_kernel_traffic.json"), "w") as f:
+        json.dump(rec, f, indent=1)
+    return rec
 
 
 def fp64_fma_rate():
@@ -447,6 +497,10 @@ def measure_sdirk(a, torch, hho, solver):
 
 def main():
     a = parse()
+    if a.traffic_record:
+        rec = write_traffic_record(*a.traffic_record)
+        print(json.dumps({k: v["dram_bytes_per_launch_per_cell_dof"] for k, v in rec.items() if isinstance(v, dict)}))
+        return
     if a.batch_nx is None:
         a.batch_nx = 2860 if a.batch_workload == "c5" else 1360
     if a.batch_ny is None:
