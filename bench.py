@@ -214,7 +214,7 @@ def measured_traffic(k, cell_dofs, arith="f64"):
     return entry["dram_bytes_per_launch_per_cell_dof"] * cell_dofs
 
 
-def write_traffic_record(csv_k2, csv_k3):
+def write_traffic_record(csv_k2, csv_k3, out_path=None):
     """profiles/stage_kernel_traffic.json from ncu --csv logs of
     dram__bytes_read.sum, dram__bytes_write.sum and gpu__time_duration.sum:
     per arithmetic and k, the mean over the captured ERK stage launches
@@ -255,7 +255,7 @@ def write_traffic_record(csv_k2, csv_k3):
                    "proportion). Keys: k<k> FP64 kernel, f32x2_k<k> double-float kernel. Written by bench.py "
                    "--traffic-record; commands in profiles/stage_kernel_traffic_bilayer.md."}
     rec.update(out)
-    with open(os.path.join(ROOT, "profiles", "stage_kernel_traffic.json"), "w") as f:
+    with open(out_path or os.path.join(ROOT, "profiles", "stage_kernel_traffic.json"), "w") as f:
         json.dump(rec, f, indent=1)
     return rec
 

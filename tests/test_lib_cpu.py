@@ -189,3 +189,47 @@ def test_tuner_coordinate_descent_on_a_synthetic_landscape():
                            measure_fn=coupled)
     assert (b2["min_blocks"], b2["acc_smem"], b2["prefetch"]) == (5, 1, 16)
     assert all(v == 1 for v in seen.values()) and len(seen) == len(res)
+
+
+def _ncu_csv(path, launches):
+    """A minimal ncu --csv log: one row per (launch, metric)."""
+    import csv
+    hdr = ["ID", "Process ID", "Process Name", "Host Name", "Kernel Name", "Context", "Stream", "Block Size",
+           "Grid Size", "Device", "CC", "Section Name", "Metric Name", "Metric Unit", "Metric Value"]
+    with open(path, "w", newline="") as f:
+        w = csv.writer(f)
+        w.writerow(hdr)
+        for i, (name, rd, wr, us) in enumerate(launches):
+            for metric, unit, val in (("dram__bytes_read.sum", "Mbyte", rd), ("dram__bytes_write.sum", "Mbyte", wr),
+                                      ("gpu__time_duration.sum", "usecond", us)):
+                w.writerow([str(i), "1", "python", "h", name, "1", "7", "(128, 1, 1)", "(1, 1, 1)", "0", "10.3",
+                            "Command line profiler metrics", metric, unit, "{:,}".format(val)])
+
+
+def test_traffic_record_from_ncu_logs(tmp_path):
+    """bench.py --traffic-record: per arithmetic and k, the mean DRAM bytes
+    of the ERK stage launches (mode 1 only) over the captured case's cell
+    DOFs, keyed by the current stage sources; bench.py scales it back."""
+    import bench
+    k2 = [("void <unnamed>::stage_kernel<f2x, 2, 1>(StageArgsT<T1>)", 200.0, 150.0, 130.0),
+          ("void <unnamed>::stage_kernel<f2x, 2, 1>(StageArgsT<T1>)", 240.0, 160.0, 140.0),
+          ("void <unnamed>::stage_kernel<f2x, 2, 0>(StageArgsT<T1>)", 999.0, 999.0, 60.0),
+          ("void <unnamed>::stage_kernel<double, 2, 1>(StageArgsT<T1>)", 300.0, 170.0, 190.0)]
+    k3 = [("void <unnamed>::stage_kernel<f2x, 3, 1>(StageArgsT<T1>)", 300.0, 180.0, 250.0),
+          ("void <unnamed>::stage_kernel<double, 3, 1>(StageArgsT<T1>)", 320.0, 190.0, 290.0)]
+    _ncu_csv(tmp_path / "k2.csv", k2)
+    _ncu_csv(tmp_path / "k3.csv", k3)
+    out = tmp_path / "traffic.json"
+    rec = bench.write_traffic_record(str(tmp_path / "k2.csv"), str(tmp_path / "k3.csv"), str(out))
+    dofs2 = 768 * 384 * 0.5 * 8 * 6
+    dofs3 = 640 * 320 * 0.5 * 8 * 10
+    assert rec["stage_sources_sha256"] == bench.stage_source_sha()
+    assert rec["f32x2_k2"]["dram_bytes_per_launch_mean"] == pytest.approx(375e6)   # (350 + 400) / 2 MB
+    assert rec["f32x2_k2"]["dram_bytes_per_launch_per_cell_dof"] == pytest.approx(375e6 / dofs2)
+    assert rec["f32x2_k2"]["kernel_time_us_mean_under_ncu"] == pytest.approx(135.0)
+    assert rec["k2"]["dram_bytes_per_launch_mean"] == pytest.approx(470e6)
+    assert rec["f32x2_k3"]["dram_bytes_per_launch_per_cell_dof"] == pytest.approx(480e6 / dofs3)
+    assert rec["k3"]["dram_bytes_per_launch_mean"] == pytest.approx(510e6)
+    assert "20 stage launches" not in rec["f32x2_k2"]["captured"] and "2 stage launches" in rec["f32x2_k2"]["captured"]
+    import json
+    assert json.load(open(out)) == rec
