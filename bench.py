@@ -11,10 +11,13 @@ resident in HBM; `e2e` is the same metric through hho_erk_run_host with the
 state in pinned host memory (every step reads it from and writes it back to
 host memory inside the timed region).
 
-Roofline: the stage kernel is bound by FP64 arithmetic on this part (FP64
-FMA rate measured live by the probe kernel), reported as "bound": "alu"
-with FP64 lane-ops from the library's cost model; the HBM view (algorithmic
-bytes / time against MEASURED_PEAKS.json) is reported next to it.
+Headline: the FP64-instruction stage path, started from a seeded random
+state.  Its roofline is the FP64 pipe on this part (FP64 multiply-add rate
+measured live by the probe kernel), reported as "bound": "alu" with FP64
+lane-ops from the library's cost model; the HBM view (algorithmic bytes /
+time against MEASURED_PEAKS.json) is reported beside it.  The double-float
+path (FP64-class accuracy on the FP32 pipes, bound by HBM) is timed on the
+same workload and state in `alternative`, with its own rooflines and e2e.
 
 --impl reference times the CPU oracle (plain FP64 numpy/scipy) on a bounded
 sample of the same workload on the host cores.
@@ -48,9 +51,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--k", type=int, default=2)
-    ap.add_argument("--arith", default="f32x2", choices=["f64", "f32x2"],
-                    help="arithmetic of the headline stage path: FP64 instructions, or double-float pairs "
-                         "(FP64-class accuracy on the FP32 pipes)")
+    ap.add_argument("--arith", default="f64", choices=["f64", "f32x2"],
+                    help="arithmetic of the headline stage path: FP64 instructions (default), or double-float "
+                         "pairs (FP64-class accuracy on the FP32 pipes); the other one is timed beside it")
     ap.add_argument("--stages", type=int, default=4)
     ap.add_argument("--nx", type=int, default=1024)
     ap.add_argument("--ny", type=int, default=512)
@@ -67,10 +70,10 @@ def parse():
     ap.add_argument("--adjoint-steps", type=int, default=800, help="steps of the adjoint (NEXT-2) measurement")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-sdirk", action="store_true")
-    ap.add_argument("--traffic-record", nargs=2, metavar=("CSV_K2", "CSV_K3"), default=None,
-                    help="write profiles/stage_kernel_traffic.json from two ncu CSV logs (dram bytes of the stage "
-                         "launches on the 768x384 k=2 and 640x320 k=3 bilayers; commands in "
-                         "profiles/stage_kernel_traffic_bilayer.md) and exit; needs no GPU")
+    ap.add_argument("--traffic-record", nargs="+", metavar="CSV NX NY K", default=None,
+                    help="write profiles/stage_kernel_traffic.json from ncu CSV logs (dram bytes of the stage "
+                         "launches on the NX x NY bilayer at degree K), given as groups of four: CSV NX NY K; "
+                         "needs no GPU")
     return ap.parse_args()
 
 
@@ -214,37 +217,51 @@ def measured_traffic(k, cell_dofs, arith="f64"):
     return entry["dram_bytes_per_launch_per_cell_dof"] * cell_dofs
 
 
-def write_traffic_record(csv_k2, csv_k3, out_path=None):
+TRAFFIC_KEYS = {"double": "k%d", "f2x": "f32x2_k%d", "float": "f32_k%d"}
+
+
+def bilayer_cell_dofs(nx, ny, k):
+    """Cell DOFs of the nx x ny bilayer (3n per fluid cell, 5n per solid cell)."""
+    import synth
+    md = synth.bilayer_c2(nx=nx, ny=ny, k=k)["mesh"]
+    n = (k + 1) * (k + 2) // 2
+    n_solid = int(np.count_nonzero(md.cell_domain == 1))
+    return (md.n_cells - n_solid) * 3 * n + n_solid * 5 * n
+
+
+def write_traffic_record(captures, out_path=None):
     """profiles/stage_kernel_traffic.json from ncu --csv logs of
-    dram__bytes_read.sum, dram__bytes_write.sum and gpu__time_duration.sum:
-    per arithmetic and k, the mean over the captured ERK stage launches
-    (stage_kernel<T, k, 1>) divided by the captured case's cell DOFs, keyed
-    by the current stage sources."""
+    dram__bytes_read.sum, dram__bytes_write.sum and gpu__time_duration.sum.
+    ``captures``: (csv path, nx, ny, k) of each capture on the nx x ny
+    bilayer.  Per arithmetic (the kernel's template type: double -> k<k>,
+    f2x -> f32x2_k<k>, float -> f32_k<k>) and k, the mean over the captured
+    ERK stage launches (stage_kernel<T, k, 1>) divided by the captured case's
+    cell DOFs, keyed by the current stage sources."""
     import csv
     import collections
+    import re
     scale = {"byte": 1.0, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "ns": 1e-3, "us": 1.0, "usecond": 1.0,
              "msecond": 1e3, "ms": 1e3}
+    pat = re.compile(r"stage_kernel<(\w+), (\d), 1>")
     out = {}
-    # captured cases: 768x384 at k = 2 and 640x320 at k = 3, half fluid (3n) and half solid (5n) cells
-    for path, k, case in ((csv_k2, 2, (768, 384)), (csv_k3, 3, (640, 320))):
-        n = (k + 1) * (k + 2) // 2
-        dofs = case[0] * case[1] * 0.5 * (3 + 5) * n
+    for path, nx, ny, k in captures:
+        nx, ny, k = int(nx), int(ny), int(k)
+        dofs = bilayer_cell_dofs(nx, ny, k)
         rows = [r for r in csv.reader(open(path)) if len(r) > 10]
         hdr, data = rows[0], rows[1:]
         ki, mi, vi, ui, ii = (hdr.index(c) for c in ("Kernel Name", "Metric Name", "Metric Value", "Metric Unit", "ID"))
         per = collections.defaultdict(dict)
         for r in data:
             per[(r[ii], r[ki])][r[mi]] = float(r[vi].replace(",", "")) * scale.get(r[ui], 1.0)
-        by_kernel = collections.defaultdict(list)
+        by_key = collections.defaultdict(list)
         for (_, name), m in per.items():
-            if (", %d, 1>" % k) in name:
-                by_kernel[name].append(m)
-        for name, ms in by_kernel.items():
+            g = pat.search(name)
+            if g and int(g.group(2)) == k and g.group(1) in TRAFFIC_KEYS:
+                by_key[TRAFFIC_KEYS[g.group(1)] % k].append(m)
+        for key, ms in by_key.items():
             b = [m["dram__bytes_read.sum"] + m["dram__bytes_write.sum"] for m in ms]
             t = [m["gpu__time_duration.sum"] for m in ms]
-            key = ("k%d" % k) if "double" in name else ("f32x2_k%d" % k)
-            out[key] = {"captured": "bilayer %dx%d, %d cell DOFs, %d stage launches" % (case[0], case[1], dofs,
-                                                                                       len(ms)),
+            out[key] = {"captured": "bilayer %dx%d, %d cell DOFs, %d stage launches" % (nx, ny, dofs, len(ms)),
                         "dram_bytes_per_launch_mean": sum(b) / len(b),
                         "dram_bytes_per_launch_per_cell_dof": sum(b) / len(b) / dofs,
                         "kernel_time_us_mean_under_ncu": sum(t) / len(t)}
@@ -252,8 +269,8 @@ def write_traffic_record(csv_k2, csv_k3, out_path=None):
            "note": "ncu dram__bytes_read.sum + dram__bytes_write.sum of the ERK stage launches (stage_kernel<T,k,1>), "
                    "mean over the captured launches, divided by the cell DOFs of the captured case; bench.py scales "
                    "by the workload's cell DOFs (one thread per cell, class-sorted SoA: traffic grows in "
-                   "proportion). Keys: k<k> FP64 kernel, f32x2_k<k> double-float kernel. Written by bench.py "
-                   "--traffic-record; commands in profiles/stage_kernel_traffic_bilayer.md."}
+                   "proportion). Keys: k<k> FP64 kernel, f32x2_k<k> double-float kernel, f32_k<k> FP32 kernel. "
+                   "Written by bench.py --traffic-record."}
     rec.update(out)
     with open(out_path or os.path.join(ROOT, "profiles", "stage_kernel_traffic.json"), "w") as f:
         json.dump(rec, f, indent=1)
@@ -495,10 +512,117 @@ def measure_sdirk(a, torch, hho, solver):
     return out
 
 
+def measure_arith(a, torch, hho, P, tab, dt, state, work, seis, stream, U0, arith, hbm_peak, peak_fma, world,
+                  clocks=None, dist=None):
+    """One arithmetic of the stage path on the headline workload: W warm-up
+    steps, then exactly K timed steps (CUDA events on the launching stream),
+    starting from the seeded random state U0 (packed on the device, so the
+    rate is measured on non-zero data).  Returns the timing, the stage
+    kernel's per-launch time (library profiler: events around every stage
+    launch on the same stream) and its rooflines."""
+    P.set_arithmetic(arith)
+    ndof = P.layout.n_canonical
+    x0 = P.to_device(U0, stream)
+
+    def run(nsteps, t0):
+        hho.hho_erk_step_record(P.ops, tab, t0, dt, nsteps, state.data_ptr(), work.data_ptr(), seis.data_ptr(),
+                                stream.cuda_stream)
+
+    state.copy_(x0)
+    run(max(a.warmup, 3), 0.0)          # warm-up (also the first touch of every buffer)
+    torch.cuda.synchronize()
+    e_warm = P.energy(state)
+    hho.hho_profile_enable(P.ops, True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    if clocks is not None:
+        clocks.start()
+        time.sleep(0.3)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    run(a.steps, a.warmup * dt)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop() if clocks is not None else None
+    if world > 1:
+        dist.barrier()
+    ms = ev0.elapsed_time(ev1)
+    stage_ms, n_launch = hho.hho_profile_read(P.ops)
+    hho.hho_profile_enable(P.ops, False)
+    e_end = P.energy(state)
+    fp64_ops, bytes_min, bytes_kernel = hho.hho_stage_cost(P.ops, tab)
+    avg_launch_s = stage_ms * 1e-3 / max(n_launch, 1)
+    ops_per_launch = fp64_ops / a.stages
+    name = "f64" if arith == hho.HHO_F64 else "f32x2"
+    kern = "stage_kernel<%s,%d,1>" % ("double" if arith == hho.HHO_F64 else "f2x", a.k)
+    hbm = {"bound": "hbm", "achieved": bytes_min / a.stages / avg_launch_s / 1e9, "peak": hbm_peak, "unit": "GB/s",
+           "frac": bytes_min / a.stages / avg_launch_s / 1e9 / hbm_peak,
+           "algorithmic_bytes_per_launch": bytes_min / a.stages,
+           "traffic": measured_traffic(a.k, ndof, name), "kernel": kern, "avg_launch_ms": avg_launch_s * 1e3,
+           "launches_timed": n_launch, "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured copy)"}
+    alu = {"bound": "alu", "achieved": ops_per_launch / avg_launch_s / 1e12,
+           "peak": (peak_fma / 1e12) if peak_fma else None, "unit": "T FP64 lane-ops/s (multiply-add = 1)",
+           "frac": (ops_per_launch / avg_launch_s / peak_fma) if peak_fma else None,
+           "fp64_lane_ops_per_launch": ops_per_launch, "kernel": kern, "avg_launch_ms": avg_launch_s * 1e3,
+           "launches_timed": n_launch, "peak_source": "live DFMA probe (libhho_probe.so), best of 3, same run"}
+    if arith == hho.HHO_F64:
+        # FP64 instructions: the FP64 pipe binds (about 13 lane-ops per cell
+        # DOF per stage against 32 bytes); HBM is the view beside it
+        roofline = dict(alu)
+        roofline["traffic"] = hbm["traffic"]
+        roofline["hbm_view"] = {k2: hbm[k2] for k2 in ("achieved", "peak", "unit", "frac",
+                                                        "algorithmic_bytes_per_launch", "peak_source")}
+    else:
+        # double-float: no FP64 instruction; the FP32 pipes have headroom, so
+        # the bound is HBM, with the FP64-equivalent lane-op rate as a view
+        roofline = dict(hbm)
+        roofline["alu_view"] = {k2: alu[k2] for k2 in ("achieved", "peak", "unit", "frac", "peak_source")}
+        roofline["alu_view"]["note"] = ("FP64-equivalent lane-ops of the cost model per second, against the FP64 "
+                                        "DFMA probe")
+    return {"arith": name, "ms": ms, "units": ndof * a.stages * a.steps, "clocks": clk, "roofline": roofline,
+            "energy_after_warmup": e_warm, "energy_after_timed": e_end}
+
+
+def measure_e2e(a, torch, hho, P, dt, stream, arith, world):
+    """End to end through hho_erk_run_host with the state in pinned host
+    memory: every step reads it from and writes it back to host memory
+    inside the timed region."""
+    P.set_arithmetic(arith)
+    ndof = P.layout.n_canonical
+    h = torch.zeros(ndof, dtype=torch.float64, pin_memory=True)
+    hn = h.numpy()
+    hn[:] = synth_random_state(ndof)
+    P.run_host(hn, a.stages, 0.0, dt, 1, stream)       # warm (allocates its buffers)
+    ne = max(3, min(a.steps, 20))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(ne):
+        P.run_host(hn, a.stages, i * dt, dt, 1, stream)
+    el = time.perf_counter() - t0
+    return {"value": world * ndof * a.stages * ne / el, "unit": UNIT, "h2d_bytes_per_step": 8 * ndof,
+            "d2h_bytes_per_step": 8 * ndof, "steps": ne, "arith": "f64" if arith == hho.HHO_F64 else "f32x2",
+            "path": "hho_erk_run_host on a pinned host buffer: the pack kernel reads the canonical state from "
+                    "host memory (NVLink-C2C), 1 ERK step, the unpack kernel writes it back to host memory, "
+                    "stream sync"}
+
+
+RANDOM_STATE_SEED = 11
+
+
+def synth_random_state(n):
+    import synth
+    return synth.random_state(n, RANDOM_STATE_SEED)
+
+
 def main():
     a = parse()
     if a.traffic_record:
-        rec = write_traffic_record(*a.traffic_record)
+        if len(a.traffic_record) % 4:
+            raise SystemExit("--traffic-record takes groups of four: CSV NX NY K")
+        t = a.traffic_record
+        rec = write_traffic_record([tuple(t[i:i + 4]) for i in range(0, len(t), 4)])
         print(json.dumps({k: v["dram_bytes_per_launch_per_cell_dof"] for k, v in rec.items() if isinstance(v, dict)}))
         return
     if a.batch_nx is None:
@@ -529,128 +653,42 @@ def main():
     P.set_sources([w["source"]], [(0.0, 1.0)], 10.0)
     P.set_receivers(w["receivers"])
     ARITH = {"f64": hho.HHO_F64, "f32x2": hho.HHO_F32X2}
-    P.set_arithmetic(ARITH[a.arith])
     tab = hho.hho_tableau_erk(a.stages)
     # CFL-limited dt (Eq. CFL): 0.9 x the ERK4 eigenvalue limit of the stage
     # operator on squares (c# dt / h = 0.233, 0.122, 0.082 for k = 1, 2, 3)
     dt = hho.hho_cfl_dt(P.ops, CFL_SQUARES_ERK4[a.k], 0.9)
     ndof = P.layout.n_canonical
+    U0 = synth_random_state(ndof)
     state = P.empty_state()
     work = P.work(tab)
     seis = torch.empty((max(a.steps, a.warmup, 3), len(w["receivers"]), 5), dtype=torch.float64, device=P.dev)
     stream = torch.cuda.current_stream()
-    sp = stream.cuda_stream
-
-    def run(nsteps, t0):
-        hho.hho_erk_step_record(P.ops, tab, t0, dt, nsteps, state.data_ptr(), work.data_ptr(), seis.data_ptr(), sp)
-
-    # warm-up (also the first-touch of every buffer)
-    run(max(a.warmup, 3), 0.0)
-    torch.cuda.synchronize()
-    e_warm = P.energy(state)
-
-    # timed region: exactly K steps
-    hho.hho_profile_enable(P.ops, True)
-    clocks = ClockSampler(local)
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    clocks.start()
-    time.sleep(0.3)
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    run(a.steps, a.warmup * dt)
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    clk = clocks.stop()
-    if world > 1:
-        dist.barrier()
-    ms = ev0.elapsed_time(ev1)
-    stage_ms, n_launch = hho.hho_profile_read(P.ops)
-    hho.hho_profile_enable(P.ops, False)
-    e_end = P.energy(state)
-    per_rank_units = ndof * a.stages * a.steps
-    ms, total_units = replica_reduce(ms, per_rank_units, world, dist, P.dev)
-    value = total_units / (ms * 1e-3)
-
-    # roofline of the stage kernel
-    fp64_ops, bytes_min, bytes_kernel = hho.hho_stage_cost(P.ops, tab)
-    avg_launch_s = stage_ms * 1e-3 / max(n_launch, 1)
-    ops_per_launch = fp64_ops / a.stages
     peak_fma = fp64_fma_rate()
     peaks = {}
     pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(pk):
         peaks = json.load(open(pk))
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
-    hbm_view = {"algorithmic_bytes_per_launch": bytes_min / a.stages,
-                "achieved_gbs": bytes_min / a.stages / avg_launch_s / 1e9,
-                "peak_gbs": hbm_peak, "frac": bytes_min / a.stages / avg_launch_s / 1e9 / hbm_peak,
-                "kernel_design_bytes_per_launch": bytes_kernel / a.stages,
-                "peak_source": "MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in peaks else "fallback"}
-    roofline = {
-        "bound": "alu",
-        "achieved": ops_per_launch / avg_launch_s / 1e12,
-        "peak": (peak_fma / 1e12) if peak_fma else None,
-        "unit": "T FP64 lane-ops/s (FMA = 1)",
-        "frac": (ops_per_launch / avg_launch_s / peak_fma) if peak_fma else None,
-        "traffic": measured_traffic(a.k, ndof),
-        "kernel": "stage_kernel<%d,1>" % a.k,
-        "avg_launch_ms": avg_launch_s * 1e3,
-        "launches_timed": n_launch,
-        "peak_source": "live DFMA probe (libhho_probe.so), best of 3",
-        "hbm_view": hbm_view,
-    }
-    if a.arith == "f32x2":
-        # double-float: no FP64 instruction in the stage kernel; the bound is
-        # HBM traffic (the FP64-equivalent lane-op rate is kept as a view)
-        alu_view = {k2: roofline[k2] for k2 in ("achieved", "peak", "unit", "frac", "peak_source")}
-        alu_view["note"] = "FP64-equivalent lane-ops of the cost model per second, against the FP64 DFMA probe"
-        roofline = {"bound": "hbm", "achieved": hbm_view["achieved_gbs"], "peak": hbm_peak, "unit": "GB/s",
-                    "frac": hbm_view["frac"], "traffic": measured_traffic(a.k, ndof, "f32x2"),
-                    "kernel": "stage_kernel<f2x,%d,1>" % a.k, "avg_launch_ms": avg_launch_s * 1e3,
-                    "launches_timed": n_launch, "peak_source": hbm_view["peak_source"],
-                    "algorithmic_bytes_per_launch": hbm_view["algorithmic_bytes_per_launch"],
-                    "alu_view": alu_view}
 
-    # the other arithmetic on the same workload, for comparison
+    head = measure_arith(a, torch, hho, P, tab, dt, state, work, seis, stream, U0, ARITH[a.arith], hbm_peak,
+                         peak_fma, world, ClockSampler(local), dist)
+    ms, total_units = replica_reduce(head["ms"], head["units"], world, dist, P.dev)
+    value = total_units / (ms * 1e-3)
+
+    # the other arithmetic on the same workload and initial state, with its own rooflines and e2e
     other_name = "f64" if a.arith == "f32x2" else "f32x2"
-    P.set_arithmetic(ARITH[other_name])
-    run(3, 0.0)
-    torch.cuda.synchronize()
-    hho.hho_profile_enable(P.ops, True)
-    o0 = torch.cuda.Event(enable_timing=True)
-    o1 = torch.cuda.Event(enable_timing=True)
-    o0.record(stream)
-    run(a.steps, 3 * dt)
-    o1.record(stream)
-    torch.cuda.synchronize()
-    o_stage_ms, o_n = hho.hho_profile_read(P.ops)
-    hho.hho_profile_enable(P.ops, False)
-    other_arith = {"arith": other_name, "value": ndof * a.stages * a.steps / (o0.elapsed_time(o1) * 1e-3),
-                   "unit": UNIT, "avg_launch_ms": o_stage_ms / max(o_n, 1),
-                   "hbm_frac": bytes_min / a.stages / (o_stage_ms * 1e-3 / max(o_n, 1)) / 1e9 / hbm_peak}
-    P.set_arithmetic(ARITH[a.arith])
-    state.zero_()
-
-    # end to end through the host-buffer entry point (pinned host state)
+    oth = measure_arith(a, torch, hho, P, tab, dt, state, work, seis, stream, U0, ARITH[other_name], hbm_peak,
+                        peak_fma, 1)
+    alternative = {"arith": other_name, "value": oth["units"] / (oth["ms"] * 1e-3), "unit": UNIT,
+                   "ms_per_step": oth["ms"] / a.steps, "roofline": oth["roofline"],
+                   "energy_after_timed": oth["energy_after_timed"],
+                   "note": ("double-float pairs on the FP32 pipes (about 48 significand bits, FP32 exponent range), "
+                            "same FP64-oracle parity bar" if other_name == "f32x2" else "FP64 instructions")}
     e2e = None
     if not a.no_e2e:
-        h = torch.zeros(ndof, dtype=torch.float64, pin_memory=True)
-        hn = h.numpy()
-        P.run_host(hn, a.stages, 0.0, dt, 1, stream)       # warm (allocates its buffers)
-        ne = max(3, min(a.steps, 20))
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for i in range(ne):
-            P.run_host(hn, a.stages, i * dt, dt, 1, stream)
-        el = time.perf_counter() - t0
-        e2e = {"value": world * ndof * a.stages * ne / el, "unit": UNIT, "h2d_bytes_per_step": 8 * ndof,
-               "d2h_bytes_per_step": 8 * ndof, "steps": ne,
-               "path": "hho_erk_run_host on a pinned host buffer: the pack kernel reads the canonical state from "
-                       "host memory (NVLink-C2C), 1 ERK step, the unpack kernel writes it back to host memory, "
-                       "stream sync"}
+        e2e = measure_e2e(a, torch, hho, P, dt, stream, ARITH[a.arith], world)
+        alternative["e2e"] = measure_e2e(a, torch, hho, P, dt, stream, ARITH[other_name], 1)
+    P.set_arithmetic(ARITH[a.arith])
 
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
@@ -677,19 +715,23 @@ def main():
         torch.cuda.empty_cache()
         adjoint = measure_adjoint(a, torch, hho)
 
-    # trace init + stages + receiver records (+ the state's conversion to and from pairs)
-    launches = 1 + a.stages * a.steps + a.steps + (2 if a.arith == "f32x2" else 0)
+    # stages + receiver records (+ the state's conversion to and from pairs)
+    launches = a.stages * a.steps + a.steps + 1 + (2 if a.arith == "f32x2" else 0)
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
                 "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": a.arith, "data": "synthetic",
                 "config": {"workload": workload_name(a), "cells": int(md.n_cells), "cell_dofs": int(ndof),
                            "k": a.k, "tableau": "erk%d" % a.stages, "dt": dt,
+                           "initial_state": "seeded standard-normal canonical state (seed %d)"
+                                            % RANDOM_STATE_SEED,
                            "l2": "inputs larger than L2 (state %.0f MB, work %.0f MB per GPU)" % (state_mb, work_mb),
                            "parallelism": "replicas" if world > 1 else "single GPU",
-                           "energy_after_warmup": e_warm, "energy_after_timed": e_end},
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
-                "other_arith": other_arith, "batched": batched, "adjoint": adjoint, "sdirk": sdirk, "small": small}
+                           "energy_after_warmup": head["energy_after_warmup"],
+                           "energy_after_timed": head["energy_after_timed"]},
+                "roofline": head["roofline"], "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "clocks": head["clocks"], "alternative": alternative, "batched": batched, "adjoint": adjoint,
+                "sdirk": sdirk, "small": small}
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()

@@ -443,11 +443,13 @@ int hho_profile_read(hho_ops* ops, double* ms_stage_total, int64_t* n_launches);
  * HHO_ENERGY_STATIC_MAX_CELLS padded cell slots (n_fluid_pad + n_solid_pad);
  * larger meshes return HHO_EINVAL.  Every GPU that loads the library holds
  * this array (512 KiB) until the process exits.
- * The first call on each device looks up the array's device address (with
- * that device current); make that first call before any stream capture.
- * All calls share the array: calls that overlap on the GPU (different
- * streams, or devices sharing nothing but the call order) race and must be
- * serialised by the caller.  Nothing in the array needs to start at zero. */
+ * Every call looks up the array's address on the current device (which
+ * allocates nothing); the first call on a device may load the library's
+ * device code, so make it before any stream capture.
+ * Each device holds its own copy of the array.  All calls on one device
+ * share it: calls on the same device that overlap on the GPU (different
+ * streams) race and must be serialised by the caller; calls on different
+ * devices do not interact.  Nothing in the array needs to start at zero. */
 #define HHO_ENERGY_STATIC_MAX_CELLS (65536LL * 256LL)
 int hho_energy_static(hho_ops* ops, const double* d_state, double* d_energy, void* stream);
 
@@ -460,6 +462,8 @@ int hho_energy_static(hho_ops* ops, const double* d_state, double* d_energy, voi
  * max(1, floor(delta N)).  *n_stable receives the last stable N (-1 if N0 is
  * unstable) and *n_unstable the first unstable N (-1 if none within
  * max_trials).  d_state: n_state doubles; d_work: hho_work_size(tab) doubles.
+ * The energy of d_state0 must be positive and finite (the test divides by
+ * it): a zero state returns HHO_EINVAL. 
  * Synchronises the stream after every step. */
 int hho_cfl_bracket(hho_ops* ops, const hho_tableau* tab, const double* d_state0, double T_f, int64_t N0,
                     double eps, double delta, int64_t max_trials, double* d_state, double* d_work,

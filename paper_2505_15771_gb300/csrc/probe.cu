@@ -81,3 +81,58 @@ extern "C" int hho_probe_ffma_rate(int iters, int reps, double* fma_per_s) {
     *fma_per_s = best;
     return rc;
 }
+
+// FP64 tensor-core (DMMA) throughput: the only FP64 matrix instruction is the
+// warp-wide mma.sync m8n8k4 (D = A B + C, 8x4 by 4x8, FP64 throughout; each
+// thread holds one element of A and B and two of C/D).  tcgen05.mma has no
+// FP64 kind.  Eight independent accumulator tiles per warp, 8 blocks of 256
+// threads per SM, as the FMA probes.
+__global__ void dmma_probe_kernel(double* out, int iters, double a0, double b0) {
+    const double a = a0 + 1e-12 * threadIdx.x, b = b0;
+    double c[8][2];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) c[j][0] = c[j][1] = 0.0;
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0, %1}, {%2}, {%3}, {%0, %1};"
+                         : "+d"(c[j][0]), "+d"(c[j][1])
+                         : "d"(a), "d"(b));
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) s += c[j][0] + c[j][1];
+    out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+// Best DMMA rate over `reps` runs, in FP64 multiply-add operations per second
+// (one m8n8k4 is 256 of them), the unit of the FMA probes.  0 on success.
+extern "C" int hho_probe_dmma_rate(int iters, int reps, double* fma_per_s) {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 1;
+    const int blocks = sms * 8, threads = 256;
+    double* out = nullptr;
+    if (cudaMalloc(&out, sizeof(double) * blocks * threads) != cudaSuccess) return 1;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    double best = 0.0;
+    int rc = 0;
+    for (int r = 0; r < reps; ++r) {
+        cudaEventRecord(e0);
+        dmma_probe_kernel<<<blocks, threads>>>(out, iters, 1e-3, 1e-3);
+        cudaEventRecord(e1);
+        if (cudaEventSynchronize(e1) != cudaSuccess) { rc = 1; break; }
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        const double warps = (double)blocks * threads / 32;
+        const double rate = warps * iters * 8 * 256 / (ms * 1e-3);
+        if (rate > best) best = rate;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(out);
+    *fma_per_s = best;
+    return rc;
+}

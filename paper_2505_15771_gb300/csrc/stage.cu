@@ -35,7 +35,6 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
-#include <mutex>
 #include <vector>
 
 #include "f2x.cuh"
@@ -2094,6 +2093,11 @@ extern "C" int hho_cfl_bracket(hho_ops* ops, const hho_tableau* tab, const doubl
         double E0 = 0.0;
         rc = hho_energy(ops, d_state, d_work, &E0, stream);
         if (rc) break;
+        if (!(E0 > 0.0) || !std::isfinite(E0)) {   // the relative increases below divide by E0
+            hho_set_error("hho_cfl_bracket: the initial energy must be positive and finite (got %g)", E0);
+            rc = HHO_EINVAL;
+            break;
+        }
         double Eprev = E0;
         bool stable = true;
         for (int64_t n = 0; n < N; ++n) {
@@ -2133,34 +2137,22 @@ extern "C" int hho_cfl_bracket(hho_ops* ops, const hho_tableau* tab, const doubl
 // Block partial sums of hho_energy_static live in this fixed array instead of
 // a caller buffer.  Host code must not take its address directly (the host
 // symbol is only a stand-in for the device variable); the device address is
-// looked up once per device with cudaGetSymbolAddress.
+// looked up with cudaGetSymbolAddress, with the device current, on every
+// call.  The lookup allocates nothing and is cheap, and an address kept from
+// an earlier call would go stale after a device reset.
 namespace {
 constexpr int kEnergyStaticMaxBlocks = (int)(HHO_ENERGY_STATIC_MAX_CELLS / 256);
 static __device__ __align__(256) double g_energy_partials[kEnergyStaticMaxBlocks];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_energy_mu;
-double* g_energy_addr[kMaxDevices] = {nullptr};
-
-// Device address of g_energy_partials for the current device (set-up on the
-// first call per device, with that device current).
+// Device address of g_energy_partials on the current device.
 int energy_scratch(double** out) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
-        hho_set_error("hho_energy_static: no usable current device");
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_energy_partials);
+    if (e != cudaSuccess || !p) {
+        hho_set_error("hho_energy_static: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
         return HHO_ECUDA;
     }
-    std::lock_guard<std::mutex> lock(g_energy_mu);
-    if (!g_energy_addr[dev]) {
-        void* p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_energy_partials);
-        if (e != cudaSuccess || !p) {
-            hho_set_error("hho_energy_static: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
-            return HHO_ECUDA;
-        }
-        g_energy_addr[dev] = (double*)p;
-    }
-    *out = g_energy_addr[dev];
+    *out = (double*)p;
     return HHO_OK;
 }
 }  // namespace

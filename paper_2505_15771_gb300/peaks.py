@@ -1,7 +1,8 @@
-"""Measured ALU ceilings of the GPU: FP64 and FP32 FMA throughput from the
-probes in libhho_probe.so (eight independent FMA chains per thread, eight
-256-thread blocks per SM, best of several runs), printed as FMA lane-ops/s
-and TFLOP/s (FMA = 2 flops).
+"""Measured ALU ceilings of the GPU: FP64 and FP32 FMA throughput and the
+FP64 tensor-core (DMMA, mma.sync m8n8k4) rate from the probes in
+libhho_probe.so (eight independent chains per thread, eight 256-thread
+blocks per SM, best of several runs), printed as multiply-add lane-ops/s and
+TFLOP/s (multiply-add = 2 flops).
 
     python -m paper_2505_15771_gb300.peaks
 """
@@ -15,7 +16,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 def rates(iters=4000, reps=5):
     lib = ctypes.CDLL(os.path.join(_HERE, "libhho_probe.so"))
     out = {}
-    for name, fn, it in (("fp64", "hho_probe_dfma_rate", iters), ("fp32", "hho_probe_ffma_rate", 16 * iters)):
+    for name, fn, it in (("fp64", "hho_probe_dfma_rate", iters), ("fp32", "hho_probe_ffma_rate", 16 * iters),
+                         ("fp64_dmma", "hho_probe_dmma_rate", iters // 4)):
         f = getattr(lib, fn)
         f.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
         r = ctypes.c_double()

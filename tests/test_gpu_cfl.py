@@ -70,3 +70,16 @@ def test_gpu_algorithm1_stage_ratios_table2(lib):
     r3, r4 = dts[1] / dts[0], dts[2] / dts[0]
     print("ratios", r3, r4)
     assert abs(r3 - 1.23) < 0.05 and abs(r4 - 1.38) < 0.05
+
+
+def test_gpu_algorithm1_rejects_zero_initial_energy(lib):
+    """Algorithm 1's test is relative to E^0, so a zero state has no answer:
+    the call fails with HHO_EINVAL instead of counting every trial stable."""
+    hho, solver = lib
+    md, media = cfl_case()
+    P = solver.Problem(md, media, 1)
+    U0 = np.zeros(P.layout.n_canonical)
+    with pytest.raises(hho.HHOError) as e:
+        gpu_bracket(hho, P, U0, 1.0, 100)
+    assert e.value.code == hho.HHO_EINVAL
+    assert "initial energy" in str(e.value)

@@ -216,13 +216,18 @@ def test_traffic_record_from_ncu_logs(tmp_path):
           ("void <unnamed>::stage_kernel<f2x, 2, 0>(StageArgsT<T1>)", 999.0, 999.0, 60.0),
           ("void <unnamed>::stage_kernel<double, 2, 1>(StageArgsT<T1>)", 300.0, 170.0, 190.0)]
     k3 = [("void <unnamed>::stage_kernel<f2x, 3, 1>(StageArgsT<T1>)", 300.0, 180.0, 250.0),
-          ("void <unnamed>::stage_kernel<double, 3, 1>(StageArgsT<T1>)", 320.0, 190.0, 290.0)]
+          ("void <unnamed>::stage_kernel<double, 3, 1>(StageArgsT<T1>)", 320.0, 190.0, 290.0),
+          ("void <unnamed>::stage_kernel<float, 3, 1>(StageArgsT<T1>)", 100.0, 50.0, 90.0),
+          ("void <unnamed>::stage_kernel<double, 2, 1>(StageArgsT<T1>)", 999.0, 999.0, 90.0)]   # other k: ignored
     _ncu_csv(tmp_path / "k2.csv", k2)
     _ncu_csv(tmp_path / "k3.csv", k3)
     out = tmp_path / "traffic.json"
-    rec = bench.write_traffic_record(str(tmp_path / "k2.csv"), str(tmp_path / "k3.csv"), str(out))
-    dofs2 = 768 * 384 * 0.5 * 8 * 6
-    dofs3 = 640 * 320 * 0.5 * 8 * 10
+    rec = bench.write_traffic_record([(str(tmp_path / "k2.csv"), 48, 24, 2), (str(tmp_path / "k3.csv"), 40, 20, 3)],
+                                     str(out))
+    # cell DOFs counted from the meshes: half the rows of the bilayer are solid (5n), half fluid (3n)
+    dofs2 = 48 * 24 * 0.5 * 8 * 6
+    dofs3 = 40 * 20 * 0.5 * 8 * 10
+    assert bench.bilayer_cell_dofs(48, 24, 2) == dofs2
     assert rec["stage_sources_sha256"] == bench.stage_source_sha()
     assert rec["f32x2_k2"]["dram_bytes_per_launch_mean"] == pytest.approx(375e6)   # (350 + 400) / 2 MB
     assert rec["f32x2_k2"]["dram_bytes_per_launch_per_cell_dof"] == pytest.approx(375e6 / dofs2)
@@ -230,6 +235,7 @@ def test_traffic_record_from_ncu_logs(tmp_path):
     assert rec["k2"]["dram_bytes_per_launch_mean"] == pytest.approx(470e6)
     assert rec["f32x2_k3"]["dram_bytes_per_launch_per_cell_dof"] == pytest.approx(480e6 / dofs3)
     assert rec["k3"]["dram_bytes_per_launch_mean"] == pytest.approx(510e6)
+    assert rec["f32_k3"]["dram_bytes_per_launch_mean"] == pytest.approx(150e6)   # float is filed apart
     assert "20 stage launches" not in rec["f32x2_k2"]["captured"] and "2 stage launches" in rec["f32x2_k2"]["captured"]
     import json
     assert json.load(open(out)) == rec
