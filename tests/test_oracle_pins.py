@@ -445,6 +445,133 @@ def test_plane_wave_reflection_transmission():
     assert errs[1] < errs[0] / 4
 
 
+def _homogeneous_strip_error(N, k, dom, wave, tf=0.25, y0=-0.3, sigma=0.15):
+    """Relative L2 error at tf of a Gaussian plane wave travelling in +y
+    through a homogeneous medium on a periodic-in-x strip [0, 3h] x [-1, 1]
+    (Dirichlet rows top and bottom, never reached: the pulse stays inside).
+
+    Closed forms, from the first-order systems of Sec. 2 with F = g(y - c t):
+    fluid (P wave, c = sqrt(kappa/rho)): p = F, m_y = -F / (rho c);
+    solid P wave (c = c_P): v_y = F, s_yy = -rho c_P F, s_xx = -lambda/c_P F;
+    solid S wave (c = c_S): v_x = F, s_xy = -rho c_S F."""
+    h = 1.0 / N
+    md = synth.quad_grid(3, 2 * N, 0.0, 3 * h, -1.0, 1.0, y_interface=(-2.0 if dom == 0 else 2.0), periodic_x=True)
+    nc = md.n_cells
+    rho, vp, vs = 1.3, 1.0, 0.6
+    mu = rho * vs * vs
+    lam = rho * vp * vp - 2 * mu
+    S = system(md, k, media=(np.full(nc, rho), np.full(nc, lam), np.full(nc, mu), np.full(nc, rho * vp * vp)))
+    c = vs if wave == "s" else vp
+    g = lambda s: np.exp(-((s - y0) / sigma) ** 2)
+
+    def fields(t):
+        def f(x, y, d):
+            z = np.zeros_like(np.asarray(x, dtype=float))
+            F = g(y - c * t)
+            if d == 0:
+                return np.array([z, -F / (rho * vp), F])
+            if wave == "s":
+                return np.array([z, z, -rho * vs * F, F, z])
+            return np.array([-lam / vp * F, -rho * vp * F, z, z, F])
+        return f
+    st = E.Stepper(S)
+    U = S.project(fields(0.0), order=k + 6)
+    nsteps = int(np.ceil(tf / (0.04 * h)))      # ERK4 time error far below the space error
+    U = st.step(U, 0.0, tf / nsteps, "erk4", nsteps)
+    e, r = D.l2_error(S, U, fields(tf), order=k + 6)
+    return e / r
+
+
+@pytest.mark.parametrize("dom,wave,k", [(0, "p", 1), (0, "p", 2), (0, "p", 3), (1, "p", 1), (1, "p", 2),
+                                        (1, "p", 3), (1, "s", 2)])
+def test_plane_wave_convergence_order_k_plus_1(dom, wave, k):
+    """L2 convergence of order k + 1 in homogeneous media (the rate the
+    efficiency study of Sec. 5.1 builds its solver tolerance 2^(-l(k+1)) on):
+    a plane Gaussian pulse through acoustic and elastic (P and S) media,
+    three refinement levels, all unknowns; the finest pair's rate is at least
+    k + 0.9 (observed 2.1 / 3.0 / 4.0 for k = 1 / 2 / 3)."""
+    errs = [_homogeneous_strip_error(N, k, dom, wave) for N in (8, 16, 32)]
+    rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert rates[-1] >= k + 0.9, (errs, rates)
+    assert rates[0] >= k + 0.7, (errs, rates)
+
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_point_load_is_the_limit_of_narrow_gaussian_loads(k):
+    """Eq. rhs read as a load vector: a point force w e_dir at x_s gives
+    b_i = phi_i(x_s) e_dir (solid, velocity rows) and a point source gives
+    b_i = phi_i(x_s) (fluid, pressure rows).  Independent route: the load
+    vectors (f, phi_i)_T of normalised Gaussians g_eps centred at x_s, built by
+    quadrature of the defining integral (load_matrix).  For a polynomial phi
+    of degree <= 3, int g_eps phi = phi(x_s) + eps^2/2 Lap phi(x_s) exactly
+    (the Gaussian's odd moments vanish and its second moments are eps^2), so
+    two widths eliminate the eps^2 term and leave phi(x_s) up to quadrature
+    and truncation (the Gaussian sits 8 widths inside its cell)."""
+    md = synth.quad_grid(2, 2, 0.0, 1.0, 0.0, 1.0, y_interface=0.5)
+    nc = md.n_cells
+    S = system(md, k, media=(np.full(nc, 2.0), np.full(nc, 1.0), np.full(nc, 1.0), np.full(nc, 3.0)))
+    Qm, xq, yq, dq = S.load_matrix(order=60)
+    e1, e2 = 0.025, 0.02
+    for xs, ys, d in ((0.27, 0.22, (0.6, 0.8)), (0.71, 0.77, None)):
+        loads = []
+        for eps in (e1, e2):
+            g = np.exp(-((xq - xs) ** 2 + (yq - ys) ** 2) / (2 * eps * eps)) / (2 * np.pi * eps * eps)
+            z = np.zeros_like(g)
+            if d is None:     # fluid: scalar source in the pressure equation
+                F = np.concatenate([np.where(dq == 0, g, 0.0), z, z])
+            else:             # solid: force along d in the velocity equation
+                F = np.concatenate([z, np.where(dq == 1, d[0] * g, 0.0), np.where(dq == 1, d[1] * g, 0.0)])
+            loads.append(Qm @ F)
+        limit = (e2 ** 2 * loads[0] - e1 ** 2 * loads[1]) / (e2 ** 2 - e1 ** 2)
+        b, cell = S.point_load(xs, ys, direction=d if d is not None else (0.0, 1.0))
+        assert np.linalg.norm(limit - b) <= 1e-11 * np.linalg.norm(b)
+        assert int(md.cell_domain[cell]) == (0 if d is None else 1)
+
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_interface_sensor_is_the_riemann_state(k):
+    """Interface sensors (face unknowns on Gamma, Sec. 5.2) against the exact
+    interface state of the 1D Riemann problem normal to Gamma.  Along the
+    normal n (solid -> fluid) the fluid carries p + Z_f m.n towards Gamma and
+    the solid s_nn - Z_P v.n; with v.n = m.n and s n = p n (Eq. coupling1-2)
+    the interface state is m* = (R_f - R_s)/(Z_f + Z_P), p* = R_f - Z_f m*, and
+    the tangential velocity is v_t - s_nt / Z (traction-free for the fluid).
+    The face solve of Eq. ex_solve is this state pointwise, with impedances
+    1/tau^f and tau^s: with eta = 1 (tau^f = 1/(rho c), tau^s = rho c_P) and
+    s_nt = 0 it is the physical Riemann state.  Fields linear in x and y
+    (exact in the cell spaces) make the state vary along the face, which pins
+    the orientation of the face coordinate and the slots [p_F, v_Fx, v_Fy]."""
+    rng = np.random.default_rng(3 + k)
+    md = synth.quad_grid(4, 4, 0.0, 1.0, 0.0, 1.0, y_interface=0.5)
+    nc = md.n_cells
+    sol = md.cell_domain == 1
+    vp, vs, cf, rs, rf = 3.0, 1.7, 1.5, 2.5, 1.0
+    media = (np.where(sol, rs, rf), np.where(sol, rs * (vp * vp - 2 * vs * vs), 0.0),
+             np.where(sol, rs * vs * vs, 0.0), np.where(sol, 0.0, rf * cf * cf))
+    xs = np.array([0.1, 0.37, 0.6, 0.88])
+    for eta_f, eta_s, shear in ((1.0, 1.0, False), (0.8, 1.5, True)):
+        S = system(md, k, media=media, eta_f=eta_f, eta_s=eta_s)
+        cF = rng.standard_normal((3, 3))
+        cS = rng.standard_normal((5, 3))
+        if not shear:
+            cS[2] = 0.0       # s_xy = 0: no tangential traction on Gamma
+
+        def fields(x, y, d):
+            c = cF if d == 0 else cS
+            return np.array([c[i, 0] + c[i, 1] * x + c[i, 2] * y for i in range(c.shape[0])])
+        U = S.project(fields, order=k + 4)
+        got = D.sensors(E.Stepper(S), U, [(x, 0.5) for x in xs])
+        Zf = rf * cf / eta_f          # 1 / tau^f
+        Zp = eta_s * rs * vp          # tau^s
+        mx, my, p = fields(xs, 0.5, 0)
+        sxx, syy, sxy, vx, vy = fields(xs, 0.5, 1)
+        Rf, Rs = p + Zf * my, syy - Zp * vy
+        m_star = (Rf - Rs) / (Zf + Zp)
+        want = np.stack([Rf - Zf * m_star, vx - sxy / Zp, m_star], axis=1)
+        assert np.allclose(got[:, :3], want, rtol=0, atol=1e-12 * np.abs(want).max())
+        assert np.all(got[:, 3:] == 0.0)
+
+
 # --------------------------------------------------------------------------- mesh conventions
 
 def test_canonical_tables_hand_example():
