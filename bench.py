@@ -242,7 +242,7 @@ def write_traffic_record(captures, out_path=None):
     import re
     scale = {"byte": 1.0, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "ns": 1e-3, "us": 1.0, "usecond": 1.0,
              "msecond": 1e3, "ms": 1e3}
-    pat = re.compile(r"stage_kernel<(\w+), (\d), 1>")
+    pat = re.compile(r"stage_kernel<(\w+), ?(?:\(int\))?(\d), ?(?:\(int\))?1>")
     out = {}
     for path, nx, ny, k in captures:
         nx, ny, k = int(nx), int(ny), int(k)

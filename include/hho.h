@@ -250,6 +250,29 @@ int hho_set_launch_mode(hho_ops* ops, int32_t mode);
 int hho_sources_set(hho_ops* ops, int32_t n_src, const double* h_xy, const double* h_dir,
                     const double* h_f0, const double* h_t0, const double* h_amp);
 
+/* Point sources with sampled time functions: the same load vectors as
+ * hho_sources_set, with source s taking the value
+ * h_samples[(s nsteps + n) s_stages + j] in stage j of step n, for steps of
+ * size dt from t_start (stage time t_start + n dt + c_j dt) of an ERK tableau
+ * with s_stages stages; zero outside those nsteps steps.  A step is located by
+ * rounding (t - t_start) / dt, so the stepping calls must use the same dt and
+ * a start time on that grid.  The samples of stages sharing a time may
+ * differ (they are independent inputs, e.g. for the wavelet gradient of
+ * hho_adjoint_vjp, whose h_grad_wavelet has this layout for t0 = t_start).
+ * Replaces any previous set.  The ERK entry points use stream launches
+ * while sampled sources are set; hho_apply and hho_sdirk_step, which have
+ * no stage index, return HHO_EINVAL.  At most 8 sources. */
+int hho_sources_set_samples(hho_ops* ops, int32_t n_src, const double* h_xy, const double* h_dir, double t_start,
+                            double dt, int64_t nsteps, int32_t s_stages, const double* h_samples);
+
+/* Ricker wavelet samples at the stage times of the tableau:
+ * h_out[n s + j] = w(t_start + n dt + c_j dt) with the wavelet of
+ * hho_sources_set, the times rounded as the ERK loops round them.
+ * So hho_sources_set_samples with these samples steps exactly like
+ * hho_sources_set with (f0, t0, amp). */
+int hho_ricker_samples(const hho_tableau* tab, double t_start, double dt, int64_t nsteps, double f0, double t0,
+                       double amp, double* h_out);
+
 /* Advances d_state (device layout, in/out) by nsteps steps of size dt from
  * time t0 with the tableau.  Each stage is one fused kernel (face values from
  * neighbour traces, reconstruction, stabilisation, coupling, inverse mass,
@@ -376,15 +399,25 @@ int hho_adjoint_work_size(const hho_ops* ops, const hho_tableau* tab, int64_t ns
  * traces that hho_erk_step_record writes after every step.  Outputs:
  *   h_grad_cell[4 c + (0,1,2,3)] = dL/d(rho, kappa, lambda, mu) of cell c
  *     (input order; kappa only in fluid cells, lambda and mu only in solid
- *     cells), with the stabilisation weights tau held at their current values;
+ *     cells).  The materials enter through the mass matrix (Eq. mass) and
+ *     through the stabilisation weights tau (Sec. 3.3, tau^f = eta_f/(rho c_P),
+ *     tau^s = eta_s rho c^s), which scale each cell's stabilisation (Eq. stab)
+ *     and with it the face solve: both parts are included for operators from
+ *     hho_operators_build.  For operators from hho_operators_build_tau the
+ *     weights are the caller's constants and only the mass part remains (the
+ *     gradient with tau frozen);
  *   h_grad_wavelet (may be NULL): [nsteps][s][n_src] dL/dw at every stage time
- *     t_{n-1} + c_j dt of every hho_sources_set source.
+ *     t_{n-1} + c_j dt of every hho_sources_set source;
+ *   h_grad_tau (may be NULL): [nc] dL/dtau_c, the partial derivative with the
+ *     weights as independent parameters (stage and interface-receiver parts).
  * The adjoint uses A^T = S M A' M^-1 S (S: sign flip of the dual fields, A':
  * the stage operator with the interface coupling reversed) on the forward
- * kernels; segments between checkpoints are recomputed.  Synchronises. */
+ * kernels; the adjoint face values needed by the tau part are those of A'.
+ * Segments between checkpoints are recomputed.  Synchronises. */
 int hho_adjoint_vjp(hho_ops* ops, const hho_tableau* tab, double t0, double dt, int64_t nsteps,
                     int64_t checkpoint_every, const double* d_state0, const double* d_cotangent, double* d_work,
-                    int64_t work_doubles, double* h_grad_cell, double* h_grad_wavelet, void* stream);
+                    int64_t work_doubles, double* h_grad_cell, double* h_grad_wavelet, double* h_grad_tau,
+                    void* stream);
 
 /* ------------------------------------------------------------------------- */
 /* Sensors and energy (Sec. 5).                                               */

@@ -13,11 +13,22 @@ reverse order mu_i = dt (b_i lambda + sum_{l>i} a_li nu_l), nu_i = A^T mu_i;
 lambda^{n-1} = lambda^n + sum_i nu_i.  Here A^T is the plain transpose of the
 dense matrix.
 
-Material gradients with the stabilisation weights held fixed: K and b do not
-depend on the materials, M does, so dk/dtheta = -M^-1 (dM/dtheta) k and
-dL/dtheta = sum mu_i^T dk_i/dtheta.  dM/dtheta is assembled per cell from the
-mass definitions (Eq. mass): rho multiplies the m / v blocks, 1/kappa the p
-block, the plane-strain compliance the s block.  dL/dw(t_i) = mu_i^T M^-1 b.
+Material gradients.  The materials enter through M (Eq. mass: rho
+multiplies the m / v blocks, 1/kappa the p block, the plane-strain
+compliance the s block) and through the stabilisation weights tau (Sec. 3.3:
+tau^f = eta_f / (rho c_P), tau^s = eta_s rho c^s), which scale each cell's
+least-squares stabilisation (Eq. stab).  So
+    dL/dtheta = sum_i mu_i^T dk_i/dtheta + sum_c dL/dtau_c dtau_c/dtheta,
+with dk/dtheta = -M^-1 (dM/dtheta) k for the mass part.  K is affine in tau
+(dK/dtau_c = the stabilisation form of cell c, System.stab_form), so with the
+face values Y_F = -K_F^-1 K_FT Y of a stage value, eta = M^-1 mu and the
+adjoint face values eta_F = -K_F^-T K_TF^T eta,
+    d(eta^T K_cond Y)/dtau_c = [eta; eta_F]^T (dK/dtau_c) [Y; Y_F]
+(K_cond = K_T - K_TF K_F^-1 K_FT), and the stage term is minus that.  The
+interface receivers read face values, which depend on tau as well: for
+d = E U_F, d(G^T d)/dtau_c = [0; zeta]^T (dK/dtau_c) [U; U_F] with
+zeta = -K_F^-T E^T G.  With tau given explicitly (tau_override) the weights
+are constants and only the mass part remains.  dL/dw(t_i) = mu_i^T M^-1 b.
 """
 from __future__ import annotations
 
@@ -31,12 +42,15 @@ from .erk import tableau
 from .spaces import eval_cell_basis
 
 
-def receiver_matrix(stepper, points):
-    """Dense R with d = R U ([n_rec*5, nT]), rows ordered (receiver, field)."""
+def receiver_matrix(stepper, points, with_face_rows=False):
+    """Dense R with d = R U ([n_rec*5, nT]), rows ordered (receiver, field).
+    With with_face_rows, also E ([n_rec*5, nF]): the rows of the interface
+    receivers as point values of the face unknowns (d = E U_F there)."""
     S = stepper.sys
     m = S.mesh
     n = S.n
     R = np.zeros((5 * len(points), S.nT))
+    Efull = np.zeros((5 * len(points), S.nF))
     KF = S.KF.toarray() if S.nF else None
     KFT = S.KFT.toarray() if S.nF else None
     for r, (x, y) in enumerate(points):
@@ -48,6 +62,7 @@ def receiver_matrix(stepper, points):
             for d in range(2):
                 E[1 + d, [S.idx_vF(F, d, l) for l in range(S.f)]] = psi
             R[5 * r: 5 * r + 3] = -E @ np.linalg.solve(KF, KFT)
+            Efull[5 * r: 5 * r + 3] = E
             continue
         c = locate_cell(m, x, y)
         xT, yT, h = S.cell_frame(c)
@@ -56,7 +71,7 @@ def receiver_matrix(stepper, points):
         fields = [2, 0, 1] if m.cell_domain[c] == mmesh.FLUID else [3, 4, 0, 1, 2]
         for j, fld in enumerate(fields):
             R[5 * r + j, o + fld * n: o + (fld + 1) * n] = phi
-    return R
+    return (R, Efull) if with_face_rows else R
 
 
 class DenseAdjoint:
@@ -69,7 +84,9 @@ class DenseAdjoint:
         Kc = KT - KTF @ np.linalg.solve(KF, KFT) if S.nF else KT
         self.M = M
         self.A = -np.linalg.solve(M, Kc)
-        self.R = receiver_matrix(stepper, points)
+        self.R, self.E = receiver_matrix(stepper, points, with_face_rows=True)
+        self.KF, self.KFT, self.KTF = KF, KFT, KTF
+        self.dK = [S.stab_form(c) for c in range(S.mesh.n_cells)]
         self.g = np.zeros(S.nT) if load is None else np.linalg.solve(M, load)
         self.wavelet = wavelet if wavelet is not None else (lambda t: 0.0)
 
@@ -88,10 +105,24 @@ class DenseAdjoint:
             U = U + dt * sum(b[i] * K[i] for i in range(s))
             stages.append((Y, K))
             traces.append(self.R @ U)
+        self._U_end = U
         return np.array(traces), stages
 
-    def vjp(self, U0, t0, dt, nsteps, cotangent, scheme="erk4"):
-        """Returns (grad [nc, 4] = dL/d(rho, kappa, lambda, mu), grad_w [nsteps, s])."""
+    def face_values(self, U):
+        """U_F = -K_F^-1 K_FT U (the face solve of Eq. ex_solve)."""
+        return -np.linalg.solve(self.KF, self.KFT @ U) if self.S.nF else np.zeros(0)
+
+    def adjoint_face_values(self, eta):
+        """eta_F = -K_F^-T K_TF^T eta."""
+        return -np.linalg.solve(self.KF.T, self.KTF.T @ eta) if self.S.nF else np.zeros(0)
+
+    def tau_form(self, a, b):
+        """[a^T (dK/dtau_c) b for every cell c] over stacked [U_T; U_F] vectors."""
+        return np.array([a @ (dK @ b) for dK in self.dK])
+
+    def vjp(self, U0, t0, dt, nsteps, cotangent, scheme="erk4", with_tau=False):
+        """Returns (grad [nc, 4] = dL/d(rho, kappa, lambda, mu), grad_w [nsteps, s]),
+        and dL/dtau [nc] as a third value when with_tau."""
         S = self.S
         m = S.mesh
         n = S.n
@@ -104,8 +135,15 @@ class DenseAdjoint:
         gw = np.zeros((nsteps, s))
         AT = self.A.T
         Minv = np.linalg.inv(self.M)
+        gtau = np.zeros(m.n_cells)
         for nn in range(nsteps - 1, -1, -1):
             lam = lam + self.R.T @ G[nn]
+            if np.any(self.E):
+                # interface receivers: d = E U_F(U^n), U^n = the next step's first stage value
+                Un = stages[nn + 1][0][0] if nn + 1 < nsteps else self._U_end
+                zeta = -np.linalg.solve(self.KF.T, self.E.T @ G[nn])
+                gtau += self.tau_form(np.concatenate([np.zeros(S.nT), zeta]),
+                                      np.concatenate([Un, self.face_values(Un)]))
             Y, K = stages[nn]
             pend = [np.zeros(S.nT) for _ in range(s)]
             acc = lam.copy()
@@ -118,6 +156,8 @@ class DenseAdjoint:
                         pend[l] += Aext[i, l] * nu
                 gw[nn, i] = mu_i @ self.g
                 eta = Minv @ mu_i          # dL/dtheta = -eta^T (dM/dtheta) k
+                gtau -= self.tau_form(np.concatenate([eta, self.adjoint_face_values(eta)]),
+                                      np.concatenate([Y[i], self.face_values(Y[i])]))
                 k = K[i]
                 for cc in range(m.n_cells):
                     M0 = S.M0[cc]
@@ -134,4 +174,5 @@ class DenseAdjoint:
                             grad[cc, p] -= sum(dD[aa, bb] * (eta[blk(aa)] @ M0 @ k[blk(bb)])
                                                for aa in range(3) for bb in range(3))
             lam = acc
-        return grad, gw
+        grad += gtau[:, None] * S.tau_material_derivatives()
+        return (grad, gw, gtau) if with_tau else (grad, gw)

@@ -121,6 +121,8 @@ class System:
             # differentiating with respect to the materials)
             tau = np.array(tau_override, dtype=np.float64)
         self.tau = tau
+        self.tau_fixed = tau_override is not None
+        self.stab_speed = stab_speed
 
         n, f = self.n, self.f
         self.cell_off = np.zeros(nc + 1, dtype=np.int64)
@@ -345,6 +347,65 @@ class System:
         self.KTF = sp.csr_matrix((TFv, (TFr, TFc)), shape=(nT, nF))
         self.KFT = sp.csr_matrix((FTv, (FTr, FTc)), shape=(nF, nT))
         self.KF = sp.csc_matrix((Fv, (Fr, Fc)), shape=(nF, nF))
+
+    # ---- dependence on the stabilisation weights -------------------------------
+    def tau_material_derivatives(self):
+        """d tau_c / d(rho, kappa, lambda, mu) per cell ([nc, 4]).
+
+        tau^f = eta_f / (rho c_P) = eta_f (rho kappa)^(-1/2) in fluid cells and
+        tau^s = eta_s rho c^s in solid cells, with c^s = c_P
+        (tau^s = eta_s (rho (lambda + 2 mu))^(1/2)) or c_S
+        (eta_s (rho mu)^(1/2)) (Sec. 3.3 with the eta weights of Sec. 5.1;
+        the optional 1/k factor cancels in the logarithmic derivatives).
+        Zero when the weights were given explicitly (tau_override)."""
+        m = self.mesh
+        d = np.zeros((m.n_cells, 4))
+        if self.tau_fixed:
+            return d
+        for c in range(m.n_cells):
+            t = self.tau[c]
+            if m.cell_domain[c] == mmesh.FLUID:
+                d[c, 0] = -0.5 * t / self.rho[c]
+                d[c, 1] = -0.5 * t / self.kappa[c]
+            elif self.stab_speed == "cp":
+                l2m = self.lam[c] + 2.0 * self.mu[c]
+                d[c, 0] = 0.5 * t / self.rho[c]
+                d[c, 2] = 0.5 * t / l2m
+                d[c, 3] = t / l2m
+            else:
+                d[c, 0] = 0.5 * t / self.rho[c]
+                d[c, 3] = 0.5 * t / self.mu[c]
+        return d
+
+    def stab_form(self, c):
+        """dK/dtau_c of the full system: the least-squares stabilisation of
+        cell c without its weight (Eq. stab), sum over the faces F of c of
+        (u_c|_F - u_F, w_c|_F - w_F)_F on the primal unknowns (p in a fluid
+        cell, both components of v in a solid cell), u_F = 0 on boundary
+        faces.  Sparse over the stacked vector [U_T; U_F] (nT + nF)."""
+        m = self.mesh
+        n, f, nT = self.n, self.f, self.nT
+        R, C, V = [], [], []
+        fluid = m.cell_domain[c] == mmesh.FLUID
+        comps = [None] if fluid else [0, 1]
+        for F in m.cell_faces[c]:
+            PP, SP, SS, _ = self.local_face_integrals(F, c)
+            bnd = m.face_type[F] in (mmesh.FT_BND_FLUID, mmesh.FT_BND_SOLID)
+            for d in comps:
+                cell = [self.idx_p(c, i) if fluid else self.idx_v(c, d, i) for i in range(n)]
+                face = [] if bnd else [nT + (self.idx_pF(F, l) if fluid else self.idx_vF(F, d, l)) for l in range(f)]
+                for i in range(n):
+                    for j in range(n):
+                        R.append(cell[i]); C.append(cell[j]); V.append(PP[i, j])
+                for i in range(n if face else 0):
+                    for l in range(len(face)):
+                        R.append(cell[i]); C.append(face[l]); V.append(-SP[i, l])
+                        R.append(face[l]); C.append(cell[i]); V.append(-SP[i, l])
+                for l in range(len(face)):
+                    for l2 in range(len(face)):
+                        R.append(face[l]); C.append(face[l2]); V.append(SS[l, l2])
+        N = nT + self.nF
+        return sp.csr_matrix((V, (R, C)), shape=(N, N))
 
     # ---- sources -------------------------------------------------------------
     def point_load(self, x: float, y: float, direction=(0.0, 1.0), cell: int | None = None):

@@ -15,18 +15,29 @@
 // of the interface coupling block reversed.  So A^T = mass kernel, forward
 // stage kernel on A' (traces + apply), mass kernel.
 //
-// Parameters: the per-cell factors of the inverse mass, theta = (1/(rho h),
-// kappa/h) in fluid cells and ((lambda+2mu)/h, lambda/(lambda+2mu), mu/h,
-// 1/(rho h)) in solid cells; dk/dtheta is the raw rate (MODE_RAW).  The
-// stabilisation weights tau (and with them the face coefficients) are held
-// fixed: the gradient is that of the discrete scheme with tau frozen at the
-// current model.  The host maps dL/dtheta to dL/d(rho, kappa, lambda, mu).
+// Parameters.  (1) The per-cell factors of the inverse mass, theta =
+// (1/(rho h), kappa/h) in fluid cells and ((lambda+2mu)/h, lambda/(lambda+2mu),
+// mu/h, 1/(rho h)) in solid cells; dk/dtheta is the raw rate (MODE_RAW).
+// (2) The stabilisation weights tau (Sec. 3.3: tau^f = eta_f/(rho c_P),
+// tau^s = eta_s rho c^s).  The full stiffness is affine in tau: dK/dtau_c is
+// cell c's least-squares stabilisation (Eq. stab) without its weight, so
+//     d(eta^T K_cond Y)/dtau_c = sum_{F of c} (eta_c - eta_F, Y_c - Y_F)_F
+// on the primal unknowns, with Y_F the face values of the stage value Y and
+// eta_F = -K_F^-T K_TF^T eta the adjoint face values of eta = M^-1 mu.  By the
+// same block structure eta_F are the face values of the coupling-reversed
+// operator A' applied to x = S eta, which the backward stage computes anyway:
+// tau_grad_kernel takes the products of both jumps from the two trace
+// buffers.  The interface receivers read face values, which depend on tau
+// too (rec_tau_kernel).  The host maps dL/dtheta and dL/dtau to
+// dL/d(rho, kappa, lambda, mu); with tau given explicitly
+// (hho_operators_build_tau) tau is a constant and only (1) remains.
 //
 // Checkpointing: U is stored every `checkpoint_every` steps in the forward
 // pass; each segment is recomputed, keeping its stage values and their face
 // traces, before its backward sweep.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -229,6 +240,126 @@ __global__ void grad_kernel(DevOps op, const double* __restrict__ mu, const doub
     }
 }
 
+// Stabilisation-weight part of one backward stage: for every cell,
+// gstab += sum_F |F|/h sum_l jY_l jX_l / (2l+1), the face integrals (Legendre
+// basis on the face) of the products of the primal jumps u_F - u|_F of the
+// forward stage value (traces trY, coefficients of op) and of x = S M^-1 mu
+// (traces trX under the coupling-reversed operator opx).  The host multiplies
+// by -h per cell.  Same jump formulas as the stage kernel's face rates.
+__global__ void tau_grad_kernel(DevOps op, DevOps opx, const double* __restrict__ trY, const double* __restrict__ trX,
+                                double* __restrict__ gstab) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= op.Nf + op.Ns) return;
+    const bool fl = g < op.Nf;
+    const int q = fl ? g : g - op.Nf;
+    const int n = op.n, f = op.f;
+    const int cls = op.warp_class[(fl ? 0 : op.n_warps_f) + (q >> 5)];
+    const int* ci = op.cls_int + cls * CI_STRIDE;
+    const int lq = q - ci[CI_START];
+    if (lq >= ci[CI_COUNT]) return;
+    const int nF = ci[CI_NF], npad = ci[CI_NPAD], sbase = ci[CI_SLOT];
+    const int nP = (n + 3) / 4 * 4, fP = (f + 3) / 4 * 4, M0P = (n * n + 3) / 4 * 4, FS = 4 + f * nP + n * fP;
+    const double* cd = op.cls_dbl + ci[CI_DOFF] + M0P;
+    const int SF = op.SF, SS = op.SS;
+    const double* yf = trY;
+    const double* ys = trY + (size_t)2 * f * SF;
+    const double* xf = trX;
+    const double* xs = trX + (size_t)2 * f * SF;
+    double acc = 0.0;
+    for (int j = 0; j < nF; ++j) {
+        const double rel = cd[j * FS + 2];   // |F| / h
+        const int slot = sbase + j * npad + lq;
+        double sum = 0.0;
+        if (fl) {
+            const int nb = op.nb_f[slot];
+            for (int l = 0; l < f; ++l) {
+                const double sg = (l & 1) ? -1.0 : 1.0;
+                double jy = yf[(size_t)(f + l) * SF + slot], jx = xf[(size_t)(f + l) * SF + slot];
+                if (nb >= 0) {
+                    const double be = op.beta_f[slot];
+                    jy += sg * be * yf[(size_t)l * SF + nb];
+                    jx += sg * be * xf[(size_t)l * SF + nb];
+                } else if (nb < NB_BOUNDARY) {
+                    const int r = -2 - nb, ns = op.if_nb[r];
+                    const double* cy = op.if_coef + 6 * r;
+                    const double* cx = opx.if_coef + 6 * r;
+                    jy += sg * (cy[1] * ys[(size_t)l * SS + ns] + cy[2] * ys[(size_t)(f + l) * SS + ns]);
+                    jx += sg * (cx[1] * xs[(size_t)l * SS + ns] + cx[2] * xs[(size_t)(f + l) * SS + ns]);
+                }
+                sum += jy * jx / (2 * l + 1);
+            }
+        } else {
+            const int nb = op.nb_s[slot];
+            for (int l = 0; l < f; ++l) {
+                const double sg = (l & 1) ? -1.0 : 1.0;
+                double jyx = ys[(size_t)(2 * f + l) * SS + slot], jyy = ys[(size_t)(3 * f + l) * SS + slot];
+                double jxx = xs[(size_t)(2 * f + l) * SS + slot], jxy = xs[(size_t)(3 * f + l) * SS + slot];
+                if (nb >= 0) {
+                    const double be = op.beta_s[slot];
+                    jyx += sg * be * ys[(size_t)l * SS + nb];
+                    jyy += sg * be * ys[(size_t)(f + l) * SS + nb];
+                    jxx += sg * be * xs[(size_t)l * SS + nb];
+                    jxy += sg * be * xs[(size_t)(f + l) * SS + nb];
+                } else if (nb < NB_BOUNDARY) {
+                    const int r = -2 - nb, nfs = op.if_nb[r];
+                    const double* cy = op.if_coef + 6 * r;
+                    const double* cx = opx.if_coef + 6 * r;
+                    const double wy = yf[(size_t)l * SF + nfs], wx = xf[(size_t)l * SF + nfs];
+                    jyx += sg * cy[4] * wy;
+                    jyy += sg * cy[5] * wy;
+                    jxx += sg * cx[4] * wx;
+                    jxy += sg * cx[5] * wx;
+                }
+                sum += (jyx * jxx + jyy * jxy) / (2 * l + 1);
+            }
+        }
+        acc += rel * sum;
+    }
+    gstab[g] += acc;
+}
+
+// d(G^T d)/dtau of the interface receivers at one time node.  Such a
+// receiver records [p_F, v_F] = Ai w at its point, w = (tau_f p - m.n_f,
+// tau_s v - s n_s) from the two cells' values there and A = [tau_f, n^T;
+// -n, tau_s I]; so dd/dtau_f = Ai e_0 (p - p_F) and dd/dtau_s = Ai [0; v - v_F].
+// grec[2r] (the fluid cell's tau) and grec[2r + 1] (the solid cell's) sum
+// these over the time nodes; other receivers do not depend on tau.
+__global__ void rec_tau_kernel(DevOps op, int n_rec, const int32_t* __restrict__ ri, const double* __restrict__ rd,
+                               const double* __restrict__ state, const double* __restrict__ G, double* grec) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n_rec || ri[4 * r] != 2) return;
+    const int n = op.n;
+    const double* d = rd + (size_t)r * (2 * n + 15);
+    const int qf = ri[4 * r + 1], qs = ri[4 * r + 2];
+    const double* sf = state;
+    const double* ss = state + (size_t)3 * n * op.Nf;
+    auto ev = [&](const double* base, int N, int q, int field, const double* phi) {
+        double v = 0.0;
+        for (int i = 0; i < n; ++i) v = fma(phi[i], base[(size_t)(field * n + i) * N + q], v);
+        return v;
+    };
+    const double* pf = d;
+    const double* ps = d + n;
+    const double tf = d[2 * n], ts = d[2 * n + 1];
+    const double nfx = d[2 * n + 2], nfy = d[2 * n + 3], nsx = d[2 * n + 4], nsy = d[2 * n + 5];
+    const double* Ai = d + 2 * n + 6;
+    const double p = ev(sf, op.Nf, qf, 2, pf), mx = ev(sf, op.Nf, qf, 0, pf), my = ev(sf, op.Nf, qf, 1, pf);
+    const double sxx = ev(ss, op.Ns, qs, 0, ps), syy = ev(ss, op.Ns, qs, 1, ps), sxy = ev(ss, op.Ns, qs, 2, ps);
+    const double vx = ev(ss, op.Ns, qs, 3, ps), vy = ev(ss, op.Ns, qs, 4, ps);
+    const double wf = tf * p - (mx * nfx + my * nfy);
+    const double wsx = ts * vx - (sxx * nsx + sxy * nsy);
+    const double wsy = ts * vy - (sxy * nsx + syy * nsy);
+    const double o0 = Ai[0] * wf + Ai[1] * wsx + Ai[2] * wsy;
+    const double o1 = Ai[3] * wf + Ai[4] * wsx + Ai[5] * wsy;
+    const double o2 = Ai[6] * wf + Ai[7] * wsx + Ai[8] * wsy;
+    const double* g = G + 5 * r;
+    const double hf = Ai[0] * g[0] + Ai[3] * g[1] + Ai[6] * g[2];   // (Ai^T g)
+    const double hx = Ai[1] * g[0] + Ai[4] * g[1] + Ai[7] * g[2];
+    const double hy = Ai[2] * g[0] + Ai[5] * g[1] + Ai[8] * g[2];
+    grec[2 * r] += hf * (p - o0);
+    grec[2 * r + 1] += hx * (vx - o1) + hy * (vy - o2);
+}
+
 // dL/dw for each point source: mu^T g over the source cell's coefficients
 // (the stage rate carries w(t) g, g the source's lifted load vector).
 struct SrcMeta {
@@ -258,6 +389,7 @@ __global__ void wavelet_grad_kernel(DevOps op, SrcMeta meta, const double* __res
 struct AdjBuffers {
     int64_t S, T;           // state and trace sizes
     double *ckpt, *stages, *stage_tr, *erk_work, *lam, *mu, *x, *y, *acc, *pend, *raw, *tr, *grad_f, *grad_s, *wgrad;
+    double *gstab, *grec;   // tau parts: per device cell slot; per receiver (fluid, solid)
 };
 
 int64_t adjoint_layout(const hho_ops* ops, const hho_tableau* tab, int64_t nsteps, int64_t C, AdjBuffers* b,
@@ -291,6 +423,8 @@ int64_t adjoint_layout(const hho_ops* ops, const hho_tableau* tab, int64_t nstep
     B.grad_f = take(2 * (int64_t)ops->dev.Nf);
     B.grad_s = take(4 * (int64_t)ops->dev.Ns);
     B.wgrad = take(nsteps * s * MAX_SOURCES);
+    B.gstab = take((int64_t)ops->dev.Nf + ops->dev.Ns);
+    B.grec = take(2 * (int64_t)std::max(ops->n_rec, 1));
     if (b) *b = B;
     return off;
 }
@@ -315,7 +449,7 @@ extern "C" int hho_adjoint_work_size(const hho_ops* ops, const hho_tableau* tab,
 extern "C" int hho_adjoint_vjp(hho_ops* ops, const hho_tableau* tab, double t0, double dt, int64_t nsteps,
                                int64_t checkpoint_every, const double* d_state0, const double* d_cotangent,
                                double* d_work, int64_t work_doubles, double* h_grad_cell, double* h_grad_wavelet,
-                               void* stream) {
+                               double* h_grad_tau, void* stream) {
     if (!ops || !tab || !d_state0 || !d_cotangent || !d_work || !h_grad_cell || nsteps < 1 || checkpoint_every < 1 ||
         !std::isfinite(dt)) {
         hho_set_error("hho_adjoint_vjp: bad arguments");
@@ -372,6 +506,8 @@ extern "C" int hho_adjoint_vjp(hho_ops* ops, const hho_tableau* tab, double t0, 
     if (ops->dev.Ns > 0)
         axpby_kernel<<<grid1(4 * (int64_t)ops->dev.Ns), 256, 0, st>>>(4 * (int64_t)ops->dev.Ns, 0.0, nullptr, 0.0,
                                                                        nullptr, B.grad_s);
+    axpby_kernel<<<grid1((int64_t)nthr), 256, 0, st>>>((int64_t)nthr, 0.0, nullptr, 0.0, nullptr, B.gstab);
+    axpby_kernel<<<1, 256, 0, st>>>(2 * (int64_t)std::max(ops->n_rec, 1), 0.0, nullptr, 0.0, nullptr, B.grec);
     const int64_t n_segments = (nsteps + C - 1) / C;
     for (int64_t seg = n_segments - 1; seg >= 0; --seg) {
         const int64_t n0 = seg * C;                                   // segment starts at U^{n0}
@@ -390,7 +526,7 @@ extern "C" int hho_adjoint_vjp(hho_ops* ops, const hho_tableau* tab, double t0, 
         a.op = ops->dev;
         a.inp = Y(0, 0);
         a.tr_out = TY(0, 0);
-        launch_stage_f64(ops, MODE_TRACES, a, 1, 0.0, false, stream);
+        launch_stage_f64(ops, MODE_TRACES, a, 1, 0.0, -1, 0.0, false, stream);
         for (int64_t m = 0; m < nst; ++m) {
             const double tn = t0 + (double)(n0 + m) * dt;
             for (int j = 0; j < s; ++j) {
@@ -406,7 +542,7 @@ extern "C" int hho_adjoint_vjp(hho_ops* ops, const hho_tableau* tab, double t0, 
                     a.tgt[t].dst = dc == SRC_STATE ? Y(m + 1, 0) : dc == SRC_X ? Y(m, j + 1) : partial(dc);
                     a.tgt[t].coef = P.t[t].a * dt;
                 }
-                launch_stage_f64(ops, MODE_STAGE, a, 1, tn + tab->c[j] * dt, true, stream);
+                launch_stage_f64(ops, MODE_STAGE, a, 1, tn, j, tab->c[j] * dt, true, stream);
             }
         }
         rc = check_cuda("hho_adjoint_vjp (segment recompute)");
@@ -419,6 +555,11 @@ extern "C" int hho_adjoint_vjp(hho_ops* ops, const hho_tableau* tab, double t0, 
                 inject_kernel<<<ops->n_inj, (5 * ops->n + 31) / 32 * 32, 0, st>>>(
                     ops->dev, ops->n_inj, ops->d_inj, ops->d_rec_int, ops->d_rec_dbl,
                     d_cotangent + (size_t)(n - 1) * 5 * ops->n_rec, B.lam);
+            if (ops->n_rec > 0)   // U^n is the next step's first stage value in the store
+                rec_tau_kernel<<<(ops->n_rec + 63) / 64, 64, 0, st>>>(ops->dev, ops->n_rec, ops->d_rec_int,
+                                                                     ops->d_rec_dbl, Y(m + 1, 0),
+                                                                     d_cotangent + (size_t)(n - 1) * 5 * ops->n_rec,
+                                                                     B.grec);
             if (!copy(B.acc, B.lam, S)) return HHO_ECUDA;
             axpby_kernel<<<grid1(s * S), 256, 0, st>>>(s * S, 0.0, nullptr, 0.0, nullptr, B.pend);
             for (int j = s - 1; j >= 0; --j) {
@@ -434,14 +575,16 @@ extern "C" int hho_adjoint_vjp(hho_ops* ops, const hho_tableau* tab, double t0, 
                 b.op = adj;
                 b.inp = B.x;
                 b.tr_out = B.tr;
-                launch_stage_f64(ops, MODE_TRACES, b, 1, 0.0, false, stream);
+                launch_stage_f64(ops, MODE_TRACES, b, 1, 0.0, -1, 0.0, false, stream);
                 b.tr_in = B.tr;
                 b.tr_out = nullptr;
                 b.n_tgt = 1;
                 b.tgt[0].src = nullptr;
                 b.tgt[0].dst = B.y;
                 b.tgt[0].coef = 1.0;
-                launch_stage_f64(ops, MODE_APPLY, b, 1, 0.0, false, stream);
+                launch_stage_f64(ops, MODE_APPLY, b, 1, 0.0, -1, 0.0, false, stream);
+                // the stabilisation weights' part: forward jumps of Y_{m,j} against those of x under A'
+                tau_grad_kernel<<<cblk, 128, 0, st>>>(ops->dev, adj, TY(m, j), B.tr, B.gstab);
                 const MassIn ni = {B.y, 1.0, nullptr, 0.0, nullptr};
                 MassOut no;
                 memset(&no, 0, sizeof(no));
@@ -463,7 +606,7 @@ extern "C" int hho_adjoint_vjp(hho_ops* ops, const hho_tableau* tab, double t0, 
                 r.tgt[0].src = nullptr;
                 r.tgt[0].dst = B.raw;
                 r.tgt[0].coef = 1.0;
-                launch_stage_f64(ops, MODE_RAW, r, 1, tn + tab->c[j] * dt, true, stream);
+                launch_stage_f64(ops, MODE_RAW, r, 1, tn, j, tab->c[j] * dt, true, stream);
                 grad_kernel<<<cblk, 128, 0, st>>>(ops->dev, B.mu, B.raw, B.grad_f, B.grad_s);
                 if (ops->n_src > 0 && h_grad_wavelet) {
                     SrcMeta meta;
@@ -483,10 +626,15 @@ extern "C" int hho_adjoint_vjp(hho_ops* ops, const hho_tableau* tab, double t0, 
     }
     // ---- gradients to the host, mapped to the materials ----------------------------------------
     std::vector<double> gf(2 * (size_t)ops->dev.Nf), gs(4 * (size_t)ops->dev.Ns);
+    std::vector<double> gstab((size_t)nthr), grec(2 * (size_t)std::max(ops->n_rec, 1));
     if ((!gf.empty() && cudaMemcpyAsync(gf.data(), B.grad_f, sizeof(double) * gf.size(), cudaMemcpyDeviceToHost, st) !=
                             cudaSuccess) ||
         (!gs.empty() && cudaMemcpyAsync(gs.data(), B.grad_s, sizeof(double) * gs.size(), cudaMemcpyDeviceToHost, st) !=
                             cudaSuccess) ||
+        (!gstab.empty() &&
+         cudaMemcpyAsync(gstab.data(), B.gstab, sizeof(double) * gstab.size(), cudaMemcpyDeviceToHost, st) !=
+             cudaSuccess) ||
+        cudaMemcpyAsync(grec.data(), B.grec, sizeof(double) * grec.size(), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess) {
         hho_set_error("hho_adjoint_vjp: gradient copy failed");
         return HHO_ECUDA;
@@ -503,6 +651,31 @@ extern "C" int hho_adjoint_vjp(hho_ops* ops, const hho_tableau* tab, double t0, 
                     h_grad_wavelet[(n * s + j) * ops->n_src + k2] = wg[(n * s + j) * MAX_SOURCES + k2];
     }
     const int Nf = ops->dev.Nf, Ns = ops->dev.Ns;
+    // dL/dtau per cell: the stage part (face integrals scale with h) and the
+    // interface receivers' part, mapped from device positions to cell ids
+    std::vector<double> gtau((size_t)ops->nc, 0.0);
+    std::vector<int64_t> orig_f((size_t)Nf, -1), orig_s((size_t)Ns, -1);
+    for (int64_t c = 0; c < ops->nc; ++c) {
+        const int q = ops->cell_pos[c];
+        (ops->cell_dom[c] == 0 ? orig_f : orig_s)[q] = c;
+        gtau[c] = -ops->diam[c] * gstab[(ops->cell_dom[c] == 0 ? 0 : Nf) + q];
+    }
+    {
+        std::vector<int32_t> ri(4 * (size_t)std::max(ops->n_rec, 1));
+        if (ops->n_rec > 0 &&
+            cudaMemcpy(ri.data(), ops->d_rec_int, sizeof(int32_t) * 4 * ops->n_rec, cudaMemcpyDeviceToHost) !=
+                cudaSuccess) {
+            hho_set_error("hho_adjoint_vjp: receiver table copy failed");
+            return HHO_ECUDA;
+        }
+        for (int r = 0; r < ops->n_rec; ++r)
+            if (ri[4 * r] == 2) {
+                gtau[orig_f[ri[4 * r + 1]]] += grec[2 * r];
+                gtau[orig_s[ri[4 * r + 2]]] += grec[2 * r + 1];
+            }
+    }
+    if (h_grad_tau)
+        for (int64_t c = 0; c < ops->nc; ++c) h_grad_tau[c] = gtau[c];
     for (int64_t c = 0; c < ops->nc; ++c) {
         double* o = h_grad_cell + 4 * c;   // [rho, kappa, lambda, mu]
         o[0] = o[1] = o[2] = o[3] = 0.0;
@@ -517,6 +690,22 @@ extern "C" int hho_adjoint_vjp(hho_ops* ops, const hho_tableau* tab, double t0, 
             o[0] = gav * (-1.0 / (rho * rho * h));                          // A_v = 1/(rho h)
             o[2] = gc1 / h + gr * (2.0 * mu / (l2m * l2m));                 // c1 = (lambda+2mu)/h, r = lambda/(lambda+2mu)
             o[3] = gc1 * 2.0 / h + gr * (-2.0 * lam / (l2m * l2m)) + gc3 / h;   // c3 = mu/h
+        }
+        if (ops->tau_explicit) continue;
+        // tau^f = eta_f (rho kappa)^-1/2; tau^s = eta_s (rho (lambda + 2 mu))^1/2 or eta_s (rho mu)^1/2
+        // (an optional 1/k factor cancels in these logarithmic derivatives)
+        const double t = ops->tau[c], gt = gtau[c];
+        if (ops->cell_dom[c] == 0) {
+            o[0] += gt * (-0.5 * t / rho);
+            o[1] += gt * (-0.5 * t / ops->kappa[c]);
+        } else if (ops->stab_speed == 0) {
+            const double l2m = ops->lam[c] + 2.0 * ops->mu[c];
+            o[0] += gt * (0.5 * t / rho);
+            o[2] += gt * (0.5 * t / l2m);
+            o[3] += gt * (t / l2m);
+        } else {
+            o[0] += gt * (0.5 * t / rho);
+            o[3] += gt * (0.5 * t / ops->mu[c]);
         }
     }
     return HHO_OK;

@@ -169,8 +169,11 @@ int build_plan(const hho_tableau* tab, std::vector<StagePlan>& plan, int* n_buf)
 // Launches one stage-kernel pass (FP64) over n_shots shots; and the receiver
 // kernel.  Defined in stage.cu, used by the adjoint driver.
 struct hho_ops;
-void launch_stage_f64(const hho_ops* ops, int mode, StageArgsT<double>& a, int n_shots, double t_src, bool sources,
-                      void* stream);
+// Stage launch for the adjoint and SDIRK drivers.  Sources (when `sources`)
+// are evaluated for step time tn, stage j (time tn + cdt); j < 0 for calls
+// that have no stage index (sampled source time functions are then zero).
+void launch_stage_f64(const hho_ops* ops, int mode, StageArgsT<double>& a, int n_shots, double tn, int j, double cdt,
+                      bool sources, void* stream);
 void launch_record_f64(const hho_ops* ops, const double* state, double* out, void* stream);
 int check_cuda(const char* what);
 
@@ -192,6 +195,8 @@ struct hho_ops {
     double c_max = 0.0, h_min = 0.0;
     // host-side per-cell data kept for sources/receivers
     std::vector<double> centroid, diam, rho, tau;
+    bool tau_explicit = false;   // tau given by the caller (hho_operators_build_tau): not a function of the materials
+    int32_t stab_speed = 0;      // c^s in tau^s: 0 = c_P, 1 = c_S
     std::vector<int32_t> cell_class_of;
     std::vector<std::vector<double>> class_M0inv;     // per class, n x n
     std::vector<std::vector<double>> class_normals;   // per class, 2 per face
@@ -228,6 +233,13 @@ struct hho_ops {
         void* exec = nullptr;                        // cudaGraphExec_t
     };
     std::vector<StepGraph> graphs;
+    // sampled source time functions (hho_sources_set_samples): the value of
+    // source s at step n, stage j is src_samples[(s samp_n + n) samp_s + j]
+    bool src_sampled = false;
+    std::vector<double> src_samples;
+    double samp_t0 = 0.0, samp_dt = 0.0;
+    int64_t samp_n = 0;
+    int32_t samp_s = 0;
     // sources
     int32_t n_src = 0;
     int32_t src_dom[MAX_SOURCES], src_q[MAX_SOURCES];

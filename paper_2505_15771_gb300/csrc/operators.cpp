@@ -386,9 +386,11 @@ extern "C" int hho_operators_build_tau(const hho_mesh* m, int32_t k, const doubl
         }
         ops->class_M0inv[cl] = M0inv;
         // Class block: M0 (n x n, padded to a multiple of 4 entries), then per
-        // face [nx, ny, 0, 0 | Tr rows of nP | Lift rows of fP] with nP, fP the
-        // row lengths n, f rounded up to multiples of 4, so that every row
-        // starts on a 16-byte boundary (vector loads in the kernels).
+        // face [nx, ny, |F|/h_T, 0 | Tr rows of nP | Lift rows of fP] with nP,
+        // fP the row lengths n, f rounded up to multiples of 4, so that every
+        // row starts on a 16-byte boundary (vector loads in the kernels).  The
+        // stage kernels read only the normal; the adjoint reads the relative
+        // face length for face integrals (|F| = h_T times it).
         cls_doff[cl] = (int32_t)cls_dbl.size();
         for (double v : M0) cls_dbl.push_back(v);
         while (cls_dbl.size() % 4) cls_dbl.push_back(0.0);
@@ -429,7 +431,7 @@ extern "C" int hho_operators_build_tau(const hho_mesh* m, int32_t k, const doubl
             const int nP = (n + 3) / 4 * 4, fP = (f + 3) / 4 * 4;
             cls_dbl.push_back(nx);
             cls_dbl.push_back(ny);
-            cls_dbl.push_back(0.0);
+            cls_dbl.push_back(L);
             cls_dbl.push_back(0.0);
             for (int l = 0; l < f; ++l)
                 for (int i = 0; i < nP; ++i) {
@@ -637,6 +639,8 @@ extern "C" int hho_operators_build_tau(const hho_mesh* m, int32_t k, const doubl
     ops->lam.assign(lam, lam + nc);
     ops->mu.assign(mu, mu + nc);
     ops->tau = tau;
+    ops->tau_explicit = h_tau != nullptr;
+    ops->stab_speed = P.stab_speed;
     ops->poly_xy = m->xy;
     ops->poly_ptr = m->cell_ptr;
     ops->poly_vtx = m->cell_vtx;
@@ -812,6 +816,7 @@ extern "C" int hho_sources_set(hho_ops* ops, int32_t n_src, const double* xy, co
         hho_set_error("hho_sources_set: bad arguments (at most %d sources)", MAX_SOURCES);
         return HHO_EINVAL;
     }
+    ops->src_sampled = false;
     const int n = ops->n;
     std::vector<double> g((size_t)n_src * 2 * n, 0.0);
     std::vector<double> phi(n);
@@ -874,6 +879,33 @@ extern "C" int hho_sources_set(hho_ops* ops, int32_t n_src, const double* xy, co
         }
     }
     ops->n_src = n_src;
+    return HHO_OK;
+}
+
+extern "C" int hho_sources_set_samples(hho_ops* ops, int32_t n_src, const double* xy, const double* dir,
+                                       double t_start, double dt, int64_t nsteps, int32_t s,
+                                       const double* samples) {
+    if (!ops || n_src < 0 || n_src > MAX_SOURCES || nsteps < 0 || s < 1 || s > 6 || !(dt > 0.0) ||
+        !std::isfinite(dt) || !std::isfinite(t_start) || (n_src > 0 && nsteps > 0 && !samples)) {
+        hho_set_error("hho_sources_set_samples: bad arguments (at most %d sources, 1 <= s <= 6, dt > 0)",
+                      MAX_SOURCES);
+        return HHO_EINVAL;
+    }
+    const std::vector<double> f0(n_src, 1.0), t0(n_src, 0.0), amp(n_src, 0.0);
+    const int rc = hho_sources_set(ops, n_src, xy, dir, f0.data(), t0.data(), amp.data());
+    if (rc) return rc;
+    const size_t cnt = (size_t)n_src * (size_t)nsteps * (size_t)s;
+    for (size_t i = 0; i < cnt; ++i)
+        if (!std::isfinite(samples[i])) {
+            hho_set_error("hho_sources_set_samples: sample %zu is not finite", i);
+            return HHO_EINVAL;
+        }
+    ops->src_samples.assign(samples, samples + cnt);
+    ops->samp_t0 = t_start;
+    ops->samp_dt = dt;
+    ops->samp_n = nsteps;
+    ops->samp_s = s;
+    ops->src_sampled = n_src > 0;
     return HHO_OK;
 }
 

@@ -222,14 +222,14 @@ void apply_op(hho_ops* ops, const double* v, double* out, double* tr, double a_d
     a.op = ops->dev;
     a.inp = v;
     a.tr_out = tr;
-    launch_stage_f64(ops, MODE_TRACES, a, 1, 0.0, false, st);
+    launch_stage_f64(ops, MODE_TRACES, a, 1, 0.0, -1, 0.0, false, st);
     a.tr_in = tr;
     a.tr_out = nullptr;
     a.n_tgt = 1;
     a.tgt[0].src = rate ? nullptr : v;
     a.tgt[0].dst = out;
     a.tgt[0].coef = rate ? 1.0 : -a_dt;
-    launch_stage_f64(ops, MODE_APPLY, a, 1, t, rate, st);
+    launch_stage_f64(ops, MODE_APPLY, a, 1, t, -1, 0.0, rate, st);
 }
 
 // dst[l] = V_l . w for l < nv, on the device (no synchronisation)
@@ -378,6 +378,11 @@ extern "C" int hho_sdirk_step(hho_ops* ops, const hho_tableau* tab, double t0, d
         max_iter < 1 || nsteps < 0 || !(dt > 0.0) || !std::isfinite(dt) || !std::isfinite(t0) || !(tol > 0.0)) {
         hho_set_error("hho_sdirk_step: bad arguments (SDIRK tableau, dt > 0, tol > 0, 1 <= restart <= %d, "
                       "max_iter >= 1)", MAX_RESTART);
+        return HHO_EINVAL;
+    }
+    if (ops->src_sampled) {
+        hho_set_error("hho_sdirk_step: sampled source time functions are indexed by ERK stages; use "
+                      "hho_sources_set for the implicit path");
         return HHO_EINVAL;
     }
     int64_t its = 0;

@@ -1321,20 +1321,32 @@ const float* shot_g_of<float>(const hho_ops* ops) { return ops->d_shot_src_g32; 
 template <>
 const f2x* shot_g_of<f2x>(const hho_ops* ops) { return ops->d_shot_src_gx; }
 
+// Value of point source s for the stage of step time tn, stage j (time
+// tn + cdt): its Ricker wavelet, or, for a sampled time function, the sample
+// of step round((tn - t_start) / dt) and stage j (zero outside the sampled
+// steps and for j < 0, a call with no stage index).
+double source_value(const hho_ops* ops, int s, double tn, int j, double cdt) {
+    if (!ops->src_sampled) return ricker(tn + cdt, ops->src_f0[s], ops->src_t0[s], ops->src_amp[s]);
+    if (j < 0 || j >= ops->samp_s) return 0.0;
+    const int64_t n = std::llround((tn - ops->samp_t0) / ops->samp_dt);
+    if (n < 0 || n >= ops->samp_n) return 0.0;
+    return ops->src_samples[((size_t)s * ops->samp_n + n) * ops->samp_s + j];
+}
+
 template <class T>
-void fill_sources(const hho_ops* ops, StageArgsT<T>& a, double t, int n_shots) {
+void fill_sources(const hho_ops* ops, StageArgsT<T>& a, double tn, int j, double cdt, int n_shots) {
     a.n_src = ops->n_src;
     a.src_g = src_g_of<T>(ops);
     for (int s = 0; s < ops->n_src; ++s) {
         a.src_dom[s] = ops->src_dom[s];
         a.src_q[s] = ops->src_q[s];
-        a.src_w[s] = T(ricker(t, ops->src_f0[s], ops->src_t0[s], ops->src_amp[s]));
+        a.src_w[s] = T(source_value(ops, s, tn, j, cdt));
     }
     if (ops->n_shot_src > 0 && n_shots <= ops->n_shot_src) {
         a.shot_src_dom = ops->d_shot_src_dom;
         a.shot_src_q = ops->d_shot_src_q;
         a.shot_src_g = shot_g_of<T>(ops);
-        a.shot_src_w = T(ricker(t, ops->shot_f0, ops->shot_t0, ops->shot_amp));
+        a.shot_src_w = T(ricker(tn + cdt, ops->shot_f0, ops->shot_t0, ops->shot_amp));
     } else {
         a.shot_src_dom = nullptr;
         a.shot_src_q = nullptr;
@@ -1344,6 +1356,21 @@ void fill_sources(const hho_ops* ops, StageArgsT<T>& a, double t, int n_shots) {
 }
 
 }  // namespace
+
+extern "C" int hho_ricker_samples(const hho_tableau* tab, double t_start, double dt, int64_t nsteps, double f0,
+                                  double t0, double amp, double* h_out) {
+    if (!tab || tab->s < 1 || tab->s > 6 || nsteps < 0 || !(dt > 0.0) || !std::isfinite(dt) ||
+        !std::isfinite(t_start) || !(f0 > 0.0) || (nsteps > 0 && !h_out)) {
+        hho_set_error("hho_ricker_samples: bad arguments");
+        return HHO_EINVAL;
+    }
+    // the same rounded stage times as the ERK loops: (t_start + n dt) + c_j dt
+    for (int64_t n = 0; n < nsteps; ++n) {
+        const double tn = t_start + (double)n * dt;
+        for (int j = 0; j < tab->s; ++j) h_out[n * tab->s + j] = ricker(tn + tab->c[j] * dt, f0, t0, amp);
+    }
+    return HHO_OK;
+}
 
 extern "C" int hho_work_size(const hho_ops* ops, const hho_tableau* tab, int64_t* out) {
     if (!ops || !tab || !out) {
@@ -1370,7 +1397,7 @@ __global__ void clock_advance_kernel(StageClock* c) { c->step += 1; }
 // Sources for a stage evaluated from the device clock (graph replay).
 template <class T>
 void fill_sources_clock(const hho_ops* ops, StageArgsT<T>& a, double c_stage, double dt, int n_shots) {
-    fill_sources<T>(ops, a, 0.0, n_shots);   // cells, vectors and pointers
+    fill_sources<T>(ops, a, 0.0, -1, 0.0, n_shots);   // cells, vectors and pointers
     for (int s = 0; s < MAX_SOURCES; ++s) a.src_w[s] = T(0);
     a.shot_src_w = T(0);
     a.clock = ops->d_clock;
@@ -1446,7 +1473,7 @@ static int erk_run(hho_ops* ops, const hho_tableau* tab, double t0, double dt, i
     a.tr_out = tr[0];
     a.n_tgt = 0;
     const bool use_graph =
-        !ops->prof_on && ops->d_clock &&
+        !ops->prof_on && ops->d_clock && !ops->src_sampled &&
         (ops->launch_mode == HHO_LAUNCH_GRAPH ||
          (ops->launch_mode == HHO_LAUNCH_AUTO && (int64_t)grid.x * n_shots <= 2048 && nsteps >= 8));
     launch_k<T, MODE_TRACES>(ops->k, a, grid, st);
@@ -1550,7 +1577,7 @@ static int erk_run(hho_ops* ops, const hho_tableau* tab, double t0, double dt, i
                 a.tgt[t].dst = resolve(P.t[t].dst);
                 a.tgt[t].coef = T(P.t[t].a * dt);
             }
-            fill_sources<T>(ops, a, tn + tab->c[j] * dt, n_shots);
+            fill_sources<T>(ops, a, tn, j, tab->c[j] * dt, n_shots);
             const bool prof = ops->prof_on && 2 * ops->prof_n + 1 < (int)ops->prof_events.size();
             if (prof) cudaEventRecord((cudaEvent_t)ops->prof_events[2 * ops->prof_n], st);
             launch_k<T, MODE_STAGE>(ops->k, a, grid, st);
@@ -1915,7 +1942,7 @@ static int apply_t(hho_ops* ops, double t, const T* d_state, T* d_rate, T* d_tra
     a.tgt[0].src = nullptr;
     a.tgt[0].dst = d_rate;
     a.tgt[0].coef = T(1.0);
-    fill_sources<T>(ops, a, t, 1);
+    fill_sources<T>(ops, a, t, -1, 0.0, 1);
     launch_k<T, MODE_APPLY>(ops->k, a, grid, st);
     return check_launch("hho_apply (stage kernel)");
 }
@@ -1924,6 +1951,10 @@ extern "C" int hho_apply(hho_ops* ops, double t, const double* d_state, double* 
                          void* stream) {
     if (!ops || !d_state || !d_rate || !d_work) {
         hho_set_error("hho_apply: null pointer");
+        return HHO_EINVAL;
+    }
+    if (ops->src_sampled) {
+        hho_set_error("hho_apply: sampled source time functions are indexed by ERK stages, not by time");
         return HHO_EINVAL;
     }
     cudaStream_t st = (cudaStream_t)stream;
@@ -2185,14 +2216,14 @@ extern "C" int hho_energy_static(hho_ops* ops, const double* d_state, double* d_
 }
 
 // ---- launchers for the adjoint driver (adjoint.cu) -----------------------------------
-void launch_stage_f64(const hho_ops* ops, int mode, StageArgsT<double>& a, int n_shots, double t_src, bool sources,
-                      void* stream) {
+void launch_stage_f64(const hho_ops* ops, int mode, StageArgsT<double>& a, int n_shots, double tn, int j, double cdt,
+                      bool sources, void* stream) {
     const dim3 grid((ops->dev.Nf + ops->dev.Ns + 127) / 128, n_shots);
     if (grid.x == 0) return;
     a.state_stride = ops->n_state;
     a.trace_stride = ops->trace_doubles;
     if (sources) {
-        fill_sources<double>(ops, a, t_src, n_shots);
+        fill_sources<double>(ops, a, tn, j, cdt, n_shots);
     } else {
         a.n_src = 0;
         a.shot_src_q = nullptr;

@@ -75,6 +75,8 @@ _SIGS = {
     "hho_tableau_erk": (C.c_int, [_I32, C.POINTER(Tableau)]),
     "hho_work_size": (C.c_int, [_P, C.POINTER(Tableau), C.POINTER(_I64)]),
     "hho_sources_set": (C.c_int, [_P, _I32, _P, _P, _P, _P, _P]),
+    "hho_sources_set_samples": (C.c_int, [_P, _I32, _P, _P, _D, _D, _I64, _I32, _P]),
+    "hho_ricker_samples": (C.c_int, [C.POINTER(Tableau), _D, _D, _I64, _D, _D, _D, _P]),
     "hho_erk_step": (C.c_int, [_P, C.POINTER(Tableau), _D, _D, _I64, _P, _P, _P]),
     "hho_set_arithmetic": (C.c_int, [_P, _I32]),
     "hho_set_launch_mode": (C.c_int, [_P, _I32]),
@@ -96,7 +98,7 @@ _SIGS = {
     "hho_cfl_bracket": (C.c_int, [_P, C.POINTER(Tableau), _P, _D, _I64, _D, _D, _I64, _P, _P, C.POINTER(_I64),
                                   C.POINTER(_I64), _P]),
     "hho_adjoint_work_size": (C.c_int, [_P, C.POINTER(Tableau), _I64, _I64, C.POINTER(_I64)]),
-    "hho_adjoint_vjp": (C.c_int, [_P, C.POINTER(Tableau), _D, _D, _I64, _I64, _P, _P, _P, _I64, _P, _P, _P]),
+    "hho_adjoint_vjp": (C.c_int, [_P, C.POINTER(Tableau), _D, _D, _I64, _I64, _P, _P, _P, _I64, _P, _P, _P, _P]),
     "hho_batch_sizes": (C.c_int, [_P, C.POINTER(Tableau), _I32, _I32, C.POINTER(_I64), C.POINTER(_I64)]),
     "hho_batch_pack": (C.c_int, [_P, _I32, _I32, _P, _P, _P]),
     "hho_batch_unpack": (C.c_int, [_P, _I32, _I32, _P, _P, _P]),
@@ -261,6 +263,25 @@ def hho_sources_set(ops, xy, direction, f0, t0, amp):
     _check(lib().hho_sources_set(ops, xy.shape[0], _ptr(xy), _ptr(d), *[_ptr(v) for v in a]))
 
 
+def hho_sources_set_samples(ops, xy, direction, t_start, dt, samples):
+    """Point sources with sampled time functions; samples: [n_src, nsteps, s] (one value per step and stage)."""
+    xy = _arr(xy, np.float64).reshape(-1, 2)
+    d = _arr(direction, np.float64).reshape(-1, 2)
+    w = _arr(samples, np.float64)
+    if w.ndim != 3 or w.shape[0] != xy.shape[0]:
+        raise ValueError("samples must have shape [n_src, nsteps, s]")
+    _check(lib().hho_sources_set_samples(ops, xy.shape[0], _ptr(xy), _ptr(d), float(t_start), float(dt),
+                                         w.shape[1], w.shape[2], _ptr(w)))
+
+
+def hho_ricker_samples(tab, t_start, dt, nsteps, f0, t0, amp):
+    """[nsteps, s] Ricker values at the tableau's stage times (the rounding of the ERK loops)."""
+    out = np.zeros((int(nsteps), tab.s), np.float64)
+    _check(lib().hho_ricker_samples(C.byref(tab), float(t_start), float(dt), int(nsteps), float(f0), float(t0),
+                                    float(amp), _ptr(out)))
+    return out
+
+
 def hho_tableau_sdirk(s):
     """SDIRK tableau: s = 1, 2 (as printed), 3 (SDIRK(3,4)) or 23 (order-3 2-stage)."""
     t = Tableau()
@@ -392,11 +413,13 @@ def hho_adjoint_work_size(ops, tab, nsteps, checkpoint_every):
 
 
 def hho_adjoint_vjp(ops, tab, t0, dt, nsteps, checkpoint_every, d_state0, d_cotangent, d_work, work_doubles,
-                    n_cells, n_src=0, stream=0):
-    """Returns (grad_cell [n_cells, 4] = dL/d(rho, kappa, lambda, mu), grad_wavelet [nsteps, s, n_src] or None)."""
+                    n_cells, n_src=0, stream=0, with_tau=False):
+    """Returns (grad_cell [n_cells, 4] = dL/d(rho, kappa, lambda, mu), grad_wavelet [nsteps, s, n_src] or None),
+    and dL/dtau [n_cells] as a third value when with_tau."""
     g = np.zeros((n_cells, 4), np.float64)
     w = np.zeros((int(nsteps), tab.s, n_src), np.float64) if n_src > 0 else None
+    gt = np.zeros(n_cells, np.float64) if with_tau else None
     _check(lib().hho_adjoint_vjp(ops, C.byref(tab), float(t0), float(dt), int(nsteps), int(checkpoint_every),
                                  d_state0, d_cotangent, d_work, int(work_doubles), _ptr(g),
-                                 None if w is None else _ptr(w), stream))
-    return g, w
+                                 None if w is None else _ptr(w), None if gt is None else _ptr(gt), stream))
+    return (g, w, gt) if with_tau else (g, w)

@@ -1,6 +1,7 @@
 """Discrete adjoint on the GPU (hho_adjoint_vjp) against the oracle's dense
 reverse mode and against central differences of the GPU forward traces.
-The stabilisation weights are held fixed (tau frozen at the model)."""
+The stabilisation weights follow the materials (Sec. 3.3) unless they are
+given explicitly (hho_operators_build_tau), which freezes them."""
 import numpy as np
 import pytest
 
@@ -58,7 +59,7 @@ def gpu_traces(hho, ops, U0, dt, nsteps, s=4):
     return seis.cpu().numpy()
 
 
-def gpu_vjp(hho, ops, U0, dt, nsteps, G, nc, s=4, ckpt=5):
+def gpu_vjp(hho, ops, U0, dt, nsteps, G, nc, s=4, ckpt=5, with_tau=False):
     tab = hho.hho_tableau_erk(s)
     lay = hho.hho_state_layout(ops)
     c = torch.as_tensor(U0).cuda()
@@ -68,17 +69,20 @@ def gpu_vjp(hho, ops, U0, dt, nsteps, G, nc, s=4, ckpt=5):
     work = torch.empty(nw, dtype=torch.float64, device="cuda")
     g = torch.as_tensor(G.reshape(nsteps, len(PTS), 5)).cuda().contiguous()
     return hho.hho_adjoint_vjp(ops, tab, 0.0, dt, nsteps, ckpt, x0.data_ptr(), g.data_ptr(), work.data_ptr(), nw,
-                               nc, n_src=1)
+                               nc, n_src=1, with_tau=with_tau)
 
 
-@pytest.mark.parametrize("k,s", [(1, 4), (2, 3)])
-def test_adjoint_matches_oracle(lib, k, s):
-    """Material gradients dL/d(rho, kappa, lambda, mu) and wavelet gradients
-    dL/dw(t_i) of L = <G, traces> agree with the oracle's dense reverse mode."""
+@pytest.mark.parametrize("k,s,frozen", [(1, 4, False), (2, 3, False), (2, 4, True)])
+def test_adjoint_matches_oracle(lib, k, s, frozen):
+    """Material gradients dL/d(rho, kappa, lambda, mu), wavelet gradients
+    dL/dw(t_i) and (tau following the materials) dL/dtau of L = <G, traces>
+    agree with the oracle's dense reverse mode; cell and interface receivers."""
     hho, solver = lib
     md = synth.quad_grid(6, 6)
     med = media(md, 1)
     Sy = oracle_system(md, k, med)
+    if frozen:
+        Sy = oracle_system(md, k, med, tau_override=Sy.tau)
     st = E.Stepper(Sy)
     load, _ = Sy.point_load(*SRC, direction=(0.0, 1.0))
     dense = ADJ.DenseAdjoint(st, PTS, load, lambda t: synth.ricker(t, F0))
@@ -87,24 +91,27 @@ def test_adjoint_matches_oracle(lib, k, s):
     U0 = synth.random_state(Sy.nT, 5)
     G = rng.standard_normal((nsteps, len(PTS) * 5))
     tr_ref, _ = dense.run(U0, 0.0, dt, nsteps, "erk%d" % s)
-    ops = gpu_problem(hho, md, k, med)
+    ops = gpu_problem(hho, md, k, med, Sy.tau if frozen else None)
     try:
         tr = gpu_traces(hho, ops, U0, dt, nsteps, s)
         assert np.linalg.norm(tr.reshape(nsteps, -1) - tr_ref) <= 1e-12 * np.linalg.norm(tr_ref)
-        g_ref, w_ref = dense.vjp(U0, 0.0, dt, nsteps, G, "erk%d" % s)
-        g, w = gpu_vjp(hho, ops, U0, dt, nsteps, G, md.n_cells, s)
+        g_ref, w_ref, t_ref = dense.vjp(U0, 0.0, dt, nsteps, G, "erk%d" % s, with_tau=True)
+        g, w, gt = gpu_vjp(hho, ops, U0, dt, nsteps, G, md.n_cells, s, with_tau=True)
     finally:
         hho.hho_ops_destroy(ops)
     eg = np.linalg.norm(g - g_ref) / np.linalg.norm(g_ref)
     ew = np.linalg.norm(w[:, :, 0] - w_ref) / np.linalg.norm(w_ref)
-    print("k=%d ERK%d gradient rel err %.3e wavelet %.3e" % (k, s, eg, ew))
-    assert eg <= 1e-10 and ew <= 1e-10
+    et = np.linalg.norm(gt - t_ref) / np.linalg.norm(t_ref)
+    print("k=%d ERK%d frozen=%s gradient rel err %.3e wavelet %.3e dL/dtau %.3e" % (k, s, frozen, eg, ew, et))
+    assert eg <= 1e-10 and ew <= 1e-10 and et <= 1e-10
 
 
-def test_adjoint_matches_finite_differences(lib):
+@pytest.mark.parametrize("frozen", [False, True])
+def test_adjoint_matches_finite_differences(lib, frozen):
     """<grad, delta> against central differences of L = <G, traces> computed
-    with the GPU forward, tau frozen (hho_operators_build_tau), on 6 seeded
-    random material directions: relative error <= 1e-6."""
+    with the GPU forward on 6 seeded random material directions, relative
+    error <= 1e-6.  Unfrozen: every forward rebuilds tau from the materials;
+    frozen: tau fixed at the base model (hho_operators_build_tau)."""
     hho, solver = lib
     md = synth.quad_grid(8, 8)
     med = media(md, 2)
@@ -113,6 +120,9 @@ def test_adjoint_matches_finite_differences(lib):
     rng = np.random.default_rng(11)
     base = gpu_problem(hho, md, 2, med)
     tau = hho.hho_ops_tau(base, nc)
+    if frozen:
+        hho.hho_ops_destroy(base)
+        base = gpu_problem(hho, md, 2, med, tau)
     lay = hho.hho_state_layout(base)
     U0 = synth.random_state(lay.n_canonical, 3)
     G = rng.standard_normal((nsteps, len(PTS) * 5))
@@ -126,7 +136,8 @@ def test_adjoint_matches_finite_differences(lib):
 
         def L(sign):
             ops = gpu_problem(hho, md, 2, (rho + sign * eps * d[:, 0], lam + sign * eps * d[:, 2],
-                                           mu + sign * eps * d[:, 3], kap + sign * eps * d[:, 1]), tau)
+                                           mu + sign * eps * d[:, 3], kap + sign * eps * d[:, 1]),
+                              tau if frozen else None)
             try:
                 tr = gpu_traces(hho, ops, U0, dt, nsteps)
             finally:
@@ -135,40 +146,72 @@ def test_adjoint_matches_finite_differences(lib):
         fd = (L(1) - L(-1)) / (2 * eps)
         an = float(np.sum(g * d))
         worst = max(worst, abs(fd - an) / abs(fd))
-    print("adjoint vs central differences, worst rel err %.3e" % worst)
+    print("adjoint (frozen=%s) vs central differences, worst rel err %.3e" % (frozen, worst))
     assert worst <= 1e-6
+
+
+def test_sampled_ricker_sources_step_like_ricker_sources(lib):
+    """hho_sources_set_samples with the library's Ricker samples
+    (hho_ricker_samples) gives bit-identical traces to hho_sources_set with
+    the same wavelet (stream launches: the same host-side values)."""
+    hho, solver = lib
+    md = synth.quad_grid(6, 6)
+    med = media(md, 3)
+    nsteps, dt, s = 12, 0.004, 4
+    U0 = 0.1 * synth.random_state(gpu_layout_n(hho, md, med), 2)
+    out = []
+    for sampled in (False, True):
+        ops = gpu_problem(hho, md, 2, med)
+        try:
+            hho.hho_set_launch_mode(ops, hho.HHO_LAUNCH_STREAM)
+            if sampled:
+                w = hho.hho_ricker_samples(hho.hho_tableau_erk(s), 0.0, dt, nsteps, F0, 1.0 / F0, 1.0)
+                hho.hho_sources_set_samples(ops, [SRC], [(0.0, 1.0)], 0.0, dt, w[None])
+            out.append(gpu_traces(hho, ops, U0, dt, nsteps, s))
+        finally:
+            hho.hho_ops_destroy(ops)
+    assert np.array_equal(out[0], out[1])
+    assert np.abs(out[0]).max() > 0
+
+
+def gpu_layout_n(hho, md, med):
+    ops = gpu_problem(hho, md, 2, med)
+    n = hho.hho_state_layout(ops).n_canonical
+    hho.hho_ops_destroy(ops)
+    return n
 
 
 def test_autograd_traces_misfit(lib):
     """torch.autograd.Function: L = 1/2 |traces - observed|^2; backward gives
-    dL/d(rho, lambda, mu, kappa, amplitude) through the GPU adjoint; checked
-    against central differences (tau frozen) in a random direction."""
+    dL/d(rho, lambda, mu, kappa) and dL/dw per step and stage of the source
+    time function through the GPU adjoint, with tau following the materials;
+    checked against central differences of the same forward in a random
+    direction of materials and wavelet."""
     hho, solver = lib
     from paper_2505_15771_gb300.autograd import TraceModel, Traces
     md = synth.quad_grid(6, 6)
     rho, lam, mu, kap = media(md, 4)
     nsteps, dt = 20, 0.004
-    model = TraceModel(md, 1, SRC, (0.0, 1.0), F0, PTS, dt, nsteps, stages=4, checkpoint_every=6)
-    lay_probe = gpu_problem(hho, md, 1, (rho, lam, mu, kap))
-    U0 = 0.1 * synth.random_state(hho.hho_state_layout(lay_probe).n_canonical, 9)
-    tau = hho.hho_ops_tau(lay_probe, md.n_cells)
-    hho.hho_ops_destroy(lay_probe)
+    model = TraceModel(md, 1, SRC, (0.0, 1.0), PTS, dt, nsteps, stages=4, checkpoint_every=6)
+    U0 = 0.1 * synth.random_state(hho_layout_k1(hho, md, (rho, lam, mu, kap)), 9)
     rng = np.random.default_rng(5)
     obs = torch.as_tensor(rng.standard_normal((nsteps, len(PTS), 5))).cuda()
     T = [torch.tensor(v, dtype=torch.float64, requires_grad=True) for v in (rho, lam, mu, kap)]
-    amp = torch.tensor(1.0, dtype=torch.float64, requires_grad=True)
-    tr = Traces.apply(T[0], T[1], T[2], T[3], amp, model, U0)
+    w0 = model.ricker(F0)
+    wav = w0.clone().requires_grad_(True)
+    tr = Traces.apply(T[0], T[1], T[2], T[3], wav, model, U0)
     loss = 0.5 * ((tr - obs) ** 2).sum()
     loss.backward()
+    assert wav.grad.shape == (nsteps, 4)
     d = rng.standard_normal((md.n_cells, 4)) * np.stack([rho, lam, mu, kap], axis=1) * 0.05
-    da = 0.3
-    an = sum(float(np.sum(T[j].grad.numpy() * d[:, j])) for j in range(4)) + float(amp.grad) * da
+    dw = rng.standard_normal((nsteps, 4)) * 0.3
+    an = sum(float(np.sum(T[j].grad.numpy() * d[:, j])) for j in range(4)) + float(np.sum(wav.grad.numpy() * dw))
     eps = 1e-6
     obs_np = obs.cpu().numpy()
 
     def L(sign):
         ops = model.build(rho + sign * eps * d[:, 0], lam + sign * eps * d[:, 1], mu + sign * eps * d[:, 2],
-                          kap + sign * eps * d[:, 3], 1.0 + sign * eps * da, tau)
+                          kap + sign * eps * d[:, 3], w0.numpy() + sign * eps * dw)
         try:
             t = gpu_traces(hho, ops, U0, dt, nsteps)
         finally:
@@ -177,3 +220,12 @@ def test_autograd_traces_misfit(lib):
     fd = (L(1) - L(-1)) / (2 * eps)
     print("autograd vs central differences: %.12e %.12e" % (an, fd))
     assert abs(fd - an) <= 1e-6 * abs(fd)
+
+
+def hho_layout_k1(hho, md, med):
+    mesh = hho.hho_mesh_create(md.xy, md.cell_ptr, md.cell_vtx, md.cell_domain)
+    ops = hho.hho_operators_build_tau(mesh, 1, *med, None)
+    hho.hho_mesh_destroy(mesh)
+    n = hho.hho_state_layout(ops).n_canonical
+    hho.hho_ops_destroy(ops)
+    return n

@@ -1,9 +1,9 @@
 """The adjoint workload at full size: 256 x 256 quads, k = 2, two-layer
 medium, true model with a +10 % Gaussian v_S anomaly, smooth background as
 the current model, 8 shots, 128 receivers, 800 ERK4 steps, checkpoints every
-50 steps, L2 receiver misfit.  The GPU gradient (tau frozen at the background)
-is checked against central differences of the GPU misfit on 20 seeded
-random directions."""
+50 steps, L2 receiver misfit.  The GPU gradient (the stabilisation weights
+following the materials, as in the forward model) is checked against
+central differences of the GPU misfit on 20 seeded random directions."""
 import time
 
 import numpy as np
@@ -34,9 +34,9 @@ def test_c4_misfit_gradient_vs_central_differences(lib):
     stream = torch.cuda.current_stream().cuda_stream
     tab = hho.hho_tableau_erk(4)
 
-    def build(media, tau=None):
+    def build(media):
         mesh = hho.hho_mesh_create(md.xy, md.cell_ptr, md.cell_vtx, md.cell_domain)
-        ops = hho.hho_operators_build_tau(mesh, k, *media, tau)
+        ops = hho.hho_operators_build(mesh, k, *media)
         hho.hho_mesh_destroy(mesh)
         hho.hho_receivers_set(ops, w["receivers"])
         return ops
@@ -45,7 +45,6 @@ def test_c4_misfit_gradient_vs_central_differences(lib):
         hho.hho_sources_set(ops, [w["sources"][s]], [(0.0, 1.0)], [w["f0"]], [1.0 / w["f0"]], [1.0])
 
     probe = build(w["background"])
-    tau = hho.hho_ops_tau(probe, nc)
     dt = hho.hho_cfl_dt(probe, 0.122, 0.9)
     lay = hho.hho_state_layout(probe)
     hho.hho_ops_destroy(probe)
@@ -60,7 +59,7 @@ def test_c4_misfit_gradient_vs_central_differences(lib):
 
     shots = len(w["sources"])
     observed = []
-    ops = build(w["true"], tau)
+    ops = build(w["true"])
     for s in range(shots):
         shot(ops, s)
         observed.append(traces(ops).clone())
@@ -68,7 +67,7 @@ def test_c4_misfit_gradient_vs_central_differences(lib):
 
     def misfit(media):
         J = 0.0
-        ops = build(media, tau)
+        ops = build(media)
         for s in range(shots):
             shot(ops, s)
             J += 0.5 * float(((traces(ops) - observed[s]) ** 2).sum())
@@ -77,7 +76,7 @@ def test_c4_misfit_gradient_vs_central_differences(lib):
 
     grad = np.zeros((nc, 4))
     zero0 = torch.zeros(lay.n_state, dtype=torch.float64, device="cuda")
-    ops = build(w["background"], tau)
+    ops = build(w["background"])
     nw = hho.hho_adjoint_work_size(ops, tab, nsteps, ckpt)
     wk = torch.empty(nw, dtype=torch.float64, device="cuda")
     torch.cuda.synchronize()

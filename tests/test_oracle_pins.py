@@ -624,9 +624,12 @@ def test_compliance_derivatives_match_finite_differences():
     assert np.allclose(A.compliance_dmu(lam, mu, Sm), dm, rtol=1e-7, atol=1e-12)
 
 
-def test_dense_adjoint_matches_finite_differences():
-    """The oracle's reverse mode (with tau frozen) against central differences
-    of the forward traces in random material directions."""
+@pytest.mark.parametrize("frozen", [False, True])
+def test_dense_adjoint_matches_finite_differences(frozen):
+    """The oracle's reverse mode against central differences of the forward
+    traces (cell and interface receivers) in random material directions.
+    Unfrozen: tau follows the materials (Sec. 3.3), as in the forward model;
+    frozen: tau given explicitly and held fixed."""
     from oracle import adjoint as ADJ
     md = synth.quad_grid(4, 4)
     rng = np.random.default_rng(3)
@@ -642,7 +645,7 @@ def test_dense_adjoint_matches_finite_differences():
     src = (0.55, 0.3)
 
     def build(r, l, m_, k_):
-        S = system(md, 1, media=(r, l, m_, k_), tau_override=tau)
+        S = system(md, 1, media=(r, l, m_, k_), tau_override=tau if frozen else None)
         st = E.Stepper(S)
         load, _ = S.point_load(*src, direction=(0.0, 1.0))
         return ADJ.DenseAdjoint(st, pts, load, lambda t: synth.ricker(t, 5.0))
@@ -662,3 +665,25 @@ def test_dense_adjoint_matches_finite_differences():
         fd = (J(1) - J(-1)) / (2 * eps)
         an = float(np.sum(grad[:, [0, 1, 2, 3]] * d))
         assert abs(fd - an) <= 1e-6 * abs(fd), (fd, an)
+
+
+def test_dense_adjoint_tau_part_changes_the_gradient():
+    """The stabilisation weights' share of the material gradient is not
+    negligible (so the unfrozen finite-difference check above tests it): with
+    tau following the materials the gradient differs from the tau-frozen one
+    by more than 1 % in norm."""
+    from oracle import adjoint as ADJ
+    md = synth.quad_grid(4, 4)
+    rng = np.random.default_rng(8)
+    nc = md.n_cells
+    sol = md.cell_domain == 1
+    med = (1 + rng.random(nc), np.where(sol, 3 + rng.random(nc), 0.0), np.where(sol, 2 + rng.random(nc), 0.0),
+           np.where(sol, 0.0, 1 + rng.random(nc)))
+    pts = [(0.3, 0.2), (0.6, 0.7), (0.4, 0.5)]
+    G = rng.standard_normal((10, len(pts) * 5))
+    out = []
+    for tau in (None, system(md, 1, media=med).tau):
+        S = system(md, 1, media=med, tau_override=tau)
+        adj = ADJ.DenseAdjoint(E.Stepper(S), pts)
+        out.append(adj.vjp(synth.random_state(S.nT, 4), 0.0, 0.01, 10, G)[0])
+    assert np.linalg.norm(out[0] - out[1]) > 0.01 * np.linalg.norm(out[1])
