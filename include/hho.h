@@ -109,6 +109,16 @@ int hho_mesh_tables(const hho_mesh* mesh, int64_t* h_face_cells, int64_t* h_cell
 
 void hho_mesh_destroy(hho_mesh* mesh);
 
+/* The sub-mesh of the listed cells of `parent` (h_cells: n_cells distinct
+ * parent cell ids; the sub-mesh numbers them 0..n_cells-1 in that order), for
+ * a subdomain of a partition: the owned cells plus one layer of ghost cells.
+ * Faces whose other cell is not listed become boundary faces.  Each class
+ * keeps the reference geometry of the parent's class (the parent's first
+ * cell of that class), so operators built on the sub-mesh use the parent's
+ * class matrices bit for bit and a cell's stage arithmetic is the same in
+ * both.  Periodic vertex identifications are kept.  Host only. */
+int hho_mesh_submesh(const hho_mesh* parent, int64_t n_cells, const int64_t* h_cells, hho_mesh** out);
+
 /* ------------------------------------------------------------------------- */
 /* Operators (Sec. 3.3: Eq. mass, Eq. rec, Eq. stab, coupling, Eq. rhs).      */
 /* ------------------------------------------------------------------------- */
@@ -265,6 +275,11 @@ int hho_sources_set(hho_ops* ops, int32_t n_src, const double* h_xy, const doubl
 int hho_sources_set_samples(hho_ops* ops, int32_t n_src, const double* h_xy, const double* h_dir, double t_start,
                             double dt, int64_t nsteps, int32_t s_stages, const double* h_samples);
 
+/* The cell (input order) that sources and receivers at the points h_xy
+ * (2 n values) belong to: the lowest-index cell containing the point, or -1
+ * outside the mesh.  Host only. */
+int hho_locate_points(const hho_ops* ops, int64_t n, const double* h_xy, int64_t* h_cells);
+
 /* Ricker wavelet samples at the stage times of the tableau:
  * h_out[n s + j] = w(t_start + n dt + c_j dt) with the wavelet of
  * hho_sources_set, the times rounded as the ERK loops round them.
@@ -382,6 +397,41 @@ int hho_batch_sources_set(hho_ops* ops, int32_t n_shots, const double* h_xy, con
  * every step.  No allocation, no host synchronisation. */
 int hho_batch_erk_step(hho_ops* ops, const hho_tableau* tab, int32_t n_shots, int32_t precision, double t0,
                        double dt, int64_t nsteps, void* d_state, void* d_work, void* d_seismogram, void* stream);
+
+/* ------------------------------------------------------------------------- */
+/* One stage at a time, for subdomain drivers (a mesh partition with a halo   */
+/* exchange of the published face traces between stages; no counterpart in   */
+/* the paper, whose implementation is serial).                                */
+/* ------------------------------------------------------------------------- */
+
+/* hho_erk_traces publishes the face traces of d_state into trace buffer 0 of
+ * d_work (as hho_erk_step does at the start of a call).  hho_erk_stage runs
+ * stage j of step n (step time tn, sources at tn + c_j dt): it reads trace
+ * buffer (n s + j) % 2 and writes the traces of its result into buffer
+ * (n s + j + 1) % 2; stage s-1 writes the new state into d_state.  The
+ * sequence traces, stage(0, 0), ..., stage(nsteps-1, s-1) gives the same bits
+ * as hho_erk_step in stream launch mode (HHO_LAUNCH_STREAM).  d_work as for
+ * hho_erk_step; FP64 arithmetic only (HHO_EINVAL otherwise).  No receivers
+ * are recorded (hho_record).  Stream-ordered, no synchronisation. */
+int hho_erk_traces(hho_ops* ops, const hho_tableau* tab, const double* d_state, double* d_work, void* stream);
+int hho_erk_stage(hho_ops* ops, const hho_tableau* tab, int64_t n, int32_t j, double tn, double dt, double* d_state,
+                  double* d_work, void* stream);
+
+/* Offset, in doubles from d_work, of trace buffer `which` (0 or 1). */
+int hho_trace_buffer_offset(const hho_ops* ops, const hho_tableau* tab, int32_t which, int64_t* offset);
+
+/* Offsets within one trace buffer of the traces w that cell h_cells[i]
+ * (mesh input order) publishes on its local face h_faces[i] (the face from
+ * its vertex i to vertex i+1), which is what the neighbour across that face
+ * reads: f values (Legendre coefficients) in a fluid cell, 2f (x then y
+ * components) in a solid cell.  h_out: [n][2f], unused entries -1.  Host. */
+int hho_trace_offsets(const hho_ops* ops, int64_t n, const int64_t* h_cells, const int32_t* h_faces,
+                      int64_t* h_out);
+
+/* d_dst[i] = d_src[d_idx[i]] (gather), d_dst[d_idx[i]] = d_src[i] (scatter),
+ * i < n, on the device: the halo exchange's packing of trace entries. */
+int hho_halo_gather(const double* d_src, const int64_t* d_idx, int64_t n, double* d_dst, void* stream);
+int hho_halo_scatter(const double* d_src, const int64_t* d_idx, int64_t n, double* d_dst, void* stream);
 
 /* ------------------------------------------------------------------------- */
 /* Discrete adjoint (vector-Jacobian product of the receiver traces).         */

@@ -46,6 +46,12 @@ struct hho_mesh {
     std::vector<double> diam, area;    // nc
     int32_t n_classes = 0, n_colours = 0, max_nf = 0;
     std::vector<int64_t> class_first;  // first cell of each class
+    // per class: vertex coordinates relative to the reference cell's centroid
+    // over its diameter, [x_0, y_0, x_1, ...] from class_ref_off[cl]; the
+    // class matrices are built from these.  A sub-mesh inherits them from its
+    // parent mesh, so its operators use the same class matrices bit for bit.
+    std::vector<double> class_ref;
+    std::vector<int64_t> class_ref_off;
 };
 
 // Per-class integer record on the device (stride CI_STRIDE ints).

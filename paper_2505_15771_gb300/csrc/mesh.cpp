@@ -279,11 +279,75 @@ extern "C" int hho_mesh_create(const double* h_xy, int64_t n_vertices, const int
             class_of_key.emplace(key, id);
             m->class_first.push_back(c);
             m->cell_class[c] = id;
+            m->class_ref_off.push_back((int64_t)m->class_ref.size());
+            for (int i = 0; i < nv; ++i) {
+                m->class_ref.push_back((px[i] - g.cx) / g.h);
+                m->class_ref.push_back((py[i] - g.cy) / g.h);
+            }
         } else {
             m->cell_class[c] = it->second;
         }
     }
     m->n_classes = (int32_t)class_of_key.size();
+    m->class_ref_off.push_back((int64_t)m->class_ref.size());
+    *out = m;
+    return HHO_OK;
+}
+
+extern "C" int hho_mesh_submesh(const hho_mesh* parent, int64_t n_cells, const int64_t* h_cells, hho_mesh** out) {
+    if (!parent || !h_cells || !out || n_cells <= 0 || n_cells > parent->nc) {
+        hho_set_error("hho_mesh_submesh: null pointer or bad cell count");
+        return HHO_EINVAL;
+    }
+    *out = nullptr;
+    std::vector<int64_t> vloc(parent->nv, -1), vlist;
+    std::vector<char> seen(parent->nc, 0);
+    auto use = [&](int64_t v) {
+        if (vloc[v] < 0) {
+            vloc[v] = (int64_t)vlist.size();
+            vlist.push_back(v);
+        }
+    };
+    std::vector<int64_t> ptr(1, 0), vtx;
+    std::vector<uint8_t> dom;
+    for (int64_t i = 0; i < n_cells; ++i) {
+        const int64_t c = h_cells[i];
+        if (c < 0 || c >= parent->nc || seen[c]) {
+            hho_set_error("hho_mesh_submesh: cell %lld out of range or repeated", (long long)c);
+            return HHO_EINVAL;
+        }
+        seen[c] = 1;
+        for (int64_t e = parent->cell_ptr[c]; e < parent->cell_ptr[c + 1]; ++e) {
+            use(parent->cell_vtx[e]);
+            vtx.push_back(vloc[parent->cell_vtx[e]]);
+        }
+        ptr.push_back((int64_t)vtx.size());
+        dom.push_back(parent->domain[c]);
+    }
+    // identified (periodic) vertices keep their representative
+    const size_t nused = vlist.size();
+    for (size_t i = 0; i < nused; ++i) use(parent->rep[vlist[i]]);
+    std::vector<double> xy(2 * vlist.size());
+    std::vector<int64_t> rep(vlist.size());
+    for (size_t i = 0; i < vlist.size(); ++i) {
+        xy[2 * i] = parent->xy[2 * vlist[i]];
+        xy[2 * i + 1] = parent->xy[2 * vlist[i] + 1];
+        rep[i] = vloc[parent->rep[vlist[i]]];
+    }
+    hho_mesh* m = nullptr;
+    int rc = hho_mesh_create(xy.data(), (int64_t)vlist.size(), ptr.data(), vtx.data(), n_cells, dom.data(),
+                             rep.data(), &m);
+    if (rc) return rc;
+    // class reference geometry from the parent's classes
+    m->class_ref.clear();
+    m->class_ref_off.clear();
+    for (int32_t cl = 0; cl < m->n_classes; ++cl) {
+        const int32_t pcl = parent->cell_class[h_cells[m->class_first[cl]]];
+        const int64_t a = parent->class_ref_off[pcl], b = parent->class_ref_off[pcl + 1];
+        m->class_ref_off.push_back((int64_t)m->class_ref.size());
+        m->class_ref.insert(m->class_ref.end(), parent->class_ref.begin() + a, parent->class_ref.begin() + b);
+    }
+    m->class_ref_off.push_back((int64_t)m->class_ref.size());
     *out = m;
     return HHO_OK;
 }

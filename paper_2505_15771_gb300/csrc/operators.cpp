@@ -353,13 +353,11 @@ extern "C" int hho_operators_build_tau(const hho_mesh* m, int32_t k, const doubl
     std::vector<double> phi(n), Pl(f);
     for (int cl = 0; cl < NCL; ++cl) {
         int64_t c = m->class_first[cl];
-        int64_t b = m->cell_ptr[c];
-        int nv = (int)(m->cell_ptr[c + 1] - b);
-        double h = m->diam[c], cx = m->centroid[2 * c], cy = m->centroid[2 * c + 1];
+        int nv = (int)(m->class_ref_off[cl + 1] - m->class_ref_off[cl]) / 2;
         std::vector<double> X(nv), Y(nv);
-        for (int i = 0; i < nv; ++i) {
-            X[i] = (m->xy[2 * m->cell_vtx[b + i]] - cx) / h;
-            Y[i] = (m->xy[2 * m->cell_vtx[b + i] + 1] - cy) / h;
+        for (int i = 0; i < nv; ++i) {   // the class reference geometry (relative to centroid, over diameter)
+            X[i] = m->class_ref[m->class_ref_off[cl] + 2 * i];
+            Y[i] = m->class_ref[m->class_ref_off[cl] + 2 * i + 1];
         }
         cls_nf[cl] = nv;
         cls_dom[cl] = m->domain[c];
@@ -879,6 +877,15 @@ extern "C" int hho_sources_set(hho_ops* ops, int32_t n_src, const double* xy, co
         }
     }
     ops->n_src = n_src;
+    return HHO_OK;
+}
+
+extern "C" int hho_locate_points(const hho_ops* ops, int64_t n, const double* h_xy, int64_t* h_cells) {
+    if (!ops || n < 0 || (n > 0 && (!h_xy || !h_cells))) {
+        hho_set_error("hho_locate_points: bad arguments");
+        return HHO_EINVAL;
+    }
+    for (int64_t i = 0; i < n; ++i) h_cells[i] = locate(ops, h_xy[2 * i], h_xy[2 * i + 1]);
     return HHO_OK;
 }
 

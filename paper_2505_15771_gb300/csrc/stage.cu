@@ -1716,6 +1716,168 @@ extern "C" int hho_erk_step_record(hho_ops* ops, const hho_tableau* tab, double 
     return erk_single(ops, tab, t0, dt, nsteps, d_state, d_work, d_seismogram, stream, "hho_erk_step_record");
 }
 
+// ---- one stage at a time (drivers that exchange halos between stages) ---------------
+// The same kernel arguments as erk_run's stream path, so a sequence
+// hho_erk_traces, hho_erk_stage(n, j) for n < nsteps, j < s reproduces
+// hho_erk_step in stream launch mode bit for bit.
+
+namespace {
+__global__ void halo_gather_kernel(const double* __restrict__ src, const int64_t* __restrict__ idx, int64_t n,
+                                   double* __restrict__ dst) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = src[idx[i]];
+}
+__global__ void halo_scatter_kernel(const double* __restrict__ src, const int64_t* __restrict__ idx, int64_t n,
+                                    double* __restrict__ dst) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[idx[i]] = src[i];
+}
+}  // namespace
+
+static int stage_api_check(const hho_ops* ops, const hho_tableau* tab, const void* d_state, const void* d_work,
+                           std::vector<StagePlan>& plan, int* nb, const char* who) {
+    if (!ops || !tab || !d_state || !d_work) {
+        hho_set_error("%s: null pointer", who);
+        return HHO_EINVAL;
+    }
+    if (ops->arith != HHO_F64) {
+        hho_set_error("%s: the stage-at-a-time entry points run the FP64 arithmetic only", who);
+        return HHO_EINVAL;
+    }
+    if (build_plan(tab, plan, nb) != HHO_OK) {
+        hho_set_error("%s: unsupported tableau", who);
+        return HHO_EINVAL;
+    }
+    return HHO_OK;
+}
+
+extern "C" int hho_trace_buffer_offset(const hho_ops* ops, const hho_tableau* tab, int32_t which, int64_t* offset) {
+    std::vector<StagePlan> plan;
+    int nb = 0;
+    if (!ops || !tab || !offset || (which != 0 && which != 1) || build_plan(tab, plan, &nb) != HHO_OK) {
+        hho_set_error("hho_trace_buffer_offset: bad arguments");
+        return HHO_EINVAL;
+    }
+    *offset = ops->n_state * (1 + nb) + (int64_t)which * ops->trace_doubles;
+    return HHO_OK;
+}
+
+extern "C" int hho_erk_traces(hho_ops* ops, const hho_tableau* tab, const double* d_state, double* d_work,
+                              void* stream) {
+    std::vector<StagePlan> plan;
+    int nb = 0;
+    int rc = stage_api_check(ops, tab, d_state, d_work, plan, &nb, "hho_erk_traces");
+    if (rc) return rc;
+    const dim3 grid((ops->dev.Nf + ops->dev.Ns + 127) / 128, 1);
+    if (grid.x == 0) return HHO_OK;
+    StageArgsT<double> a;
+    memset(&a, 0, sizeof(a));
+    a.op = ops->dev;
+    a.state_stride = ops->n_state;
+    a.trace_stride = ops->trace_doubles;
+    a.inp = d_state;
+    a.tr_out = d_work + ops->n_state * (1 + nb);
+    launch_k<double, MODE_TRACES>(ops->k, a, grid, (cudaStream_t)stream);
+    return check_launch("hho_erk_traces");
+}
+
+extern "C" int hho_erk_stage(hho_ops* ops, const hho_tableau* tab, int64_t n, int32_t j, double tn, double dt,
+                             double* d_state, double* d_work, void* stream) {
+    std::vector<StagePlan> plan;
+    int nb = 0;
+    int rc = stage_api_check(ops, tab, d_state, d_work, plan, &nb, "hho_erk_stage");
+    if (rc) return rc;
+    if (n < 0 || j < 0 || j >= tab->s || !std::isfinite(tn) || !std::isfinite(dt)) {
+        hho_set_error("hho_erk_stage: bad step or stage index");
+        return HHO_EINVAL;
+    }
+    const dim3 grid((ops->dev.Nf + ops->dev.Ns + 127) / 128, 1);
+    if (grid.x == 0) return HHO_OK;
+    const int64_t S = ops->n_state;
+    double* X = d_work;
+    double* bufs = d_work + S;
+    double* tr[2] = {d_work + S * (1 + nb), d_work + S * (1 + nb) + ops->trace_doubles};
+    const int cur = (int)((n * tab->s + j) & 1);
+    auto resolve = [&](int code) -> double* {
+        if (code == SRC_STATE) return d_state;
+        if (code == SRC_X) return X;
+        if (code == SRC_ZERO) return nullptr;
+        return bufs + S * code;
+    };
+    StageArgsT<double> a;
+    memset(&a, 0, sizeof(a));
+    a.op = ops->dev;
+    a.state_stride = ops->n_state;
+    a.trace_stride = ops->trace_doubles;
+    const StagePlan& P = plan[j];
+    a.inp = (j == 0) ? d_state : X;
+    a.tr_in = tr[cur];
+    a.tr_out = tr[cur ^ 1];
+    a.n_tgt = P.n_tgt;
+    for (int t = 0; t < P.n_tgt; ++t) {
+        a.tgt[t].src = resolve(P.t[t].src);
+        a.tgt[t].dst = resolve(P.t[t].dst);
+        a.tgt[t].coef = P.t[t].a * dt;
+    }
+    fill_sources<double>(ops, a, tn, j, tab->c[j] * dt, 1);
+    launch_k<double, MODE_STAGE>(ops->k, a, grid, (cudaStream_t)stream);
+    return check_launch("hho_erk_stage");
+}
+
+extern "C" int hho_trace_offsets(const hho_ops* ops, int64_t n, const int64_t* h_cells, const int32_t* h_faces,
+                                 int64_t* h_out) {
+    if (!ops || n < 0 || (n > 0 && (!h_cells || !h_faces || !h_out))) {
+        hho_set_error("hho_trace_offsets: bad arguments");
+        return HHO_EINVAL;
+    }
+    const int f = ops->f;
+    for (int64_t i = 0; i < n; ++i) {
+        const int64_t c = h_cells[i];
+        if (c < 0 || c >= ops->nc) {
+            hho_set_error("hho_trace_offsets: cell %lld out of range", (long long)c);
+            return HHO_EINVAL;
+        }
+        const int32_t* ci = &ops->h_cls_int[ops->cell_class_of[c] * CI_STRIDE];
+        const int j = h_faces[i];
+        if (j < 0 || j >= ci[CI_NF]) {
+            hho_set_error("hho_trace_offsets: cell %lld has no local face %d", (long long)c, j);
+            return HHO_EINVAL;
+        }
+        const int64_t slot = ci[CI_SLOT] + (int64_t)j * ci[CI_NPAD] + (ops->cell_pos[c] - ci[CI_START]);
+        int64_t* o = h_out + i * 2 * f;
+        if (ops->cell_dom[c] == 0) {
+            for (int l = 0; l < f; ++l) o[l] = (int64_t)l * ops->dev.SF + slot;
+            for (int l = f; l < 2 * f; ++l) o[l] = -1;
+        } else {
+            const int64_t base = (int64_t)2 * f * ops->dev.SF;
+            for (int l = 0; l < 2 * f; ++l) o[l] = base + (int64_t)l * ops->dev.SS + slot;
+        }
+    }
+    return HHO_OK;
+}
+
+extern "C" int hho_halo_gather(const double* d_src, const int64_t* d_idx, int64_t n, double* d_dst, void* stream) {
+    if (n < 0 || (n > 0 && (!d_src || !d_idx || !d_dst))) {
+        hho_set_error("hho_halo_gather: bad arguments");
+        return HHO_EINVAL;
+    }
+    if (n == 0) return HHO_OK;
+    const int64_t blocks = std::min<int64_t>((n + 255) / 256, 4096);
+    halo_gather_kernel<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(d_src, d_idx, n, d_dst);
+    return check_launch("hho_halo_gather");
+}
+
+extern "C" int hho_halo_scatter(const double* d_src, const int64_t* d_idx, int64_t n, double* d_dst, void* stream) {
+    if (n < 0 || (n > 0 && (!d_src || !d_idx || !d_dst))) {
+        hho_set_error("hho_halo_scatter: bad arguments");
+        return HHO_EINVAL;
+    }
+    if (n == 0) return HHO_OK;
+    const int64_t blocks = std::min<int64_t>((n + 255) / 256, 4096);
+    halo_scatter_kernel<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(d_src, d_idx, n, d_dst);
+    return check_launch("hho_halo_scatter");
+}
+
 // ---- batched shots -----------------------------------------------------------------
 
 static bool batch_args_ok(const hho_ops* ops, int32_t n_shots, int32_t precision, const char* who) {

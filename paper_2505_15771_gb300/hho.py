@@ -76,6 +76,14 @@ _SIGS = {
     "hho_work_size": (C.c_int, [_P, C.POINTER(Tableau), C.POINTER(_I64)]),
     "hho_sources_set": (C.c_int, [_P, _I32, _P, _P, _P, _P, _P]),
     "hho_sources_set_samples": (C.c_int, [_P, _I32, _P, _P, _D, _D, _I64, _I32, _P]),
+    "hho_mesh_submesh": (C.c_int, [_P, _I64, _P, C.POINTER(_P)]),
+    "hho_locate_points": (C.c_int, [_P, _I64, _P, _P]),
+    "hho_erk_traces": (C.c_int, [_P, C.POINTER(Tableau), _P, _P, _P]),
+    "hho_erk_stage": (C.c_int, [_P, C.POINTER(Tableau), _I64, _I32, _D, _D, _P, _P, _P]),
+    "hho_trace_buffer_offset": (C.c_int, [_P, C.POINTER(Tableau), _I32, C.POINTER(_I64)]),
+    "hho_trace_offsets": (C.c_int, [_P, _I64, _P, _P, _P]),
+    "hho_halo_gather": (C.c_int, [_P, _P, _I64, _P, _P]),
+    "hho_halo_scatter": (C.c_int, [_P, _P, _I64, _P, _P]),
     "hho_ricker_samples": (C.c_int, [C.POINTER(Tableau), _D, _D, _I64, _D, _D, _D, _P]),
     "hho_erk_step": (C.c_int, [_P, C.POINTER(Tableau), _D, _D, _I64, _P, _P, _P]),
     "hho_set_arithmetic": (C.c_int, [_P, _I32]),
@@ -272,6 +280,53 @@ def hho_sources_set_samples(ops, xy, direction, t_start, dt, samples):
         raise ValueError("samples must have shape [n_src, nsteps, s]")
     _check(lib().hho_sources_set_samples(ops, xy.shape[0], _ptr(xy), _ptr(d), float(t_start), float(dt),
                                          w.shape[1], w.shape[2], _ptr(w)))
+
+
+def hho_mesh_submesh(parent, cells):
+    """Sub-mesh of the listed parent cells (in that order), with the parent's class geometry."""
+    c = _arr(cells, np.int64)
+    out = _P()
+    _check(lib().hho_mesh_submesh(parent, len(c), _ptr(c), C.byref(out)))
+    return out
+
+
+def hho_locate_points(ops, xy):
+    """Owning cell (lowest-index containing cell, input order) of every point; -1 outside."""
+    p = _arr(xy, np.float64).reshape(-1, 2)
+    out = np.empty(p.shape[0], np.int64)
+    _check(lib().hho_locate_points(ops, p.shape[0], _ptr(p), _ptr(out)))
+    return out
+
+
+def hho_erk_traces(ops, tab, d_state, d_work, stream=0):
+    _check(lib().hho_erk_traces(ops, C.byref(tab), d_state, d_work, stream))
+
+
+def hho_erk_stage(ops, tab, n, j, tn, dt, d_state, d_work, stream=0):
+    _check(lib().hho_erk_stage(ops, C.byref(tab), int(n), int(j), float(tn), float(dt), d_state, d_work, stream))
+
+
+def hho_trace_buffer_offset(ops, tab, which):
+    o = _I64()
+    _check(lib().hho_trace_buffer_offset(ops, C.byref(tab), int(which), C.byref(o)))
+    return o.value
+
+
+def hho_trace_offsets(ops, f, cells, faces):
+    """[n, 2f] offsets (within one trace buffer) of the traces each (cell, local face) publishes; -1 padded."""
+    c = _arr(cells, np.int64)
+    j = _arr(faces, np.int32)
+    out = np.full((len(c), 2 * f), -1, np.int64)
+    _check(lib().hho_trace_offsets(ops, len(c), _ptr(c), _ptr(j), _ptr(out)))
+    return out
+
+
+def hho_halo_gather(d_src, d_idx, n, d_dst, stream=0):
+    _check(lib().hho_halo_gather(d_src, d_idx, int(n), d_dst, stream))
+
+
+def hho_halo_scatter(d_src, d_idx, n, d_dst, stream=0):
+    _check(lib().hho_halo_scatter(d_src, d_idx, int(n), d_dst, stream))
 
 
 def hho_ricker_samples(tab, t_start, dt, nsteps, f0, t0, amp):

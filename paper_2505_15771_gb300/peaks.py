@@ -24,7 +24,27 @@ def rates(iters=4000, reps=5):
         if f(it, reps, ctypes.byref(r)) != 0:
             raise RuntimeError("%s failed" % fn)
         out[name] = {"fma_lane_ops_per_s": r.value, "tflops": 2.0 * r.value / 1e12}
+    # DFMA and DMMA together: time per loop of the mixed probe against the
+    # two halves alone (same chains, same launch)
+    f = lib.hho_probe_mixed_time
+    f.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
+    r = ctypes.c_double()
+    it = iters // 4
+    if f(it, reps, ctypes.byref(r)) != 0:
+        raise RuntimeError("hho_probe_mixed_time failed")
+    lanes = _lanes()
+    t_dfma = lanes * 8 / out["fp64"]["fma_lane_ops_per_s"]            # one loop of 8 DFMA per thread
+    t_dmma = lanes / 32 * 8 * 256 / out["fp64_dmma"]["fma_lane_ops_per_s"]   # 8 m8n8k4 per warp
+    out["fp64_dfma_plus_dmma"] = {"seconds_per_loop": r.value, "dfma_alone": t_dfma, "dmma_alone": t_dmma,
+                                  "overlap": (t_dfma + t_dmma) / r.value,
+                                  "note": "overlap 1: the two share the FP64 hardware; 2: fully concurrent"}
     return out
+
+
+def _lanes():
+    """Threads of the probe launch: 8 blocks of 256 per SM."""
+    import torch
+    return torch.cuda.get_device_properties(0).multi_processor_count * 8 * 256
 
 
 if __name__ == "__main__":
