@@ -4,12 +4,17 @@ equals the oracle shot by shot, test_gpu_batched.py).  The bar on
 seismograms is 1e-5 relative (the benchmark spec); the figures are printed.
 
 * hybrid quads/triangles, 1360 x 680 (1.2 M cells), k = 3, ERK4, 500 steps,
-  two of its shots: FP32 batched against FP64 batched; final state and
-  seismograms (the receivers may still be silent after 500 CFL steps).
+  two of its shots: FP32 batched against FP64 batched.
 * basin section, 2860 x 715 coarse squares (3.3 M cells, hanging nodes),
-  k = 2, ERK4, 4000 steps, two shots: seismograms.
+  k = 2, ERK4, 4000 steps, two shots.
 * bilayer 1024 x 512, k = 2 and 3, ERK3 and ERK4, 1000 steps: FP32 single
-  shot (the batched path with one shot) against FP64."""
+  shot (the batched path with one shot) against FP64.
+
+Within these step counts the waves have not reached the workloads' own
+receivers (surface or seabed lines; their FP64 traces are below 1e-20), so
+the seismograms are recorded on rings of 8 receivers around each source,
+at a distance the waves cover within the run.  Both the final states and
+these seismograms are compared."""
 import numpy as np
 import pytest
 
@@ -50,6 +55,19 @@ def rel(a, b):
     return float(np.linalg.norm(a - b) / nb) if nb > 0 else float("nan")
 
 
+def source_rings(sources, radius, per_ring=8):
+    """per_ring receivers on a circle of the given radius around every source."""
+    a = 2 * np.pi * (np.arange(per_ring) + 0.25) / per_ring
+    return [(x + radius * np.cos(t), y + radius * np.sin(t)) for (x, y) in sources for t in a]
+
+
+def reach(media, dt, nsteps, frac=0.3):
+    """A distance the slowest body wave covers in the run (a fraction of c_min t)."""
+    rho, lam, mu, kappa = (np.asarray(m) for m in media)
+    c = np.where(mu > 0, np.sqrt(np.maximum(mu, 1e-300) / rho), np.sqrt(np.maximum(kappa, 1e-300) / rho))
+    return frac * float(c.min()) * dt * nsteps
+
+
 def compare(hho, P, S, s, dt, nsteps, n_rec, label):
     c64, s64 = run(hho, P, S, s, dt, nsteps, hho.HHO_F64, n_rec)
     c32, s32 = run(hho, P, S, s, dt, nsteps, hho.HHO_F32, n_rec)
@@ -68,13 +86,14 @@ def test_c3_hybrid_full_size_500_steps(lib):
     P = solver.Problem(w["mesh"], w["media"], 3)
     try:
         P.set_shot_sources(w["sources"], [(0.0, 1.0)] * S, w["f0"])
-        P.set_receivers(w["receivers"])
         dt = hho.hho_cfl_dt(P.ops, CFL_TRI_K3, 0.9)
-        st, se = compare(hho, P, S, 4, dt, 500, len(w["receivers"]), "C3 1360x680 k=3 500 steps")
+        rec = source_rings(w["sources"], reach(w["media"], dt, 500))
+        P.set_receivers(rec)
+        st, se = compare(hho, P, S, 4, dt, 500, len(rec), "C3 1360x680 k=3 500 steps")
     finally:
         P.close()
     assert max(st) <= 1e-5
-    assert all(np.isnan(v) or v <= 1e-5 for v in se)
+    assert all(np.isfinite(se)) and max(se) <= 1e-5
 
 
 def test_c5_basin_full_size_4000_steps(lib):
@@ -84,11 +103,13 @@ def test_c5_basin_full_size_4000_steps(lib):
     P = solver.Problem(w["mesh"], w["media"], w["k"])
     try:
         P.set_shot_sources(w["sources"], [(0.0, 1.0)] * S, w["f0"])
-        P.set_receivers(w["receivers"])
         dt = hho.hho_cfl_dt(P.ops, CFL_TRI_K3, 0.9)
-        st, se = compare(hho, P, S, 4, dt, 4000, len(w["receivers"]), "C5 basin 2860x715 k=2 4000 steps")
+        rec = source_rings(w["sources"], reach(w["media"], dt, 4000))
+        P.set_receivers(rec)
+        st, se = compare(hho, P, S, 4, dt, 4000, len(rec), "C5 basin 2860x715 k=2 4000 steps")
     finally:
         P.close()
+    assert max(st) <= 1e-5
     assert all(np.isfinite(se)) and max(se) <= 1e-5
 
 
@@ -99,13 +120,13 @@ def test_bilayer_fp32_single_shot_1000_steps(lib, k, s):
     P = solver.Problem(w["mesh"], w["media"], k)
     try:
         P.set_shot_sources([w["source"]], [(0.0, 1.0)], w["f0"])
-        P.set_receivers(w["receivers"])
         # ERK3's limit is below ERK4's (Table 2 ratio 1.25 / 1.38 of ERK2's)
         cfl = CFL_SQUARES_ERK4[k] * (1.0 if s == 4 else 1.25 / 1.38)
         dt = hho.hho_cfl_dt(P.ops, cfl, 0.9)
-        st, se = compare(hho, P, 1, s, dt, 1000, len(w["receivers"]), "bilayer 1024x512 k=%d ERK%d 1000 steps"
-                         % (k, s))
+        rec = source_rings([w["source"]], reach(w["media"], dt, 1000))
+        P.set_receivers(rec)
+        st, se = compare(hho, P, 1, s, dt, 1000, len(rec), "bilayer 1024x512 k=%d ERK%d 1000 steps" % (k, s))
     finally:
         P.close()
     assert st[0] <= 1e-5
-    assert np.isnan(se[0]) or se[0] <= 1e-5
+    assert np.isfinite(se[0]) and se[0] <= 1e-5

@@ -687,3 +687,24 @@ def test_dense_adjoint_tau_part_changes_the_gradient():
         adj = ADJ.DenseAdjoint(E.Stepper(S), pts)
         out.append(adj.vjp(synth.random_state(S.nT, 4), 0.0, 0.01, 10, G)[0])
     assert np.linalg.norm(out[0] - out[1]) > 0.01 * np.linalg.norm(out[1])
+
+
+def test_cfl_readings_table_matches_the_bench_constants():
+    """tests/golden/cfl_readings.json (oracle eigenvalue limits, written by
+    tests/golden/make_cfl_readings.py): the reading kept (tau^s with c_P, h the
+    edge length) gives the ERK4 limits on squares that bench.py's time steps
+    use, and the alternative readings straddle Table 2's printed values."""
+    import json
+    import os
+    import bench
+    rec = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "cfl_readings.json")))
+    cp = rec["squares_by_k"]["tau_s_cp"]
+    for k in (1, 2, 3):
+        assert abs(cp[str(k)]["eigen_cfl_edge"] - bench.CFL_SQUARES_ERK4[k]) <= 0.002
+    cs = rec["squares_by_k"]["tau_s_cs"]
+    for k in ("1", "2", "3"):
+        assert cp[k]["eigen_cfl_edge"] < rec["table_k"][k] < cs[k]["eigen_cfl_edge"]
+    sq = rec["cases"]["squares_tau_s_cp"]
+    # Algorithm 1 brackets the eigenvalue limit from random and from the paper's smooth data
+    for ic in ("algorithm1_random_ic", "algorithm1_sinusoid_ic"):
+        assert 0.97 * sq["eigen_cfl_edge"] <= sq[ic]["cfl_edge"] <= 1.05 * sq["eigen_cfl_edge"]
