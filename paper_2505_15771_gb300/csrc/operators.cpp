@@ -471,6 +471,23 @@ extern "C" int hho_operators_build_tau(const hho_mesh* m, int32_t k, const doubl
                     if (!li_nz && fm[4 + f * nP + i * fP + l] != 0.0) ok = false;
                 }
         }
+        // the kernels lift both faces of an orientation pair with the first
+        // face's matrix: the mirror through the centroid maps face j to
+        // face j + 2 with Lift_{j+2} = P Lift_j F, P = (-1)^(exponent along
+        // the normal) on the rows, F = (-1)^l on the columns
+        double lmax = 0.0;
+        for (int j = 0; j < 4 && ok; ++j)
+            for (int i = 0; i < n; ++i)
+                for (int l = 0; l < f; ++l) lmax = std::max(lmax, std::fabs(cd[j * FS + 4 + f * nP + i * fP + l]));
+        for (int j = 0; j < 2 && ok; ++j)
+            for (int i = 0; i < n && ok; ++i)
+                for (int l = 0; l < f && ok; ++l) {
+                    const int en = (j == 0) ? EB[i] : EA[i];
+                    const double sgn = (((en + l) & 1) ? -1.0 : 1.0);
+                    const double a = cd[j * FS + 4 + f * nP + i * fP + l];
+                    const double b = cd[(j + 2) * FS + 4 + f * nP + i * fP + l];
+                    if (std::fabs(b - sgn * a) > 1e-12 * lmax) ok = false;
+                }
         if (ok) cls_kind[cl] = KIND_RECT;
     }
 

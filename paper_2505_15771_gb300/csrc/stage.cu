@@ -481,6 +481,96 @@ __device__ __forceinline__ T shot_src_value(const StageArgsT<T>& A) {
 // ---- fluid cells -------------------------------------------------------------------
 // Lift the face jump of one face into the raw rate accumulators
 // (kmx, kmy: grad p part; kp: div m part, tau folded).
+// The jump p_F - p|_F on local face j (Legendre coefficients, the cell's
+// orientation): own omega plus the neighbour's w (interior), or the
+// interface combination of the solid neighbour's traces.
+template <class T, int K>
+__device__ __forceinline__ void fluid_face_jump(const StageArgsT<T>& A, const CellCtx<T>& c, int j, T* jmp) {
+    constexpr int f = Dims<K>::f;
+    const DevOps& op = A.op;
+    const int slot = c.sbase + j * c.npad + c.lq;
+    const int nb = __ldg(op.nb_f + slot);
+#pragma unroll
+    for (int l = 0; l < f; ++l) jmp[l] = __ldg(c.trf_in + (size_t)(f + l) * c.SF + slot);
+    if (nb >= 0) {
+        const T be = __ldg(OpData<T>::beta_f(op) + slot);
+#pragma unroll
+        for (int l = 0; l < f; ++l) {
+            const T w = __ldg(c.trf_in + (size_t)l * c.SF + nb);
+            jmp[l] = (l & 1) ? fma(-be, w, jmp[l]) : fma(be, w, jmp[l]);
+        }
+    } else if (nb < NB_BOUNDARY) {
+        const int r = -2 - nb;
+        const int ns = __ldg(op.if_nb + r);
+        const T* co = OpData<T>::if_coef(op) + 6 * r;
+        const T bx = __ldg(co + 1), by = __ldg(co + 2);
+#pragma unroll
+        for (int l = 0; l < f; ++l) {
+            const T ws = fma(bx, __ldg(c.trs_in + (size_t)l * c.SS + ns), by * __ldg(c.trs_in + (size_t)(f + l) * c.SS + ns));
+            jmp[l] = (l & 1) ? jmp[l] - ws : jmp[l] + ws;
+        }
+    }
+}
+
+// Both faces of one orientation of a rectangle (AX = 0: faces 0 and 2,
+// normals -/+ e_y; AX = 1: faces 1 and 3, normals +/- e_x), lifted with the
+// first face's matrix L.  The mirror through the centroid maps face AX to
+// face AX + 2 with Lift_{AX+2} = P L F (P: (-1)^(exponent along the normal)
+// on the rows, F: (-1)^l on the face coefficients; checked when the class is
+// built).  With s the first face's normal sign, jb, jp the two jumps and
+// jh = F jp, sigma = jb + jh and delta = jb - jh:
+//     normal accumulator  += s L delta (rows with P = +1), s L sigma (P = -1)
+//     tau accumulator     += tau L sigma (P = +1), tau L delta (P = -1)
+// Each lifted row is accumulated straight into its target: 4f + 2 nnz(L)
+// operations per pair instead of 2 (nnz(L) + 2n) for two separate lifts.
+template <class T, int K, int AX>
+__device__ __forceinline__ void lift_pair(const T* __restrict__ L, const T* jb, const T* jp, T tau, T* ke, T* kt) {
+    constexpr int n = Dims<K>::n, f = Dims<K>::f, fP = Dims<K>::fP, w = Vec16<T>::w;
+    using P = RectAxis<AX>;
+    constexpr bool neg = AX == 0;   // face 0 has normal -e_y, face 1 +e_x
+    T sg[f], dl[f], ts[f], td[f];
+#pragma unroll
+    for (int l = 0; l < f; ++l) {
+        const T jh = (l & 1) ? -jp[l] : jp[l];
+        sg[l] = jb[l] + jh;
+        dl[l] = jb[l] - jh;
+        ts[l] = tau * sg[l];
+        td[l] = tau * dl[l];
+    }
+#pragma unroll
+    for (int i = 0; i < n; ++i) {
+        const int en = AX == 0 ? eb(i) : ea(i);   // exponent along the normal
+        const bool even = (en & 1) == 0;
+        T row[fP];
+#pragma unroll
+        for (int c0 = 0; c0 < fP; c0 += w) {
+            bool need = false;
+#pragma unroll
+            for (int e = 0; e < w; ++e) need = need || (c0 + e < f && P::lift_nz(i, c0 + e));
+            if (need) cls_row<T>(L + i * fP + c0, row + c0);
+        }
+        T e = ke[i], k = kt[i];
+#pragma unroll
+        for (int l = 0; l < f; ++l)
+            if (P::lift_nz(i, l)) {
+                const T a = even ? dl[l] : sg[l];
+                e = neg ? fma(-row[l], a, e) : fma(row[l], a, e);
+                k = fma(row[l], even ? ts[l] : td[l], k);
+            }
+        ke[i] = e;
+        kt[i] = k;
+    }
+}
+
+template <class T, int K, int AX>
+__device__ __forceinline__ void fluid_pair_rate(const StageArgsT<T>& A, const CellCtx<T>& c, T* kmx, T* kmy, T* kp) {
+    constexpr int f = Dims<K>::f, FS = Dims<K>::FS;
+    T jb[f], jp[f];
+    fluid_face_jump<T, K>(A, c, AX, jb);
+    fluid_face_jump<T, K>(A, c, AX + 2, jp);
+    lift_pair<T, K, AX>(c.cd + AX * FS + Dims<K>::LI, jb, jp, c.tau, AX == 0 ? kmy : kmx, kp);
+}
+
 template <class T, int K, class P>
 __device__ __forceinline__ void fluid_face_rate(const StageArgsT<T>& A, const CellCtx<T>& c, int j, int sg, T* kmx,
                                                 T* kmy, T* kp) {
@@ -618,10 +708,8 @@ __device__ __forceinline__ void fluid_cell(const StageArgsT<T>& A, int q, int sh
                 for (int v = 0; v < 2; ++v)
                     fluid_face_rate<T, K, RectAxis<1>>(A, c, 1 + 2 * v, 1 - 2 * v, kmx, kmy, kp);
             } else {
-                fluid_face_rate<T, K, RectAxis<0>>(A, c, 0, -1, kmx, kmy, kp);
-                fluid_face_rate<T, K, RectAxis<1>>(A, c, 1, 1, kmx, kmy, kp);
-                fluid_face_rate<T, K, RectAxis<0>>(A, c, 2, 1, kmx, kmy, kp);
-                fluid_face_rate<T, K, RectAxis<1>>(A, c, 3, -1, kmx, kmy, kp);
+                fluid_pair_rate<T, K, 0>(A, c, kmx, kmy, kp);   // faces 0 and 2
+                fluid_pair_rate<T, K, 1>(A, c, kmx, kmy, kp);   // faces 1 and 3
             }
         } else {
 #pragma unroll 1
@@ -736,6 +824,56 @@ __device__ __forceinline__ void solid_face_rate(const StageArgsT<T>& A, const Ce
         kvx[i] = fma(c.tau, lx[i], kvx[i]);
         kvy[i] = fma(c.tau, ly[i], kvy[i]);
     }
+}
+
+// The velocity jump v_F - v|_F on local face j (components x, y).
+template <class T, int K>
+__device__ __forceinline__ void solid_face_jump(const StageArgsT<T>& A, const CellCtx<T>& c, int j, T* jx, T* jy) {
+    constexpr int f = Dims<K>::f;
+    const DevOps& op = A.op;
+    const int slot = c.sbase + j * c.npad + c.lq;
+    const int nb = __ldg(op.nb_s + slot);
+#pragma unroll
+    for (int l = 0; l < f; ++l) {
+        jx[l] = __ldg(c.trs_in + (size_t)(2 * f + l) * c.SS + slot);
+        jy[l] = __ldg(c.trs_in + (size_t)(3 * f + l) * c.SS + slot);
+    }
+    if (nb >= 0) {
+        const T be = __ldg(OpData<T>::beta_s(op) + slot);
+#pragma unroll
+        for (int l = 0; l < f; ++l) {
+            const T wx = __ldg(c.trs_in + (size_t)l * c.SS + nb);
+            const T wy = __ldg(c.trs_in + (size_t)(f + l) * c.SS + nb);
+            jx[l] = (l & 1) ? fma(-be, wx, jx[l]) : fma(be, wx, jx[l]);
+            jy[l] = (l & 1) ? fma(-be, wy, jy[l]) : fma(be, wy, jy[l]);
+        }
+    } else if (nb < NB_BOUNDARY) {
+        const int r = -2 - nb;
+        const int nfs = __ldg(op.if_nb + r);
+        const T* co = OpData<T>::if_coef(op) + 6 * r;
+        const T b0 = __ldg(co + 4), b1 = __ldg(co + 5);
+#pragma unroll
+        for (int l = 0; l < f; ++l) {
+            const T wf = __ldg(c.trf_in + (size_t)l * c.SF + nfs);
+            jx[l] = (l & 1) ? fma(-b0, wf, jx[l]) : fma(b0, wf, jx[l]);
+            jy[l] = (l & 1) ? fma(-b1, wf, jy[l]) : fma(b1, wf, jy[l]);
+        }
+    }
+}
+
+// Both faces of one rectangle orientation (see lift_pair): horizontal faces
+// feed e_yy (y component) and e_xy (x component), vertical ones e_xx (x) and
+// e_xy (y); tau times both components feeds kv.
+template <class T, int K, int AX>
+__device__ __forceinline__ void solid_pair_rate(const StageArgsT<T>& A, const CellCtx<T>& c, T* exx, T* eyy, T* exy,
+                                                T* kvx, T* kvy) {
+    constexpr int f = Dims<K>::f, FS = Dims<K>::FS;
+    T bx[f], by[f], px[f], py[f];
+    solid_face_jump<T, K>(A, c, AX, bx, by);
+    solid_face_jump<T, K>(A, c, AX + 2, px, py);
+    const T* L = c.cd + AX * FS + Dims<K>::LI;
+    lift_pair<T, K, AX>(L, bx, px, c.tau, AX == 0 ? exy : exx, kvx);
+    lift_pair<T, K, AX>(L, by, py, c.tau, AX == 0 ? eyy : exy, kvy);
 }
 
 // Publish w = tau v|_F - (s n)|_F and omega = alpha w - v|_F for one face.
@@ -871,10 +1009,8 @@ __device__ __forceinline__ void solid_cell(const StageArgsT<T>& A, int q, int sh
                 for (int v = 0; v < 2; ++v)
                     solid_face_rate<T, K, RectAxis<1>>(A, c, 1 + 2 * v, 1 - 2 * v, exx, eyy, exy, kvx, kvy);
             } else {
-                solid_face_rate<T, K, RectAxis<0>>(A, c, 0, -1, exx, eyy, exy, kvx, kvy);
-                solid_face_rate<T, K, RectAxis<1>>(A, c, 1, 1, exx, eyy, exy, kvx, kvy);
-                solid_face_rate<T, K, RectAxis<0>>(A, c, 2, 1, exx, eyy, exy, kvx, kvy);
-                solid_face_rate<T, K, RectAxis<1>>(A, c, 3, -1, exx, eyy, exy, kvx, kvy);
+                solid_pair_rate<T, K, 0>(A, c, exx, eyy, exy, kvx, kvy);   // faces 0 and 2
+                solid_pair_rate<T, K, 1>(A, c, exx, eyy, exy, kvx, kvy);   // faces 1 and 3
             }
         } else {
 #pragma unroll 1
@@ -2050,8 +2186,9 @@ extern "C" int hho_stage_cost(const hho_ops* ops, const hho_tableau* tab, int64_
                 const int32_t nb = (dom ? ops->h_nb_s : ops->h_nb_f)[sbase + j * npad + r];
                 const bool bnd = nb == NB_BOUNDARY, ifc = nb < NB_BOUNDARY;
                 rate += bnd ? 0 : (ifc && !dom ? 3 * f : pc * f);                  // jump
-                rate += pc * nnzL;                                                  // lift
-                rate += dom ? (rect ? 4 * n : 6 * n) : (rect ? 2 * n : 3 * n);    // normal / tau combinations
+                // lift and the normal / tau combinations; rectangles lift each mirror
+                // pair of faces at once (lift_pair: 4f + 2 nnz(L) per pair and component)
+                rate += rect ? pc * (nnzL + 2 * f) : pc * nnzL + (dom ? 6 * n : 3 * n);
                 traces += dom ? (rect ? 4 * nnzT : 4 * n + 4 * nnzT) + 2 * f + (ifc ? 4 * f : 2 * f)
                               : (rect ? 2 * nnzT : 2 * n + 2 * nnzT) + 2 * f;
                 bytes_faces += 8 * (int64_t)pc * f * (1 + (bnd ? 0 : 1) + 2) + 4 + 8;
