@@ -434,6 +434,20 @@ int hho_halo_gather(const double* d_src, const int64_t* d_idx, int64_t n, double
 int hho_halo_scatter(const double* d_src, const int64_t* d_idx, int64_t n, double* d_dst, void* stream);
 
 /* ------------------------------------------------------------------------- */
+/* Tensor cores (tcgen05).                                                    */
+/* ------------------------------------------------------------------------- */
+
+/* Self-check of the split-BF16 tensor-core products (no counterpart in the
+ * paper): D = A B for one 128-row tile on the tcgen05 tensor cores, each
+ * operand split as x = hi + lo (two BF16 numbers), three products
+ * (hi hi + hi lo + lo hi) accumulated in FP32 in tensor memory, read back
+ * with tcgen05.ld.  Host buffers, row-major: h_A [128][K], h_B [K][N],
+ * h_D [128][N]; 16 <= K <= 64 and 16 <= N <= 128, multiples of 16.
+ * *h_status = 0, or 1 if the MMA completion wait gave up.  Allocates its
+ * own device buffers and synchronises. */
+int hho_tc_gemm_check(int32_t K, int32_t N, const float* h_A, const float* h_B, float* h_D, int32_t* h_status);
+
+/* ------------------------------------------------------------------------- */
 /* Discrete adjoint (vector-Jacobian product of the receiver traces).         */
 /* ------------------------------------------------------------------------- */
 

@@ -78,6 +78,7 @@ _SIGS = {
     "hho_sources_set_samples": (C.c_int, [_P, _I32, _P, _P, _D, _D, _I64, _I32, _P]),
     "hho_mesh_submesh": (C.c_int, [_P, _I64, _P, C.POINTER(_P)]),
     "hho_locate_points": (C.c_int, [_P, _I64, _P, _P]),
+    "hho_tc_gemm_check": (C.c_int, [_I32, _I32, _P, _P, _P, _P]),
     "hho_erk_traces": (C.c_int, [_P, C.POINTER(Tableau), _P, _P, _P]),
     "hho_erk_stage": (C.c_int, [_P, C.POINTER(Tableau), _I64, _I32, _D, _D, _P, _P, _P]),
     "hho_trace_buffer_offset": (C.c_int, [_P, C.POINTER(Tableau), _I32, C.POINTER(_I64)]),
@@ -296,6 +297,16 @@ def hho_locate_points(ops, xy):
     out = np.empty(p.shape[0], np.int64)
     _check(lib().hho_locate_points(ops, p.shape[0], _ptr(p), _ptr(out)))
     return out
+
+
+def hho_tc_gemm_check(A, B):
+    """D = A B (A [128, K], B [K, N], float32) through the split-BF16 tcgen05 path; returns (D, status)."""
+    A = _arr(A, np.float32)
+    B = _arr(B, np.float32)
+    D = np.zeros((128, B.shape[1]), np.float32)
+    st = C.c_int32(0)
+    _check(lib().hho_tc_gemm_check(int(A.shape[1]), int(B.shape[1]), _ptr(A), _ptr(B), _ptr(D), C.byref(st)))
+    return D, st.value
 
 
 def hho_erk_traces(ops, tab, d_state, d_work, stream=0):
