@@ -369,6 +369,11 @@ int hho_sdirk_step(hho_ops* ops, const hho_tableau* tab, double t0, double dt, i
                        significant bits, 8 bytes), arithmetic by error-free transforms on
                        the FP32 pipes; operators built in FP64 and split into pairs;
                        seismograms in FP64 */
+#define HHO_BF16X3 3 /* state, traces and seismograms in FP32 as HHO_F32, with the dense local
+                        products (every face's lifted jump, every face's traces) on the
+                        tcgen05 tensor cores: operands split into two BF16 numbers each,
+                        three products (hi hi + hi lo + lo hi) accumulated in FP32 in tensor
+                        memory; blocks of 128 (cell, shot) rows of one class */
 
 /* Element counts (of the precision's type) of a batched state
  * (n_shots x n_state, shot-major) and of the work buffer hho_batch_erk_step
@@ -397,6 +402,11 @@ int hho_batch_sources_set(hho_ops* ops, int32_t n_shots, const double* h_xy, con
  * every step.  No allocation, no host synchronisation. */
 int hho_batch_erk_step(hho_ops* ops, const hho_tableau* tab, int32_t n_shots, int32_t precision, double t0,
                        double dt, int64_t nsteps, void* d_state, void* d_work, void* d_seismogram, void* stream);
+
+/* Reads and clears the tensor-core stage's error flag (HHO_BF16X3): *h_flag
+ * = 1 if a block's wait for its MMAs gave up since the last call (its
+ * results are then invalid), else 0.  Synchronises the device. */
+int hho_tc_error(hho_ops* ops, int32_t* h_flag);
 
 /* ------------------------------------------------------------------------- */
 /* One stage at a time, for subdomain drivers (a mesh partition with a halo   */

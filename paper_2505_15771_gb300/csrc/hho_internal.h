@@ -270,6 +270,17 @@ struct hho_ops {
     int64_t host_work_size = 0;
     int64_t n_state = 0;
     int64_t trace_doubles = 0;    // one trace buffer (fluid + solid parts)
+    // tensor-core batched stage (HHO_BF16X3): per class the split-BF16
+    // operand tiles of its two GEMMs (all faces' lifts, all faces' traces),
+    // see tc_tiles in operators.cpp; meta [n_classes][6] = K1, N1, K2, N2,
+    // offset of the class's tiles (16-byte units), tile bytes
+    void* d_tc_b = nullptr;
+    int32_t* d_tc_meta = nullptr;
+    int32_t tc_kmax = 0;          // widest A tile (K) over the classes
+    int64_t tc_bmax = 0;          // largest tile bytes of one class
+    uint32_t tc_cols = 32;        // tensor-memory columns a block allocates
+    int32_t* d_tc_err = nullptr;  // set by a tensor-core block whose MMA wait gave up
+    bool tc_on = false;           // the current batched call runs the tensor-core stage
     // adjoint support: interface coefficients of the operator with the
     // coupling sign reversed, and per-class M0^-1 (n x n each)
     double* d_if_coef_adj = nullptr;

@@ -228,6 +228,122 @@ void build_locator(hho_ops* ops) {
 
 }  // namespace
 
+// BF16 value nearest to x (ties to even), as raw bits
+static uint16_t bf16_bits(float x) {
+    uint32_t u;
+    std::memcpy(&u, &x, 4);
+    if ((u & 0x7fffffffu) > 0x7f800000u) return 0x7fc0;   // NaN
+    const uint32_t r = u + 0x7fffu + ((u >> 16) & 1u);
+    return (uint16_t)(r >> 16);
+}
+static float bf16_value(uint16_t b) {
+    const uint32_t u = (uint32_t)b << 16;
+    float x;
+    std::memcpy(&x, &u, 4);
+    return x;
+}
+static int pad16(int v) { return (v + 15) / 16 * 16; }
+
+// Operand tiles of the tensor-core batched stage, per class.  With one
+// 128-row block of (cell, shot) pairs of the class:
+//   GEMM 1 (lifts):  D1 = J B1, J the face jumps [face][l] (fluid: p; solid:
+//     x components, then y components), D1's column blocks of 16 the rate
+//     accumulators (fluid: m_x, m_y, p before tau; solid: e_xx, e_yy, e_xy,
+//     v_x, v_y before tau): B1 = n_F-weighted Lift_F (Eq. rec lifted by M0^-1).
+//   GEMM 2 (traces): D2 = X B2, X the stage value's fields, D2's 16-column
+//     block per face holding that face's traces (fluid: p, m.n; solid: v_x,
+//     v_y, (s n)_x, (s n)_y), f Legendre coefficients each.
+// Each B is stored transposed (N x K) in the K-major core-matrix layout of
+// tc.cuh, as two BF16 tiles hi and lo with B = hi + lo.
+static int tc_tiles(hho_ops* ops, const std::vector<double>& cls_dbl, const std::vector<int32_t>& doff,
+                    const std::vector<int32_t>& nfs, const std::vector<int32_t>& doms) {
+    const int n = ops->n, f = ops->f, NCL = ops->n_classes;
+    const int nP = (n + 3) / 4 * 4, fP = (f + 3) / 4 * 4, M0P = (n * n + 3) / 4 * 4, FS = 4 + f * nP + n * fP;
+    std::vector<uint16_t> tiles;
+    std::vector<int32_t> meta(6 * (size_t)NCL);
+    int kmax = 16, cols = 32;
+    int64_t bmax = 0;
+    auto off = [](int r, int k, int K) { return (size_t)((r >> 3) * (K >> 3) * 64 + (k >> 3) * 64 + (r & 7) * 8 + (k & 7)); };
+    for (int cl = 0; cl < NCL; ++cl) {
+        const int nF = nfs[cl];
+        const bool sol = doms[cl] != 0;
+        const int K1 = pad16(sol ? 2 * nF * f : nF * f), N1 = (sol ? 5 : 3) * 16;
+        const int K2 = pad16((sol ? 5 : 3) * n), N2 = nF * 16;
+        std::vector<double> B1((size_t)N1 * K1, 0.0), B2((size_t)N2 * K2, 0.0);   // transposed: [col][k]
+        const double* cd = &cls_dbl[doff[cl] + M0P];
+        for (int F = 0; F < nF; ++F) {
+            const double* fm = cd + F * FS;
+            const double nx = fm[0], ny = fm[1];
+            const double* Tr = fm + 4;
+            const double* L = fm + 4 + f * nP;
+            for (int l = 0; l < f; ++l)
+                for (int i = 0; i < n; ++i) {
+                    const double lift = L[i * fP + l], tr = Tr[l * nP + i];
+                    if (!sol) {
+                        const int k = F * f + l;
+                        B1[(size_t)(0 * 16 + i) * K1 + k] = nx * lift;   // m_x rate
+                        B1[(size_t)(1 * 16 + i) * K1 + k] = ny * lift;   // m_y rate
+                        B1[(size_t)(2 * 16 + i) * K1 + k] = lift;        // p rate, times tau
+                        B2[(size_t)(F * 16 + l) * K2 + 2 * n + i] = tr;                // trace of p
+                        B2[(size_t)(F * 16 + f + l) * K2 + i] = nx * tr;               // trace of m.n
+                        B2[(size_t)(F * 16 + f + l) * K2 + n + i] = ny * tr;
+                    } else {
+                        const int kx = F * f + l, ky = nF * f + F * f + l;
+                        B1[(size_t)(0 * 16 + i) * K1 + kx] = nx * lift;  // e_xx
+                        B1[(size_t)(1 * 16 + i) * K1 + ky] = ny * lift;  // e_yy
+                        B1[(size_t)(2 * 16 + i) * K1 + kx] = ny * lift;  // e_xy
+                        B1[(size_t)(2 * 16 + i) * K1 + ky] = nx * lift;
+                        B1[(size_t)(3 * 16 + i) * K1 + kx] = lift;       // v_x rate, times tau
+                        B1[(size_t)(4 * 16 + i) * K1 + ky] = lift;       // v_y rate, times tau
+                        B2[(size_t)(F * 16 + l) * K2 + 3 * n + i] = tr;          // v_x
+                        B2[(size_t)(F * 16 + f + l) * K2 + 4 * n + i] = tr;      // v_y
+                        B2[(size_t)(F * 16 + 2 * f + l) * K2 + i] = nx * tr;     // (s n)_x = nx s_xx + ny s_xy
+                        B2[(size_t)(F * 16 + 2 * f + l) * K2 + 2 * n + i] = ny * tr;
+                        B2[(size_t)(F * 16 + 3 * f + l) * K2 + 2 * n + i] = nx * tr;   // (s n)_y = nx s_xy + ny s_yy
+                        B2[(size_t)(F * 16 + 3 * f + l) * K2 + n + i] = ny * tr;
+                    }
+                }
+        }
+        const size_t base = tiles.size();
+        meta[6 * cl + 0] = K1;
+        meta[6 * cl + 1] = N1;
+        meta[6 * cl + 2] = K2;
+        meta[6 * cl + 3] = N2;
+        meta[6 * cl + 4] = (int32_t)(base * 2 / 16);
+        const size_t s1 = (size_t)N1 * K1, s2 = (size_t)N2 * K2;
+        meta[6 * cl + 5] = (int32_t)(2 * (2 * s1 + 2 * s2));
+        tiles.resize(base + 2 * s1 + 2 * s2, 0);
+        uint16_t* t1h = &tiles[base];
+        uint16_t* t1l = t1h + s1;
+        uint16_t* t2h = t1l + s1;
+        uint16_t* t2l = t2h + s2;
+        auto put = [&](const std::vector<double>& B, int N, int K, uint16_t* hi, uint16_t* lo) {
+            for (int r = 0; r < N; ++r)
+                for (int k = 0; k < K; ++k) {
+                    const float v = (float)B[(size_t)r * K + k];
+                    const uint16_t h = bf16_bits(v);
+                    hi[off(r, k, K)] = h;
+                    lo[off(r, k, K)] = bf16_bits(v - bf16_value(h));
+                }
+        };
+        put(B1, N1, K1, t1h, t1l);
+        put(B2, N2, K2, t2h, t2l);
+        kmax = std::max(kmax, std::max(K1, K2));
+        bmax = std::max<int64_t>(bmax, meta[6 * cl + 5]);
+        while (cols < std::max(N1, N2)) cols <<= 1;
+    }
+    int err = HHO_OK;
+    ops->d_tc_b = dev_upload(ops, tiles, &err);
+    if (err) return err;
+    ops->d_tc_meta = dev_upload(ops, meta, &err);
+    if (err) return err;
+    ops->d_tc_err = dev_upload(ops, std::vector<int32_t>(1, 0), &err);
+    ops->tc_kmax = kmax;
+    ops->tc_bmax = bmax;
+    ops->tc_cols = (uint32_t)cols;
+    return err;
+}
+
 extern "C" void hho_params_default(hho_params* p) {
     if (!p) return;
     p->eta_f = 0.8;
@@ -744,6 +860,12 @@ extern "C" int hho_operators_build_tau(const hho_mesh* m, int32_t k, const doubl
     ops->d_mass_s = dev_upload(ops, mass_s, &err);
     if (err != HHO_OK) {
         hho_set_error("hho_operators_build: device allocation or upload failed");
+        hho_ops_destroy(ops);
+        return err;
+    }
+    err = tc_tiles(ops, cls_dbl, cls_doff, cls_nf, cls_dom);
+    if (err) {
+        hho_set_error("hho_operators_build: tensor-core tile upload failed");
         hho_ops_destroy(ops);
         return err;
     }

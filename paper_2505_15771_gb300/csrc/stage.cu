@@ -35,9 +35,11 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <type_traits>
 #include <vector>
 
 #include "f2x.cuh"
+#include "tc.cuh"
 #include "hho_internal.h"
 #include "stage_tuning.h"
 
@@ -1075,6 +1077,8 @@ __device__ __forceinline__ void solid_cell(const StageArgsT<T>& A, int q, int sh
     }
 }
 
+#include "stage_tc.cuh"
+
 // Resident blocks per SM asked of the register allocator (128 threads a
 // block): 2 blocks allow 255 registers, 3 allow 168, 4 allow 128, 5 allow 96,
 // 6 allow 80, 8 allow 64.  The stage kernels are bound by load latency, so
@@ -1385,6 +1389,50 @@ void launch_k(int k, const StageArgsT<T>& a, dim3 grid, cudaStream_t s) {
     else launch_kk<T, 3, MODE>(a, grid, s);
 }
 
+// The tensor-core stage (HHO_BF16X3): C cells of one class times 128 / C
+// shots per block, C = 128 / (shots rounded up to a power of two), at most 32.
+template <int K, int MODE>
+void launch_tc_k(const hho_ops* ops, const StageArgsT<float>& a, int n_shots, cudaStream_t s) {
+    int P = 1;
+    while (P < n_shots && P < 128) P <<= 1;
+    const int C = std::min(32, 128 / P), S_blk = 128 / C;
+    const dim3 grid((unsigned)((ops->dev.Nf + ops->dev.Ns) / C), (unsigned)((n_shots + S_blk - 1) / S_blk));
+    if (grid.x == 0) return;
+    TcArgs T;
+    T.tiles = (const uint4*)ops->d_tc_b;
+    T.meta = ops->d_tc_meta;
+    T.C = C;
+    T.S_blk = S_blk;
+    T.n_shots = n_shots;
+    T.kmax = ops->tc_kmax;
+    T.cols = ops->tc_cols;
+    T.error = ops->d_tc_err;
+    const size_t smem = (size_t)2 * 2 * 128 * ops->tc_kmax + (size_t)ops->tc_bmax;
+    static size_t opted[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (smem > 48 * 1024 && (dev < 0 || dev >= 64 || opted[dev] < smem)) {
+        cudaFuncSetAttribute(stage_tc_kernel<K, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (dev >= 0 && dev < 64) opted[dev] = smem;
+    }
+    stage_tc_kernel<K, MODE><<<grid, 128, smem, s>>>(a, T);
+}
+
+// A stage launch of erk_run: the tensor-core stage when the batched call
+// asked for HHO_BF16X3, else the stage kernel of the arithmetic.
+template <class T, int MODE>
+void launch_stage(const hho_ops* ops, const StageArgsT<T>& a, dim3 grid, int n_shots, cudaStream_t s) {
+    if constexpr (std::is_same<T, float>::value) {
+        if (ops->tc_on) {
+            if (ops->k == 1) launch_tc_k<1, MODE>(ops, a, n_shots, s);
+            else if (ops->k == 2) launch_tc_k<2, MODE>(ops, a, n_shots, s);
+            else launch_tc_k<3, MODE>(ops, a, n_shots, s);
+            return;
+        }
+    }
+    launch_k<T, MODE>(ops->k, a, grid, s);
+}
+
 }  // namespace
 
 int build_plan(const hho_tableau* tab, std::vector<StagePlan>& plan, int* n_buf) {
@@ -1612,7 +1660,7 @@ static int erk_run(hho_ops* ops, const hho_tableau* tab, double t0, double dt, i
         !ops->prof_on && ops->d_clock && !ops->src_sampled &&
         (ops->launch_mode == HHO_LAUNCH_GRAPH ||
          (ops->launch_mode == HHO_LAUNCH_AUTO && (int64_t)grid.x * n_shots <= 2048 && nsteps >= 8));
-    launch_k<T, MODE_TRACES>(ops->k, a, grid, st);
+    launch_stage<T, MODE_TRACES>(ops, a, grid, n_shots, st);
     int rc = check_launch(who);
     if (rc) return rc;
     int cur = 0;
@@ -1631,6 +1679,7 @@ static int erk_run(hho_ops* ops, const hho_tableau* tab, double t0, double dt, i
             int c2 = par;
             std::vector<unsigned char> key;
             append_bytes(key, (int)sizeof(T));
+            append_bytes(key, ops->tc_on);
             append_bytes(key, grid);
             for (int j = 0; j < tab->s; ++j) {
                 StageArgsT<T>& b = args[j];
@@ -1671,7 +1720,7 @@ static int erk_run(hho_ops* ops, const hho_tableau* tab, double t0, double dt, i
                     hho_set_error("%s: stream capture failed to start", who);
                     return HHO_ECUDA;
                 }
-                for (int j = 0; j < tab->s; ++j) launch_k<T, MODE_STAGE>(ops->k, args[j], grid, cs);
+                for (int j = 0; j < tab->s; ++j) launch_stage<T, MODE_STAGE>(ops, args[j], grid, n_shots, cs);
                 if (rec)
                     record_kernel<T, TS><<<rgrid, 64, 0, cs>>>(ops->dev, ops->n_rec, ops->d_rec_int, ops->d_rec_dbl,
                                                              d_state, ops->n_state, d_seis, ops->d_clock);
@@ -1716,7 +1765,7 @@ static int erk_run(hho_ops* ops, const hho_tableau* tab, double t0, double dt, i
             fill_sources<T>(ops, a, tn, j, tab->c[j] * dt, n_shots);
             const bool prof = ops->prof_on && 2 * ops->prof_n + 1 < (int)ops->prof_events.size();
             if (prof) cudaEventRecord((cudaEvent_t)ops->prof_events[2 * ops->prof_n], st);
-            launch_k<T, MODE_STAGE>(ops->k, a, grid, st);
+            launch_stage<T, MODE_STAGE>(ops, a, grid, n_shots, st);
             if (prof) cudaEventRecord((cudaEvent_t)ops->prof_events[2 * ops->prof_n++ + 1], st);
             rc = check_launch(who);
             if (rc) return rc;
@@ -2018,8 +2067,9 @@ extern "C" int hho_halo_scatter(const double* d_src, const int64_t* d_idx, int64
 
 static bool batch_args_ok(const hho_ops* ops, int32_t n_shots, int32_t precision, const char* who) {
     if (!ops || n_shots < 1 || n_shots > 65535 ||
-        (precision != HHO_F64 && precision != HHO_F32 && precision != HHO_F32X2)) {
-        hho_set_error("%s: bad arguments (1 <= n_shots <= 65535, precision HHO_F64, HHO_F32 or HHO_F32X2)", who);
+        (precision != HHO_F64 && precision != HHO_F32 && precision != HHO_F32X2 && precision != HHO_BF16X3)) {
+        hho_set_error("%s: bad arguments (1 <= n_shots <= 65535, precision HHO_F64, HHO_F32, HHO_F32X2 or HHO_BF16X3)",
+                      who);
         return false;
     }
     return true;
@@ -2100,8 +2150,26 @@ extern "C" int hho_batch_erk_step(hho_ops* ops, const hho_tableau* tab, int32_t 
     if (precision == HHO_F32X2)
         return erk_run<f2x>(ops, tab, t0, dt, nsteps, n_shots, (f2x*)d_state, (f2x*)d_work, d_seismogram, stream,
                             "hho_batch_erk_step");
-    return erk_run<float>(ops, tab, t0, dt, nsteps, n_shots, (float*)d_state, (float*)d_work, d_seismogram, stream,
-                          "hho_batch_erk_step");
+    ops->tc_on = precision == HHO_BF16X3;
+    const int rc = erk_run<float>(ops, tab, t0, dt, nsteps, n_shots, (float*)d_state, (float*)d_work, d_seismogram,
+                                  stream, "hho_batch_erk_step");
+    ops->tc_on = false;
+    return rc;
+}
+
+extern "C" int hho_tc_error(hho_ops* ops, int32_t* h_flag) {
+    if (!ops || !h_flag) {
+        hho_set_error("hho_tc_error: null pointer");
+        return HHO_EINVAL;
+    }
+    int32_t v = 0;
+    if (cudaMemcpy(&v, ops->d_tc_err, sizeof(v), cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemset(ops->d_tc_err, 0, sizeof(v)) != cudaSuccess) {
+        hho_set_error("hho_tc_error: copy failed");
+        return HHO_ECUDA;
+    }
+    *h_flag = v;
+    return HHO_OK;
 }
 
 extern "C" int hho_profile_enable(hho_ops* ops, int32_t on) {

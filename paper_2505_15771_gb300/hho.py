@@ -20,7 +20,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 # builds this way); by default the in-tree one is loaded.
 LIB_PATH = os.environ.get("HHO_LIB") or os.path.join(_HERE, "libhho.so")
 
-HHO_F64, HHO_F32, HHO_F32X2 = 0, 1, 2
+HHO_F64, HHO_F32, HHO_F32X2, HHO_BF16X3 = 0, 1, 2, 3
 HHO_FIELD_RICKER = 0
 HHO_LAUNCH_STREAM, HHO_LAUNCH_GRAPH, HHO_LAUNCH_AUTO = 0, 1, 2
 (HHO_OK, HHO_EINVAL, HHO_EMESH, HHO_EMATERIAL, HHO_EDEGREE, HHO_ECFL, HHO_EUNSTABLE, HHO_ECUDA, HHO_ENOMEM,
@@ -79,6 +79,7 @@ _SIGS = {
     "hho_mesh_submesh": (C.c_int, [_P, _I64, _P, C.POINTER(_P)]),
     "hho_locate_points": (C.c_int, [_P, _I64, _P, _P]),
     "hho_tc_gemm_check": (C.c_int, [_I32, _I32, _P, _P, _P, _P]),
+    "hho_tc_error": (C.c_int, [_P, _P]),
     "hho_erk_traces": (C.c_int, [_P, C.POINTER(Tableau), _P, _P, _P]),
     "hho_erk_stage": (C.c_int, [_P, C.POINTER(Tableau), _I64, _I32, _D, _D, _P, _P, _P]),
     "hho_trace_buffer_offset": (C.c_int, [_P, C.POINTER(Tableau), _I32, C.POINTER(_I64)]),
@@ -307,6 +308,13 @@ def hho_tc_gemm_check(A, B):
     st = C.c_int32(0)
     _check(lib().hho_tc_gemm_check(int(A.shape[1]), int(B.shape[1]), _ptr(A), _ptr(B), _ptr(D), C.byref(st)))
     return D, st.value
+
+
+def hho_tc_error(ops):
+    """Reads and clears the tensor-core stage's error flag (1: an MMA wait gave up)."""
+    v = C.c_int32(0)
+    _check(lib().hho_tc_error(ops, C.byref(v)))
+    return v.value
 
 
 def hho_erk_traces(ops, tab, d_state, d_work, stream=0):

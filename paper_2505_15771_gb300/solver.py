@@ -119,8 +119,9 @@ class Problem:
     # ---- batched shots ---------------------------------------------------------------
     @staticmethod
     def _elem_dtype(precision):
-        # HHO_F32X2 pairs occupy 8 bytes an element: float64 tensors serve as raw storage
-        return torch.float32 if precision == hho.HHO_F32 else torch.float64
+        # HHO_F32X2 pairs occupy 8 bytes an element: float64 tensors serve as raw storage;
+        # HHO_BF16X3 keeps FP32 state (only its products run in split BF16)
+        return torch.float32 if precision in (hho.HHO_F32, hho.HHO_BF16X3) else torch.float64
 
     def set_launch_mode(self, mode):
         """hho.HHO_LAUNCH_STREAM, HHO_LAUNCH_GRAPH or HHO_LAUNCH_AUTO for step / batch_step / run_host."""
