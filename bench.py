@@ -60,7 +60,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--shots", type=int, default=16, help="shots of the batched (NEXT-1) measurement")
-    ap.add_argument("--batch-precision", default="f32", choices=["f32", "f64", "f32x2"])
+    ap.add_argument("--batch-precision", default="f32", choices=["f32", "f64", "f32x2", "bf16x3"])
     ap.add_argument("--batch-steps", type=int, default=10)
     ap.add_argument("--batch-workload", default="c3", choices=["c3", "c5"],
                     help="c3: 1360x680 hybrid quads/triangles, k=3; c5: basin section with hanging nodes, k=2")
@@ -296,7 +296,7 @@ def measure_batched(a, torch, hho, solver, hbm_peak):
     on the same mesh (the "S sequential FP64 runs" comparison)."""
     import synth
     S = a.shots
-    prec = {"f32": hho.HHO_F32, "f64": hho.HHO_F64, "f32x2": hho.HHO_F32X2}[a.batch_precision]
+    prec = {"f32": hho.HHO_F32, "f64": hho.HHO_F64, "f32x2": hho.HHO_F32X2, "bf16x3": hho.HHO_BF16X3}[a.batch_precision]
     if a.batch_workload == "c5":
         w = synth.basin_c5(nx=a.batch_nx, ny=a.batch_ny, n_shots=S)
         kk = w["k"]
@@ -322,7 +322,8 @@ def measure_batched(a, torch, hho, solver, hbm_peak):
     state, work = P.batch_buffers(4, S, prec)
     steps = max(1, a.batch_steps)
     seis = torch.empty((max(steps, 3), S, len(w["receivers"]), 5),
-                       dtype=torch.float32 if prec == hho.HHO_F32 else torch.float64, device=P.dev)   # FP64 for f32x2
+                       dtype=torch.float32 if prec in (hho.HHO_F32, hho.HHO_BF16X3) else torch.float64,
+                       device=P.dev)   # FP64 for f32x2
     stream = torch.cuda.current_stream()
     P.batch_step(state, work, S, 4, 0.0, dt, 3, precision=prec, seismogram=seis)
     torch.cuda.synchronize()
@@ -352,6 +353,45 @@ def measure_batched(a, torch, hho, solver, hbm_peak):
     torch.cuda.synchronize()
     graph_ms = g0.elapsed_time(g1)
     P.set_launch_mode(hho.HHO_LAUNCH_AUTO)
+    # the same shots with the dense local products on the tcgen05 tensor
+    # cores (split BF16, FP32 accumulation), from the same start
+    tensor_core = None
+    if prec == hho.HHO_F32:
+        xf, wf = P.batch_buffers(4, S, hho.HHO_F32)   # the FP32 trajectory of the same schedule
+        P.batch_step(xf, wf, S, 4, 0.0, dt, 3, precision=hho.HHO_F32)
+        P.batch_step(xf, wf, S, 4, 3 * dt, dt, steps, precision=hho.HHO_F32)
+        canon32 = P.batch_to_canonical(xf, S, hho.HHO_F32)[0]
+        del xf, wf
+        xt, wt = P.batch_buffers(4, S, hho.HHO_BF16X3)
+        P.batch_step(xt, wt, S, 4, 0.0, dt, 3, precision=hho.HHO_BF16X3)
+        torch.cuda.synchronize()
+        hho.hho_profile_enable(P.ops, True)
+        t0e = torch.cuda.Event(enable_timing=True)
+        t1e = torch.cuda.Event(enable_timing=True)
+        t0e.record(stream)
+        P.batch_step(xt, wt, S, 4, 3 * dt, dt, steps, precision=hho.HHO_BF16X3)
+        t1e.record(stream)
+        torch.cuda.synchronize()
+        tc_ms = t0e.elapsed_time(t1e)
+        tc_stage_ms, tc_nl = hho.hho_profile_read(P.ops)
+        hho.hho_profile_enable(P.ops, False)
+        canon_tc = P.batch_to_canonical(xt, S, hho.HHO_BF16X3)[0]
+        tc_err = hho.hho_tc_error(P.ops)
+        tc_avg = tc_stage_ms * 1e-3 / max(tc_nl, 1)
+        _, bmin, _ = hho.hho_stage_cost(P.ops, tab)
+        tc_bytes = bmin / 8 * 4 * S / 4
+        tensor_core = {"precision": "bf16x3", "value": S * ndof * 4 * steps / (tc_ms * 1e-3),
+                       "ms_per_step": tc_ms / steps, "avg_launch_ms": tc_avg * 1e3,
+                       "over_fp32": (S * ndof * 4 * steps / (tc_ms * 1e-3)) / value,
+                       "rel_diff_vs_fp32_shot0": float(np.linalg.norm(canon_tc - canon32) /
+                                                      max(np.linalg.norm(canon32), 1e-300)),
+                       "mma_wait_error": tc_err,
+                       "roofline": {"bound": "hbm", "achieved": tc_bytes / tc_avg / 1e9, "peak": hbm_peak,
+                                    "unit": "GB/s", "frac": tc_bytes / tc_avg / 1e9 / hbm_peak,
+                                    "kernel": "stage_tc_kernel<%d,1>" % kk},
+                       "note": "lift and trace products of every face as two tcgen05 GEMMs per stage per block of "
+                               "32 cells x 4 shots, operands split into BF16 hi + lo, three MMAs per K step"}
+        del xt, wt
     # FP64 single shot on the same mesh
     x1 = P.empty_state()
     w1 = P.work(tab)
@@ -365,13 +405,14 @@ def measure_batched(a, torch, hho, solver, hbm_peak):
     torch.cuda.synchronize()
     v64 = ndof * 4 * steps / (f0.elapsed_time(f1) * 1e-3)
     _, bytes_min, bytes_kernel = hho.hho_stage_cost(P.ops, tab)
-    elt = 4 if prec == hho.HHO_F32 else 8
+    elt = 4 if prec in (hho.HHO_F32, hho.HHO_BF16X3) else 8
     per_launch = bytes_min / 8 * elt * S / 4
     avg = stage_ms * 1e-3 / max(nl, 1)
     out = {"metric": "shot-cell-DOF updates/s per ERK stage", "value": value, "unit": "shot-cell-DOF-stage/s",
            "precision": a.batch_precision, "shots": S, "steps": steps, "ms_per_step": ms / steps,
            "workload": desc,
            "cells": int(md.n_cells), "cell_dofs": int(ndof), "dt": dt, "seismograms_finite": finite,
+           "tensor_core": tensor_core,
            "graph_replay": {"value": S * ndof * 4 * steps / (graph_ms * 1e-3), "ms_per_step": graph_ms / steps,
                             "launch": "one captured graph per step (s stage kernels + record + clock)"},
            "fp64_single_shot_same_mesh": v64, "speedup_vs_sequential_fp64": value / v64,

@@ -246,8 +246,9 @@ static int pad16(int v) { return (v + 15) / 16 * 16; }
 
 // Operand tiles of the tensor-core batched stage, per class.  With one
 // 128-row block of (cell, shot) pairs of the class:
-//   GEMM 1 (lifts):  D1 = J B1, J the face jumps [face][l] (fluid: p; solid:
-//     x components, then y components), D1's column blocks of 16 the rate
+//   GEMM 1 (lifts):  D1 = J B1, J the face jumps at columns 4 face + l
+//     (fluid: p; solid: x components, then y components from column
+//     4 n_F), D1's column blocks of 16 the rate
 //     accumulators (fluid: m_x, m_y, p before tau; solid: e_xx, e_yy, e_xy,
 //     v_x, v_y before tau): B1 = n_F-weighted Lift_F (Eq. rec lifted by M0^-1).
 //   GEMM 2 (traces): D2 = X B2, X the stage value's fields, D2's 16-column
@@ -267,7 +268,8 @@ static int tc_tiles(hho_ops* ops, const std::vector<double>& cls_dbl, const std:
     for (int cl = 0; cl < NCL; ++cl) {
         const int nF = nfs[cl];
         const bool sol = doms[cl] != 0;
-        const int K1 = pad16(sol ? 2 * nF * f : nF * f), N1 = (sol ? 5 : 3) * 16;
+        // jumps: 4 columns per face (f <= 4), x components then y components
+        const int K1 = pad16(sol ? 8 * nF : 4 * nF), N1 = (sol ? 5 : 3) * 16;
         const int K2 = pad16((sol ? 5 : 3) * n), N2 = nF * 16;
         std::vector<double> B1((size_t)N1 * K1, 0.0), B2((size_t)N2 * K2, 0.0);   // transposed: [col][k]
         const double* cd = &cls_dbl[doff[cl] + M0P];
@@ -280,7 +282,7 @@ static int tc_tiles(hho_ops* ops, const std::vector<double>& cls_dbl, const std:
                 for (int i = 0; i < n; ++i) {
                     const double lift = L[i * fP + l], tr = Tr[l * nP + i];
                     if (!sol) {
-                        const int k = F * f + l;
+                        const int k = 4 * F + l;
                         B1[(size_t)(0 * 16 + i) * K1 + k] = nx * lift;   // m_x rate
                         B1[(size_t)(1 * 16 + i) * K1 + k] = ny * lift;   // m_y rate
                         B1[(size_t)(2 * 16 + i) * K1 + k] = lift;        // p rate, times tau
@@ -288,7 +290,7 @@ static int tc_tiles(hho_ops* ops, const std::vector<double>& cls_dbl, const std:
                         B2[(size_t)(F * 16 + f + l) * K2 + i] = nx * tr;               // trace of m.n
                         B2[(size_t)(F * 16 + f + l) * K2 + n + i] = ny * tr;
                     } else {
-                        const int kx = F * f + l, ky = nF * f + F * f + l;
+                        const int kx = 4 * F + l, ky = 4 * nF + 4 * F + l;
                         B1[(size_t)(0 * 16 + i) * K1 + kx] = nx * lift;  // e_xx
                         B1[(size_t)(1 * 16 + i) * K1 + ky] = ny * lift;  // e_yy
                         B1[(size_t)(2 * 16 + i) * K1 + kx] = ny * lift;  // e_xy

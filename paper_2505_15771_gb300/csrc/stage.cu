@@ -1389,13 +1389,12 @@ void launch_k(int k, const StageArgsT<T>& a, dim3 grid, cudaStream_t s) {
     else launch_kk<T, 3, MODE>(a, grid, s);
 }
 
-// The tensor-core stage (HHO_BF16X3): C cells of one class times 128 / C
-// shots per block, C = 128 / (shots rounded up to a power of two), at most 32.
+// The tensor-core stage (HHO_BF16X3): 32 consecutive cells of one class
+// (a class run is padded to 32 cells) times 4 shots per block, so that each
+// warp reads 32 consecutive cells of one shot, as the FP32 kernel does.
 template <int K, int MODE>
 void launch_tc_k(const hho_ops* ops, const StageArgsT<float>& a, int n_shots, cudaStream_t s) {
-    int P = 1;
-    while (P < n_shots && P < 128) P <<= 1;
-    const int C = std::min(32, 128 / P), S_blk = 128 / C;
+    const int C = 32, S_blk = 128 / C;
     const dim3 grid((unsigned)((ops->dev.Nf + ops->dev.Ns) / C), (unsigned)((n_shots + S_blk - 1) / S_blk));
     if (grid.x == 0) return;
     TcArgs T;

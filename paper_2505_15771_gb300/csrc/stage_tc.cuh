@@ -2,14 +2,16 @@
 // cores in split BF16 (HHO_BF16X3).  Included by stage.cu (uses its cell
 // helpers, in its anonymous namespace).
 //
-// A block is 128 (cell, shot) rows: C cells of one class (C divides 32, so
-// the cells share a class and a domain) times 128 / C shots; thread t owns
-// row t = (cell t % C, shot t / C), which is also tensor-memory lane t.  Per
+// A block is 128 (cell, shot) rows: C = 32 consecutive cells of one class
+// (class runs are padded to 32 cells, so they share a class and a domain)
+// times 4 shots; thread t owns row t = (cell t % 32, shot t / 32), which is
+// also tensor-memory lane t.  Per
 // stage, with the class's operand tiles (tc_tiles in operators.cpp) staged
 // in shared memory:
 //   1. each row forms its exact derivative terms in registers and its face
 //      jumps (own omega plus the neighbour's w, as the FP32 kernel does);
-//   2. GEMM 1: the jumps of all faces (split into BF16 hi + lo) times the
+//   2. GEMM 1: the jumps of all faces (4 columns per face, split into BF16
+//      hi + lo; one 8-byte store per face and tile) times the
 //      n_F-weighted lifting matrices gives every face's lifted contribution
 //      to every rate accumulator at once (three MMAs per K step: hi hi,
 //      hi lo, lo hi, FP32 accumulation in tensor memory);
@@ -34,22 +36,37 @@ struct TcArgs {
 
 constexpr int TC_WAIT_LIMIT = 1 << 22;
 
-// A row of the A tile: values[0..nval) split into BF16 hi / lo at columns
-// 0..nval, zeros up to K
+// Four consecutive columns k0..k0+3 (k0 a multiple of 4) of one row of the
+// A tile, split into BF16 hi / lo: one 8-byte store per tile.
+__device__ __forceinline__ void tc_put4(__nv_bfloat16* hi, __nv_bfloat16* lo, int row, int k0, int K, float a,
+                                        float b, float c, float d) {
+    __nv_bfloat16 h[4], l[4];
+    tc::split_bf16(a, h[0], l[0]);
+    tc::split_bf16(b, h[1], l[1]);
+    tc::split_bf16(c, h[2], l[2]);
+    tc::split_bf16(d, h[3], l[3]);
+    const uint32_t o = tc::tile_off(row, k0, K);
+    *reinterpret_cast<uint2*>(reinterpret_cast<char*>(hi) + o) = *reinterpret_cast<const uint2*>(h);
+    *reinterpret_cast<uint2*>(reinterpret_cast<char*>(lo) + o) = *reinterpret_cast<const uint2*>(l);
+}
+
+// A row of the A tile: values[0..NV) at columns 0..NV, zeros up to K
+// (inactive rows: zeros)
 template <int NV>
 __device__ __forceinline__ void tc_put_row(__nv_bfloat16* hi, __nv_bfloat16* lo, int row, int K, const float* v,
                                            bool active) {
+    auto val = [&](int k) { return (active && k < NV) ? v[k] : 0.0f; };
 #pragma unroll
-    for (int k = 0; k < NV; ++k) {
-        __nv_bfloat16 h = __float2bfloat16_rn(0.0f), l = h;
-        if (active) tc::split_bf16(v[k], h, l);
-        hi[tc::tile_off(row, k, K) / 2] = h;
-        lo[tc::tile_off(row, k, K) / 2] = l;
-    }
-    for (int k = NV; k < K; ++k) {
-        hi[tc::tile_off(row, k, K) / 2] = __float2bfloat16_rn(0.0f);
-        lo[tc::tile_off(row, k, K) / 2] = __float2bfloat16_rn(0.0f);
-    }
+    for (int k0 = 0; k0 < (NV + 3) / 4 * 4; k0 += 4) tc_put4(hi, lo, row, k0, K, val(k0), val(k0 + 1), val(k0 + 2), val(k0 + 3));
+    for (int k0 = (NV + 3) / 4 * 4; k0 < K; k0 += 4) tc_put4(hi, lo, row, k0, K, 0.0f, 0.0f, 0.0f, 0.0f);
+}
+
+// the f <= 4 jump coefficients of one face at columns k0..k0+3
+template <int F>
+__device__ __forceinline__ void tc_put_jump(__nv_bfloat16* hi, __nv_bfloat16* lo, int row, int k0, int K,
+                                            const float* j, bool active) {
+    auto val = [&](int l) { return (active && l < F) ? j[l] : 0.0f; };
+    tc_put4(hi, lo, row, k0, K, val(0), val(1), val(2), val(3));
 }
 
 // Block-wide: make the A tile visible to the tensor cores, issue D = A B
@@ -165,18 +182,9 @@ __global__ void __launch_bounds__(128) stage_tc_kernel(const StageArgsT<float> A
             for (int j = 0; j < c.nF; ++j) {
                 float jm[f];
                 if (active) fluid_face_jump<float, K>(A, c, j, jm);
-#pragma unroll
-                for (int l = 0; l < f; ++l) {
-                    __nv_bfloat16 h = __float2bfloat16_rn(0.0f), lo = h;
-                    if (active) tc::split_bf16(jm[l], h, lo);
-                    Ahi[tc::tile_off(t, j * f + l, K1) / 2] = h;
-                    Alo[tc::tile_off(t, j * f + l, K1) / 2] = lo;
-                }
+                tc_put_jump<f>(Ahi, Alo, t, 4 * j, K1, jm, active);
             }
-            for (int k = c.nF * f; k < K1; ++k) {
-                Ahi[tc::tile_off(t, k, K1) / 2] = __float2bfloat16_rn(0.0f);
-                Alo[tc::tile_off(t, k, K1) / 2] = __float2bfloat16_rn(0.0f);
-            }
+            for (int k0 = 4 * c.nF; k0 < K1; k0 += 4) tc_put4(Ahi, Alo, t, k0, K1, 0.0f, 0.0f, 0.0f, 0.0f);
         } else {
             float* exx = U;
             float* eyy = U + n;
@@ -203,22 +211,10 @@ __global__ void __launch_bounds__(128) stage_tc_kernel(const StageArgsT<float> A
             for (int j = 0; j < c.nF; ++j) {
                 float jx[f], jy[f];
                 if (active) solid_face_jump<float, K>(A, c, j, jx, jy);
-#pragma unroll
-                for (int l = 0; l < f; ++l) {
-                    __nv_bfloat16 h = __float2bfloat16_rn(0.0f), lo = h;
-                    if (active) tc::split_bf16(jx[l], h, lo);
-                    Ahi[tc::tile_off(t, j * f + l, K1) / 2] = h;
-                    Alo[tc::tile_off(t, j * f + l, K1) / 2] = lo;
-                    h = lo = __float2bfloat16_rn(0.0f);
-                    if (active) tc::split_bf16(jy[l], h, lo);
-                    Ahi[tc::tile_off(t, c.nF * f + j * f + l, K1) / 2] = h;
-                    Alo[tc::tile_off(t, c.nF * f + j * f + l, K1) / 2] = lo;
-                }
+                tc_put_jump<f>(Ahi, Alo, t, 4 * j, K1, jx, active);
+                tc_put_jump<f>(Ahi, Alo, t, 4 * (c.nF + j), K1, jy, active);
             }
-            for (int k = 2 * c.nF * f; k < K1; ++k) {
-                Ahi[tc::tile_off(t, k, K1) / 2] = __float2bfloat16_rn(0.0f);
-                Alo[tc::tile_off(t, k, K1) / 2] = __float2bfloat16_rn(0.0f);
-            }
+            for (int k0 = 8 * c.nF; k0 < K1; k0 += 4) tc_put4(Ahi, Alo, t, k0, K1, 0.0f, 0.0f, 0.0f, 0.0f);
         }
         // 2. all faces' lifted jumps: 16-column block b of D1 is accumulator block b
         ok = tc_gemm(tmem, &bar, phase, Ahi, Alo, B1h, B1l, K1, N1) && ok;
