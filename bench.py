@@ -469,6 +469,18 @@ def measure_adjoint(a, torch, hho):
     e[3].record(stream)
     torch.cuda.synchronize()
     adj_ms = e[2].elapsed_time(e[3])
+    # the FP32 reverse mode on the same problem and cotangent
+    nw32 = hho.hho_adjoint_work_size_f32(ops, tab, nsteps, ckpt)
+    aw32 = torch.empty(nw32, dtype=torch.float32, device="cuda")
+    x32, g32c = x0.float(), g.float().contiguous()
+    del aw
+    torch.cuda.synchronize()
+    e[2].record(stream)
+    grad32, _ = hho.hho_adjoint_vjp_f32(ops, tab, 0.0, dt, nsteps, ckpt, x32.data_ptr(), g32c.data_ptr(),
+                                        aw32.data_ptr(), nw32, nc, n_src=1, stream=stream.cuda_stream)
+    e[3].record(stream)
+    torch.cuda.synchronize()
+    adj32_ms = e[2].elapsed_time(e[3])
     ndof = lay.n_canonical
     out = {"metric": "adjoint cell-DOF-stages/s (forward-equivalent work / gradient time)",
            "value": ndof * 4 * nsteps / (adj_ms * 1e-3), "unit": "cell-DOF-stage/s",
@@ -477,7 +489,10 @@ def measure_adjoint(a, torch, hho):
                        % (nsteps, ckpt),
            "cells": int(nc), "cell_dofs": int(ndof), "steps": nsteps, "gradient_ms": adj_ms,
            "forward_record_ms": fwd_ms, "adjoint_over_forward": adj_ms / fwd_ms,
-           "gradient_finite": bool(np.isfinite(grad).all()), "dtype": "f64"}
+           "gradient_finite": bool(np.isfinite(grad).all()), "dtype": "f64",
+           "fp32": {"gradient_ms": adj32_ms, "value": ndof * 4 * nsteps / (adj32_ms * 1e-3),
+                    "rel_diff_vs_fp64": float(np.linalg.norm(grad32 - grad) / np.linalg.norm(grad)),
+                    "note": "hho_adjoint_vjp_f32: FP32 stage kernels and adjoint vectors, FP64 gradient sums"}}
     hho.hho_ops_destroy(ops)
     return out
 

@@ -493,6 +493,19 @@ int hho_adjoint_vjp(hho_ops* ops, const hho_tableau* tab, double t0, double dt, 
                     int64_t work_doubles, double* h_grad_cell, double* h_grad_wavelet, double* h_grad_tau,
                     void* stream);
 
+/* The same reverse mode in FP32 (BASELINE-style "FP32 adjoint"): the FP32
+ * stage kernels (the batched FP32 path with one shot) for the forward
+ * checkpoints, the segment recompute and the transposed stages; states,
+ * traces, adjoint vectors, d_state0 and d_cotangent ([nsteps][n_rec][5]) in
+ * FP32; the gradient sums in FP64; outputs as hho_adjoint_vjp.  d_work:
+ * hho_adjoint_work_size_f32 floats. */
+int hho_adjoint_work_size_f32(const hho_ops* ops, const hho_tableau* tab, int64_t nsteps, int64_t checkpoint_every,
+                              int64_t* n_floats);
+int hho_adjoint_vjp_f32(hho_ops* ops, const hho_tableau* tab, double t0, double dt, int64_t nsteps,
+                        int64_t checkpoint_every, const float* d_state0, const float* d_cotangent, float* d_work,
+                        int64_t work_floats, double* h_grad_cell, double* h_grad_wavelet, double* h_grad_tau,
+                        void* stream);
+
 /* ------------------------------------------------------------------------- */
 /* Sensors and energy (Sec. 5).                                               */
 /* ------------------------------------------------------------------------- */

@@ -35,6 +35,11 @@
 // Checkpointing: U is stored every `checkpoint_every` steps in the forward
 // pass; each segment is recomputed, keeping its stage values and their face
 // traces, before its backward sweep.
+//
+// Arithmetic: the driver and its kernels are templates on the state type,
+// FP64 (hho_adjoint_vjp) or FP32 (hho_adjoint_vjp_f32: the FP32 stage
+// kernels, states, traces and adjoint vectors in FP32); the gradient sums
+// are accumulated in FP64 in both.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -50,20 +55,22 @@ constexpr int MAX_STAGES = 6;   // the largest tableau build_plan accepts
 
 // The operand of the mass kernel: in = a1 in1 + a2 in2 (in2 may be null),
 // rounded as axpby_kernel does; stored to `keep` when that is not null.
+template <class T>
 struct MassIn {
-    const double* in1;
+    const T* in1;
     double a1;
-    const double* in2;
+    const T* in2;
     double a2;
-    double* keep;
+    T* keep;
 };
 // Where the result v = S M in (or S M^-1 in) goes: `out` (may be null), and
 // the ERK adjoint accumulations acc += v, pend[l] += a[l] v.
+template <class T>
 struct MassOut {
-    double* out;
-    double* acc;
+    T* out;
+    T* acc;
     int n_pend;
-    double* pend[MAX_STAGES];
+    T* pend[MAX_STAGES];
     double a[MAX_STAGES];
 };
 
@@ -71,8 +78,9 @@ struct MassOut {
 // dual fields (m_x, m_y / s_xx, s_yy, s_xy), +1 on the primal fields.  One
 // thread per cell; the operand combination and the accumulations of the
 // adjoint stage recursion are fused in (MassIn, MassOut).
+template <class T>
 __global__ void mass_kernel(DevOps op, const double* __restrict__ mass_f, const double* __restrict__ mass_s,
-                            const double* __restrict__ cls_minv, MassIn I, MassOut O, int inverse) {
+                            const double* __restrict__ cls_minv, MassIn<T> I, MassOut<T> O, int inverse) {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= op.Nf + op.Ns) return;
     const bool fl = g < op.Nf;
@@ -85,33 +93,33 @@ __global__ void mass_kernel(DevOps op, const double* __restrict__ mass_f, const 
     const int N = fl ? op.Nf : op.Ns;
     const size_t off = fl ? 0 : (size_t)3 * n * op.Nf;
     auto idx = [&](int field, int i) { return off + (size_t)(field * n + i) * N + q; };
-    double u[10], r[10];
+    T u[10], r[10];
     auto matvec = [&](int field) {
         for (int i = 0; i < n; ++i) {
             const size_t e = idx(field, i);
-            double v = I.a1 * I.in1[e];
-            if (I.in2) v = fma(I.a2, I.in2[e], v);
+            T v = T(I.a1) * I.in1[e];
+            if (I.in2) v = fma(T(I.a2), I.in2[e], v);
             if (I.keep) I.keep[e] = v;
             u[i] = v;
         }
         for (int i = 0; i < n; ++i) {
-            double s = 0.0;
-            for (int j = 0; j < n; ++j) s = fma(Mat[i * n + j], u[j], s);
+            T s = T(0);
+            for (int j = 0; j < n; ++j) s = fma(T(Mat[i * n + j]), u[j], s);
             r[i] = s;
         }
     };
-    auto emit = [&](int field, int i, double v) {
+    auto emit = [&](int field, int i, T v) {
         const size_t e = idx(field, i);
         if (O.out) O.out[e] = v;
         if (O.acc) O.acc[e] = O.acc[e] + v;
-        for (int l = 0; l < O.n_pend; ++l) O.pend[l][e] = fma(O.a[l], v, O.pend[l][e]);
+        for (int l = 0; l < O.n_pend; ++l) O.pend[l][e] = fma(T(O.a[l]), v, O.pend[l][e]);
     };
     if (fl) {
-        const double cm = inverse ? 1.0 / mass_f[q] : mass_f[q];               // rho h^2
-        const double cp = inverse ? 1.0 / mass_f[N + q] : mass_f[N + q];       // h^2 / kappa
+        const T cm = T(inverse ? 1.0 / mass_f[q] : mass_f[q]);                 // rho h^2
+        const T cp = T(inverse ? 1.0 / mass_f[N + q] : mass_f[N + q]);         // h^2 / kappa
         for (int fld = 0; fld < 3; ++fld) {
             matvec(fld);
-            const double c = fld < 2 ? -cm : cp;                               // S: m negated
+            const T c = fld < 2 ? -cm : cp;                                    // S: m negated
             for (int i = 0; i < n; ++i) emit(fld, i, c * r[i]);
         }
     } else {
@@ -125,31 +133,33 @@ __global__ void mass_kernel(DevOps op, const double* __restrict__ mass_f, const 
             d1 = e1;
             d2 = 1.0 / d2;
         }
-        double t0[10], t1[10];
+        const T D0 = T(d0), D1 = T(d1), D2 = T(d2), RV = T(rv);
+        T t0[10], t1[10];
         matvec(0);
         for (int i = 0; i < n; ++i) t0[i] = r[i];
         matvec(1);
         for (int i = 0; i < n; ++i) t1[i] = r[i];
         for (int i = 0; i < n; ++i) {
-            emit(0, i, -(d0 * t0[i] + d1 * t1[i]));
-            emit(1, i, -(d1 * t0[i] + d0 * t1[i]));
+            emit(0, i, -(D0 * t0[i] + D1 * t1[i]));
+            emit(1, i, -(D1 * t0[i] + D0 * t1[i]));
         }
         matvec(2);
-        for (int i = 0; i < n; ++i) emit(2, i, -d2 * r[i]);
+        for (int i = 0; i < n; ++i) emit(2, i, -D2 * r[i]);
         for (int fld = 3; fld < 5; ++fld) {
             matvec(fld);
-            for (int i = 0; i < n; ++i) emit(fld, i, rv * r[i]);
+            for (int i = 0; i < n; ++i) emit(fld, i, RV * r[i]);
         }
     }
 }
 
 // out = a x + b y over n values (x or y may be null: treated as zero; out may
 // alias x or y, each element is read before it is written by the same thread).
-__global__ void axpby_kernel(int64_t n, double a, const double* x, double b, const double* y, double* out) {
+template <class T>
+__global__ void axpby_kernel(int64_t n, double a, const T* x, double b, const T* y, T* out) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        double v = 0.0;
-        if (x) v = a * x[i];
-        if (y) v = fma(b, y[i], v);
+        T v = T(0);
+        if (x) v = T(a) * x[i];
+        if (y) v = fma(T(b), y[i], v);
         out[i] = v;
     }
 }
@@ -159,8 +169,9 @@ __global__ void axpby_kernel(int64_t n, double a, const double* x, double b, con
 // contributions of that cell's receivers to lambda[field, i] in increasing
 // receiver order, so each entry receives the same sums in the same order as a
 // walk over the receivers one by one.  blockDim >= 5 n.
+template <class T>
 __global__ void inject_kernel(DevOps op, int n_inj, const int32_t* __restrict__ inj, const int32_t* __restrict__ ri,
-                              const double* __restrict__ rd, const double* __restrict__ G, double* lam) {
+                              const double* __restrict__ rd, const T* __restrict__ G, T* lam) {
     const int t = blockIdx.x;
     const int n = op.n;
     const int fld = threadIdx.x / n, i = threadIdx.x - fld * n;
@@ -170,14 +181,15 @@ __global__ void inject_kernel(DevOps op, int n_inj, const int32_t* __restrict__ 
     const int32_t* recs = inj + 3 * n_inj + 1;
     const int stride = 2 * n + 15;
     const int N = dom == 0 ? op.Nf : op.Ns;
-    double* base = dom == 0 ? lam : lam + (size_t)3 * n * op.Nf;
+    T* base = dom == 0 ? lam : lam + (size_t)3 * n * op.Nf;
     const size_t idx = (size_t)(fld * n + i) * N + q;
     double acc = base[idx];
     for (int e = inj[t]; e < inj[t + 1]; ++e) {
         const int r = recs[e];
         const double* d = rd + (size_t)r * stride;
         const int kind = ri[4 * r];
-        const double* g = G + 5 * r;
+        double g[5];
+        for (int j = 0; j < 5; ++j) g[j] = (double)G[5 * r + j];
         double v;
         const double* phi = d;
         if (kind == 0) {          // [p, m_x, m_y]
@@ -204,12 +216,13 @@ __global__ void inject_kernel(DevOps op, int n_inj, const int32_t* __restrict__ 
         }
         if (v != 0.0) acc += v * phi[i];
     }
-    base[idx] = acc;
+    base[idx] = T(acc);
 }
 
 // dL/dtheta += mu^T dk/dtheta with dk/dtheta from the raw rate (MODE_RAW).
 // grad: fluid [2][Nf] (1/(rho h), kappa/h), solid [4][Ns] (c1, r, c3, 1/(rho h)).
-__global__ void grad_kernel(DevOps op, const double* __restrict__ mu, const double* __restrict__ raw,
+template <class T>
+__global__ void grad_kernel(DevOps op, const T* __restrict__ mu, const T* __restrict__ raw,
                             double* __restrict__ grad_f, double* __restrict__ grad_s) {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= op.Nf + op.Ns) return;
@@ -224,7 +237,7 @@ __global__ void grad_kernel(DevOps op, const double* __restrict__ mu, const doub
     auto dot = [&](int fa, int fb) {
         double s = 0.0;
         for (int i = 0; i < n; ++i)
-            s = fma(mu[off + (size_t)(fa * n + i) * N + q], raw[off + (size_t)(fb * n + i) * N + q], s);
+            s = fma((double)mu[off + (size_t)(fa * n + i) * N + q], (double)raw[off + (size_t)(fb * n + i) * N + q], s);
         return s;
     };
     if (fl) {
@@ -246,7 +259,8 @@ __global__ void grad_kernel(DevOps op, const double* __restrict__ mu, const doub
 // forward stage value (traces trY, coefficients of op) and of x = S M^-1 mu
 // (traces trX under the coupling-reversed operator opx).  The host multiplies
 // by -h per cell.  Same jump formulas as the stage kernel's face rates.
-__global__ void tau_grad_kernel(DevOps op, DevOps opx, const double* __restrict__ trY, const double* __restrict__ trX,
+template <class T>
+__global__ void tau_grad_kernel(DevOps op, DevOps opx, const T* __restrict__ trY, const T* __restrict__ trX,
                                 double* __restrict__ gstab) {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= op.Nf + op.Ns) return;
@@ -261,10 +275,10 @@ __global__ void tau_grad_kernel(DevOps op, DevOps opx, const double* __restrict_
     const int nP = (n + 3) / 4 * 4, fP = (f + 3) / 4 * 4, M0P = (n * n + 3) / 4 * 4, FS = 4 + f * nP + n * fP;
     const double* cd = op.cls_dbl + ci[CI_DOFF] + M0P;
     const int SF = op.SF, SS = op.SS;
-    const double* yf = trY;
-    const double* ys = trY + (size_t)2 * f * SF;
-    const double* xf = trX;
-    const double* xs = trX + (size_t)2 * f * SF;
+    const T* yf = trY;
+    const T* ys = trY + (size_t)2 * f * SF;
+    const T* xf = trX;
+    const T* xs = trX + (size_t)2 * f * SF;
     double acc = 0.0;
     for (int j = 0; j < nF; ++j) {
         const double rel = cd[j * FS + 2];   // |F| / h
@@ -274,7 +288,7 @@ __global__ void tau_grad_kernel(DevOps op, DevOps opx, const double* __restrict_
             const int nb = op.nb_f[slot];
             for (int l = 0; l < f; ++l) {
                 const double sg = (l & 1) ? -1.0 : 1.0;
-                double jy = yf[(size_t)(f + l) * SF + slot], jx = xf[(size_t)(f + l) * SF + slot];
+                double jy = (double)yf[(size_t)(f + l) * SF + slot], jx = (double)xf[(size_t)(f + l) * SF + slot];
                 if (nb >= 0) {
                     const double be = op.beta_f[slot];
                     jy += sg * be * yf[(size_t)l * SF + nb];
@@ -292,8 +306,8 @@ __global__ void tau_grad_kernel(DevOps op, DevOps opx, const double* __restrict_
             const int nb = op.nb_s[slot];
             for (int l = 0; l < f; ++l) {
                 const double sg = (l & 1) ? -1.0 : 1.0;
-                double jyx = ys[(size_t)(2 * f + l) * SS + slot], jyy = ys[(size_t)(3 * f + l) * SS + slot];
-                double jxx = xs[(size_t)(2 * f + l) * SS + slot], jxy = xs[(size_t)(3 * f + l) * SS + slot];
+                double jyx = (double)ys[(size_t)(2 * f + l) * SS + slot], jyy = (double)ys[(size_t)(3 * f + l) * SS + slot];
+                double jxx = (double)xs[(size_t)(2 * f + l) * SS + slot], jxy = (double)xs[(size_t)(3 * f + l) * SS + slot];
                 if (nb >= 0) {
                     const double be = op.beta_s[slot];
                     jyx += sg * be * ys[(size_t)l * SS + nb];
@@ -304,7 +318,7 @@ __global__ void tau_grad_kernel(DevOps op, DevOps opx, const double* __restrict_
                     const int r = -2 - nb, nfs = op.if_nb[r];
                     const double* cy = op.if_coef + 6 * r;
                     const double* cx = opx.if_coef + 6 * r;
-                    const double wy = yf[(size_t)l * SF + nfs], wx = xf[(size_t)l * SF + nfs];
+                    const double wy = (double)yf[(size_t)l * SF + nfs], wx = (double)xf[(size_t)l * SF + nfs];
                     jyx += sg * cy[4] * wy;
                     jyy += sg * cy[5] * wy;
                     jxx += sg * cx[4] * wx;
@@ -324,18 +338,19 @@ __global__ void tau_grad_kernel(DevOps op, DevOps opx, const double* __restrict_
 // -n, tau_s I]; so dd/dtau_f = Ai e_0 (p - p_F) and dd/dtau_s = Ai [0; v - v_F].
 // grec[2r] (the fluid cell's tau) and grec[2r + 1] (the solid cell's) sum
 // these over the time nodes; other receivers do not depend on tau.
+template <class T>
 __global__ void rec_tau_kernel(DevOps op, int n_rec, const int32_t* __restrict__ ri, const double* __restrict__ rd,
-                               const double* __restrict__ state, const double* __restrict__ G, double* grec) {
+                               const T* __restrict__ state, const T* __restrict__ G, double* grec) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n_rec || ri[4 * r] != 2) return;
     const int n = op.n;
     const double* d = rd + (size_t)r * (2 * n + 15);
     const int qf = ri[4 * r + 1], qs = ri[4 * r + 2];
-    const double* sf = state;
-    const double* ss = state + (size_t)3 * n * op.Nf;
-    auto ev = [&](const double* base, int N, int q, int field, const double* phi) {
+    const T* sf = state;
+    const T* ss = state + (size_t)3 * n * op.Nf;
+    auto ev = [&](const T* base, int N, int q, int field, const double* phi) {
         double v = 0.0;
-        for (int i = 0; i < n; ++i) v = fma(phi[i], base[(size_t)(field * n + i) * N + q], v);
+        for (int i = 0; i < n; ++i) v = fma(phi[i], (double)base[(size_t)(field * n + i) * N + q], v);
         return v;
     };
     const double* pf = d;
@@ -352,7 +367,8 @@ __global__ void rec_tau_kernel(DevOps op, int n_rec, const int32_t* __restrict__
     const double o0 = Ai[0] * wf + Ai[1] * wsx + Ai[2] * wsy;
     const double o1 = Ai[3] * wf + Ai[4] * wsx + Ai[5] * wsy;
     const double o2 = Ai[6] * wf + Ai[7] * wsx + Ai[8] * wsy;
-    const double* g = G + 5 * r;
+    double g[3];
+    for (int j = 0; j < 3; ++j) g[j] = (double)G[5 * r + j];
     const double hf = Ai[0] * g[0] + Ai[3] * g[1] + Ai[6] * g[2];   // (Ai^T g)
     const double hx = Ai[1] * g[0] + Ai[4] * g[1] + Ai[7] * g[2];
     const double hy = Ai[2] * g[0] + Ai[5] * g[1] + Ai[8] * g[2];
@@ -367,33 +383,40 @@ struct SrcMeta {
     int dom[MAX_SOURCES];
     int q[MAX_SOURCES];
 };
-__global__ void wavelet_grad_kernel(DevOps op, SrcMeta meta, const double* __restrict__ g,
-                                    const double* __restrict__ mu, double* out) {
+template <class T>
+__global__ void wavelet_grad_kernel(DevOps op, SrcMeta meta, const T* __restrict__ g, const T* __restrict__ mu,
+                                    double* out) {
     const int s = threadIdx.x;
     if (s >= meta.n) return;
     const int n = op.n;
     const int q = meta.q[s];
     double acc = 0.0;
     if (meta.dom[s] == 0) {
-        for (int i = 0; i < n; ++i) acc = fma(mu[(size_t)(2 * n + i) * op.Nf + q], g[(size_t)s * 2 * n + i], acc);
+        for (int i = 0; i < n; ++i)
+            acc = fma((double)mu[(size_t)(2 * n + i) * op.Nf + q], (double)g[(size_t)s * 2 * n + i], acc);
     } else {
-        const double* ms = mu + (size_t)3 * n * op.Nf;
+        const T* ms = mu + (size_t)3 * n * op.Nf;
         for (int i = 0; i < n; ++i) {
-            acc = fma(ms[(size_t)(3 * n + i) * op.Ns + q], g[(size_t)s * 2 * n + i], acc);
-            acc = fma(ms[(size_t)(4 * n + i) * op.Ns + q], g[(size_t)s * 2 * n + n + i], acc);
+            acc = fma((double)ms[(size_t)(3 * n + i) * op.Ns + q], (double)g[(size_t)s * 2 * n + i], acc);
+            acc = fma((double)ms[(size_t)(4 * n + i) * op.Ns + q], (double)g[(size_t)s * 2 * n + n + i], acc);
         }
     }
     out[s] = acc;
 }
 
+template <class E>
 struct AdjBuffers {
     int64_t S, T;           // state and trace sizes
-    double *ckpt, *stages, *stage_tr, *erk_work, *lam, *mu, *x, *y, *acc, *pend, *raw, *tr, *grad_f, *grad_s, *wgrad;
+    E *ckpt, *stages, *stage_tr, *erk_work, *lam, *mu, *x, *y, *acc, *pend, *raw, *tr;
+    double *grad_f, *grad_s, *wgrad;
     double *gstab, *grec;   // tau parts: per device cell slot; per receiver (fluid, solid)
 };
 
-int64_t adjoint_layout(const hho_ops* ops, const hho_tableau* tab, int64_t nsteps, int64_t C, AdjBuffers* b,
-                       double* base) {
+// Work layout in elements of E; the FP64 gradient sums take 8 / sizeof(E)
+// elements per value (every piece starts on a 128-byte boundary).
+template <class E>
+int64_t adjoint_layout(const hho_ops* ops, const hho_tableau* tab, int64_t nsteps, int64_t C, AdjBuffers<E>* b,
+                       E* base) {
     const int s = tab->s;
     const int64_t S = ops->n_state, T = ops->trace_doubles;
     const int64_t n_ckpt = (nsteps + C - 1) / C + 1;
@@ -401,11 +424,13 @@ int64_t adjoint_layout(const hho_ops* ops, const hho_tableau* tab, int64_t nstep
     hho_work_size(ops, tab, &erk);
     int64_t off = 0;
     auto take = [&](int64_t n) {
-        double* p = base ? base + off : nullptr;
+        E* p = base ? base + off : nullptr;
         off += (n + 31) / 32 * 32;
         return p;
     };
-    AdjBuffers B;
+    constexpr int64_t DW = (int64_t)(sizeof(double) / sizeof(E));
+    auto take_d = [&](int64_t n) { return reinterpret_cast<double*>(take(n * DW)); };
+    AdjBuffers<E> B;
     B.S = S;
     B.T = T;
     B.ckpt = take(n_ckpt * S);
@@ -420,11 +445,11 @@ int64_t adjoint_layout(const hho_ops* ops, const hho_tableau* tab, int64_t nstep
     B.pend = take(s * S);
     B.raw = take(S);
     B.tr = take(T);
-    B.grad_f = take(2 * (int64_t)ops->dev.Nf);
-    B.grad_s = take(4 * (int64_t)ops->dev.Ns);
-    B.wgrad = take(nsteps * s * MAX_SOURCES);
-    B.gstab = take((int64_t)ops->dev.Nf + ops->dev.Ns);
-    B.grec = take(2 * (int64_t)std::max(ops->n_rec, 1));
+    B.grad_f = take_d(2 * (int64_t)ops->dev.Nf);
+    B.grad_s = take_d(4 * (int64_t)ops->dev.Ns);
+    B.wgrad = take_d(nsteps * s * MAX_SOURCES);
+    B.gstab = take_d((int64_t)ops->dev.Nf + ops->dev.Ns);
+    B.grec = take_d(2 * (int64_t)std::max(ops->n_rec, 1));
     if (b) *b = B;
     return off;
 }
@@ -434,6 +459,36 @@ int64_t grid1(int64_t n) {
     return g > 4096 ? 4096 : (g < 1 ? 1 : g);
 }
 
+// the stage launcher and the operator data of the arithmetic
+template <class E>
+void launch_stage_t(const hho_ops* ops, int mode, StageArgsT<E>& a, double tn, int j, double cdt, bool sources,
+                    void* stream);
+template <>
+void launch_stage_t<double>(const hho_ops* ops, int mode, StageArgsT<double>& a, double tn, int j, double cdt,
+                            bool sources, void* stream) {
+    launch_stage_f64(ops, mode, a, 1, tn, j, cdt, sources, stream);
+}
+template <>
+void launch_stage_t<float>(const hho_ops* ops, int mode, StageArgsT<float>& a, double tn, int j, double cdt,
+                           bool sources, void* stream) {
+    launch_stage_f32(ops, mode, a, 1, tn, j, cdt, sources, stream);
+}
+int forward_steps(hho_ops* ops, const hho_tableau* tab, double t0, double dt, int64_t n, double* x, double* w,
+                  void* stream) {
+    return hho_erk_step(ops, tab, t0, dt, n, x, w, stream);
+}
+int forward_steps(hho_ops* ops, const hho_tableau* tab, double t0, double dt, int64_t n, float* x, float* w,
+                  void* stream) {
+    return erk_steps_f32(ops, tab, t0, dt, n, x, w, stream);
+}
+const double* src_vectors(const hho_ops* ops, const double*) { return ops->d_src_g; }
+const float* src_vectors(const hho_ops* ops, const float*) { return ops->d_src_g32; }
+
+template <class E>
+int adjoint_vjp_t(hho_ops* ops, const hho_tableau* tab, double t0, double dt, int64_t nsteps, int64_t checkpoint_every,
+                  const E* d_state0, const E* d_cotangent, E* d_work, int64_t work_elems, double* h_grad_cell,
+                  double* h_grad_wavelet, double* h_grad_tau, void* stream, const char* who);
+
 }  // namespace
 
 extern "C" int hho_adjoint_work_size(const hho_ops* ops, const hho_tableau* tab, int64_t nsteps,
@@ -442,7 +497,17 @@ extern "C" int hho_adjoint_work_size(const hho_ops* ops, const hho_tableau* tab,
         hho_set_error("hho_adjoint_work_size: bad arguments");
         return HHO_EINVAL;
     }
-    *n_doubles = adjoint_layout(ops, tab, nsteps, checkpoint_every, nullptr, nullptr);
+    *n_doubles = adjoint_layout<double>(ops, tab, nsteps, checkpoint_every, nullptr, nullptr);
+    return HHO_OK;
+}
+
+extern "C" int hho_adjoint_work_size_f32(const hho_ops* ops, const hho_tableau* tab, int64_t nsteps,
+                                         int64_t checkpoint_every, int64_t* n_floats) {
+    if (!ops || !tab || !n_floats || nsteps < 1 || checkpoint_every < 1) {
+        hho_set_error("hho_adjoint_work_size_f32: bad arguments");
+        return HHO_EINVAL;
+    }
+    *n_floats = adjoint_layout<float>(ops, tab, nsteps, checkpoint_every, nullptr, nullptr);
     return HHO_OK;
 }
 
@@ -450,24 +515,40 @@ extern "C" int hho_adjoint_vjp(hho_ops* ops, const hho_tableau* tab, double t0, 
                                int64_t checkpoint_every, const double* d_state0, const double* d_cotangent,
                                double* d_work, int64_t work_doubles, double* h_grad_cell, double* h_grad_wavelet,
                                double* h_grad_tau, void* stream) {
+    return adjoint_vjp_t<double>(ops, tab, t0, dt, nsteps, checkpoint_every, d_state0, d_cotangent, d_work,
+                                 work_doubles, h_grad_cell, h_grad_wavelet, h_grad_tau, stream, "hho_adjoint_vjp");
+}
+
+extern "C" int hho_adjoint_vjp_f32(hho_ops* ops, const hho_tableau* tab, double t0, double dt, int64_t nsteps,
+                                   int64_t checkpoint_every, const float* d_state0, const float* d_cotangent,
+                                   float* d_work, int64_t work_floats, double* h_grad_cell, double* h_grad_wavelet,
+                                   double* h_grad_tau, void* stream) {
+    return adjoint_vjp_t<float>(ops, tab, t0, dt, nsteps, checkpoint_every, d_state0, d_cotangent, d_work,
+                                work_floats, h_grad_cell, h_grad_wavelet, h_grad_tau, stream, "hho_adjoint_vjp_f32");
+}
+
+namespace {
+template <class E>
+int adjoint_vjp_t(hho_ops* ops, const hho_tableau* tab, double t0, double dt, int64_t nsteps, int64_t checkpoint_every,
+                  const E* d_state0, const E* d_cotangent, E* d_work, int64_t work_doubles, double* h_grad_cell,
+                  double* h_grad_wavelet, double* h_grad_tau, void* stream, const char* who) {
     if (!ops || !tab || !d_state0 || !d_cotangent || !d_work || !h_grad_cell || nsteps < 1 || checkpoint_every < 1 ||
         !std::isfinite(dt)) {
-        hho_set_error("hho_adjoint_vjp: bad arguments");
+        hho_set_error("%s: bad arguments", who);
         return HHO_EINVAL;
     }
     std::vector<StagePlan> plan;
     int nb = 0;
     if (build_plan(tab, plan, &nb) != HHO_OK) {
-        hho_set_error("hho_adjoint_vjp: unsupported tableau");
+        hho_set_error("%s: unsupported tableau", who);
         return HHO_EINVAL;
     }
     const int64_t C = checkpoint_every;
     const int s = tab->s;
-    AdjBuffers B;
-    const int64_t need = adjoint_layout(ops, tab, nsteps, C, &B, d_work);
+    AdjBuffers<E> B;
+    const int64_t need = adjoint_layout<E>(ops, tab, nsteps, C, &B, d_work);
     if (work_doubles < need) {
-        hho_set_error("hho_adjoint_vjp: work buffer has %lld doubles, needs %lld", (long long)work_doubles,
-                      (long long)need);
+        hho_set_error("%s: work buffer has %lld elements, needs %lld", who, (long long)work_doubles, (long long)need);
         return HHO_EINVAL;
     }
     cudaStream_t st = (cudaStream_t)stream;
@@ -475,39 +556,40 @@ extern "C" int hho_adjoint_vjp(hho_ops* ops, const hho_tableau* tab, double t0, 
     const int nthr = ops->dev.Nf + ops->dev.Ns;
     const int cblk = (nthr + 127) / 128;
     int rc = HHO_OK;
-    auto copy = [&](double* dst, const double* src, int64_t n) {
-        return cudaMemcpyAsync(dst, src, sizeof(double) * n, cudaMemcpyDeviceToDevice, st) == cudaSuccess;
+    auto copy = [&](E* dst, const E* src, int64_t n) {
+        return cudaMemcpyAsync(dst, src, sizeof(E) * n, cudaMemcpyDeviceToDevice, st) == cudaSuccess;
     };
     // the ERK partial-sum buffers of the segment recompute, laid out as in
     // erk_run ([X][partial sums][2 traces]; X and the traces live in the
     // segment store here)
-    double* bufs = B.erk_work + S;
-    auto partial = [&](int code) -> double* { return code == SRC_ZERO ? nullptr : bufs + S * code; };
+    E* bufs = B.erk_work + S;
+    auto partial = [&](int code) -> E* { return code == SRC_ZERO ? nullptr : bufs + S * code; };
     DevOps adj = ops->dev;
     adj.if_coef = ops->d_if_coef_adj;
+    adj.if_coef_f32 = ops->d_if_coef_adj_f32;
 
     // ---- forward pass: checkpoints ------------------------------------------------
     if (!copy(B.ckpt, d_state0, S)) {
-        hho_set_error("hho_adjoint_vjp: copy failed");
+        hho_set_error("%s: copy failed", who);
         return HHO_ECUDA;
     }
     const int64_t n_ckpt = (nsteps + C - 1) / C;
     for (int64_t c = 1; c < n_ckpt + 1 && c * C <= nsteps; ++c) {
         if (!copy(B.ckpt + c * S, B.ckpt + (c - 1) * S, S)) return HHO_ECUDA;
-        rc = hho_erk_step(ops, tab, t0 + (double)((c - 1) * C) * dt, dt, C, B.ckpt + c * S, B.erk_work, stream);
+        rc = forward_steps(ops, tab, t0 + (double)((c - 1) * C) * dt, dt, C, B.ckpt + c * S, B.erk_work, stream);
         if (rc) return rc;
     }
 
     // ---- backward sweep ---------------------------------------------------------------
-    axpby_kernel<<<grid1(S), 256, 0, st>>>(S, 0.0, nullptr, 0.0, nullptr, B.lam);
+    axpby_kernel<E><<<grid1(S), 256, 0, st>>>(S, 0.0, nullptr, 0.0, nullptr, B.lam);
     if (ops->dev.Nf > 0)
-        axpby_kernel<<<grid1(2 * (int64_t)ops->dev.Nf), 256, 0, st>>>(2 * (int64_t)ops->dev.Nf, 0.0, nullptr, 0.0,
-                                                                       nullptr, B.grad_f);
+        axpby_kernel<double><<<grid1(2 * (int64_t)ops->dev.Nf), 256, 0, st>>>(2 * (int64_t)ops->dev.Nf, 0.0, nullptr,
+                                                                               0.0, nullptr, B.grad_f);
     if (ops->dev.Ns > 0)
-        axpby_kernel<<<grid1(4 * (int64_t)ops->dev.Ns), 256, 0, st>>>(4 * (int64_t)ops->dev.Ns, 0.0, nullptr, 0.0,
-                                                                       nullptr, B.grad_s);
-    axpby_kernel<<<grid1((int64_t)nthr), 256, 0, st>>>((int64_t)nthr, 0.0, nullptr, 0.0, nullptr, B.gstab);
-    axpby_kernel<<<1, 256, 0, st>>>(2 * (int64_t)std::max(ops->n_rec, 1), 0.0, nullptr, 0.0, nullptr, B.grec);
+        axpby_kernel<double><<<grid1(4 * (int64_t)ops->dev.Ns), 256, 0, st>>>(4 * (int64_t)ops->dev.Ns, 0.0, nullptr,
+                                                                               0.0, nullptr, B.grad_s);
+    axpby_kernel<double><<<grid1((int64_t)nthr), 256, 0, st>>>((int64_t)nthr, 0.0, nullptr, 0.0, nullptr, B.gstab);
+    axpby_kernel<double><<<1, 256, 0, st>>>(2 * (int64_t)std::max(ops->n_rec, 1), 0.0, nullptr, 0.0, nullptr, B.grec);
     const int64_t n_segments = (nsteps + C - 1) / C;
     for (int64_t seg = n_segments - 1; seg >= 0; --seg) {
         const int64_t n0 = seg * C;                                   // segment starts at U^{n0}
@@ -521,12 +603,12 @@ extern "C" int hho_adjoint_vjp(hho_ops* ops, const hho_tableau* tab, double t0, 
         auto Y = [&](int64_t m, int j) { return B.stages + (m * s + j) * S; };
         auto TY = [&](int64_t m, int j) { return B.stage_tr + (m * s + j) * B.T; };
         if (!copy(Y(0, 0), B.ckpt + seg * S, S)) return HHO_ECUDA;
-        StageArgsT<double> a;
+        StageArgsT<E> a;
         memset(&a, 0, sizeof(a));
         a.op = ops->dev;
         a.inp = Y(0, 0);
         a.tr_out = TY(0, 0);
-        launch_stage_f64(ops, MODE_TRACES, a, 1, 0.0, -1, 0.0, false, stream);
+        launch_stage_t<E>(ops, MODE_TRACES, a, 0.0, -1, 0.0, false, stream);
         for (int64_t m = 0; m < nst; ++m) {
             const double tn = t0 + (double)(n0 + m) * dt;
             for (int j = 0; j < s; ++j) {
@@ -540,53 +622,53 @@ extern "C" int hho_adjoint_vjp(hho_ops* ops, const hho_tableau* tab, double t0, 
                     const int sc = P.t[t].src, dc = P.t[t].dst;
                     a.tgt[t].src = sc == SRC_STATE ? Y(m, 0) : partial(sc);
                     a.tgt[t].dst = dc == SRC_STATE ? Y(m + 1, 0) : dc == SRC_X ? Y(m, j + 1) : partial(dc);
-                    a.tgt[t].coef = P.t[t].a * dt;
+                    a.tgt[t].coef = E(P.t[t].a * dt);
                 }
-                launch_stage_f64(ops, MODE_STAGE, a, 1, tn, j, tab->c[j] * dt, true, stream);
+                launch_stage_t<E>(ops, MODE_STAGE, a, tn, j, tab->c[j] * dt, true, stream);
             }
         }
-        rc = check_cuda("hho_adjoint_vjp (segment recompute)");
+        rc = check_cuda(who);
         if (rc) return rc;
         // backward through the segment
         for (int64_t m = nst - 1; m >= 0; --m) {
             const int64_t n = n0 + m + 1;                            // step n: U^{n-1} -> U^n
             const double tn = t0 + (double)(n - 1) * dt;
             if (ops->n_inj > 0)
-                inject_kernel<<<ops->n_inj, (5 * ops->n + 31) / 32 * 32, 0, st>>>(
+                inject_kernel<E><<<ops->n_inj, (5 * ops->n + 31) / 32 * 32, 0, st>>>(
                     ops->dev, ops->n_inj, ops->d_inj, ops->d_rec_int, ops->d_rec_dbl,
                     d_cotangent + (size_t)(n - 1) * 5 * ops->n_rec, B.lam);
             if (ops->n_rec > 0)   // U^n is the next step's first stage value in the store
-                rec_tau_kernel<<<(ops->n_rec + 63) / 64, 64, 0, st>>>(ops->dev, ops->n_rec, ops->d_rec_int,
+                rec_tau_kernel<E><<<(ops->n_rec + 63) / 64, 64, 0, st>>>(ops->dev, ops->n_rec, ops->d_rec_int,
                                                                      ops->d_rec_dbl, Y(m + 1, 0),
                                                                      d_cotangent + (size_t)(n - 1) * 5 * ops->n_rec,
                                                                      B.grec);
             if (!copy(B.acc, B.lam, S)) return HHO_ECUDA;
-            axpby_kernel<<<grid1(s * S), 256, 0, st>>>(s * S, 0.0, nullptr, 0.0, nullptr, B.pend);
+            axpby_kernel<E><<<grid1(s * S), 256, 0, st>>>(s * S, 0.0, nullptr, 0.0, nullptr, B.pend);
             for (int j = s - 1; j >= 0; --j) {
                 // mu_j = dt (b_j lambda + P_j), x = M^-1 S mu_j
-                const MassIn mi = {B.lam, dt * tab->b[j], B.pend + j * S, dt, B.mu};
-                MassOut mo;
+                const MassIn<E> mi = {B.lam, dt * tab->b[j], B.pend + j * S, dt, B.mu};
+                MassOut<E> mo;
                 memset(&mo, 0, sizeof(mo));
                 mo.out = B.x;
-                mass_kernel<<<cblk, 128, 0, st>>>(ops->dev, ops->d_mass_f, ops->d_mass_s, ops->d_cls_minv, mi, mo, 1);
+                mass_kernel<E><<<cblk, 128, 0, st>>>(ops->dev, ops->d_mass_f, ops->d_mass_s, ops->d_cls_minv, mi, mo, 1);
                 // nu_j = S M A' x, accumulated into acc and the pending sums P_l (l < j)
-                StageArgsT<double> b;
+                StageArgsT<E> b;
                 memset(&b, 0, sizeof(b));
                 b.op = adj;
                 b.inp = B.x;
                 b.tr_out = B.tr;
-                launch_stage_f64(ops, MODE_TRACES, b, 1, 0.0, -1, 0.0, false, stream);
+                launch_stage_t<E>(ops, MODE_TRACES, b, 0.0, -1, 0.0, false, stream);
                 b.tr_in = B.tr;
                 b.tr_out = nullptr;
                 b.n_tgt = 1;
                 b.tgt[0].src = nullptr;
                 b.tgt[0].dst = B.y;
-                b.tgt[0].coef = 1.0;
-                launch_stage_f64(ops, MODE_APPLY, b, 1, 0.0, -1, 0.0, false, stream);
+                b.tgt[0].coef = E(1.0);
+                launch_stage_t<E>(ops, MODE_APPLY, b, 0.0, -1, 0.0, false, stream);
                 // the stabilisation weights' part: forward jumps of Y_{m,j} against those of x under A'
-                tau_grad_kernel<<<cblk, 128, 0, st>>>(ops->dev, adj, TY(m, j), B.tr, B.gstab);
-                const MassIn ni = {B.y, 1.0, nullptr, 0.0, nullptr};
-                MassOut no;
+                tau_grad_kernel<E><<<cblk, 128, 0, st>>>(ops->dev, adj, TY(m, j), B.tr, B.gstab);
+                const MassIn<E> ni = {B.y, 1.0, nullptr, 0.0, nullptr};
+                MassOut<E> no;
                 memset(&no, 0, sizeof(no));
                 no.acc = B.acc;
                 for (int l = 0; l < j; ++l)
@@ -594,9 +676,9 @@ extern "C" int hho_adjoint_vjp(hho_ops* ops, const hho_tableau* tab, double t0, 
                         no.pend[no.n_pend] = B.pend + l * S;
                         no.a[no.n_pend++] = tab->a[j][l];
                     }
-                mass_kernel<<<cblk, 128, 0, st>>>(ops->dev, ops->d_mass_f, ops->d_mass_s, ops->d_cls_minv, ni, no, 0);
+                mass_kernel<E><<<cblk, 128, 0, st>>>(ops->dev, ops->d_mass_f, ops->d_mass_s, ops->d_cls_minv, ni, no, 0);
                 // parameter and wavelet gradients of stage j (the forward traces of Y_{m,j} are stored)
-                StageArgsT<double> r;
+                StageArgsT<E> r;
                 memset(&r, 0, sizeof(r));
                 r.op = ops->dev;
                 r.inp = Y(m, j);
@@ -605,9 +687,9 @@ extern "C" int hho_adjoint_vjp(hho_ops* ops, const hho_tableau* tab, double t0, 
                 r.n_tgt = 1;
                 r.tgt[0].src = nullptr;
                 r.tgt[0].dst = B.raw;
-                r.tgt[0].coef = 1.0;
-                launch_stage_f64(ops, MODE_RAW, r, 1, tn, j, tab->c[j] * dt, true, stream);
-                grad_kernel<<<cblk, 128, 0, st>>>(ops->dev, B.mu, B.raw, B.grad_f, B.grad_s);
+                r.tgt[0].coef = E(1.0);
+                launch_stage_t<E>(ops, MODE_RAW, r, tn, j, tab->c[j] * dt, true, stream);
+                grad_kernel<E><<<cblk, 128, 0, st>>>(ops->dev, B.mu, B.raw, B.grad_f, B.grad_s);
                 if (ops->n_src > 0 && h_grad_wavelet) {
                     SrcMeta meta;
                     meta.n = ops->n_src;
@@ -615,10 +697,10 @@ extern "C" int hho_adjoint_vjp(hho_ops* ops, const hho_tableau* tab, double t0, 
                         meta.dom[k2] = ops->src_dom[k2];
                         meta.q[k2] = ops->src_q[k2];
                     }
-                    wavelet_grad_kernel<<<1, 32, 0, st>>>(ops->dev, meta, ops->d_src_g, B.mu,
-                                                          B.wgrad + ((n - 1) * s + j) * MAX_SOURCES);
+                    wavelet_grad_kernel<E><<<1, 32, 0, st>>>(ops->dev, meta, src_vectors(ops, (const E*)nullptr), B.mu,
+                                                             B.wgrad + ((n - 1) * s + j) * MAX_SOURCES);
                 }
-                rc = check_cuda("hho_adjoint_vjp (backward stage)");
+                rc = check_cuda(who);
                 if (rc) return rc;
             }
             if (!copy(B.lam, B.acc, S)) return HHO_ECUDA;
@@ -636,13 +718,13 @@ extern "C" int hho_adjoint_vjp(hho_ops* ops, const hho_tableau* tab, double t0, 
              cudaSuccess) ||
         cudaMemcpyAsync(grec.data(), B.grec, sizeof(double) * grec.size(), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess) {
-        hho_set_error("hho_adjoint_vjp: gradient copy failed");
+        hho_set_error("%s: gradient copy failed", who);
         return HHO_ECUDA;
     }
     if (ops->n_src > 0 && h_grad_wavelet) {
         std::vector<double> wg((size_t)nsteps * s * MAX_SOURCES);
         if (cudaMemcpy(wg.data(), B.wgrad, sizeof(double) * wg.size(), cudaMemcpyDeviceToHost) != cudaSuccess) {
-            hho_set_error("hho_adjoint_vjp: wavelet gradient copy failed");
+            hho_set_error("%s: wavelet gradient copy failed", who);
             return HHO_ECUDA;
         }
         for (int64_t n = 0; n < nsteps; ++n)
@@ -665,7 +747,7 @@ extern "C" int hho_adjoint_vjp(hho_ops* ops, const hho_tableau* tab, double t0, 
         if (ops->n_rec > 0 &&
             cudaMemcpy(ri.data(), ops->d_rec_int, sizeof(int32_t) * 4 * ops->n_rec, cudaMemcpyDeviceToHost) !=
                 cudaSuccess) {
-            hho_set_error("hho_adjoint_vjp: receiver table copy failed");
+            hho_set_error("%s: receiver table copy failed", who);
             return HHO_ECUDA;
         }
         for (int r = 0; r < ops->n_rec; ++r)
@@ -710,3 +792,4 @@ extern "C" int hho_adjoint_vjp(hho_ops* ops, const hho_tableau* tab, double t0, 
     }
     return HHO_OK;
 }
+}  // namespace

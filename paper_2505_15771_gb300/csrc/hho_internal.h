@@ -180,7 +180,12 @@ struct hho_ops;
 // that have no stage index (sampled source time functions are then zero).
 void launch_stage_f64(const hho_ops* ops, int mode, StageArgsT<double>& a, int n_shots, double tn, int j, double cdt,
                       bool sources, void* stream);
+void launch_stage_f32(const hho_ops* ops, int mode, StageArgsT<float>& a, int n_shots, double tn, int j, double cdt,
+                      bool sources, void* stream);
 void launch_record_f64(const hho_ops* ops, const double* state, double* out, void* stream);
+// nsteps ERK steps of one FP32 state (the batched FP32 path with one shot)
+int erk_steps_f32(hho_ops* ops, const hho_tableau* tab, double t0, double dt, int64_t nsteps, float* d_state,
+                  float* d_work, void* stream);
 int check_cuda(const char* what);
 
 struct hho_ops {
@@ -284,6 +289,7 @@ struct hho_ops {
     // adjoint support: interface coefficients of the operator with the
     // coupling sign reversed, and per-class M0^-1 (n x n each)
     double* d_if_coef_adj = nullptr;
+    float* d_if_coef_adj_f32 = nullptr;   // its FP32 copy (the FP32 adjoint)
     double* d_cls_minv = nullptr;
     // host copies for the cost model
     std::vector<double> h_cls_dbl;

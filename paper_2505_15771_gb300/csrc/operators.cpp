@@ -848,6 +848,7 @@ extern "C" int hho_operators_build_tau(const hho_mesh* m, int32_t k, const doubl
     D.beta_s_x = dev_upload(ops, to_x(beta_s), &err);
     D.if_coef_x = dev_upload(ops, to_x(if_coef), &err);
     ops->d_if_coef_adj = dev_upload(ops, if_coef_adj, &err);
+    ops->d_if_coef_adj_f32 = dev_upload(ops, to_f32(if_coef_adj), &err);
     {
         std::vector<double> minv;
         for (int cl = 0; cl < NCL; ++cl)

@@ -2605,6 +2605,34 @@ void launch_stage_f64(const hho_ops* ops, int mode, StageArgsT<double>& a, int n
     }
 }
 
+void launch_stage_f32(const hho_ops* ops, int mode, StageArgsT<float>& a, int n_shots, double tn, int j, double cdt,
+                      bool sources, void* stream) {
+    const dim3 grid((ops->dev.Nf + ops->dev.Ns + 127) / 128, n_shots);
+    if (grid.x == 0) return;
+    a.state_stride = ops->n_state;
+    a.trace_stride = ops->trace_doubles;
+    if (sources) {
+        fill_sources<float>(ops, a, tn, j, cdt, n_shots);
+    } else {
+        a.n_src = 0;
+        a.shot_src_q = nullptr;
+        a.shot_src_dom = nullptr;
+        a.shot_src_g = nullptr;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    switch (mode) {
+        case MODE_TRACES: launch_k<float, MODE_TRACES>(ops->k, a, grid, st); break;
+        case MODE_STAGE: launch_k<float, MODE_STAGE>(ops->k, a, grid, st); break;
+        case MODE_APPLY: launch_k<float, MODE_APPLY>(ops->k, a, grid, st); break;
+        default: launch_k<float, MODE_RAW>(ops->k, a, grid, st); break;
+    }
+}
+
+int erk_steps_f32(hho_ops* ops, const hho_tableau* tab, double t0, double dt, int64_t nsteps, float* d_state,
+                  float* d_work, void* stream) {
+    return erk_run<float>(ops, tab, t0, dt, nsteps, 1, d_state, d_work, nullptr, stream, "hho_adjoint_vjp_f32");
+}
+
 void launch_record_f64(const hho_ops* ops, const double* state, double* out, void* stream) {
     if (ops->n_rec == 0) return;
     record_kernel<double><<<dim3((ops->n_rec + 63) / 64, 1), 64, 0, (cudaStream_t)stream>>>(

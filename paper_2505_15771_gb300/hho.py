@@ -80,6 +80,8 @@ _SIGS = {
     "hho_locate_points": (C.c_int, [_P, _I64, _P, _P]),
     "hho_tc_gemm_check": (C.c_int, [_I32, _I32, _P, _P, _P, _P]),
     "hho_tc_error": (C.c_int, [_P, _P]),
+    "hho_adjoint_work_size_f32": (C.c_int, [_P, C.POINTER(Tableau), _I64, _I64, C.POINTER(_I64)]),
+    "hho_adjoint_vjp_f32": (C.c_int, [_P, C.POINTER(Tableau), _D, _D, _I64, _I64, _P, _P, _P, _I64, _P, _P, _P, _P]),
     "hho_erk_traces": (C.c_int, [_P, C.POINTER(Tableau), _P, _P, _P]),
     "hho_erk_stage": (C.c_int, [_P, C.POINTER(Tableau), _I64, _I32, _D, _D, _P, _P, _P]),
     "hho_trace_buffer_offset": (C.c_int, [_P, C.POINTER(Tableau), _I32, C.POINTER(_I64)]),
@@ -496,4 +498,22 @@ def hho_adjoint_vjp(ops, tab, t0, dt, nsteps, checkpoint_every, d_state0, d_cota
     _check(lib().hho_adjoint_vjp(ops, C.byref(tab), float(t0), float(dt), int(nsteps), int(checkpoint_every),
                                  d_state0, d_cotangent, d_work, int(work_doubles), _ptr(g),
                                  None if w is None else _ptr(w), None if gt is None else _ptr(gt), stream))
+    return (g, w, gt) if with_tau else (g, w)
+
+
+def hho_adjoint_work_size_f32(ops, tab, nsteps, checkpoint_every):
+    n = _I64()
+    _check(lib().hho_adjoint_work_size_f32(ops, C.byref(tab), int(nsteps), int(checkpoint_every), C.byref(n)))
+    return n.value
+
+
+def hho_adjoint_vjp_f32(ops, tab, t0, dt, nsteps, checkpoint_every, d_state0, d_cotangent, d_work, work_floats,
+                        n_cells, n_src=0, stream=0, with_tau=False):
+    """FP32 reverse mode (float32 state, cotangent and work); outputs as hho_adjoint_vjp."""
+    g = np.zeros((n_cells, 4), np.float64)
+    w = np.zeros((int(nsteps), tab.s, n_src), np.float64) if n_src > 0 else None
+    gt = np.zeros(n_cells, np.float64) if with_tau else None
+    _check(lib().hho_adjoint_vjp_f32(ops, C.byref(tab), float(t0), float(dt), int(nsteps), int(checkpoint_every),
+                                     d_state0, d_cotangent, d_work, int(work_floats), _ptr(g),
+                                     None if w is None else _ptr(w), None if gt is None else _ptr(gt), stream))
     return (g, w, gt) if with_tau else (g, w)

@@ -229,3 +229,38 @@ def hho_layout_k1(hho, md, med):
     n = hho.hho_state_layout(ops).n_canonical
     hho.hho_ops_destroy(ops)
     return n
+
+
+def test_fp32_adjoint_against_fp64(lib):
+    """The FP32 reverse mode (FP32 stage kernels, FP64 gradient sums) against
+    the FP64 one on the same problem, tau following the materials: material,
+    wavelet and tau gradients within 1e-3 relative (FP32 rounding over 30
+    steps), with cell and interface receivers."""
+    hho, solver = lib
+    md = synth.quad_grid(8, 8)
+    med = media(md, 6)
+    nc = md.n_cells
+    nsteps, dt, ckpt = 30, 0.003, 7
+    tab = hho.hho_tableau_erk(4)
+    ops = gpu_problem(hho, md, 2, med)
+    try:
+        lay = hho.hho_state_layout(ops)
+        U0 = synth.random_state(lay.n_canonical, 12)
+        G = np.random.default_rng(13).standard_normal((nsteps, len(PTS), 5))
+        g64, w64, t64 = gpu_vjp(hho, ops, U0, dt, nsteps, G, nc, 4, ckpt=ckpt, with_tau=True)
+        c = torch.as_tensor(U0).cuda()
+        x64 = torch.zeros(lay.n_state, dtype=torch.float64, device="cuda")
+        hho.hho_state_pack(ops, c.data_ptr(), x64.data_ptr())
+        x32 = x64.float()
+        g32t = torch.as_tensor(G).float().cuda().contiguous()
+        nw = hho.hho_adjoint_work_size_f32(ops, tab, nsteps, ckpt)
+        work = torch.empty(nw, dtype=torch.float32, device="cuda")
+        g32, w32, t32 = hho.hho_adjoint_vjp_f32(ops, tab, 0.0, dt, nsteps, ckpt, x32.data_ptr(), g32t.data_ptr(),
+                                                work.data_ptr(), nw, nc, n_src=1, with_tau=True)
+    finally:
+        hho.hho_ops_destroy(ops)
+    eg = np.linalg.norm(g32 - g64) / np.linalg.norm(g64)
+    ew = np.linalg.norm(w32 - w64) / np.linalg.norm(w64)
+    et = np.linalg.norm(t32 - t64) / np.linalg.norm(t64)
+    print("FP32 adjoint vs FP64: materials %.2e, wavelet %.2e, tau %.2e" % (eg, ew, et))
+    assert eg <= 1e-3 and ew <= 1e-3 and et <= 1e-3
