@@ -703,16 +703,8 @@ __device__ __forceinline__ void fluid_cell(const StageArgsT<T>& A, int q, int sh
                                                             OpData<T>::beta_f(op), rect ? 4 : c.nF);
         if (rect) {
             // faces 0 (s = -1) and 2 (s = +1) are horizontal, 1 (s = +1) and 3 (s = -1) vertical
-            if constexpr (RectLoop<T>::value) {
-#pragma unroll 1
-                for (int h = 0; h < 2; ++h) fluid_face_rate<T, K, RectAxis<0>>(A, c, 2 * h, 2 * h - 1, kmx, kmy, kp);
-#pragma unroll 1
-                for (int v = 0; v < 2; ++v)
-                    fluid_face_rate<T, K, RectAxis<1>>(A, c, 1 + 2 * v, 1 - 2 * v, kmx, kmy, kp);
-            } else {
-                fluid_pair_rate<T, K, 0>(A, c, kmx, kmy, kp);   // faces 0 and 2
-                fluid_pair_rate<T, K, 1>(A, c, kmx, kmy, kp);   // faces 1 and 3
-            }
+            fluid_pair_rate<T, K, 0>(A, c, kmx, kmy, kp);   // faces 0 and 2
+            fluid_pair_rate<T, K, 1>(A, c, kmx, kmy, kp);   // faces 1 and 3
         } else {
 #pragma unroll 1
             for (int j = 0; j < c.nF; ++j) fluid_face_rate<T, K, GenericFace>(A, c, j, 1, kmx, kmy, kp);
@@ -1003,17 +995,8 @@ __device__ __forceinline__ void solid_cell(const StageArgsT<T>& A, int q, int sh
             prefetch_cell<T, K, 5 * n, 2 * f, 1, MODE != MODE_RAW>(A, c, soff, c.trs_in, c.SS, op.nb_s,
                                                                 OpData<T>::beta_s(op), rect ? 4 : c.nF);
         if (rect) {
-            if constexpr (RectLoop<T>::value) {
-#pragma unroll 1
-                for (int h = 0; h < 2; ++h)
-                    solid_face_rate<T, K, RectAxis<0>>(A, c, 2 * h, 2 * h - 1, exx, eyy, exy, kvx, kvy);
-#pragma unroll 1
-                for (int v = 0; v < 2; ++v)
-                    solid_face_rate<T, K, RectAxis<1>>(A, c, 1 + 2 * v, 1 - 2 * v, exx, eyy, exy, kvx, kvy);
-            } else {
-                solid_pair_rate<T, K, 0>(A, c, exx, eyy, exy, kvx, kvy);   // faces 0 and 2
-                solid_pair_rate<T, K, 1>(A, c, exx, eyy, exy, kvx, kvy);   // faces 1 and 3
-            }
+            solid_pair_rate<T, K, 0>(A, c, exx, eyy, exy, kvx, kvy);   // faces 0 and 2
+            solid_pair_rate<T, K, 1>(A, c, exx, eyy, exy, kvx, kvy);   // faces 1 and 3
         } else {
 #pragma unroll 1
             for (int j = 0; j < c.nF; ++j) solid_face_rate<T, K, GenericFace>(A, c, j, 1, exx, eyy, exy, kvx, kvy);
