@@ -579,29 +579,8 @@ __device__ __forceinline__ void fluid_face_rate(const StageArgsT<T>& A, const Ce
     constexpr int n = Dims<K>::n, f = Dims<K>::f, FS = Dims<K>::FS;
     const DevOps& op = A.op;
     const T* fm = c.cd + j * FS;
-    const int slot = c.sbase + j * c.npad + c.lq;
-    const int nb = __ldg(op.nb_f + slot);
     T jmp[f];
-#pragma unroll
-    for (int l = 0; l < f; ++l) jmp[l] = __ldg(c.trf_in + (size_t)(f + l) * c.SF + slot);
-    if (nb >= 0) {
-        const T be = __ldg(OpData<T>::beta_f(op) + slot);
-#pragma unroll
-        for (int l = 0; l < f; ++l) {
-            const T w = __ldg(c.trf_in + (size_t)l * c.SF + nb);
-            jmp[l] = (l & 1) ? fma(-be, w, jmp[l]) : fma(be, w, jmp[l]);
-        }
-    } else if (nb < NB_BOUNDARY) {
-        const int r = -2 - nb;
-        const int ns = __ldg(op.if_nb + r);
-        const T* co = OpData<T>::if_coef(op) + 6 * r;
-        const T bx = __ldg(co + 1), by = __ldg(co + 2);
-#pragma unroll
-        for (int l = 0; l < f; ++l) {
-            const T ws = fma(bx, __ldg(c.trs_in + (size_t)l * c.SS + ns), by * __ldg(c.trs_in + (size_t)(f + l) * c.SS + ns));
-            jmp[l] = (l & 1) ? jmp[l] - ws : jmp[l] + ws;
-        }
-    }
+    fluid_face_jump<T, K>(A, c, j, jmp);
     T lv[n];
     lift_apply<T, K, P>(fm + Dims<K>::LI, jmp, lv);
     if constexpr (P::rect) {
@@ -755,71 +734,6 @@ __device__ __forceinline__ void fluid_cell(const StageArgsT<T>& A, int q, int sh
 }
 
 // ---- solid cells -------------------------------------------------------------------
-// Lift one face's velocity jump into the raw accumulators: e (strain rate,
-// symmetric-gradient part) and kv (div s part, tau folded).
-template <class T, int K, class P>
-__device__ __forceinline__ void solid_face_rate(const StageArgsT<T>& A, const CellCtx<T>& c, int j, int sg, T* exx,
-                                                T* eyy, T* exy, T* kvx, T* kvy) {
-    constexpr int n = Dims<K>::n, f = Dims<K>::f, FS = Dims<K>::FS;
-    const DevOps& op = A.op;
-    const T* fm = c.cd + j * FS;
-    const int slot = c.sbase + j * c.npad + c.lq;
-    const int nb = __ldg(op.nb_s + slot);
-    T jx[f], jy[f];
-#pragma unroll
-    for (int l = 0; l < f; ++l) {
-        jx[l] = __ldg(c.trs_in + (size_t)(2 * f + l) * c.SS + slot);
-        jy[l] = __ldg(c.trs_in + (size_t)(3 * f + l) * c.SS + slot);
-    }
-    if (nb >= 0) {
-        const T be = __ldg(OpData<T>::beta_s(op) + slot);
-#pragma unroll
-        for (int l = 0; l < f; ++l) {
-            const T wx = __ldg(c.trs_in + (size_t)l * c.SS + nb);
-            const T wy = __ldg(c.trs_in + (size_t)(f + l) * c.SS + nb);
-            jx[l] = (l & 1) ? fma(-be, wx, jx[l]) : fma(be, wx, jx[l]);
-            jy[l] = (l & 1) ? fma(-be, wy, jy[l]) : fma(be, wy, jy[l]);
-        }
-    } else if (nb < NB_BOUNDARY) {
-        const int r = -2 - nb;
-        const int nfs = __ldg(op.if_nb + r);
-        const T* co = OpData<T>::if_coef(op) + 6 * r;
-        const T b0 = __ldg(co + 4), b1 = __ldg(co + 5);
-#pragma unroll
-        for (int l = 0; l < f; ++l) {
-            const T wf = __ldg(c.trf_in + (size_t)l * c.SF + nfs);
-            jx[l] = (l & 1) ? fma(-b0, wf, jx[l]) : fma(b0, wf, jx[l]);
-            jy[l] = (l & 1) ? fma(-b1, wf, jy[l]) : fma(b1, wf, jy[l]);
-        }
-    }
-    const T* L = fm + Dims<K>::LI;
-    T lx[n], ly[n];
-    lift_apply<T, K, P>(L, jx, lx);
-    lift_apply<T, K, P>(L, jy, ly);
-    if constexpr (P::rect) {
-        if constexpr (P::horiz) {
-            add_signed<n>(ly, eyy, sg);
-            add_signed<n>(lx, exy, sg);
-        } else {
-            add_signed<n>(lx, exx, sg);
-            add_signed<n>(ly, exy, sg);
-        }
-    } else {
-        const T nx = cls_val(fm), ny = cls_val(fm + 1);
-#pragma unroll
-        for (int i = 0; i < n; ++i) {
-            exx[i] = fma(nx, lx[i], exx[i]);
-            eyy[i] = fma(ny, ly[i], eyy[i]);
-            exy[i] = fma(nx, ly[i], fma(ny, lx[i], exy[i]));
-        }
-    }
-#pragma unroll
-    for (int i = 0; i < n; ++i) {
-        kvx[i] = fma(c.tau, lx[i], kvx[i]);
-        kvy[i] = fma(c.tau, ly[i], kvy[i]);
-    }
-}
-
 // The velocity jump v_F - v|_F on local face j (components x, y).
 template <class T, int K>
 __device__ __forceinline__ void solid_face_jump(const StageArgsT<T>& A, const CellCtx<T>& c, int j, T* jx, T* jy) {
@@ -852,6 +766,44 @@ __device__ __forceinline__ void solid_face_jump(const StageArgsT<T>& A, const Ce
             jx[l] = (l & 1) ? fma(-b0, wf, jx[l]) : fma(b0, wf, jx[l]);
             jy[l] = (l & 1) ? fma(-b1, wf, jy[l]) : fma(b1, wf, jy[l]);
         }
+    }
+}
+
+// Lift one face's velocity jump into the raw accumulators: e (strain rate,
+// symmetric-gradient part) and kv (div s part, tau folded).
+template <class T, int K, class P>
+__device__ __forceinline__ void solid_face_rate(const StageArgsT<T>& A, const CellCtx<T>& c, int j, int sg, T* exx,
+                                                T* eyy, T* exy, T* kvx, T* kvy) {
+    constexpr int n = Dims<K>::n, f = Dims<K>::f, FS = Dims<K>::FS;
+    const DevOps& op = A.op;
+    const T* fm = c.cd + j * FS;
+    T jx[f], jy[f];
+    solid_face_jump<T, K>(A, c, j, jx, jy);
+    const T* L = fm + Dims<K>::LI;
+    T lx[n], ly[n];
+    lift_apply<T, K, P>(L, jx, lx);
+    lift_apply<T, K, P>(L, jy, ly);
+    if constexpr (P::rect) {
+        if constexpr (P::horiz) {
+            add_signed<n>(ly, eyy, sg);
+            add_signed<n>(lx, exy, sg);
+        } else {
+            add_signed<n>(lx, exx, sg);
+            add_signed<n>(ly, exy, sg);
+        }
+    } else {
+        const T nx = cls_val(fm), ny = cls_val(fm + 1);
+#pragma unroll
+        for (int i = 0; i < n; ++i) {
+            exx[i] = fma(nx, lx[i], exx[i]);
+            eyy[i] = fma(ny, ly[i], eyy[i]);
+            exy[i] = fma(nx, ly[i], fma(ny, lx[i], exy[i]));
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < n; ++i) {
+        kvx[i] = fma(c.tau, lx[i], kvx[i]);
+        kvy[i] = fma(c.tau, ly[i], kvy[i]);
     }
 }
 
