@@ -253,9 +253,19 @@ __global__ void grad_kernel(DevOps op, const T* __restrict__ mu, const T* __rest
     }
 }
 
+// (psi_l, psi_m) over a face of unit length: the face basis
+// psi_l = (rho0 xi)^l, xi in [-1, 1], gives rho0^(l+m) / (l+m+1) for even
+// l + m and 0 otherwise.
+__device__ __forceinline__ double face_gram(int l, int m) {
+    if ((l + m) & 1) return 0.0;
+    double r = 1.0;
+    for (int e = 0; e < l + m; ++e) r *= FACE_RHO;
+    return r / (l + m + 1);
+}
+
 // Stabilisation-weight part of one backward stage: for every cell,
-// gstab += sum_F |F|/h sum_l jY_l jX_l / (2l+1), the face integrals (Legendre
-// basis on the face) of the products of the primal jumps u_F - u|_F of the
+// gstab += sum_F |F|/h jY^T G jX, the face integrals (G = face_gram) of the
+// products of the primal jumps u_F - u|_F of the
 // forward stage value (traces trY, coefficients of op) and of x = S M^-1 mu
 // (traces trX under the coupling-reversed operator opx).  The host multiplies
 // by -h per cell.  Same jump formulas as the stage kernel's face rates.
@@ -284,6 +294,7 @@ __global__ void tau_grad_kernel(DevOps op, DevOps opx, const T* __restrict__ trY
         const double rel = cd[j * FS + 2];   // |F| / h
         const int slot = sbase + j * npad + lq;
         double sum = 0.0;
+        double ja[2][4], jb[2][4];   // jumps (Y, X) of up to two components
         if (fl) {
             const int nb = op.nb_f[slot];
             for (int l = 0; l < f; ++l) {
@@ -300,8 +311,11 @@ __global__ void tau_grad_kernel(DevOps op, DevOps opx, const T* __restrict__ trY
                     jy += sg * (cy[1] * ys[(size_t)l * SS + ns] + cy[2] * ys[(size_t)(f + l) * SS + ns]);
                     jx += sg * (cx[1] * xs[(size_t)l * SS + ns] + cx[2] * xs[(size_t)(f + l) * SS + ns]);
                 }
-                sum += jy * jx / (2 * l + 1);
+                ja[0][l] = jy;
+                jb[0][l] = jx;
             }
+            for (int l = 0; l < f; ++l)
+                for (int m = 0; m < f; ++m) sum += ja[0][l] * face_gram(l, m) * jb[0][m];
         } else {
             const int nb = op.nb_s[slot];
             for (int l = 0; l < f; ++l) {
@@ -324,8 +338,14 @@ __global__ void tau_grad_kernel(DevOps op, DevOps opx, const T* __restrict__ trY
                     jxx += sg * cx[4] * wx;
                     jxy += sg * cx[5] * wx;
                 }
-                sum += (jyx * jxx + jyy * jxy) / (2 * l + 1);
+                ja[0][l] = jyx;
+                ja[1][l] = jyy;
+                jb[0][l] = jxx;
+                jb[1][l] = jxy;
             }
+            for (int l = 0; l < f; ++l)
+                for (int m = 0; m < f; ++m)
+                    sum += (ja[0][l] * jb[0][m] + ja[1][l] * jb[1][m]) * face_gram(l, m);
         }
         acc += rel * sum;
     }

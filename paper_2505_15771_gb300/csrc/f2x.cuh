@@ -23,8 +23,12 @@
 // saving is three instructions per operation and a shorter dependency chain
 // through each accumulator.  No step relies on FMA contraction of a separate
 // multiply and add: where the exact product error is needed the FMA is
-// explicit.  The type is a plain pair so that arrays of it have the layout of
-// FP64 arrays (8 bytes a value).
+// explicit.  Nor may the compiler contract one (nvcc does by default, and a
+// product fused into the TwoSum that follows it breaks the error-free
+// transformation, leaving FP32-level errors): every rounded sum, difference
+// and product here is an __f*_rn intrinsic, which is never contracted.  The
+// type is a plain pair so that arrays of it have the layout of FP64 arrays
+// (8 bytes a value).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -32,21 +36,21 @@
 #include "hho_internal.h"
 
 __device__ __forceinline__ f2x f2x_fast_two_sum(float a, float b) {
-    const float s = a + b;
-    const float z = s - a;
-    return f2x{s, b - z};
+    const float s = __fadd_rn(a, b);
+    const float z = __fsub_rn(s, a);
+    return f2x{s, __fsub_rn(b, z)};
 }
 
 __device__ __forceinline__ f2x f2x_two_sum(float a, float b) {
-    const float s = a + b;
-    const float ap = s - b;
-    const float bp = s - ap;
-    return f2x{s, (a - ap) + (b - bp)};
+    const float s = __fadd_rn(a, b);
+    const float ap = __fsub_rn(s, b);
+    const float bp = __fsub_rn(s, ap);
+    return f2x{s, __fadd_rn(__fsub_rn(a, ap), __fsub_rn(b, bp))};
 }
 
 __device__ __forceinline__ f2x operator+(f2x x, f2x y) {
     const f2x s = f2x_two_sum(x.hi, y.hi);
-    const float w = s.lo + (x.lo + y.lo);
+    const float w = __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo));
     return f2x{s.hi, w};
 }
 __device__ __forceinline__ f2x operator-(f2x x) { return f2x{-x.hi, -x.lo}; }
@@ -55,7 +59,7 @@ __device__ __forceinline__ f2x& operator+=(f2x& x, f2x y) { return x = x + y; }
 __device__ __forceinline__ f2x& operator-=(f2x& x, f2x y) { return x = x - y; }
 
 __device__ __forceinline__ f2x operator*(f2x x, f2x y) {
-    const float p = x.hi * y.hi;
+    const float p = __fmul_rn(x.hi, y.hi);
     float e = fmaf(x.hi, y.hi, -p);
     e = fmaf(x.hi, y.lo, e);
     e = fmaf(x.lo, y.hi, e);
@@ -64,37 +68,37 @@ __device__ __forceinline__ f2x operator*(f2x x, f2x y) {
 
 // x * y + z
 __device__ __forceinline__ f2x fma(f2x x, f2x y, f2x z) {
-    const float p = x.hi * y.hi;
+    const float p = __fmul_rn(x.hi, y.hi);
     float e = fmaf(x.hi, y.hi, -p);
     e = fmaf(x.hi, y.lo, e);
     e = fmaf(x.lo, y.hi, e);
     const f2x s = f2x_two_sum(p, z.hi);
-    const float w = s.lo + (e + z.lo);
+    const float w = __fadd_rn(s.lo, __fadd_rn(e, z.lo));
     return f2x{s.hi, w};
 }
 
 // c * x and c * x + z for an FP32 constant c (the exact small integers of
 // the polynomial derivatives)
 __device__ __forceinline__ f2x mulc(float c, f2x x) {
-    const float p = c * x.hi;
+    const float p = __fmul_rn(c, x.hi);
     float e = fmaf(c, x.hi, -p);
     e = fmaf(c, x.lo, e);
     return f2x{p, e};
 }
 __device__ __forceinline__ f2x fmac(float c, f2x x, f2x z) {
-    const float p = c * x.hi;
+    const float p = __fmul_rn(c, x.hi);
     float e = fmaf(c, x.hi, -p);
     e = fmaf(c, x.lo, e);
     const f2x s = f2x_two_sum(p, z.hi);
-    const float w = s.lo + (e + z.lo);
+    const float w = __fadd_rn(s.lo, __fadd_rn(e, z.lo));
     return f2x{s.hi, w};
 }
 
 __device__ __forceinline__ f2x operator/(f2x x, f2x y) {
     y = f2x_fast_two_sum(y.hi, y.lo);
-    const float q = x.hi / y.hi;
+    const float q = __fdiv_rn(x.hi, y.hi);
     const f2x r = x - mulc(q, y);
-    return f2x_fast_two_sum(q, (r.hi + r.lo) / y.hi);
+    return f2x_fast_two_sum(q, __fdiv_rn(__fadd_rn(r.hi, r.lo), y.hi));
 }
 
 // Read-only load of a pair (one 8-byte load).

@@ -59,8 +59,14 @@ enum { CI_DOMAIN = 0, CI_NF, CI_START, CI_COUNT, CI_NPAD, CI_SLOT, CI_DOFF, CI_K
 
 // Class kinds: generic polygon (dense class matrices) or axis-aligned
 // rectangle with faces ordered bottom, right, top, left, whose trace and
-// lifting matrices have a sparsity pattern fixed by monomial parity.
-enum { KIND_GENERIC = 0, KIND_RECT = 1 };
+// lifting matrices have a sparsity pattern fixed by monomial parity; a
+// square rectangle's traces are known in closed form (operators.cpp).
+enum { KIND_GENERIC = 0, KIND_RECT = 1, KIND_SQUARE = 2 };
+
+// Scale of the face basis psi_l = (FACE_RHO xi)^l, xi in [-1, 1] along a
+// face: 1/(2 sqrt 2), the half side over the diameter of a square, so that a
+// square cell's scaled coordinates are +-FACE_RHO on its faces.
+#define FACE_RHO 0.35355339059327376220
 
 // Device-side description of one stage launch and the static operator data.
 struct DevOps {

@@ -3,10 +3,11 @@
 //
 // What a stage needs, per cell T of diameter h (all matrices dimensionless, in
 // the scaled-monomial basis phi_(a,b) = X^a Y^b, X = (x - x_T)/h):
-//   * the trace of a cell polynomial on local face j in the Legendre basis of
-//     that face, Tr_j (f x n), with xi running along the counter-clockwise edge;
+//   * the trace of a cell polynomial on local face j in the face basis
+//     psi_l = (rho0 xi)^l, l <= k, rho0 = 1/(2 sqrt 2) (FACE_RHO), with xi in
+//     [-1, 1] running along the counter-clockwise edge: Tr_j (f x n);
 //   * the lifting of a face polynomial, Lift_j = M0^-1 B_j (n x f), where
-//     M0 = (phi_j, phi_i)_T and B_j = (P_l, phi_i)_F in scaled coordinates;
+//     M0 = (phi_j, phi_i)_T and B_j = (psi_l, phi_i)_F in scaled coordinates;
 //   * the outward unit normal n_j.
 // With these, the weak form (Eq. rec, Eq. stab, mass Eq. mass) gives, for the
 // jump J_F = u_F - u_T|_F on each face:
@@ -16,6 +17,15 @@
 //   dv/dt = 1/(rho h) [ div^ s  + tau sum_F Lift_F J_F ]
 // (hats: derivatives in scaled coordinates), which is the condensed operator
 // of Eq. ex_solve applied cell by cell.
+//
+// Any basis of P_k(F) serves the face solve (Eq. ex_solve): the trace of a
+// cell polynomial on a straight face is a polynomial of degree k, so both
+// sides' traces, fluxes and the face unknown are exact coefficient vectors
+// and the face equations hold coefficient by coefficient.  The scaled
+// monomials psi_l make the traces of a square cell (X, Y = +-rho0 on its
+// faces) single terms: X^a Y^b traces to (+-rho0)^b psi_a on a horizontal
+// face, so the square kernels evaluate them by Horner's rule in +-rho0
+// without reading a matrix.
 //
 // Integration route: fan of triangles from the centroid, each integrated with
 // a collapsed (Duffy) Gauss-Legendre rule; Legendre nodes by Newton's method.
@@ -62,10 +72,37 @@ void gauss_legendre(int q, std::vector<double>& x, std::vector<double>& w) {
     }
 }
 
-void legendre_values(int f, double xi, double* P) {
+// psi_l(xi) = (rho0 xi)^l, l < f
+void face_basis_values(int f, double xi, double* P) {
     P[0] = 1.0;
-    if (f > 1) P[1] = xi;
-    for (int l = 2; l < f; ++l) P[l] = ((2.0 * l - 1.0) * xi * P[l - 1] - (l - 1.0) * P[l - 2]) / l;
+    for (int l = 1; l < f; ++l) P[l] = P[l - 1] * (FACE_RHO * xi);
+}
+
+double ipow(double x, int e) {
+    double r = 1.0;
+    for (int i = 0; i < e; ++i) r *= x;
+    return r;
+}
+
+double binom(int a, int p) {
+    double r = 1.0;
+    for (int i = 1; i <= p; ++i) r = r * (a - p + i) / i;
+    return r;
+}
+
+// Trace of X^a Y^b on the edge (X, Y) = (Xm + Xd xi, Ym + Yd xi), xi in
+// [-1, 1], in the basis psi_l: the binomial expansion of both factors,
+// coefficient of xi^m divided by rho0^m.
+void face_trace_row(int a, int b, double Xm, double Xd, double Ym, double Yd, int f, double* tr) {
+    for (int m = 0; m < f; ++m) {
+        double c = 0.0;
+        for (int p = 0; p <= a && p <= m; ++p) {
+            const int q = m - p;
+            if (q > b) continue;
+            c += binom(a, p) * ipow(Xm, a - p) * ipow(Xd, p) * binom(b, q) * ipow(Ym, b - q) * ipow(Yd, q);
+        }
+        tr[m] = c / ipow(FACE_RHO, m);
+    }
 }
 
 void exponents(int k, std::vector<int>& A, std::vector<int>& B) {
@@ -253,7 +290,7 @@ static int pad16(int v) { return (v + 15) / 16 * 16; }
 //     v_x, v_y before tau): B1 = n_F-weighted Lift_F (Eq. rec lifted by M0^-1).
 //   GEMM 2 (traces): D2 = X B2, X the stage value's fields, D2's 16-column
 //     block per face holding that face's traces (fluid: p, m.n; solid: v_x,
-//     v_y, (s n)_x, (s n)_y), f Legendre coefficients each.
+//     v_y, (s n)_x, (s n)_y), f face-basis coefficients each.
 // Each B is stored transposed (N x K) in the K-major core-matrix layout of
 // tc.cuh, as two BF16 tiles hi and lo with B = hi + lo.
 static int tc_tiles(hho_ops* ops, const std::vector<double>& cls_dbl, const std::vector<int32_t>& doff,
@@ -519,17 +556,19 @@ extern "C" int hho_operators_build_tau(const hho_mesh* m, int32_t k, const doubl
             if (std::fabs(ny) < 1e-15) ny = 0.0;
             ops->class_normals[cl].push_back(nx);
             ops->class_normals[cl].push_back(ny);
-            std::vector<double> Tr(f * n, 0.0), Bm(n * f, 0.0);
-            for (size_t g = 0; g < fx.size(); ++g) {
+            std::vector<double> Tr(f * n, 0.0), Bm(n * f, 0.0), row(f);
+            for (int i = 0; i < n; ++i) {
+                face_trace_row(EA[i], EB[i], 0.5 * (X[j] + X[j1]), 0.5 * ex, 0.5 * (Y[j] + Y[j1]), 0.5 * ey, f,
+                               row.data());
+                for (int l = 0; l < f; ++l) Tr[l * n + i] = row[l];
+            }
+            for (size_t g = 0; g < fx.size(); ++g) {   // k + 2 points: exact for degree 2k
                 double xi = fx[g];
                 double s = 0.5 * (xi + 1.0);
                 basis_values(EA, EB, X[j] + s * ex, Y[j] + s * ey, phi.data());
-                legendre_values(f, xi, Pl.data());
+                face_basis_values(f, xi, Pl.data());
                 for (int l = 0; l < f; ++l)
-                    for (int i = 0; i < n; ++i) {
-                        Tr[l * n + i] += (2.0 * l + 1.0) / 2.0 * fw[g] * phi[i] * Pl[l];
-                        Bm[i * f + l] += 0.5 * L * fw[g] * phi[i] * Pl[l];
-                    }
+                    for (int i = 0; i < n; ++i) Bm[i * f + l] += 0.5 * L * fw[g] * phi[i] * Pl[l];
             }
             std::vector<double> Lift(n * f, 0.0);
             for (int i = 0; i < n; ++i)
@@ -565,7 +604,7 @@ extern "C" int hho_operators_build_tau(const hho_mesh* m, int32_t k, const doubl
     // ---- class kinds: axis-aligned rectangles (faces bottom, right, top, left) ----
     // The rectangle kernels skip, at compile time, the entries that vanish by
     // parity: on a horizontal face a cell monomial X^a Y^b traces to a
-    // multiple of xi^a, so Tr[l][i] = 0 unless l <= a and l = a (mod 2);
+    // multiple of xi^a, so Tr[l][i] = 0 unless l = a;
     // Lift[i][l] = 0 unless a_i = l (mod 2) (M0 couples only equal parities);
     // vertical faces use b.  The pattern is checked against the computed
     // matrices before a class is marked.
@@ -583,7 +622,7 @@ extern "C" int hho_operators_build_tau(const hho_mesh* m, int32_t k, const doubl
             for (int l = 0; l < f && ok; ++l)
                 for (int i = 0; i < n && ok; ++i) {
                     int e = (j % 2 == 0) ? EA[i] : EB[i];
-                    bool tr_nz = e >= l && ((e - l) % 2) == 0;
+                    bool tr_nz = e == l;
                     bool li_nz = ((e + l) % 2) == 0;
                     if (!tr_nz && fm[4 + l * nP + i] != 0.0) ok = false;
                     if (!li_nz && fm[4 + f * nP + i * fP + l] != 0.0) ok = false;
@@ -606,7 +645,24 @@ extern "C" int hho_operators_build_tau(const hho_mesh* m, int32_t k, const doubl
                     const double b = cd[(j + 2) * FS + 4 + f * nP + i * fP + l];
                     if (std::fabs(b - sgn * a) > 1e-12 * lmax) ok = false;
                 }
-        if (ok) cls_kind[cl] = KIND_RECT;
+        if (!ok) continue;
+        cls_kind[cl] = KIND_RECT;
+        // A square (X, Y in [-rho0, rho0]) traces X^a Y^b on face j to
+        // s_t^l (s_n rho0)^(e_n) psi_l, l = e_t, with e_t / e_n the exponent
+        // along / across the face, s_n the sign of the face's normal
+        // coordinate and s_t of its direction: (s_n, s_t) = (-1, 1), (1, 1),
+        // (1, -1), (-1, -1) for faces 0..3.  The square kernels use these
+        // values instead of the stored rows.
+        const int sn[4] = {-1, 1, 1, -1}, st[4] = {1, 1, -1, -1};
+        bool sq = true;
+        for (int j = 0; j < 4 && sq; ++j)
+            for (int l = 0; l < f && sq; ++l)
+                for (int i = 0; i < n && sq; ++i) {
+                    const int et = (j % 2 == 0) ? EA[i] : EB[i], en = (j % 2 == 0) ? EB[i] : EA[i];
+                    const double want = et != l ? 0.0 : ((l & 1) && st[j] < 0 ? -1.0 : 1.0) * ipow(sn[j] * FACE_RHO, en);
+                    if (std::fabs(cd[j * FS + 4 + l * nP + i] - want) > 1e-14) sq = false;
+                }
+        if (sq) cls_kind[cl] = KIND_SQUARE;
     }
 
     // ---- device layout: cells sorted by (domain, class), classes padded to 32 ----

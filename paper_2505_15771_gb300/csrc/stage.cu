@@ -3,12 +3,13 @@
 // One stage of Eq. ex_solve (Sec. 4.2) is ONE kernel.  Thread q owns cell q of
 // its domain (cells sorted by class, so a warp shares one class and its class
 // matrices are read with warp-uniform loads).  The face unknowns are never
-// stored: every cell publishes, per local face, two small vectors in the face's
-// Legendre basis (its own counter-clockwise orientation):
+// stored: every cell publishes, per local face, two small vectors in the face
+// basis psi_l = (rho0 xi)^l (xi along the face in the cell's own
+// counter-clockwise orientation; operators.cpp):
 //     w     = tau u_T|_F - (dual flux of T on F)      (what the neighbour needs)
 //     omega = alpha w - u_T|_F                         (what the cell itself needs)
 // where u is p (fluid) or v (solid) and the dual flux is m.n_T or s n_T.  The
-// face solve of Eq. ex_solve is block-diagonal; its closed form per Legendre
+// face solve of Eq. ex_solve is block-diagonal; its closed form per
 // coefficient is
 //     interior:  u_F = (w_T + w_N) / (tau_T + tau_N)
 //     boundary:  u_F = 0
@@ -193,8 +194,11 @@ __device__ __forceinline__ void add_ddy(const T* u, T* out) {
 // argument, the parity sparsity of Tr and Lift is compile-time and entries
 // outside the pattern are never loaded.  One body per orientation, looped
 // over its two faces, keeps the kernel's instruction footprint small.
+// SquareAxis<A>: the faces of a square cell; their traces are Horner sums
+// with compile-time coefficients (trace_square) and Tr is never read.
 struct GenericFace {
     static constexpr bool rect = false;
+    static constexpr bool square = false;
     static constexpr bool horiz = false;
     __host__ __device__ static constexpr bool tr_nz(int, int) { return true; }
     __host__ __device__ static constexpr bool lift_nz(int, int) { return true; }
@@ -202,10 +206,15 @@ struct GenericFace {
 template <int AX>
 struct RectAxis {
     static constexpr bool rect = true;
+    static constexpr bool square = false;
     static constexpr bool horiz = AX == 0;
     __host__ __device__ static constexpr int e(int i) { return horiz ? ea(i) : eb(i); }
-    __host__ __device__ static constexpr bool tr_nz(int l, int i) { return e(i) >= l && ((e(i) - l) % 2) == 0; }
+    __host__ __device__ static constexpr bool tr_nz(int l, int i) { return e(i) == l; }
     __host__ __device__ static constexpr bool lift_nz(int i, int l) { return ((e(i) + l) % 2) == 0; }
+};
+template <int AX>
+struct SquareAxis : RectAxis<AX> {
+    static constexpr bool square = true;
 };
 
 // Class matrices of the double-float kernel are read from a per-warp copy in
@@ -257,6 +266,28 @@ __device__ __forceinline__ void trace_apply(const T* __restrict__ Tr, const T* x
             if (P::tr_nz(l, i)) acc = fma(row[i], x[i], acc);
         y[l] = acc;
     }
+}
+// Traces on a square's face with outward normal sign sg (faces 0 and 3:
+// -1, faces 1 and 2: +1): the monomial with exponent l along the face and m
+// across it traces to s_t^l (sg rho0)^m psi_l, s_t = -sg on horizontal and
+// sg on vertical faces, so y[l] = s_t^l sum_m (sg rho0)^m x[(l, m)] by
+// Horner's rule (K - l multiply-adds).
+template <class T, int K, bool HORIZ>
+__device__ __forceinline__ void trace_square(const T* x, T* y, int sg) {
+    const T c = T(sg > 0 ? FACE_RHO : -FACE_RHO);
+    const bool flip = HORIZ ? sg > 0 : sg < 0;   // s_t = -1
+#pragma unroll
+    for (int l = 0; l <= K; ++l) {
+        T acc = x[HORIZ ? eidx(l, K - l) : eidx(K - l, l)];
+#pragma unroll
+        for (int m = K - l - 1; m >= 0; --m) acc = fma(c, acc, x[HORIZ ? eidx(l, m) : eidx(m, l)]);
+        y[l] = ((l & 1) && flip) ? -acc : acc;
+    }
+}
+template <class T, int K, class P>
+__device__ __forceinline__ void face_trace_apply(const T* __restrict__ Tr, const T* x, T* y, int sg) {
+    if constexpr (P::square) trace_square<T, K, P::horiz>(x, y, sg);
+    else trace_apply<T, K, P>(Tr, x, y);
 }
 // y[i] = sum_l L[i][l] j[l] over the policy's pattern (rows of fP entries).
 template <class T, int K, class P>
@@ -483,7 +514,7 @@ __device__ __forceinline__ T shot_src_value(const StageArgsT<T>& A) {
 // ---- fluid cells -------------------------------------------------------------------
 // Lift the face jump of one face into the raw rate accumulators
 // (kmx, kmy: grad p part; kp: div m part, tau folded).
-// The jump p_F - p|_F on local face j (Legendre coefficients, the cell's
+// The jump p_F - p|_F on local face j (face-basis coefficients, the cell's
 // orientation): own omega plus the neighbour's w (interior), or the
 // interface combination of the solid neighbour's traces.
 template <class T, int K>
@@ -609,15 +640,15 @@ __device__ __forceinline__ void fluid_face_trace(const StageArgsT<T>& A, const C
     const T* my = U + n;
     const T* p = U + 2 * n;
     T tp[f], tm[f];
-    trace_apply<T, K, P>(Tr, p, tp);
+    face_trace_apply<T, K, P>(Tr, p, tp, sg);
     if constexpr (P::rect) {
-        trace_apply<T, K, P>(Tr, P::horiz ? my : mx, tm);
+        face_trace_apply<T, K, P>(Tr, P::horiz ? my : mx, tm, sg);
     } else {
         const T nx = cls_val(fm), ny = cls_val(fm + 1);
         T mn[n];
 #pragma unroll
         for (int i = 0; i < n; ++i) mn[i] = fma(nx, mx[i], ny * my[i]);
-        trace_apply<T, K, P>(Tr, mn, tm);
+        face_trace_apply<T, K, P>(Tr, mn, tm, sg);
     }
     const int sgn = P::rect ? sg : 1;   // rect: tm holds the unsigned trace
     const int slot = c.sbase + j * c.npad + c.lq;
@@ -628,6 +659,23 @@ __device__ __forceinline__ void fluid_face_trace(const StageArgsT<T>& A, const C
         const T w = fma(c.tau, tp[l], (sgn > 0) ? -tm[l] : tm[l]);
         c.trf_out[(size_t)l * c.SF + slot] = norm(w);
         c.trf_out[(size_t)(f + l) * c.SF + slot] = norm(fma(al, w, -tp[l]));
+    }
+}
+
+// The four faces of a rectangle: one body per orientation looped over its
+// two faces (RectLoop), or unrolled with constant signs.
+template <class T, int K, class PH, class PV>
+__device__ __forceinline__ void fluid_rect_traces(const StageArgsT<T>& A, const CellCtx<T>& c, const T* U) {
+    if constexpr (RectLoop<T>::value) {
+#pragma unroll 1
+        for (int h = 0; h < 2; ++h) fluid_face_trace<T, K, PH>(A, c, 2 * h, 2 * h - 1, U);
+#pragma unroll 1
+        for (int v = 0; v < 2; ++v) fluid_face_trace<T, K, PV>(A, c, 1 + 2 * v, 1 - 2 * v, U);
+    } else {
+        fluid_face_trace<T, K, PH>(A, c, 0, -1, U);
+        fluid_face_trace<T, K, PV>(A, c, 1, 1, U);
+        fluid_face_trace<T, K, PH>(A, c, 2, 1, U);
+        fluid_face_trace<T, K, PV>(A, c, 3, -1, U);
     }
 }
 
@@ -655,7 +703,8 @@ __device__ __forceinline__ void fluid_cell(const StageArgsT<T>& A, int q, int sh
     c.trf_out = A.tr_out + toff;
     c.trs_out = A.tr_out + toff + (size_t)2 * f * c.SF;
     const size_t soff = (size_t)shot * A.state_stride;
-    const bool rect = __ldg(ci + CI_KIND) == KIND_RECT;
+    const int kind = __ldg(ci + CI_KIND);
+    const bool rect = kind != KIND_GENERIC;
     T Ureg[AccSmem<T, K>::value ? 1 : 3 * n];
     T* U = AccSmem<T, K>::value ? acc_smem : Ureg;   // [m_x | m_y | p]
     if constexpr (MODE == MODE_TRACES) {
@@ -715,18 +764,10 @@ __device__ __forceinline__ void fluid_cell(const StageArgsT<T>& A, int q, int sh
         write_targets<3 * n, FluidGroups<n>>(A, c.N, soff, q, U, sc);
         if constexpr (MODE == MODE_APPLY) return;
     }
-    if (rect) {
-        if constexpr (RectLoop<T>::value) {
-#pragma unroll 1
-            for (int h = 0; h < 2; ++h) fluid_face_trace<T, K, RectAxis<0>>(A, c, 2 * h, 2 * h - 1, U);
-#pragma unroll 1
-            for (int v = 0; v < 2; ++v) fluid_face_trace<T, K, RectAxis<1>>(A, c, 1 + 2 * v, 1 - 2 * v, U);
-        } else {
-            fluid_face_trace<T, K, RectAxis<0>>(A, c, 0, -1, U);
-            fluid_face_trace<T, K, RectAxis<1>>(A, c, 1, 1, U);
-            fluid_face_trace<T, K, RectAxis<0>>(A, c, 2, 1, U);
-            fluid_face_trace<T, K, RectAxis<1>>(A, c, 3, -1, U);
-        }
+    if (kind == KIND_SQUARE) {
+        fluid_rect_traces<T, K, SquareAxis<0>, SquareAxis<1>>(A, c, U);
+    } else if (rect) {
+        fluid_rect_traces<T, K, RectAxis<0>, RectAxis<1>>(A, c, U);
     } else {
 #pragma unroll 1
         for (int j = 0; j < c.nF; ++j) fluid_face_trace<T, K, GenericFace>(A, c, j, 1, U);
@@ -836,16 +877,16 @@ __device__ __forceinline__ void solid_face_trace(const StageArgsT<T>& A, const C
     const T* vx = U + 3 * n;
     const T* vy = U + 4 * n;
     T tvx[f], tvy[f], tsx[f], tsy[f];
-    trace_apply<T, K, P>(Tr, vx, tvx);
-    trace_apply<T, K, P>(Tr, vy, tvy);
+    face_trace_apply<T, K, P>(Tr, vx, tvx, sg);
+    face_trace_apply<T, K, P>(Tr, vy, tvy, sg);
     if constexpr (P::rect) {
         // s n = (nx s_xx + ny s_xy, nx s_xy + ny s_yy) with one of nx, ny = +-1
         if constexpr (!P::horiz) {
-            trace_apply<T, K, P>(Tr, sxx, tsx);
-            trace_apply<T, K, P>(Tr, sxy, tsy);
+            face_trace_apply<T, K, P>(Tr, sxx, tsx, sg);
+            face_trace_apply<T, K, P>(Tr, sxy, tsy, sg);
         } else {
-            trace_apply<T, K, P>(Tr, sxy, tsx);
-            trace_apply<T, K, P>(Tr, syy, tsy);
+            face_trace_apply<T, K, P>(Tr, sxy, tsx, sg);
+            face_trace_apply<T, K, P>(Tr, syy, tsy, sg);
         }
     } else {
         const T nx = cls_val(fm), ny = cls_val(fm + 1);
@@ -855,8 +896,8 @@ __device__ __forceinline__ void solid_face_trace(const StageArgsT<T>& A, const C
             snx[i] = fma(nx, sxx[i], ny * sxy[i]);
             sny[i] = fma(nx, sxy[i], ny * syy[i]);
         }
-        trace_apply<T, K, P>(Tr, snx, tsx);
-        trace_apply<T, K, P>(Tr, sny, tsy);
+        face_trace_apply<T, K, P>(Tr, snx, tsx, sg);
+        face_trace_apply<T, K, P>(Tr, sny, tsy, sg);
     }
     const int sgn = P::rect ? sg : 1;
     const int slot = c.sbase + j * c.npad + c.lq;
@@ -888,6 +929,23 @@ __device__ __forceinline__ void solid_face_trace(const StageArgsT<T>& A, const C
     }
 }
 
+// The four faces of a rectangle: one body per orientation looped over its
+// two faces (RectLoop), or unrolled with constant signs.
+template <class T, int K, class PH, class PV>
+__device__ __forceinline__ void solid_rect_traces(const StageArgsT<T>& A, const CellCtx<T>& c, const T* U) {
+    if constexpr (RectLoop<T>::value) {
+#pragma unroll 1
+        for (int h = 0; h < 2; ++h) solid_face_trace<T, K, PH>(A, c, 2 * h, 2 * h - 1, U);
+#pragma unroll 1
+        for (int v = 0; v < 2; ++v) solid_face_trace<T, K, PV>(A, c, 1 + 2 * v, 1 - 2 * v, U);
+    } else {
+        solid_face_trace<T, K, PH>(A, c, 0, -1, U);
+        solid_face_trace<T, K, PV>(A, c, 1, 1, U);
+        solid_face_trace<T, K, PH>(A, c, 2, 1, U);
+        solid_face_trace<T, K, PV>(A, c, 3, -1, U);
+    }
+}
+
 template <class T, int K, int MODE>
 __device__ __forceinline__ void solid_cell(const StageArgsT<T>& A, int q, int shot, const T* cd_smem, T* acc_smem) {
     constexpr int n = Dims<K>::n, f = Dims<K>::f;
@@ -911,7 +969,8 @@ __device__ __forceinline__ void solid_cell(const StageArgsT<T>& A, int q, int sh
     c.trs_in = A.tr_in + toff + (size_t)2 * f * c.SF;
     c.trf_out = A.tr_out + toff;
     c.trs_out = A.tr_out + toff + (size_t)2 * f * c.SF;
-    const bool rect = __ldg(ci + CI_KIND) == KIND_RECT;
+    const int kind = __ldg(ci + CI_KIND);
+    const bool rect = kind != KIND_GENERIC;
     const size_t soff = (size_t)shot * A.state_stride + (size_t)3 * n * op.Nf;
     const T* inp = A.inp + soff;
     T Ureg[AccSmem<T, K>::value ? 1 : 5 * n];
@@ -994,18 +1053,10 @@ __device__ __forceinline__ void solid_cell(const StageArgsT<T>& A, int q, int sh
         write_targets<5 * n, SolidGroups<n>>(A, c.N, soff, q, U, sc);
         if constexpr (MODE == MODE_APPLY) return;
     }
-    if (rect) {
-        if constexpr (RectLoop<T>::value) {
-#pragma unroll 1
-            for (int h = 0; h < 2; ++h) solid_face_trace<T, K, RectAxis<0>>(A, c, 2 * h, 2 * h - 1, U);
-#pragma unroll 1
-            for (int v = 0; v < 2; ++v) solid_face_trace<T, K, RectAxis<1>>(A, c, 1 + 2 * v, 1 - 2 * v, U);
-        } else {
-            solid_face_trace<T, K, RectAxis<0>>(A, c, 0, -1, U);
-            solid_face_trace<T, K, RectAxis<1>>(A, c, 1, 1, U);
-            solid_face_trace<T, K, RectAxis<0>>(A, c, 2, 1, U);
-            solid_face_trace<T, K, RectAxis<1>>(A, c, 3, -1, U);
-        }
+    if (kind == KIND_SQUARE) {
+        solid_rect_traces<T, K, SquareAxis<0>, SquareAxis<1>>(A, c, U);
+    } else if (rect) {
+        solid_rect_traces<T, K, RectAxis<0>, RectAxis<1>>(A, c, U);
     } else {
 #pragma unroll 1
         for (int j = 0; j < c.nF; ++j) solid_face_trace<T, K, GenericFace>(A, c, j, 1, U);
@@ -2163,12 +2214,14 @@ extern "C" int hho_stage_cost(const hho_ops* ops, const hho_tableau* tab, int64_
     }
     const int K = ops->k, n = ops->n, f = ops->f;
     const int64_t dsm = (int64_t)K * (K - 1) / 2, dvalid = (int64_t)K * (K + 1) / 2;
-    // entries of the rectangle parity patterns (the same count on every face)
+    // entries of the rectangle parity patterns (the same count on every face);
+    // a square's trace takes K(K+1)/2 multiply-adds (trace_square)
     int64_t rect_tr = 0, rect_lift = 0;
+    const int64_t square_tr = (int64_t)K * (K + 1) / 2;
     for (int i = 0; i < n; ++i) {
         const int e = ea(i);
         for (int l = 0; l < f; ++l) {
-            rect_tr += (e >= l && ((e - l) % 2) == 0);
+            rect_tr += (e == l);
             rect_lift += (((e + l) % 2) == 0);
         }
     }
@@ -2177,9 +2230,10 @@ extern "C" int hho_stage_cost(const hho_ops* ops, const hho_tableau* tab, int64_
         const int32_t* ci = &ops->h_cls_int[cl * CI_STRIDE];
         const int dom = ci[CI_DOMAIN], nF = ci[CI_NF], count = ci[CI_COUNT];
         const int npad = ci[CI_NPAD], sbase = ci[CI_SLOT];
-        const bool rect = ci[CI_KIND] == KIND_RECT;
+        const bool rect = ci[CI_KIND] != KIND_GENERIC;
         const int nv = (dom ? 5 : 3) * n, pc = dom ? 2 : 1;   // state values, primal components
-        const int64_t nnzT = rect ? rect_tr : (int64_t)f * n, nnzL = rect ? rect_lift : (int64_t)f * n;
+        const int64_t nnzT = ci[CI_KIND] == KIND_SQUARE ? square_tr : rect ? rect_tr : (int64_t)f * n;
+        const int64_t nnzL = rect ? rect_lift : (int64_t)f * n;
         dofs += (int64_t)count * nv;
         for (int r = 0; r < count; ++r) {
             int64_t rate = dom ? 5 * dsm + 3 * dvalid + 2 * n : 3 * dsm + dvalid;   // derivatives (+ stress mix)
