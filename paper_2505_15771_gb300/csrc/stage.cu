@@ -437,8 +437,8 @@ struct CellCtx {
 // and 32 neighbour traces just before the face loop.  The FP32 kernel gains
 // about 20 % from them (mask 50, the best of a sweep on GB300).  The 8-byte
 // kernels with register accumulators (spilled) lost with every mask; the
-// double-float k = 2 kernel with shared-memory accumulators gains 7 % from
-// prefetching the target sources (mask 16).
+// 8-byte k = 2 kernels with shared-memory accumulators gain from mask 50 too
+// (double-float about 10 % over no hints, FP64 a few per cent).
 template <class T, int K>
 struct L2Prefetch {
     static constexpr int mask = Tuned<T>::t.prefetch[K - 1];

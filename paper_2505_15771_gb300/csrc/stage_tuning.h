@@ -21,5 +21,5 @@ struct StageTuning {
 // tune.py: begin tables
 constexpr StageTuning TUNED_F64 = {{8, 8, 8}, {0, 1, 0}, {0, 50, 0}};
 constexpr StageTuning TUNED_F32 = {{8, 10, 8}, {0, 1, 1}, {50, 50, 50}};
-constexpr StageTuning TUNED_F2X = {{8, 5, 5}, {0, 1, 0}, {0, 16, 0}};
+constexpr StageTuning TUNED_F2X = {{8, 5, 5}, {0, 1, 0}, {0, 50, 0}};
 // tune.py: end tables
