@@ -272,9 +272,21 @@ __device__ __forceinline__ void trace_apply(const T* __restrict__ Tr, const T* x
 // across it traces to s_t^l (sg rho0)^m psi_l, s_t = -sg on horizontal and
 // sg on vertical faces, so y[l] = s_t^l sum_m (sg rho0)^m x[(l, m)] by
 // Horner's rule (K - l multiply-adds).
+// sg * rho0 in T; the double-float split is formed at compile time (a
+// run-time split would issue FP64 instructions on the slow FP64 pipe)
+template <class T>
+__device__ __forceinline__ T signed_face_rho(int sg) {
+    return T(sg > 0 ? FACE_RHO : -FACE_RHO);
+}
+template <>
+__device__ __forceinline__ f2x signed_face_rho<f2x>(int sg) {
+    constexpr float hi = (float)FACE_RHO;
+    constexpr float lo = (float)(FACE_RHO - (double)hi);
+    return sg > 0 ? f2x(hi, lo) : f2x(-hi, -lo);
+}
 template <class T, int K, bool HORIZ>
 __device__ __forceinline__ void trace_square(const T* x, T* y, int sg) {
-    const T c = T(sg > 0 ? FACE_RHO : -FACE_RHO);
+    const T c = signed_face_rho<T>(sg);
     const bool flip = HORIZ ? sg > 0 : sg < 0;   // s_t = -1
 #pragma unroll
     for (int l = 0; l <= K; ++l) {
