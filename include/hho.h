@@ -433,8 +433,10 @@ int hho_trace_buffer_offset(const hho_ops* ops, const hho_tableau* tab, int32_t 
 /* Offsets within one trace buffer of the traces w that cell h_cells[i]
  * (mesh input order) publishes on its local face h_faces[i] (the face from
  * its vertex i to vertex i+1), which is what the neighbour across that face
- * reads: f values (Legendre coefficients) in a fluid cell, 2f (x then y
- * components) in a solid cell.  h_out: [n][2f], unused entries -1.  Host. */
+ * reads: f values in a fluid cell, 2f (x then y components) in a solid
+ * cell, coefficients in the face basis (rho0 xi)^l, rho0 = 1/(2 sqrt 2),
+ * xi in [-1, 1] along the face in the publishing cell's counter-clockwise
+ * direction.  h_out: [n][2f], unused entries -1.  Host. */
 int hho_trace_offsets(const hho_ops* ops, int64_t n, const int64_t* h_cells, const int32_t* h_faces,
                       int64_t* h_out);
 
