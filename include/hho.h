@@ -460,6 +460,20 @@ int hho_halo_scatter(const double* d_src, const int64_t* d_idx, int64_t n, doubl
 int hho_tc_gemm_check(int32_t K, int32_t N, const float* h_A, const float* h_B, float* h_D, int32_t* h_status);
 
 /* ------------------------------------------------------------------------- */
+/* Double-float arithmetic.                                                   */
+/* ------------------------------------------------------------------------- */
+
+/* Self-check of the double-float (FP32 pair) arithmetic of the HHO_F32X2
+ * kernels (no counterpart in the paper): for each of n items, pairs
+ * x = (hi, lo), y, z given as h_in [n][3][2] floats (value hi + lo), the
+ * GPU computes x + y, x - y, x * y, x * y + z, x / y and the Horner chain
+ * ((x z + y) z + x) z + y with the kernels' operations and writes the
+ * resulting pairs, unnormalised (value hi + lo), to h_out [n][6][2].  The
+ * caller compares them with exact arithmetic.  Allocates its own device
+ * buffers and synchronises; HHO_EINVAL for n < 1 or null buffers. */
+int hho_f2x_check(int32_t n, const float* h_in, float* h_out);
+
+/* ------------------------------------------------------------------------- */
 /* Discrete adjoint (vector-Jacobian product of the receiver traces).         */
 /* ------------------------------------------------------------------------- */
 

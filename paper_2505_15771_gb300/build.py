@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libhho.so")
 PROBE_LIB = os.path.join(HERE, "libhho_probe.so")
-SOURCES = ["mesh.cpp", "operators.cpp", "stage.cu", "adjoint.cu", "sdirk.cu", "tc.cu", "probe.cu"]
+SOURCES = ["mesh.cpp", "operators.cpp", "stage.cu", "adjoint.cu", "sdirk.cu", "tc.cu", "f2x_check.cu", "probe.cu"]
 
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

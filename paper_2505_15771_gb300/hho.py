@@ -79,6 +79,7 @@ _SIGS = {
     "hho_mesh_submesh": (C.c_int, [_P, _I64, _P, C.POINTER(_P)]),
     "hho_locate_points": (C.c_int, [_P, _I64, _P, _P]),
     "hho_tc_gemm_check": (C.c_int, [_I32, _I32, _P, _P, _P, _P]),
+    "hho_f2x_check": (C.c_int, [_I32, _P, _P]),
     "hho_tc_error": (C.c_int, [_P, _P]),
     "hho_adjoint_work_size_f32": (C.c_int, [_P, C.POINTER(Tableau), _I64, _I64, C.POINTER(_I64)]),
     "hho_adjoint_vjp_f32": (C.c_int, [_P, C.POINTER(Tableau), _D, _D, _I64, _I64, _P, _P, _P, _I64, _P, _P, _P, _P]),
@@ -310,6 +311,15 @@ def hho_tc_gemm_check(A, B):
     st = C.c_int32(0)
     _check(lib().hho_tc_gemm_check(int(A.shape[1]), int(B.shape[1]), _ptr(A), _ptr(B), _ptr(D), C.byref(st)))
     return D, st.value
+
+
+def hho_f2x_check(pairs):
+    """Double-float operations on the GPU: pairs [n, 3, 2] float32 (x, y, z as hi, lo) ->
+    [n, 6, 2] float32 pairs of x+y, x-y, x*y, x*y+z, x/y, ((x z + y) z + x) z + y."""
+    p = _arr(pairs, np.float32).reshape(-1, 3, 2)
+    out = np.zeros((p.shape[0], 6, 2), np.float32)
+    _check(lib().hho_f2x_check(int(p.shape[0]), _ptr(p), _ptr(out)))
+    return out
 
 
 def hho_tc_error(ops):
