@@ -290,6 +290,40 @@ def fp64_fma_rate():
 CFL_TRIANGLES_ERK4_K3 = 0.045   # below the ERK4 eigenvalue limit of the right-triangle grid at k = 3
 
 
+def batched_accuracy(a, torch, hho, P, w, dt, n_shots=2, nsteps=500):
+    """FP32 batched seismograms and states against the FP64 batched path (which
+    equals the oracle shot by shot) on the first shots of the workload, over
+    enough steps for the waves to reach receivers on rings of 8 around each
+    source (radius 0.3 c_min t: the workload's own receivers are not reached
+    within such runs).  Relative L2 per shot, the worst reported."""
+    src = [tuple(x) for x in np.asarray(w["sources"], dtype=np.float64)[:n_shots]]
+    rho, lam, mu, kappa = (np.asarray(m, dtype=np.float64) for m in w["media"])
+    c = np.where(mu > 0, np.sqrt(np.maximum(mu, 1e-300) / rho), np.sqrt(np.maximum(kappa, 1e-300) / rho))
+    radius = 0.3 * float(c.min()) * dt * nsteps
+    ang = 2 * np.pi * (np.arange(8) + 0.25) / 8
+    ring = [(x + radius * np.cos(t), y + radius * np.sin(t)) for (x, y) in src for t in ang]
+    P.set_shot_sources(src, [(0.0, 1.0)] * n_shots, np.asarray(w["f0"], dtype=np.float64).reshape(-1)[:n_shots]
+                       if np.ndim(w["f0"]) else w["f0"])
+    P.set_receivers(ring)
+    out = {}
+    for name, prec in (("f64", hho.HHO_F64), ("f32", hho.HHO_F32)):
+        state, work = P.batch_buffers(4, n_shots, prec)
+        seis = torch.zeros((nsteps, n_shots, len(ring), 5), dtype=torch.float32 if prec == hho.HHO_F32 else
+                           torch.float64, device=P.dev)
+        P.batch_step(state, work, n_shots, 4, 0.0, dt, nsteps, precision=prec, seismogram=seis)
+        torch.cuda.synchronize()
+        out[name] = (P.batch_to_canonical(state, n_shots, prec), seis.double().cpu().numpy())
+        del state, work, seis
+    rel = lambda x, y: float(np.linalg.norm(x - y) / max(np.linalg.norm(y), 1e-300))
+    c64, s64 = out["f64"]
+    c32, s32 = out["f32"]
+    return {"shots": n_shots, "steps": nsteps, "receivers": "rings of 8 at radius %.3g around each source" % radius,
+            "seismogram_rel_l2_max": max(rel(s32[:, i], s64[:, i]) for i in range(n_shots)),
+            "state_rel_l2_max": max(rel(c32[i], c64[i]) for i in range(n_shots)),
+            "against": "the FP64 batched path on the same shots (equal to the FP64 oracle shot by shot)",
+            "bar": 1e-5}
+
+
 def measure_batched(a, torch, hho, solver, hbm_peak):
     """Batched shots on the ~1.2 M-cell hybrid mesh (k = 3): S shots in one
     launch per stage, FP32 (default) or FP64, against FP64 single-shot runs
@@ -404,6 +438,7 @@ def measure_batched(a, torch, hho, solver, hbm_peak):
     f1.record(stream)
     torch.cuda.synchronize()
     v64 = ndof * 4 * steps / (f0.elapsed_time(f1) * 1e-3)
+    accuracy = batched_accuracy(a, torch, hho, P, w, dt) if prec == hho.HHO_F32 else None
     _, bytes_min, bytes_kernel = hho.hho_stage_cost(P.ops, tab)
     elt = 4 if prec in (hho.HHO_F32, hho.HHO_BF16X3) else 8
     per_launch = bytes_min / 8 * elt * S / 4
@@ -412,7 +447,7 @@ def measure_batched(a, torch, hho, solver, hbm_peak):
            "precision": a.batch_precision, "shots": S, "steps": steps, "ms_per_step": ms / steps,
            "workload": desc,
            "cells": int(md.n_cells), "cell_dofs": int(ndof), "dt": dt, "seismograms_finite": finite,
-           "tensor_core": tensor_core,
+           "tensor_core": tensor_core, "fp32_accuracy": accuracy,
            "graph_replay": {"value": S * ndof * 4 * steps / (graph_ms * 1e-3), "ms_per_step": graph_ms / steps,
                             "launch": "one captured graph per step (s stage kernels + record + clock)"},
            "fp64_single_shot_same_mesh": v64, "speedup_vs_sequential_fp64": value / v64,
