@@ -324,16 +324,9 @@ __device__ __forceinline__ void lift_apply(const T* __restrict__ L, const T* j, 
 }
 // Rectangle faces: one body per orientation looped over its two faces
 // (compact code: the double-float kernel is bound by instruction fetch
-// otherwise), or the four faces unrolled with constant signs (the FP64 and
-// FP32 kernels schedule better fully unrolled).
-template <class T>
-struct RectLoop {
-    static constexpr bool value = false;
-};
-template <>
-struct RectLoop<f2x> {
-    static constexpr bool value = true;
-};
+// otherwise), or the four faces unrolled with constant signs (the FP64
+// kernel schedules better fully unrolled); per arithmetic and k from the
+// tuning table.
 
 // Where a stage thread keeps its 3n (fluid) or 5n (solid) accumulators.  In
 // registers they do not fit the 64-register budget of 8 resident blocks and
@@ -358,6 +351,10 @@ struct Tuned<float> {
 template <>
 struct Tuned<f2x> {
     static constexpr StageTuning t = TUNED_F2X;
+};
+template <class T, int K>
+struct RectLoop {
+    static constexpr bool value = Tuned<T>::t.rect_loop[K - 1] != 0;
 };
 template <class T, int K>
 struct AccSmem {
@@ -678,7 +675,7 @@ __device__ __forceinline__ void fluid_face_trace(const StageArgsT<T>& A, const C
 // two faces (RectLoop), or unrolled with constant signs.
 template <class T, int K, class PH, class PV>
 __device__ __forceinline__ void fluid_rect_traces(const StageArgsT<T>& A, const CellCtx<T>& c, const T* U) {
-    if constexpr (RectLoop<T>::value) {
+    if constexpr (RectLoop<T, K>::value) {
 #pragma unroll 1
         for (int h = 0; h < 2; ++h) fluid_face_trace<T, K, PH>(A, c, 2 * h, 2 * h - 1, U);
 #pragma unroll 1
@@ -945,7 +942,7 @@ __device__ __forceinline__ void solid_face_trace(const StageArgsT<T>& A, const C
 // two faces (RectLoop), or unrolled with constant signs.
 template <class T, int K, class PH, class PV>
 __device__ __forceinline__ void solid_rect_traces(const StageArgsT<T>& A, const CellCtx<T>& c, const T* U) {
-    if constexpr (RectLoop<T>::value) {
+    if constexpr (RectLoop<T, K>::value) {
 #pragma unroll 1
         for (int h = 0; h < 2; ++h) solid_face_trace<T, K, PH>(A, c, 2 * h, 2 * h - 1, U);
 #pragma unroll 1

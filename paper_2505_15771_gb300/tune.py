@@ -1,10 +1,11 @@
 """Build-time tuner of the stage kernels' launch parameters.
 
 The ERK stage kernel of each arithmetic (FP64, double-float, FP32) and
-degree k has three compile-time parameters, kept in csrc/stage_tuning.h:
+degree k has four compile-time parameters, kept in csrc/stage_tuning.h:
 the resident blocks per SM asked of the register allocator, whether the
-cell's rate accumulators live in shared memory, and the mask of L2 prefetch
-hints.  Which combination is fastest depends on the GPU, the arithmetic, k
+cell's rate accumulators live in shared memory, the mask of L2 prefetch
+hints, and whether a rectangle's faces are traced by one body per
+orientation looped over its two faces or by four unrolled bodies.  Which combination is fastest depends on the GPU, the arithmetic, k
 and the workload, and is not predictable from the register counts alone
 (for instance, on GB300 shared accumulators lose without prefetch hints and
 win with them).  This tool measures it:
@@ -39,15 +40,16 @@ from . import build as B
 
 HEADER = os.path.join(B.CSRC, "stage_tuning.h")
 TABLE = {"f64": "TUNED_F64", "f32": "TUNED_F32", "f2x": "TUNED_F2X"}
-AXES = {"min_blocks": [4, 5, 6, 8, 10, 12], "acc_smem": [0, 1], "prefetch": [0, 16, 48, 50]}
-FIELDS = ("min_blocks", "acc_smem", "prefetch")
+AXES = {"min_blocks": [4, 5, 6, 8, 10, 12], "acc_smem": [0, 1], "prefetch": [0, 16, 48, 50], "rect_loop": [0, 1]}
+FIELDS = ("min_blocks", "acc_smem", "prefetch", "rect_loop")
+_TABLE_RE = r"constexpr StageTuning %s = \{\{([^}]*)\}, \{([^}]*)\}, \{([^}]*)\}, \{([^}]*)\}\};"
 
 
 def read_tables(text):
     """{arith: {field: [k1, k2, k3]}} from the header text."""
     out = {}
     for arith, name in TABLE.items():
-        m = re.search(r"constexpr StageTuning %s = \{\{([^}]*)\}, \{([^}]*)\}, \{([^}]*)\}\};" % name, text)
+        m = re.search(_TABLE_RE % name, text)
         if not m:
             raise ValueError("table %s not found in stage_tuning.h" % name)
         out[arith] = {f: [int(v) for v in m.group(i + 1).split(",")] for i, f in enumerate(FIELDS)}
@@ -57,17 +59,16 @@ def read_tables(text):
 def write_tables(text, tables):
     for arith, name in TABLE.items():
         t = tables[arith]
-        line = "constexpr StageTuning %s = {{%s}, {%s}, {%s}};" % (
-            name, ", ".join(map(str, t["min_blocks"])), ", ".join(map(str, t["acc_smem"])),
-            ", ".join(map(str, t["prefetch"])))
-        text = re.sub(r"constexpr StageTuning %s = \{\{[^}]*\}, \{[^}]*\}, \{[^}]*\}\};" % name, line, text)
+        line = "constexpr StageTuning %s = {%s};" % (
+            name, ", ".join("{%s}" % ", ".join(map(str, t[f])) for f in FIELDS))
+        text = re.sub(_TABLE_RE % name, line, text)
     return text
 
 
 def with_entry(tables, arith, k, entry):
     t = json.loads(json.dumps(tables))
     for f in FIELDS:
-        t[arith][f][k - 1] = entry[f]
+        t[arith][f][k - 1] = entry.get(f, t[arith][f][k - 1])
     return t
 
 
@@ -126,11 +127,15 @@ def measure(lib, arith, k, workload, steps, warmup):
 
 # ---- search ----------------------------------------------------------------------------
 
+def describe(entry):
+    return " ".join("%s=%d" % (f, entry[f]) for f in FIELDS)
+
+
 def tune(arith, k, workload, steps=20, warmup=3, passes=1, jobs=4, log=print, header_text=None, build_fn=None,
          measure_fn=None):
     """Coordinate descent over AXES from the table's current (arith, k)
-    entry.  Returns (best entry, {(min_blocks, acc_smem, prefetch): rate},
-    tables).  build_fn(header_text, out_dir) -> library path and
+    entry.  Returns (best entry, {(min_blocks, acc_smem, prefetch,
+    rect_loop): rate}, tables).  build_fn(header_text, out_dir) -> library path and
     measure_fn(library, arith, k, workload, steps, warmup) -> rate default to
     a candidate build and a timing in a fresh process."""
     base_text = header_text if header_text is not None else open(HEADER).read()
@@ -139,10 +144,10 @@ def tune(arith, k, workload, steps=20, warmup=3, passes=1, jobs=4, log=print, he
     tables = read_tables(base_text)
     best = {f: tables[arith][f][k - 1] for f in FIELDS}
     results = {}
-    key = lambda e: (e["min_blocks"], e["acc_smem"], e["prefetch"])
+    key = lambda e: tuple(e[f] for f in FIELDS)
     with tempfile.TemporaryDirectory(prefix="hho_tune_") as tmp:
         def build(entry):
-            d = os.path.join(tmp, "mb%d_acc%d_pf%d" % key(entry))
+            d = os.path.join(tmp, "mb%d_acc%d_pf%d_rl%d" % key(entry))
             return build_fn(write_tables(base_text, with_entry(tables, arith, k, entry)), d)
 
         for _ in range(passes):
@@ -153,7 +158,7 @@ def tune(arith, k, workload, steps=20, warmup=3, passes=1, jobs=4, log=print, he
                     libs = list(ex.map(build, cands))
                 for c, lib in zip(cands, libs):
                     results[key(c)] = measure_fn(lib, arith, k, workload, steps, warmup)
-                    log("  %-40s %.4e" % ("min_blocks=%d acc_smem=%d prefetch=%d" % key(c), results[key(c)]))
+                    log("  %-52s %.4e" % (describe(c), results[key(c)]))
                 best = max((dict(zip(FIELDS, kk)) for kk in results), key=lambda e: results[key(e)])
     return best, results, tables
 
@@ -175,12 +180,10 @@ def main(argv=None):
         ap.error("the batched workloads are timed in FP32")
     print("tuning %s k=%d on %s" % (a.arith, a.k, a.workload))
     best, results, tables = tune(a.arith, a.k, a.workload, a.steps, a.warmup, a.passes, a.jobs)
-    cur = tuple(tables[a.arith][f][a.k - 1] for f in FIELDS)
-    print("current min_blocks=%d acc_smem=%d prefetch=%d: %s" % (cur + ("%.4e" % results[cur] if cur in results
-                                                                          else "not timed",)))
-    print("best    min_blocks=%d acc_smem=%d prefetch=%d: %.4e" % (
-        best["min_blocks"], best["acc_smem"], best["prefetch"],
-        results[(best["min_blocks"], best["acc_smem"], best["prefetch"])]))
+    cur = {f: tables[a.arith][f][a.k - 1] for f in FIELDS}
+    ck = tuple(cur[f] for f in FIELDS)
+    print("current %s: %s" % (describe(cur), "%.4e" % results[ck] if ck in results else "not timed"))
+    print("best    %s: %.4e" % (describe(best), results[tuple(best[f] for f in FIELDS)]))
     if a.write:
         text = write_tables(open(HEADER).read(), with_entry(tables, a.arith, a.k, best))
         with open(HEADER, "w") as f:

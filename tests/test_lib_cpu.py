@@ -118,9 +118,12 @@ def test_tuning_tables_round_trip():
         assert all(m in (2, 3, 4, 5, 6, 8, 10, 12) for m in t["min_blocks"])
         assert all(a in (0, 1) for a in t["acc_smem"])
         assert all(0 <= p < 64 for p in t["prefetch"])
-    new = tune.with_entry(tables, "f2x", 2, {"min_blocks": 6, "acc_smem": 0, "prefetch": 48})
+        assert all(r in (0, 1) for r in t["rect_loop"])
+    new = tune.with_entry(tables, "f2x", 2, {"min_blocks": 6, "acc_smem": 0, "prefetch": 48,
+                                             "rect_loop": 1 - tables["f2x"]["rect_loop"][1]})
     back = tune.read_tables(tune.write_tables(text, new))
     assert back["f2x"]["min_blocks"][1] == 6 and back["f2x"]["prefetch"][1] == 48
+    assert back["f2x"]["rect_loop"][1] == 1 - tables["f2x"]["rect_loop"][1]
     assert back["f64"] == tables["f64"] and back["f32"] == tables["f32"]
     assert back["f2x"]["min_blocks"][0] == tables["f2x"]["min_blocks"][0]
 
@@ -139,7 +142,8 @@ def test_tuner_candidate_build_is_a_complete_library(hho, tmp_path):
     lib = ctypes.CDLL(path)
     for name in declared:
         assert hasattr(lib, name), name
-    assert "TUNED_F2X = {{8, 6, 5}, {0, 0, 0}, {0, 48, 0}}" in open(tmp_path / "csrc" / "stage_tuning.h").read()
+    rl = ", ".join(map(str, t["f2x"]["rect_loop"]))
+    assert "TUNED_F2X = {{8, 6, 5}, {0, 0, 0}, {0, 48, 0}, {%s}}" % rl in open(tmp_path / "csrc" / "stage_tuning.h").read()
 
 
 def test_tuner_coordinate_descent_on_a_synthetic_landscape():
@@ -156,18 +160,18 @@ def test_tuner_coordinate_descent_on_a_synthetic_landscape():
     def build(header, out_dir):
         t = tune.read_tables(header)
         assert t["f64"] == tables["f64"] and t["f32"] == tables["f32"]
-        e = (t["f2x"]["min_blocks"][1], t["f2x"]["acc_smem"][1], t["f2x"]["prefetch"][1])
+        e = tuple(t["f2x"][f][1] for f in tune.FIELDS)
         assert t["f2x"]["min_blocks"][0] == tables["f2x"]["min_blocks"][0]
         return e
 
     def separable(e, *_):
         seen[e] = seen.get(e, 0) + 1
-        mb, acc, pf = e
-        return 100.0 - (mb - 6) ** 2 + 3.0 * acc - abs(pf - 48) / 16.0
+        mb, acc, pf, rl = e
+        return 100.0 - (mb - 6) ** 2 + 3.0 * acc - abs(pf - 48) / 16.0 + 0.5 * rl
 
     best, res, _ = tune.tune("f2x", 2, "bilayer", log=lambda *a: None, header_text=text, build_fn=build,
                              measure_fn=separable)
-    assert (best["min_blocks"], best["acc_smem"], best["prefetch"]) == (6, 1, 48)
+    assert (best["min_blocks"], best["acc_smem"], best["prefetch"], best["rect_loop"]) == (6, 1, 48, 1)
     assert all(v == 1 for v in seen.values())
 
     # coupled: the best block count moves from 8 to 5 once the accumulators
@@ -176,18 +180,18 @@ def test_tuner_coordinate_descent_on_a_synthetic_landscape():
 
     def coupled(e, *_):
         seen[e] = seen.get(e, 0) + 1
-        mb, acc, pf = e
-        return 50.0 - abs(mb - (5 if acc else 8)) + 4.0 * acc + (1.0 if pf == 16 else 0.0)
+        mb, acc, pf, rl = e
+        return 50.0 - abs(mb - (5 if acc else 8)) + 4.0 * acc + (1.0 if pf == 16 else 0.0) - 0.5 * rl
 
     start = tune.write_tables(text, tune.with_entry(tables, "f2x", 2, {"min_blocks": 8, "acc_smem": 0,
-                                                                        "prefetch": 0}))
+                                                                        "prefetch": 0, "rect_loop": 1}))
     b1, _, _ = tune.tune("f2x", 2, "bilayer", log=lambda *a: None, header_text=start, build_fn=build,
                          measure_fn=coupled)
-    assert (b1["min_blocks"], b1["acc_smem"], b1["prefetch"]) == (8, 1, 16)
+    assert (b1["min_blocks"], b1["acc_smem"], b1["prefetch"], b1["rect_loop"]) == (8, 1, 16, 0)
     seen.clear()
     b2, res, _ = tune.tune("f2x", 2, "bilayer", passes=2, log=lambda *a: None, header_text=start, build_fn=build,
                            measure_fn=coupled)
-    assert (b2["min_blocks"], b2["acc_smem"], b2["prefetch"]) == (5, 1, 16)
+    assert (b2["min_blocks"], b2["acc_smem"], b2["prefetch"], b2["rect_loop"]) == (5, 1, 16, 0)
     assert all(v == 1 for v in seen.values()) and len(seen) == len(res)
 
 
