@@ -356,6 +356,16 @@ int hho_sdirk_step(hho_ops* ops, const hho_tableau* tab, double t0, double dt, i
                    int32_t restart, int32_t max_iter, double* d_state, double* d_work, int64_t* h_iterations,
                    void* stream);
 
+/* Preconditioner of hho_sdirk_step's GMRES (no counterpart in the paper's
+ * direct solves): kind 1 (the default) = block Jacobi, right
+ * preconditioning by the exact cell blocks (I - a* dt J_TT)^-1, which are the
+ * local cell solves of Eq. sc2; kind 0 = none.  The blocks (9n^2 doubles a
+ * fluid cell, 25n^2 a solid cell, owned by ops) are built on the first step
+ * with a new a* dt from the stage operator applied to unit vectors on one
+ * colour of cells at a time, and inverted on the GPU; HHO_EUNSTABLE if a
+ * block is singular.  HHO_EINVAL for another kind. */
+int hho_sdirk_set_preconditioner(hho_ops* ops, int32_t kind);
+
 /* ------------------------------------------------------------------------- */
 /* Batched shots: S independent states (right-hand sides, e.g. one point     */
 /* source each) on the same mesh, advanced by the same stage kernels with    */

@@ -297,9 +297,17 @@ struct hho_ops {
     double* d_if_coef_adj = nullptr;
     float* d_if_coef_adj_f32 = nullptr;   // its FP32 copy (the FP32 adjoint)
     double* d_cls_minv = nullptr;
-    // host copies for the cost model
+    // host copies for the cost model and the SDIRK preconditioner's colouring
     std::vector<double> h_cls_dbl;
-    std::vector<int32_t> h_cls_int, h_nb_f, h_nb_s;
+    std::vector<int32_t> h_cls_int, h_nb_f, h_nb_s, h_if_nb;
+    // SDIRK block-Jacobi preconditioner: (I - a* dt J_TT)^-1 of every cell,
+    // entry (r, c) of a fluid cell q at d_bj[(r 3n + c) Nf + q], of a solid
+    // cell at d_bj[9n^2 Nf + (r 5n + c) Ns + q], built for a* dt = bj_adt
+    int32_t sdirk_precond = 1;
+    double* d_bj = nullptr;
+    double bj_adt = 0.0;
+    int32_t* d_bj_colour = nullptr;   // cell colouring, fluid then solid slots
+    int32_t bj_colours = 0;
     // stage-kernel timing (hho_profile_*)
     bool prof_on = false;
     int32_t prof_n = 0;

@@ -932,6 +932,7 @@ extern "C" int hho_operators_build_tau(const hho_mesh* m, int32_t k, const doubl
     ops->h_cls_int = cls_int;
     ops->h_nb_f = nb_f;
     ops->h_nb_s = nb_s;
+    ops->h_if_nb = if_nb;
     ops->n_state = (int64_t)3 * n * Nf + (int64_t)5 * n * Ns;
     ops->trace_doubles = (int64_t)2 * f * SF + (int64_t)4 * f * SS;
     *out = ops;
@@ -955,6 +956,8 @@ extern "C" void hho_ops_destroy(hho_ops* ops) {
     if (ops->d_host_state) cudaFree(ops->d_host_state);
     if (ops->d_host_canon) cudaFree(ops->d_host_canon);
     if (ops->d_host_work) cudaFree(ops->d_host_work);
+    if (ops->d_bj) cudaFree(ops->d_bj);
+    if (ops->d_bj_colour) cudaFree(ops->d_bj_colour);
     for (void* e : ops->prof_events) cudaEventDestroy((cudaEvent_t)e);
     for (auto& g : ops->graphs)
         if (g.exec) cudaGraphExecDestroy((cudaGraphExec_t)g.exec);

@@ -10,7 +10,9 @@
 //     U^n = U^{n-1} + dt sum_j b_j k_j.
 // The paper condenses the cell unknowns and solves a global face system.
 // Here each stage system is solved matrix-free on the cell unknowns by
-// restarted GMRES.  One operator application is the ERK stage kernel (the
+// restarted GMRES, right-preconditioned by the exact cell blocks
+// (I - a* dt J_TT)^-1, the local solves of Eq. sc2 (block Jacobi; see
+// build_block_jacobi).  One operator application is the ERK stage kernel (the
 // closed-form face solve on every face, reconstruction, stabilisation and
 // inverse mass) with the target v - a* dt J v, so no global matrix is
 // assembled or stored and the implicit path reuses the explicit one's
@@ -183,9 +185,10 @@ bool sdirk_tableau_ok(const hho_tableau* tab) {
 }
 
 // Work layout (doubles; vectors of n_state): Z | Y | T | W | K[s] |
-// V[restart + 1] | zero | traces | reduction partials | reduction sums | coefficients
+// V[restart + 1] | zero | traces | reduction partials | reduction sums | coefficients |
+// preconditioned vector
 struct SdirkWork {
-    double *Z, *Y, *T, *W, *K, *V, *zero, *tr, *partial, *sums, *coef;
+    double *Z, *Y, *T, *W, *K, *V, *zero, *tr, *partial, *sums, *coef, *PZ;
     int64_t n;
 };
 
@@ -210,6 +213,7 @@ int64_t sdirk_layout(const hho_ops* ops, int s, int m, SdirkWork* w, double* bas
     W.partial = take((int64_t)RED_BLOCKS * (m + 1));
     W.sums = take(2 * (m + 1) + 2);
     W.coef = take(m + 1);
+    W.PZ = take(n);
     if (w) *w = W;
     return off;
 }
@@ -230,6 +234,218 @@ void apply_op(hho_ops* ops, const double* v, double* out, double* tr, double a_d
     a.tgt[0].dst = out;
     a.tgt[0].coef = rate ? 1.0 : -a_dt;
     launch_stage_f64(ops, MODE_APPLY, a, 1, t, -1, 0.0, rate, st);
+}
+
+// ---- block-Jacobi preconditioner --------------------------------------------------
+// The stage system's cell-diagonal blocks P_T = I - a* dt J_TT (J_TT: the
+// rate of cell T's unknowns with every other cell at zero, its own face
+// terms included) are the local solves of Eq. sc2.  Their columns come from
+// the stage operator itself: on a state that is the unit vector e_i in every
+// cell of one colour and zero elsewhere, v - a* dt J v restricted to a cell of
+// that colour is column i of its block, because no two cells of a colour
+// share a face (nor an interface face).  The blocks are inverted in place
+// (Gauss-Jordan with partial pivoting, one CTA per cell) and applied as
+// y = P^-1 x, one thread per (row, cell), coalesced over cells.
+
+// Greedy colouring of the cells (fluid slots 0..Nf-1, solid Nf..Nf+Ns-1;
+// padding slots -1) so that face neighbours, across an interface too,
+// differ.
+std::vector<int32_t> cell_colours(const hho_ops* ops, int* n_colours) {
+    const int Nf = ops->dev.Nf, Ns = ops->dev.Ns;
+    std::vector<int32_t> slot_cell[2] = {std::vector<int32_t>(ops->dev.SF, -1), std::vector<int32_t>(ops->dev.SS, -1)};
+    std::vector<std::vector<int32_t>> adj(Nf + Ns);
+    for (int pass = 0; pass < 2; ++pass)
+        for (int cl = 0; cl < ops->n_classes; ++cl) {
+            const int32_t* ci = &ops->h_cls_int[cl * CI_STRIDE];
+            const int d = ci[CI_DOMAIN], base = d ? Nf : 0;
+            const std::vector<int32_t>& nbt = d ? ops->h_nb_s : ops->h_nb_f;
+            for (int j = 0; j < ci[CI_NF]; ++j)
+                for (int lq = 0; lq < ci[CI_COUNT]; ++lq) {
+                    const int slot = ci[CI_SLOT] + j * ci[CI_NPAD] + lq;
+                    const int g = base + ci[CI_START] + lq;
+                    if (pass == 0) {
+                        slot_cell[d][slot] = g;
+                        continue;
+                    }
+                    const int nb = nbt[slot];
+                    int other = -1;
+                    if (nb >= 0) other = slot_cell[d][nb];
+                    else if (nb < NB_BOUNDARY) other = slot_cell[1 - d][ops->h_if_nb[-2 - nb]];
+                    if (other >= 0) adj[g].push_back(other);
+                }
+        }
+    std::vector<int32_t> colour(Nf + Ns, -1);
+    int nc = 0;
+    for (int g = 0; g < Nf + Ns; ++g) {
+        if (adj[g].empty()) {
+            bool real = false;   // a cell with no neighbour (one-cell mesh) is still a cell
+            for (int cl = 0; cl < ops->n_classes && !real; ++cl) {
+                const int32_t* ci = &ops->h_cls_int[cl * CI_STRIDE];
+                const int start = (ci[CI_DOMAIN] ? Nf : 0) + ci[CI_START];
+                real = g >= start && g < start + ci[CI_COUNT];
+            }
+            if (!real) continue;
+        }
+        std::vector<bool> used(nc + 1, false);
+        for (int o : adj[g])
+            if (colour[o] >= 0) used[colour[o]] = true;
+        int c = 0;
+        while (used[c]) ++c;
+        colour[g] = c;
+        nc = std::max(nc, c + 1);
+    }
+    *n_colours = nc;
+    return colour;
+}
+
+// x = e_i on every cell of colour c, 0 elsewhere (device state layout)
+__global__ void unit_state_kernel(double* __restrict__ x, const int32_t* __restrict__ colour, int c, int i, int Nf,
+                                  int Ns, int n) {
+    const int64_t nf = (int64_t)3 * n * Nf, tot = nf + (int64_t)5 * n * Ns;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+        const bool fl = e < nf;
+        const int64_t e2 = fl ? e : e - nf;
+        const int N = fl ? Nf : Ns;
+        const int field = (int)(e2 / N), q = (int)(e2 % N);
+        x[e] = (field == i && colour[fl ? q : Nf + q] == c) ? 1.0 : 0.0;
+    }
+}
+
+// column i of the block of every cell of colour c from y = x - a* dt J x
+__global__ void bj_column_kernel(const double* __restrict__ y, const int32_t* __restrict__ colour, int c, int i,
+                                 int Nf, int Ns, int n, double* __restrict__ bj) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= Nf + Ns || colour[g] != c) return;
+    const bool fl = g < Nf;
+    const int q = fl ? g : g - Nf, N = fl ? Nf : Ns, nv = (fl ? 3 : 5) * n;
+    if (i >= nv) return;
+    const double* yb = fl ? y : y + (size_t)3 * n * Nf;
+    double* b = fl ? bj : bj + (size_t)9 * n * n * Nf;
+    for (int r = 0; r < nv; ++r) b[((size_t)r * nv + i) * N + q] = yb[(size_t)r * N + q];
+}
+
+// In-place inverse of every cell's block; one CTA of 64 threads per cell,
+// [P | I] in shared memory (2 nv^2 doubles).  Padding slots get zeros.
+__global__ void bj_invert_kernel(double* __restrict__ bj, const int32_t* __restrict__ colour, int Nf, int Ns, int n,
+                                 int* __restrict__ status) {
+    extern __shared__ double A[];
+    __shared__ double fac[5 * 10];   // column k of every row (nv <= 5n <= 50)
+    __shared__ int piv;
+    const int g = blockIdx.x;
+    const bool fl = g < Nf;
+    const int q = fl ? g : g - Nf, N = fl ? Nf : Ns, nv = (fl ? 3 : 5) * n, w = 2 * nv;
+    double* b = fl ? bj : bj + (size_t)9 * n * n * Nf;
+    if (colour[g] < 0) {
+        for (int e = threadIdx.x; e < nv * nv; e += blockDim.x) b[(size_t)e * N + q] = 0.0;
+        return;
+    }
+    for (int e = threadIdx.x; e < nv * w; e += blockDim.x) {
+        const int r = e / w, c = e % w;
+        A[e] = c < nv ? b[((size_t)r * nv + c) * N + q] : (c - nv == r ? 1.0 : 0.0);
+    }
+    __syncthreads();
+    for (int k = 0; k < nv; ++k) {
+        if (threadIdx.x == 0) {
+            int p = k;
+            for (int r = k + 1; r < nv; ++r)
+                if (fabs(A[r * w + k]) > fabs(A[p * w + k])) p = r;
+            piv = p;
+            if (A[p * w + k] == 0.0) atomicExch(status, 1);
+        }
+        __syncthreads();
+        const int p = piv;
+        if (p != k)
+            for (int c = threadIdx.x; c < w; c += blockDim.x) {
+                const double t = A[k * w + c];
+                A[k * w + c] = A[p * w + c];
+                A[p * w + c] = t;
+            }
+        __syncthreads();
+        const double d = A[k * w + k];
+        __syncthreads();
+        for (int c = threadIdx.x; c < w; c += blockDim.x) A[k * w + c] = d != 0.0 ? A[k * w + c] / d : 0.0;
+        for (int r = threadIdx.x; r < nv; r += blockDim.x) fac[r] = A[r * w + k];
+        __syncthreads();
+        for (int e = threadIdx.x; e < nv * w; e += blockDim.x) {
+            const int r = e / w, c = e % w;
+            if (r != k) A[e] = fma(-fac[r], A[k * w + c], A[e]);
+        }
+        __syncthreads();
+    }
+    for (int e = threadIdx.x; e < nv * nv; e += blockDim.x) {
+        const int r = e / nv, c = e % nv;
+        b[((size_t)r * nv + c) * N + q] = A[r * w + nv + c];
+    }
+}
+
+// y = P^-1 x (accumulate: y += P^-1 x); one thread per state entry (row r of
+// cell q at r N + q)
+__global__ void bj_apply_kernel(const double* __restrict__ bj, const double* __restrict__ x, double* __restrict__ y,
+                                int accumulate, int Nf, int Ns, int n) {
+    const int64_t nf = (int64_t)3 * n * Nf, tot = nf + (int64_t)5 * n * Ns;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+        const bool fl = e < nf;
+        const int64_t e2 = fl ? e : e - nf;
+        const int N = fl ? Nf : Ns, nv = (fl ? 3 : 5) * n;
+        const int r = (int)(e2 / N), q = (int)(e2 % N);
+        const double* b = (fl ? bj : bj + (size_t)9 * n * n * Nf) + (size_t)r * nv * N + q;
+        const double* xb = (fl ? x : x + nf) + q;
+        double s = 0.0;
+        for (int c = 0; c < nv; ++c) s = fma(b[(size_t)c * N], xb[(size_t)c * N], s);
+        y[e] = accumulate ? y[e] + s : s;
+    }
+}
+
+// Builds (or reuses, for the same a* dt) the inverse blocks; scratch: x, y, tr.
+int build_block_jacobi(hho_ops* ops, double a_dt, double* x, double* y, double* tr, cudaStream_t st) {
+    const int Nf = ops->dev.Nf, Ns = ops->dev.Ns, n = ops->n;
+    if (ops->d_bj && ops->bj_adt == a_dt) return HHO_OK;
+    if (!ops->d_bj_colour) {
+        int nc = 0;
+        std::vector<int32_t> col = cell_colours(ops, &nc);
+        if (cudaMalloc((void**)&ops->d_bj_colour, sizeof(int32_t) * std::max<size_t>(col.size(), 1)) != cudaSuccess ||
+            cudaMemcpy(ops->d_bj_colour, col.data(), sizeof(int32_t) * col.size(), cudaMemcpyHostToDevice) !=
+                cudaSuccess) {
+            hho_set_error("hho_sdirk_step: preconditioner colouring upload failed");
+            return HHO_ECUDA;
+        }
+        ops->bj_colours = nc;
+    }
+    const size_t nbj = (size_t)9 * n * n * Nf + (size_t)25 * n * n * Ns;
+    if (!ops->d_bj && cudaMalloc((void**)&ops->d_bj, sizeof(double) * std::max<size_t>(nbj, 1)) != cudaSuccess) {
+        ops->d_bj = nullptr;
+        hho_set_error("hho_sdirk_step: preconditioner allocation failed (%zu doubles)", nbj);
+        return HHO_ENOMEM;
+    }
+    const int cells = Nf + Ns;
+    for (int c = 0; c < ops->bj_colours; ++c)
+        for (int i = 0; i < 5 * n; ++i) {
+            if (i >= 3 * n && Ns == 0) break;
+            unit_state_kernel<<<grid_for(ops->n_state), 256, 0, st>>>(x, ops->d_bj_colour, c, i, Nf, Ns, n);
+            apply_op(ops, x, y, tr, a_dt, false, 0.0, st);
+            bj_column_kernel<<<(cells + 127) / 128, 128, 0, st>>>(y, ops->d_bj_colour, c, i, Nf, Ns, n, ops->d_bj);
+        }
+    int* status = nullptr;
+    if (cudaMalloc((void**)&status, sizeof(int)) != cudaSuccess || cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess) {
+        hho_set_error("hho_sdirk_step: preconditioner status allocation failed");
+        return HHO_ECUDA;
+    }
+    const size_t smem = sizeof(double) * 2 * (5 * n) * (5 * n);
+    bj_invert_kernel<<<cells, 64, smem, st>>>(ops->d_bj, ops->d_bj_colour, Nf, Ns, n, status);
+    int h_status = 0;
+    const bool ok = cudaMemcpyAsync(&h_status, status, sizeof(int), cudaMemcpyDeviceToHost, st) == cudaSuccess &&
+                    cudaStreamSynchronize(st) == cudaSuccess;
+    cudaFree(status);
+    if (!ok) {
+        hho_set_error("hho_sdirk_step: preconditioner build failed: %s", cudaGetErrorString(cudaGetLastError()));
+        return HHO_ECUDA;
+    }
+    if (h_status) {
+        hho_set_error("hho_sdirk_step: a cell block I - a* dt J_TT is singular");
+        return HHO_EUNSTABLE;
+    }
+    ops->bj_adt = a_dt;
+    return HHO_OK;
 }
 
 // dst[l] = V_l . w for l < nv, on the device (no synchronisation)
@@ -260,10 +476,16 @@ int combine(const SdirkWork& W, double* y, double alpha, const double* V, int nv
     return HHO_OK;
 }
 
-// Restarted GMRES for (I - a_dt J) x = b, x holding the initial guess.
-// Adds its operator applications to *its; HHO_ENOCONV if tol is missed.
+// Restarted GMRES for (I - a_dt J) x = b, x holding the initial guess; with
+// bj, right-preconditioned (the Krylov space of A P^-1, x = x0 + P^-1 V y).
+// Applying the inverted blocks rounds at a level set by their condition
+// (about 1e-14 relative at k = 3), so when a preconditioned restart cycle
+// does not halve the true residual the remaining cycles run without the
+// preconditioner, which reaches the FP64 floor.  Adds its operator
+// applications to *its; HHO_ENOCONV if tol is missed.
 int gmres(hho_ops* ops, const SdirkWork& W, const double* b, double* x, double a_dt, double tol, int m,
-          int max_iter, int64_t* its, cudaStream_t st) {
+          int max_iter, const double* bj, int64_t* its, cudaStream_t st) {
+    const int Nf = ops->dev.Nf, Ns = ops->dev.Ns, nn = ops->n;
     double bn = 0.0;
     int rc = dots(W, b, 1, b, &bn, st);
     if (rc) return rc;
@@ -274,7 +496,7 @@ int gmres(hho_ops* ops, const SdirkWork& W, const double* b, double* x, double a
     }
     std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m), hs(2 * (m + 1) + 1);
     int used = 0;
-    double rn = 0.0;
+    double rn = 0.0, rn_prev = 0.0;
     while (true) {
         // r = b - A x into V_0; the true residual decides convergence
         apply_op(ops, x, W.W, W.tr, a_dt, false, 0.0, st);
@@ -295,13 +517,20 @@ int gmres(hho_ops* ops, const SdirkWork& W, const double* b, double* x, double a
             return HHO_EUNSTABLE;
         }
         if (rn <= tol * bn || used >= max_iter) break;
+        if (bj && rn_prev > 0.0 && rn > 0.5 * rn_prev) bj = nullptr;   // stagnation: finish unpreconditioned
+        rn_prev = rn;
         scale_kernel<<<grid_for(W.n), 256, 0, st>>>(W.V, 1.0 / rn, W.n);
         std::fill(g.begin(), g.end(), 0.0);
         g[0] = rn;
         int j = 0;
         for (; j < m && used < max_iter; ++j) {
             double* vj1 = W.V + (size_t)(j + 1) * W.n;
-            apply_op(ops, W.V + (size_t)j * W.n, vj1, W.tr, a_dt, false, 0.0, st);
+            if (bj) {
+                bj_apply_kernel<<<grid_for(W.n), 256, 0, st>>>(bj, W.V + (size_t)j * W.n, W.PZ, 0, Nf, Ns, nn);
+                apply_op(ops, W.PZ, vj1, W.tr, a_dt, false, 0.0, st);
+            } else {
+                apply_op(ops, W.V + (size_t)j * W.n, vj1, W.tr, a_dt, false, 0.0, st);
+            }
             ++used;
             // classical Gram-Schmidt twice, coefficients kept on the device
             double* S1 = W.sums;
@@ -346,7 +575,12 @@ int gmres(hho_ops* ops, const SdirkWork& W, const double* b, double* x, double a
             for (int c2 = r + 1; c2 < j; ++c2) v -= H[(size_t)c2 * (m + 1) + r] * y[c2];
             y[r] = v / H[(size_t)r * (m + 1) + r];
         }
-        if (j > 0) {
+        if (j > 0 && bj) {   // x += P^-1 (V y)
+            cudaMemsetAsync(W.W, 0, sizeof(double) * W.n, st);
+            rc = combine(W, W.W, 0.0, W.V, j, y.data(), st);
+            if (rc) return rc;
+            bj_apply_kernel<<<grid_for(W.n), 256, 0, st>>>(bj, W.W, x, 1, Nf, Ns, nn);
+        } else if (j > 0) {
             rc = combine(W, x, 1.0, W.V, j, y.data(), st);
             if (rc) return rc;
         }
@@ -400,6 +634,11 @@ extern "C" int hho_sdirk_step(hho_ops* ops, const hho_tableau* tab, double t0, d
     const double a_dt = tab->a[0][0] * dt;
     const int64_t n = W.n;
     int rc = HHO_OK;
+    if (ops->sdirk_precond) {
+        rc = build_block_jacobi(ops, a_dt, W.Z, W.W, W.tr, st);
+        if (rc) return rc;
+    }
+    const double* bj = ops->sdirk_precond ? ops->d_bj : nullptr;
     for (int64_t step = 0; step < nsteps && rc == HHO_OK; ++step) {
         const double tn = t0 + (double)step * dt;
         for (int i = 0; i < s && rc == HHO_OK; ++i) {
@@ -438,7 +677,7 @@ extern "C" int hho_sdirk_step(hho_ops* ops, const hho_tableau* tab, double t0, d
             terms_kernel<<<grid_for(n), 256, 0, st>>>(W.Y, G, n);
             rc = check_cuda("hho_sdirk_step");
             if (rc) break;
-            rc = gmres(ops, W, W.T, W.Y, a_dt, tol, restart, max_iter, &its, st);
+            rc = gmres(ops, W, W.T, W.Y, a_dt, tol, restart, max_iter, bj, &its, st);
             if (rc) break;
             // k_i = J Y_i + s(t_i)
             apply_op(ops, W.Y, W.K + (size_t)i * n, W.tr, 0.0, true, ti, st);
@@ -459,4 +698,13 @@ extern "C" int hho_sdirk_step(hho_ops* ops, const hho_tableau* tab, double t0, d
     }
     if (h_iterations) *h_iterations = its;
     return rc;
+}
+
+extern "C" int hho_sdirk_set_preconditioner(hho_ops* ops, int32_t kind) {
+    if (!ops || kind < 0 || kind > 1) {
+        hho_set_error("hho_sdirk_set_preconditioner: bad arguments (kind 0: none, 1: block Jacobi)");
+        return HHO_EINVAL;
+    }
+    ops->sdirk_precond = kind;
+    return HHO_OK;
 }

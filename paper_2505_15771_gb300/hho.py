@@ -95,6 +95,7 @@ _SIGS = {
     "hho_set_launch_mode": (C.c_int, [_P, _I32]),
     "hho_tableau_sdirk": (C.c_int, [_I32, C.POINTER(Tableau)]),
     "hho_sdirk_work_size": (C.c_int, [_P, C.POINTER(Tableau), _I32, C.POINTER(_I64)]),
+    "hho_sdirk_set_preconditioner": (C.c_int, [_P, _I32]),
     "hho_sdirk_step": (C.c_int, [_P, C.POINTER(Tableau), _D, _D, _I64, _D, _I32, _I32, _P, _P, C.POINTER(_I64),
                                  _P]),
     "hho_erk_run_host": (C.c_int, [_P, C.POINTER(Tableau), _D, _D, _I64, _P, _P]),
@@ -379,6 +380,11 @@ def hho_sdirk_work_size(ops, tab, restart):
     n = _I64()
     _check(lib().hho_sdirk_work_size(ops, C.byref(tab), int(restart), C.byref(n)))
     return n.value
+
+
+def hho_sdirk_set_preconditioner(ops, kind):
+    """GMRES preconditioner of hho_sdirk_step: 1 block Jacobi (default), 0 none."""
+    _check(lib().hho_sdirk_set_preconditioner(ops, int(kind)))
 
 
 def hho_sdirk_step(ops, tab, t0, dt, nsteps, tol, restart, max_iter, d_state, d_work, stream=0):
