@@ -519,7 +519,7 @@ int hho_adjoint_vjp(hho_ops* ops, const hho_tableau* tab, double t0, double dt, 
                     int64_t work_doubles, double* h_grad_cell, double* h_grad_wavelet, double* h_grad_tau,
                     void* stream);
 
-/* The same reverse mode in FP32 (BASELINE-style "FP32 adjoint"): the FP32
+/* The same reverse mode in FP32: the FP32
  * stage kernels (the batched FP32 path with one shot) for the forward
  * checkpoints, the segment recompute and the transposed stages; states,
  * traces, adjoint vectors, d_state0 and d_cotangent ([nsteps][n_rec][5]) in

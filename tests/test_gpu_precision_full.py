@@ -1,7 +1,7 @@
 """Precision of the FP32 paths at the sizes and step counts they are
 measured on, against the FP64 path on the same shots (the FP64 batched path
 equals the oracle shot by shot, test_gpu_batched.py).  The bar on
-seismograms is 1e-5 relative (the benchmark spec); the figures are printed.
+seismograms is 1e-5 relative; the figures are printed.
 
 * hybrid quads/triangles, 1360 x 680 (1.2 M cells), k = 3, ERK4, 500 steps,
   two of its shots: FP32 batched against FP64 batched.
