@@ -581,7 +581,7 @@ def measure_sdirk(a, torch, hho, solver):
     """Implicit SDIRK(3,4) (matrix-free GMRES on the stage systems,
     block-Jacobi preconditioned) against ERK4 over the same simulated time on
     the bilayer at 256 x 128, k = 2: SDIRK at 4 x the ERK4 square CFL step,
-    tol 1e-8, restart 20; the same SDIRK run without the preconditioner
+    tol 1e-8, restart 10; the same SDIRK run without the preconditioner
     beside it.  The first timed SDIRK call includes the preconditioner build
     (the warm-up call builds it for the same step, so it is reused)."""
     import synth
@@ -592,12 +592,12 @@ def measure_sdirk(a, torch, hho, solver):
     dt_erk = hho.hho_cfl_dt(P.ops, CFL_SQUARES_ERK4[2], 0.9)
     ratio, n_sdirk = 4, 4
     x = P.to_device(np.zeros(n))
-    P.sdirk_step(x, 3, 0.0, ratio * dt_erk, 1, tol=1e-8, restart=20, max_iter=5000)   # warm-up
+    P.sdirk_step(x, 3, 0.0, ratio * dt_erk, 1, tol=1e-8, restart=10, max_iter=5000)   # warm-up
     P.step(x, 4, 0.0, dt_erk, 3)
     x.zero_()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    its = P.sdirk_step(x, 3, 0.0, ratio * dt_erk, n_sdirk, tol=1e-8, restart=20, max_iter=5000)
+    its = P.sdirk_step(x, 3, 0.0, ratio * dt_erk, n_sdirk, tol=1e-8, restart=10, max_iter=5000)
     torch.cuda.synchronize()
     t_sd = time.perf_counter() - t0
     e_sd = P.energy(x)
@@ -616,13 +616,13 @@ def measure_sdirk(a, torch, hho, solver):
     z = P.to_device(np.zeros(n))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    its0 = P.sdirk_step(z, 3, 0.0, ratio * dt_erk, n_sdirk, tol=1e-8, restart=20, max_iter=5000)
+    its0 = P.sdirk_step(z, 3, 0.0, ratio * dt_erk, n_sdirk, tol=1e-8, restart=10, max_iter=5000)
     torch.cuda.synchronize()
     t_sd0 = time.perf_counter() - t0
     hho.hho_sdirk_set_preconditioner(P.ops, 1)
     out = {"metric": "wall time for the same simulated interval, SDIRK(3,4) vs ERK4",
            "workload": "bilayer 256x128 on [0,2]x[0,1], k=2, Ricker source, SDIRK(3,4) dt = %d x ERK4 dt, "
-                       "%d SDIRK steps, GMRES tol 1e-8 restart 20, FP64" % (ratio, n_sdirk),
+                       "%d SDIRK steps, GMRES tol 1e-8 restart 10, FP64" % (ratio, n_sdirk),
            "cell_dofs": int(n), "sdirk_wall_s": t_sd, "erk4_s": t_erk, "sdirk_over_erk4": t_sd / t_erk,
            "gmres_applications": int(its), "applications_per_stage": its / stages,
            "rel_diff_vs_erk4": diff, "energy_sdirk": e_sd,
