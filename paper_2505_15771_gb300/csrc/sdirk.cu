@@ -426,8 +426,13 @@ int build_block_jacobi(hho_ops* ops, double a_dt, double* x, double* y, double* 
             bj_column_kernel<<<(cells + 127) / 128, 128, 0, st>>>(y, ops->d_bj_colour, c, i, Nf, Ns, n, ops->d_bj);
         }
     int* status = nullptr;
-    if (cudaMalloc((void**)&status, sizeof(int)) != cudaSuccess || cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess) {
+    if (cudaMalloc((void**)&status, sizeof(int)) != cudaSuccess) {
         hho_set_error("hho_sdirk_step: preconditioner status allocation failed");
+        return HHO_ECUDA;
+    }
+    if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess) {
+        cudaFree(status);
+        hho_set_error("hho_sdirk_step: preconditioner status initialisation failed");
         return HHO_ECUDA;
     }
     const size_t smem = sizeof(double) * 2 * (5 * n) * (5 * n);
