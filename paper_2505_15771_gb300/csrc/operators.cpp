@@ -661,6 +661,9 @@ extern "C" int hho_operators_build_tau(const hho_mesh* m, int32_t k, const doubl
                     const int et = (j % 2 == 0) ? EA[i] : EB[i], en = (j % 2 == 0) ? EB[i] : EA[i];
                     const double want = et != l ? 0.0 : ((l & 1) && st[j] < 0 ? -1.0 : 1.0) * ipow(sn[j] * FACE_RHO, en);
                     if (std::fabs(cd[j * FS + 4 + l * nP + i] - want) > 1e-14) sq = false;
+                    // the square kernels skip Lift[i][l] for e_t - l = 2 (zero for
+                    // squares at k <= 3; stored as an exact zero by the noise cut)
+                    if (et - l == 2 && cd[j * FS + 4 + f * nP + i * fP + l] != 0.0) sq = false;
                 }
         if (sq) cls_kind[cl] = KIND_SQUARE;
     }

@@ -195,7 +195,10 @@ __device__ __forceinline__ void add_ddy(const T* u, T* out) {
 // outside the pattern are never loaded.  One body per orientation, looped
 // over its two faces, keeps the kernel's instruction footprint small.
 // SquareAxis<A>: the faces of a square cell; their traces are Horner sums
-// with compile-time coefficients (trace_square) and Tr is never read.
+// with compile-time coefficients (trace_square) and Tr is never read, and
+// their lifting matrices also vanish where the exponent along the face
+// exceeds the face coefficient's degree by 2 (checked when the class is
+// built, up to k = 3).
 struct GenericFace {
     static constexpr bool rect = false;
     static constexpr bool square = false;
@@ -215,6 +218,9 @@ struct RectAxis {
 template <int AX>
 struct SquareAxis : RectAxis<AX> {
     static constexpr bool square = true;
+    __host__ __device__ static constexpr bool lift_nz(int i, int l) {
+        return RectAxis<AX>::lift_nz(i, l) && RectAxis<AX>::e(i) - l != 2;
+    }
 };
 
 // Class matrices of the double-float kernel are read from a per-warp copy in
@@ -565,10 +571,10 @@ __device__ __forceinline__ void fluid_face_jump(const StageArgsT<T>& A, const Ce
 //     tau accumulator     += tau L sigma (P = +1), tau L delta (P = -1)
 // Each lifted row is accumulated straight into its target: 4f + 2 nnz(L)
 // operations per pair instead of 2 (nnz(L) + 2n) for two separate lifts.
-template <class T, int K, int AX>
+template <class T, int K, int AX, bool SQ = false>
 __device__ __forceinline__ void lift_pair(const T* __restrict__ L, const T* jb, const T* jp, T tau, T* ke, T* kt) {
     constexpr int n = Dims<K>::n, f = Dims<K>::f, fP = Dims<K>::fP, w = Vec16<T>::w;
-    using P = RectAxis<AX>;
+    using P = typename std::conditional<SQ, SquareAxis<AX>, RectAxis<AX>>::type;
     constexpr bool neg = AX == 0;   // face 0 has normal -e_y, face 1 +e_x
     T sg[f], dl[f], ts[f], td[f];
 #pragma unroll
@@ -604,13 +610,13 @@ __device__ __forceinline__ void lift_pair(const T* __restrict__ L, const T* jb, 
     }
 }
 
-template <class T, int K, int AX>
+template <class T, int K, int AX, bool SQ = false>
 __device__ __forceinline__ void fluid_pair_rate(const StageArgsT<T>& A, const CellCtx<T>& c, T* kmx, T* kmy, T* kp) {
     constexpr int f = Dims<K>::f, FS = Dims<K>::FS;
     T jb[f], jp[f];
     fluid_face_jump<T, K>(A, c, AX, jb);
     fluid_face_jump<T, K>(A, c, AX + 2, jp);
-    lift_pair<T, K, AX>(c.cd + AX * FS + Dims<K>::LI, jb, jp, c.tau, AX == 0 ? kmy : kmx, kp);
+    lift_pair<T, K, AX, SQ>(c.cd + AX * FS + Dims<K>::LI, jb, jp, c.tau, AX == 0 ? kmy : kmx, kp);
 }
 
 template <class T, int K, class P>
@@ -740,8 +746,13 @@ __device__ __forceinline__ void fluid_cell(const StageArgsT<T>& A, int q, int sh
                                                             OpData<T>::beta_f(op), rect ? 4 : c.nF);
         if (rect) {
             // faces 0 (s = -1) and 2 (s = +1) are horizontal, 1 (s = +1) and 3 (s = -1) vertical
-            fluid_pair_rate<T, K, 0>(A, c, kmx, kmy, kp);   // faces 0 and 2
-            fluid_pair_rate<T, K, 1>(A, c, kmx, kmy, kp);   // faces 1 and 3
+            if (kind == KIND_SQUARE) {
+                fluid_pair_rate<T, K, 0, true>(A, c, kmx, kmy, kp);   // faces 0 and 2
+                fluid_pair_rate<T, K, 1, true>(A, c, kmx, kmy, kp);   // faces 1 and 3
+            } else {
+                fluid_pair_rate<T, K, 0>(A, c, kmx, kmy, kp);
+                fluid_pair_rate<T, K, 1>(A, c, kmx, kmy, kp);
+            }
         } else {
 #pragma unroll 1
             for (int j = 0; j < c.nF; ++j) fluid_face_rate<T, K, GenericFace>(A, c, j, 1, kmx, kmy, kp);
@@ -860,7 +871,7 @@ __device__ __forceinline__ void solid_face_rate(const StageArgsT<T>& A, const Ce
 // Both faces of one rectangle orientation (see lift_pair): horizontal faces
 // feed e_yy (y component) and e_xy (x component), vertical ones e_xx (x) and
 // e_xy (y); tau times both components feeds kv.
-template <class T, int K, int AX>
+template <class T, int K, int AX, bool SQ = false>
 __device__ __forceinline__ void solid_pair_rate(const StageArgsT<T>& A, const CellCtx<T>& c, T* exx, T* eyy, T* exy,
                                                 T* kvx, T* kvy) {
     constexpr int f = Dims<K>::f, FS = Dims<K>::FS;
@@ -868,8 +879,8 @@ __device__ __forceinline__ void solid_pair_rate(const StageArgsT<T>& A, const Ce
     solid_face_jump<T, K>(A, c, AX, bx, by);
     solid_face_jump<T, K>(A, c, AX + 2, px, py);
     const T* L = c.cd + AX * FS + Dims<K>::LI;
-    lift_pair<T, K, AX>(L, bx, px, c.tau, AX == 0 ? exy : exx, kvx);
-    lift_pair<T, K, AX>(L, by, py, c.tau, AX == 0 ? eyy : exy, kvy);
+    lift_pair<T, K, AX, SQ>(L, bx, px, c.tau, AX == 0 ? exy : exx, kvx);
+    lift_pair<T, K, AX, SQ>(L, by, py, c.tau, AX == 0 ? eyy : exy, kvy);
 }
 
 // Publish w = tau v|_F - (s n)|_F and omega = alpha w - v|_F for one face.
@@ -1015,8 +1026,13 @@ __device__ __forceinline__ void solid_cell(const StageArgsT<T>& A, int q, int sh
             prefetch_cell<T, K, 5 * n, 2 * f, 1, MODE != MODE_RAW>(A, c, soff, c.trs_in, c.SS, op.nb_s,
                                                                 OpData<T>::beta_s(op), rect ? 4 : c.nF);
         if (rect) {
-            solid_pair_rate<T, K, 0>(A, c, exx, eyy, exy, kvx, kvy);   // faces 0 and 2
-            solid_pair_rate<T, K, 1>(A, c, exx, eyy, exy, kvx, kvy);   // faces 1 and 3
+            if (kind == KIND_SQUARE) {
+                solid_pair_rate<T, K, 0, true>(A, c, exx, eyy, exy, kvx, kvy);   // faces 0 and 2
+                solid_pair_rate<T, K, 1, true>(A, c, exx, eyy, exy, kvx, kvy);   // faces 1 and 3
+            } else {
+                solid_pair_rate<T, K, 0>(A, c, exx, eyy, exy, kvx, kvy);
+                solid_pair_rate<T, K, 1>(A, c, exx, eyy, exy, kvx, kvy);
+            }
         } else {
 #pragma unroll 1
             for (int j = 0; j < c.nF; ++j) solid_face_rate<T, K, GenericFace>(A, c, j, 1, exx, eyy, exy, kvx, kvy);
@@ -2225,13 +2241,14 @@ extern "C" int hho_stage_cost(const hho_ops* ops, const hho_tableau* tab, int64_
     const int64_t dsm = (int64_t)K * (K - 1) / 2, dvalid = (int64_t)K * (K + 1) / 2;
     // entries of the rectangle parity patterns (the same count on every face);
     // a square's trace takes K(K+1)/2 multiply-adds (trace_square)
-    int64_t rect_tr = 0, rect_lift = 0;
+    int64_t rect_tr = 0, rect_lift = 0, square_lift = 0;
     const int64_t square_tr = (int64_t)K * (K + 1) / 2;
     for (int i = 0; i < n; ++i) {
         const int e = ea(i);
         for (int l = 0; l < f; ++l) {
             rect_tr += (e == l);
             rect_lift += (((e + l) % 2) == 0);
+            square_lift += (((e + l) % 2) == 0) && e - l != 2;
         }
     }
     int64_t ops_total = 0, bytes_k = 0, dofs = 0;
@@ -2242,7 +2259,7 @@ extern "C" int hho_stage_cost(const hho_ops* ops, const hho_tableau* tab, int64_
         const bool rect = ci[CI_KIND] != KIND_GENERIC;
         const int nv = (dom ? 5 : 3) * n, pc = dom ? 2 : 1;   // state values, primal components
         const int64_t nnzT = ci[CI_KIND] == KIND_SQUARE ? square_tr : rect ? rect_tr : (int64_t)f * n;
-        const int64_t nnzL = rect ? rect_lift : (int64_t)f * n;
+        const int64_t nnzL = ci[CI_KIND] == KIND_SQUARE ? square_lift : rect ? rect_lift : (int64_t)f * n;
         dofs += (int64_t)count * nv;
         for (int r = 0; r < count; ++r) {
             int64_t rate = dom ? 5 * dsm + 3 * dvalid + 2 * n : 3 * dsm + dvalid;   // derivatives (+ stress mix)
