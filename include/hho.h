@@ -363,7 +363,9 @@ int hho_sdirk_step(hho_ops* ops, const hho_tableau* tab, double t0, double dt, i
  * fluid cell, 25n^2 a solid cell, owned by ops) are built on the first step
  * with a new a* dt from the stage operator applied to unit vectors on one
  * colour of cells at a time, and inverted on the GPU; HHO_EUNSTABLE if a
- * block is singular.  HHO_EINVAL for another kind. */
+ * block is singular.  Where the device has no room for the blocks the step
+ * runs unpreconditioned (same solution, more iterations).  HHO_EINVAL for
+ * another kind. */
 int hho_sdirk_set_preconditioner(hho_ops* ops, int32_t kind);
 
 /* ------------------------------------------------------------------------- */

@@ -639,11 +639,17 @@ extern "C" int hho_sdirk_step(hho_ops* ops, const hho_tableau* tab, double t0, d
     const double a_dt = tab->a[0][0] * dt;
     const int64_t n = W.n;
     int rc = HHO_OK;
-    if (ops->sdirk_precond) {
+    bool precond = ops->sdirk_precond != 0;
+    if (precond) {
         rc = build_block_jacobi(ops, a_dt, W.Z, W.W, W.tr, st);
+        if (rc == HHO_ENOMEM) {   // no room for the blocks: the same solve, unpreconditioned
+            cudaGetLastError();
+            precond = false;
+            rc = HHO_OK;
+        }
         if (rc) return rc;
     }
-    const double* bj = ops->sdirk_precond ? ops->d_bj : nullptr;
+    const double* bj = precond ? ops->d_bj : nullptr;
     for (int64_t step = 0; step < nsteps && rc == HHO_OK; ++step) {
         const double tn = t0 + (double)step * dt;
         for (int i = 0; i < s && rc == HHO_OK; ++i) {
