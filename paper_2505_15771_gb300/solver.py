@@ -92,8 +92,12 @@ class Problem:
         tab = hho.hho_tableau_erk(s)
         hho.hho_erk_step(self.ops, tab, t0, dt, nsteps, state.data_ptr(), self.work(tab).data_ptr(), _stream(stream))
 
-    def sdirk_step(self, state, s, t0, dt, nsteps, tol=1e-12, restart=40, max_iter=2000, stream=None):
-        """Implicit SDIRK steps (hho_sdirk_step); returns the GMRES operator applications."""
+    def sdirk_step(self, state, s, t0, dt, nsteps, tol=1e-12, restart=40, max_iter=2000, stream=None,
+                   preconditioner=None):
+        """Implicit SDIRK steps (hho_sdirk_step); returns the GMRES operator applications.
+        preconditioner: None keeps the current setting, 1 block Jacobi, 0 none."""
+        if preconditioner is not None:
+            hho.hho_sdirk_set_preconditioner(self.ops, preconditioner)
         tab = hho.hho_tableau_sdirk(s)
         n = hho.hho_sdirk_work_size(self.ops, tab, restart)
         key = ("sdirk", s, restart)
